@@ -1,0 +1,237 @@
+"""Plain CPU oracle for the Loop-of-stencil-reduce hot path (arXiv 1609.04567).
+
+TEST INFRASTRUCTURE ONLY.  The tests, ``__graft_entry__.smoke()`` and the
+``cpu_baseline`` / ``--impl reference`` legs of ``bench.py`` are the only callers.
+The CUDA library neither imports nor links anything from here, and this module
+imports nothing from the CUDA package.
+
+The arithmetic lives in ``slr_oracle.c`` (plain C, no fused multiply-add); this
+module compiles it with gcc on first use and marshals numpy arrays through
+ctypes.  Every function returns ``(state, Result)`` and never modifies its
+inputs.
+
+Parity status: every solver here is pinned by the ``-m "not gpu"`` tests in
+``tests/test_oracle_*.py`` (closed forms, known patterns, brute force, library
+rounding); none is "parity unpinned".
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "slr_oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+_lib = None
+
+STORAGE = {"f32": 0, "bf16": 1, "f16": 2}
+
+
+class _CResult(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int64), ("value", ctypes.c_double),
+                ("converged", ctypes.c_int32), ("changed", ctypes.c_int32),
+                ("count", ctypes.c_uint64)]
+
+
+@dataclass
+class Result:
+    iters: int
+    value: float
+    converged: bool
+    changed: bool
+    count: int
+
+
+def build(force: bool = False) -> str:
+    """Compile ``slr_oracle.c`` into ``liboracle.so`` next to it (gcc, -O2,
+    -ffp-contract=off).  Returns the path of the shared object."""
+    if not force and os.path.exists(_LIB) and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC):
+        return _LIB
+    tmp = _LIB + ".%d.tmp" % os.getpid()
+    cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math",
+           "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"]
+    subprocess.check_call(cmd)
+    os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    if _lib is not None:
+        return _lib
+    lib = ctypes.CDLL(build())
+    P = ctypes.c_void_p
+    i64, f64, i32 = ctypes.c_int64, ctypes.c_double, ctypes.c_int
+    R = ctypes.POINTER(_CResult)
+    lib.orc_j2d5_f64.argtypes = [P, P, i64, i64, f64, f64, i32, f64, f64, i64, R]
+    lib.orc_j2d5_f32.argtypes = [P, P, i64, i64, f64, f64, i32, ctypes.c_float, i32, f64, i64, R]
+    lib.orc_j3d7_f64.argtypes = [P, P, i64, i64, i64, f64, f64, i32, f64, f64, i64, R]
+    lib.orc_j3d7_f32.argtypes = [P, P, i64, i64, i64, f64, f64, i32, ctypes.c_float, i32, f64, i64, R]
+    lib.orc_life.argtypes = [P, i64, i64, i32, i64, R]
+    lib.orc_restore8.argtypes = [P, P, i64, i64, ctypes.c_float, f64, i64, R]
+    lib.orc_j2d5_dc.argtypes = [P, P, i64, i64, f64, f64, f64, i64, i64, R]
+    lib.orc_j2d5_scaled_defect.argtypes = [P, P, i64, i64, f64, f64]
+    lib.orc_j2d5_scaled_defect.restype = f64
+    for name in ("orc_j2d5_f64", "orc_j2d5_f32", "orc_j3d7_f64", "orc_j3d7_f32",
+                 "orc_life", "orc_restore8", "orc_j2d5_dc"):
+        getattr(lib, name).restype = i32
+    lib.orc_f32_to_bf16.argtypes = [ctypes.c_float]
+    lib.orc_f32_to_bf16.restype = ctypes.c_uint16
+    lib.orc_f32_to_f16.argtypes = [ctypes.c_float]
+    lib.orc_f32_to_f16.restype = ctypes.c_uint16
+    lib.orc_round_storage.argtypes = [ctypes.c_float, i32]
+    lib.orc_round_storage.restype = ctypes.c_float
+    for name in ("orc_f32_to_bf16_array", "orc_f32_to_f16_array", "orc_f16_to_f32_array"):
+        getattr(lib, name).argtypes = [P, P, i64]
+        getattr(lib, name).restype = None
+    lib.orc_round_storage_array.argtypes = [P, P, i64, i32]
+    lib.orc_round_storage_array.restype = None
+    _lib = lib
+    return lib
+
+
+def _ptr(a: np.ndarray) -> int:
+    return a.ctypes.data
+
+
+def _res(r: _CResult) -> Result:
+    return Result(int(r.iters), float(r.value), bool(r.converged), bool(r.changed), int(r.count))
+
+
+def _check(rc: int, name: str) -> None:
+    if rc != 0:
+        raise ValueError(f"oracle {name} failed with code {rc}")
+
+
+def j2d5(u0, f, *, sigma=1.0, h=0.0, wrap=False, ghost=0.0, tol=1e-6, max_iters=5000,
+         storage=None):
+    """2D 5-point Helmholtz Jacobi loop (Sec. 4.1 solver, Sec. 3.1 loop).
+
+    ``storage=None`` runs in FP64 on float64 arrays; ``storage`` in
+    {"f32","bf16","f16"} runs FP32 arithmetic with the state rounded to that
+    precision after every update (arrays given as float32 holding values
+    representable in the storage precision)."""
+    lib = _load()
+    r = _CResult()
+    if storage is None:
+        u = np.array(u0, dtype=np.float64, order="C", copy=True)
+        ff = np.ascontiguousarray(f, dtype=np.float64)
+        ny, nx = u.shape
+        _check(lib.orc_j2d5_f64(_ptr(u), _ptr(ff), nx, ny, sigma, h, int(wrap), ghost,
+                                tol, max_iters, ctypes.byref(r)), "j2d5_f64")
+    else:
+        u = np.array(u0, dtype=np.float32, order="C", copy=True)
+        ff = np.ascontiguousarray(f, dtype=np.float32)
+        ny, nx = u.shape
+        _check(lib.orc_j2d5_f32(_ptr(u), _ptr(ff), nx, ny, sigma, h, int(wrap), ghost,
+                                STORAGE[storage], tol, max_iters, ctypes.byref(r)), "j2d5_f32")
+    return u, _res(r)
+
+
+def j3d7(u0, f, *, sigma=1.0, h=0.0, wrap=False, ghost=0.0, tol=1e-6, max_iters=5000,
+         storage=None):
+    """3D 7-point Helmholtz Jacobi loop; arrays are (nz, ny, nx), x contiguous."""
+    lib = _load()
+    r = _CResult()
+    if storage is None:
+        u = np.array(u0, dtype=np.float64, order="C", copy=True)
+        ff = np.ascontiguousarray(f, dtype=np.float64)
+        nz, ny, nx = u.shape
+        _check(lib.orc_j3d7_f64(_ptr(u), _ptr(ff), nx, ny, nz, sigma, h, int(wrap), ghost,
+                                tol, max_iters, ctypes.byref(r)), "j3d7_f64")
+    else:
+        u = np.array(u0, dtype=np.float32, order="C", copy=True)
+        ff = np.ascontiguousarray(f, dtype=np.float32)
+        nz, ny, nx = u.shape
+        _check(lib.orc_j3d7_f32(_ptr(u), _ptr(ff), nx, ny, nz, sigma, h, int(wrap), ghost,
+                                STORAGE[storage], tol, max_iters, ctypes.byref(r)), "j3d7_f32")
+    return u, _res(r)
+
+
+def life(cells, *, wrap=True, max_gens=2000):
+    """Game of Life B3/S23 loop (Fig. 1 elemental function); uint8 cells."""
+    lib = _load()
+    r = _CResult()
+    a = np.array(cells, dtype=np.uint8, order="C", copy=True)
+    ny, nx = a.shape
+    _check(lib.orc_life(_ptr(a), nx, ny, int(wrap), max_gens, ctypes.byref(r)), "life")
+    return a, _res(r)
+
+
+def restore8(u0, mask, *, alpha=100.0, tol=1e-3, max_iters=5000):
+    """Restoration loop of the Sec. 4.3 denoiser on float32 state and a uint8
+    noisy-pixel mask."""
+    lib = _load()
+    r = _CResult()
+    u = np.array(u0, dtype=np.float32, order="C", copy=True)
+    m = np.ascontiguousarray(mask, dtype=np.uint8)
+    ny, nx = u.shape
+    _check(lib.orc_restore8(_ptr(u), _ptr(m), nx, ny, alpha, tol, max_iters,
+                            ctypes.byref(r)), "restore8")
+    return u, _res(r)
+
+
+def j2d5_dc(u0, f, *, sigma=1.0, h=0.0, tol=1e-10, k_in=50, max_outer=100000):
+    """FP64 defect correction with FP32 Jacobi inner solves (ghost 0)."""
+    lib = _load()
+    r = _CResult()
+    u = np.array(u0, dtype=np.float64, order="C", copy=True)
+    ff = np.ascontiguousarray(f, dtype=np.float64)
+    ny, nx = u.shape
+    _check(lib.orc_j2d5_dc(_ptr(u), _ptr(ff), nx, ny, sigma, h, tol, k_in, max_outer,
+                           ctypes.byref(r)), "j2d5_dc")
+    return u, _res(r)
+
+
+def j2d5_scaled_defect(u, f, *, sigma=1.0, h=0.0) -> float:
+    lib = _load()
+    uu = np.ascontiguousarray(u, dtype=np.float64)
+    ff = np.ascontiguousarray(f, dtype=np.float64)
+    ny, nx = uu.shape
+    return float(lib.orc_j2d5_scaled_defect(_ptr(uu), _ptr(ff), nx, ny, sigma, h))
+
+
+def f32_to_bf16_bits(x: float) -> int:
+    return int(_load().orc_f32_to_bf16(ctypes.c_float(x)))
+
+
+def f32_to_f16_bits(x: float) -> int:
+    return int(_load().orc_f32_to_f16(ctypes.c_float(x)))
+
+
+def round_storage(a, storage: str) -> np.ndarray:
+    """Round a float32 array to the storage precision and back with the
+    oracle's own bit-level routine (round to nearest even)."""
+    lib = _load()
+    x = np.ascontiguousarray(a, dtype=np.float32)
+    out = np.empty_like(x)
+    lib.orc_round_storage_array(_ptr(x), _ptr(out), x.size, STORAGE[storage])
+    return out
+
+
+def f32_to_bf16_array(a) -> np.ndarray:
+    lib = _load()
+    x = np.ascontiguousarray(a, dtype=np.float32)
+    out = np.empty(x.shape, dtype=np.uint16)
+    lib.orc_f32_to_bf16_array(_ptr(x), _ptr(out), x.size)
+    return out
+
+
+def f32_to_f16_array(a) -> np.ndarray:
+    lib = _load()
+    x = np.ascontiguousarray(a, dtype=np.float32)
+    out = np.empty(x.shape, dtype=np.uint16)
+    lib.orc_f32_to_f16_array(_ptr(x), _ptr(out), x.size)
+    return out
+
+
+def f16_bits_to_f32_array(a) -> np.ndarray:
+    lib = _load()
+    x = np.ascontiguousarray(a, dtype=np.uint16)
+    out = np.empty(x.shape, dtype=np.float32)
+    lib.orc_f16_to_f32_array(_ptr(x), _ptr(out), x.size)
+    return out

@@ -1,0 +1,222 @@
+"""Pins for the oracle's Helmholtz Jacobi solvers (Sec. 4.1 problem, Sec. 3.1 loop).
+
+Nothing here compares the oracle with a retyped copy of itself.  The pins are:
+  * discrete sine modes, eigenfunctions of the 5-point (7-point) operator with
+    zero Dirichlet ghosts: from u0 = 0 the n-th Jacobi iterate is exactly
+    c*(1 - mu^n) v, so the state, the reduced max|change| and the iteration
+    count at which the repeat-until test first passes are all closed forms;
+  * brute force: the converged loop equals a dense linear solve of the
+    discrete system (numpy.linalg.solve) on tiny grids, for Dirichlet ghosts
+    of any value, wrap-around and non-square grids;
+  * the storage-precision paths: one sweep equals the FP32 sweep rounded by
+    torch/numpy's own conversions; every stored value is representable;
+  * defect correction: converges to the dense solution to its tolerance.
+"""
+import math
+
+import numpy as np
+import pytest
+
+
+def sine_mode_2d(n, p, q):
+    h = 1.0 / (n + 1)
+    x = np.arange(1, n + 1) * h
+    return np.outer(np.sin(q * math.pi * x), np.sin(p * math.pi * x)), h
+
+
+def jacobi_factor(h, sigma, modes):
+    """mu and c* of a sine mode: neighbour sum of the mode is 2*sum(cos(p pi h)) v."""
+    dim = len(modes)
+    d = 2 * dim + sigma * h * h
+    mu = 2.0 * sum(math.cos(m * math.pi * h) for m in modes) / d
+    lam = (4.0 / (h * h)) * sum(math.sin(m * math.pi * h / 2) ** 2 for m in modes)
+    cstar = 1.0 / (lam + sigma)
+    return mu, cstar
+
+
+def predicted_iters(cstar, mu, vmax, tol, cap):
+    for n in range(1, cap + 1):
+        if abs(cstar) * mu ** (n - 1) * (1 - mu) * vmax < tol:
+            return n
+    return cap
+
+
+@pytest.mark.parametrize("n,p,q,sigma", [(31, 1, 1, 1.0), (31, 1, 2, 0.0), (24, 3, 1, 5.0)])
+def test_j2d5_sine_mode_closed_form(orc, n, p, q, sigma):
+    v, h = sine_mode_2d(n, p, q)
+    mu, cstar = jacobi_factor(h, sigma, (p, q))
+    for sweeps in (1, 2, 7, 40):
+        u, r = orc.j2d5(np.zeros_like(v), v, sigma=sigma, tol=0.0, max_iters=sweeps)
+        assert r.iters == sweeps and not r.converged
+        expect = cstar * (1 - mu ** sweeps) * v
+        assert np.max(np.abs(u - expect)) <= 1e-13 * abs(cstar)
+        dmax = abs(cstar) * mu ** (sweeps - 1) * (1 - mu) * np.max(np.abs(v))
+        assert r.value == pytest.approx(dmax, rel=1e-9, abs=1e-16)
+
+
+@pytest.mark.parametrize("tol", [1e-6, 3e-7, 1e-9])
+def test_j2d5_iteration_count_closed_form(orc, tol):
+    n, p, q, sigma = 31, 1, 1, 1.0
+    v, h = sine_mode_2d(n, p, q)
+    mu, cstar = jacobi_factor(h, sigma, (p, q))
+    expect_n = predicted_iters(cstar, mu, np.max(np.abs(v)), tol, 5000)
+    u, r = orc.j2d5(np.zeros_like(v), v, sigma=sigma, tol=tol, max_iters=5000)
+    assert r.converged and r.iters == expect_n
+    # repeat-until: the test fails one sweep earlier
+    u2, r2 = orc.j2d5(np.zeros_like(v), v, sigma=sigma, tol=tol, max_iters=expect_n - 1)
+    assert not r2.converged and r2.value >= tol
+
+
+def test_j2d5_cap_stops_loop(orc):
+    v, _ = sine_mode_2d(16, 1, 1)
+    _, r = orc.j2d5(np.zeros_like(v), v, tol=1e-30, max_iters=3)
+    assert r.iters == 3 and not r.converged
+
+
+def dense_helmholtz(ny, nx, h, sigma, wrap, ghost, f, dim_d=4.0):
+    """Dense matrix of (d u - sum nbrs)/h^2 with the boundary moved to the RHS."""
+    n = nx * ny
+    A = np.zeros((n, n))
+    b = f.reshape(-1).astype(np.float64).copy()
+    d = dim_d + sigma * h * h
+    for i in range(ny):
+        for j in range(nx):
+            r = i * nx + j
+            A[r, r] += d / (h * h)
+            for di, dj in ((-1, 0), (1, 0), (0, -1), (0, 1)):
+                y, x = i + di, j + dj
+                if wrap:
+                    A[r, (y % ny) * nx + (x % nx)] -= 1.0 / (h * h)
+                elif 0 <= y < ny and 0 <= x < nx:
+                    A[r, y * nx + x] -= 1.0 / (h * h)
+                else:
+                    b[r] += ghost / (h * h)
+    return A, b
+
+
+@pytest.mark.parametrize("ny,nx,h,wrap,ghost,sigma", [
+    (8, 8, 0.0, False, 0.0, 1.0),
+    (5, 9, 0.1, False, 0.0, 2.0),
+    (6, 7, 0.125, True, 0.0, 1.0),
+    (8, 8, 0.0, False, 0.75, 1.0),
+])
+def test_j2d5_brute_force_dense_solve(orc, ny, nx, h, wrap, ghost, sigma):
+    from paper_1609_04567_gb300 import inputs
+    f = inputs.helmholtz_rhs((ny, nx), seed=7)
+    hh = h if h > 0 else 1.0 / (nx + 1)
+    A, b = dense_helmholtz(ny, nx, hh, sigma, wrap, ghost, f)
+    exact = np.linalg.solve(A, b).reshape(ny, nx)
+    u, r = orc.j2d5(np.zeros((ny, nx)), f, sigma=sigma, h=h, wrap=wrap, ghost=ghost,
+                    tol=1e-15, max_iters=200000)
+    assert r.converged
+    # stopping at max|change| < tol leaves an error of at most about
+    # tol * rho / (1 - rho), rho the spectral radius of the Jacobi iteration
+    jac = np.eye(A.shape[0]) - A / np.diag(A)[:, None]
+    rho = np.max(np.abs(np.linalg.eigvals(jac)))
+    bound = 2e-15 / (1 - rho) + 1e-13 * np.max(np.abs(exact))
+    assert np.max(np.abs(u - exact)) <= bound
+
+
+def test_j3d7_sine_mode_closed_form(orc):
+    n, modes, sigma = 11, (1, 2, 1), 1.0
+    h = 1.0 / (n + 1)
+    x = np.arange(1, n + 1) * h
+    v = (np.sin(modes[2] * math.pi * x)[:, None, None] * np.sin(modes[1] * math.pi * x)[None, :, None]
+         * np.sin(modes[0] * math.pi * x)[None, None, :])
+    mu, cstar = jacobi_factor(h, sigma, modes)
+    for sweeps in (1, 5, 30):
+        u, r = orc.j3d7(np.zeros_like(v), v, sigma=sigma, tol=0.0, max_iters=sweeps)
+        expect = cstar * (1 - mu ** sweeps) * v
+        assert np.max(np.abs(u - expect)) <= 1e-13 * abs(cstar)
+        dmax = abs(cstar) * mu ** (sweeps - 1) * (1 - mu) * np.max(np.abs(v))
+        assert r.value == pytest.approx(dmax, rel=1e-9)
+    expect_n = predicted_iters(cstar, mu, np.max(np.abs(v)), 1e-7, 5000)
+    _, r = orc.j3d7(np.zeros_like(v), v, sigma=sigma, tol=1e-7, max_iters=5000)
+    assert r.converged and r.iters == expect_n
+
+
+def test_j3d7_brute_force_dense_solve(orc):
+    from paper_1609_04567_gb300 import inputs
+    nz, ny, nx, sigma = 3, 4, 5, 1.0
+    f = inputs.helmholtz_rhs((nz, ny, nx), seed=11)
+    h = 1.0 / (nx + 1)
+    n = nx * ny * nz
+    A = np.zeros((n, n))
+    for k in range(nz):
+        for i in range(ny):
+            for j in range(nx):
+                r = (k * ny + i) * nx + j
+                A[r, r] = (6 + sigma * h * h) / (h * h)
+                for dk, di, dj in ((-1, 0, 0), (1, 0, 0), (0, -1, 0), (0, 1, 0), (0, 0, -1), (0, 0, 1)):
+                    z, y, x = k + dk, i + di, j + dj
+                    if 0 <= z < nz and 0 <= y < ny and 0 <= x < nx:
+                        A[r, (z * ny + y) * nx + x] = -1.0 / (h * h)
+    exact = np.linalg.solve(A, f.reshape(-1)).reshape(nz, ny, nx)
+    u, r = orc.j3d7(np.zeros_like(f), f, sigma=sigma, tol=1e-15, max_iters=100000)
+    assert r.converged
+    assert np.max(np.abs(u - exact)) <= 1e-12 * np.max(np.abs(exact))
+
+
+def test_j2d5_f32_closed_form(orc):
+    n, p, q, sigma = 31, 1, 2, 1.0
+    v, h = sine_mode_2d(n, p, q)
+    mu, cstar = jacobi_factor(h, sigma, (p, q))
+    v32 = v.astype(np.float32)
+    u, r = orc.j2d5(np.zeros_like(v32), v32, sigma=sigma, tol=0.0, max_iters=50, storage="f32")
+    expect = cstar * (1 - mu ** 50) * v
+    assert np.max(np.abs(u - expect)) <= 1e-5 * abs(cstar)
+
+
+@pytest.mark.parametrize("storage", ["bf16", "f16"])
+def test_storage_path_one_sweep_is_rounded_f32_sweep(orc, storage):
+    import torch
+    from paper_1609_04567_gb300 import inputs
+    f64 = inputs.helmholtz_rhs((20, 24), seed=3)
+    tdt = torch.bfloat16 if storage == "bf16" else torch.float16
+    f_s = torch.from_numpy(f64.astype(np.float32)).to(tdt).float().numpy()
+    u0 = torch.from_numpy((0.01 * f64).astype(np.float32)).to(tdt).float().numpy()
+    u32, _ = orc.j2d5(u0, f_s, tol=0.0, max_iters=1, storage="f32")
+    us, _ = orc.j2d5(u0, f_s, tol=0.0, max_iters=1, storage=storage)
+    lib_rounded = torch.from_numpy(u32).to(tdt).float().numpy()
+    assert np.array_equal(us.view(np.uint32), lib_rounded.view(np.uint32))
+
+
+@pytest.mark.parametrize("storage", ["bf16", "f16"])
+def test_storage_path_state_representable_and_bounded(orc, storage):
+    import torch
+    n = 31
+    v, h = sine_mode_2d(n, 1, 1)
+    mu, cstar = jacobi_factor(h, 1.0, (1, 1))
+    tdt = torch.bfloat16 if storage == "bf16" else torch.float16
+    f_s = torch.from_numpy(v.astype(np.float32)).to(tdt).float().numpy()
+    u, r = orc.j2d5(np.zeros_like(f_s), f_s, tol=1e-6, max_iters=20000, storage=storage)
+    again = torch.from_numpy(u).to(tdt).float().numpy()
+    assert np.array_equal(u, again)                       # stored values are representable
+    # the loop stops when no stored value moves by tol or more; the state is
+    # then a fixed point of the rounded iteration, within the stagnation bound
+    # (half an ulp of the state divided by the contraction gap 1 - mu) of c* v
+    ulp = {"bf16": 2.0 ** -8, "f16": 2.0 ** -11}[storage] * np.max(np.abs(cstar * v))
+    bound = ulp / (1 - mu) + 1e-3 * abs(cstar)
+    assert r.converged
+    assert np.max(np.abs(u - cstar * v)) <= bound
+
+
+def test_defect_correction_reaches_dense_solution(orc):
+    from paper_1609_04567_gb300 import inputs
+    ny = nx = 12
+    f = inputs.helmholtz_rhs((ny, nx), seed=5)
+    h = 1.0 / (nx + 1)
+    A, b = dense_helmholtz(ny, nx, h, 1.0, False, 0.0, f)
+    exact = np.linalg.solve(A, b).reshape(ny, nx)
+    u, r = orc.j2d5_dc(np.zeros((ny, nx)), f, tol=1e-10, k_in=20)
+    assert r.converged and r.value < 1e-10
+    assert orc.j2d5_scaled_defect(u, f) == pytest.approx(r.value, rel=0, abs=0)
+    # the scaled defect bounds the error by rho / (1 - mu) for the slowest mode
+    mu, _ = jacobi_factor(h, 1.0, (1, 1))
+    assert np.max(np.abs(u - exact)) <= 1e-10 / (1 - mu) * 1.01
+
+
+def test_scaled_defect_of_zero_state(orc):
+    v, h = sine_mode_2d(9, 1, 1)
+    d = 4 + h * h
+    assert orc.j2d5_scaled_defect(np.zeros_like(v), v) == pytest.approx(h * h * np.max(np.abs(v)) / d, rel=1e-14)
