@@ -1,0 +1,169 @@
+/*
+ * slr.h -- C ABI of the GB300-native Loop-of-stencil-reduce library (libslr.so).
+ *
+ * The pattern (Aldinucci et al., "A Parallel Pattern for Iterative Stencil +
+ * Reduce", arXiv 1609.04567, Sec. 3.1, procedures loop-of-stencil-reduce-d and
+ * -s): repeat { one stencil sweep over the grid; reduce the per-item change
+ * (or the new items) with an associative operator; count the iteration } until
+ * the convergence test on the reduced value and the iteration count passes.
+ * The library runs the sweep, the reduce and the test on one GPU; the loop
+ * stays on the device.
+ *
+ * Conventions for every call:
+ *   - Pointers named u, aux, workspace are DEVICE pointers owned by the caller.
+ *     The library never allocates, frees or retains device memory beyond the
+ *     handle's lifetime; the handle owns only host metadata.
+ *   - Grids are dense row-major arrays: item (z, y, x) is at index
+ *     (z * ny + y) * nx + x, x contiguous.  u must be 16-byte aligned.
+ *   - All device work is enqueued on the CUDA stream given at creation
+ *     (a cudaStream_t passed as void*, NULL = legacy default stream) and is
+ *     asynchronous; slr_reduce_value() is the only call that waits.
+ *   - Calls return an slr_status and never abort.  After an error,
+ *     slr_last_error() returns a message.
+ *   - A handle is not thread-safe; distinct handles may be used concurrently
+ *     from distinct threads on distinct streams.
+ */
+#ifndef SLR_H
+#define SLR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct slr_ctx *slr_handle;
+
+typedef enum {
+    SLR_OK = 0,                /* converged (the test, not the cap, stopped the loop) */
+    SLR_NOT_CONVERGED = 1,     /* the iteration cap stopped the loop; state is valid */
+    SLR_ERR_INVALID_ARG = -1,  /* bad descriptor, pointer or size */
+    SLR_ERR_WORKSPACE = -2,    /* workspace smaller than slr_workspace_size() */
+    SLR_ERR_CUDA = -3,         /* a CUDA call failed; see slr_last_error() */
+    SLR_ERR_TIMEOUT = -4,      /* a device-side wait ran out its limit */
+    SLR_ERR_UNSUPPORTED = -5   /* valid but unimplemented combination */
+} slr_status;
+
+/* Elemental functions (the f of stencil(sigma_1, f), Sec. 3.1). */
+typedef enum {
+    /* 2D 5-point Helmholtz Jacobi (Sec. 4.1):
+     *   u' = (h^2 f + ((u_N + u_S) + u_W) + u_E) / (4 + sigma h^2)
+     * aux = f (same storage type as u). */
+    SLR_J2D5 = 0,
+    /* 3D 7-point form: u' = (h^2 f + sum of 6 neighbours) / (6 + sigma h^2),
+     * neighbours summed x-, x+, y-, y+, z-, z+.  aux = f. */
+    SLR_J3D7 = 1,
+    /* Game of Life B3/S23 over the 8 Moore neighbours (Fig. 1).  Cells are
+     * uint8 0/1 (any non-zero input reads as alive; outputs are 0/1).
+     * aux = NULL. */
+    SLR_LIFE = 2,
+    /* Restoration update of the two-phase denoiser (Sec. 4.3), binary32 state:
+     * for masked pixels u' = sum_j w_j u_j / sum_j w_j over the in-range
+     * 8-neighbours, w_j = 1/sqrt(alpha + (u - u_j)^2); unmasked pixels are
+     * copied.  aux = uint8 mask (non-zero = noisy). */
+    SLR_RESTORE8 = 3
+} slr_stencil;
+
+/* What lies beyond the grid (the bottom items of the stencil operator). */
+typedef enum {
+    SLR_DIRICHLET = 0,  /* a fixed ghost value (desc.ghost; Life: dead cell) */
+    SLR_WRAP = 1        /* toroidal wrap_around */
+} slr_boundary;
+
+/* The reduce operator applied to the per-item change (delta) or item. */
+typedef enum {
+    SLR_RED_MAX_ABS_DELTA = 0,          /* max |u' - u|, identity 0 (Jacobi) */
+    SLR_RED_MEAN_ABS_DELTA_MASKED = 1,  /* sum over mask of |u'-u| (each truncated to a
+                                           multiple of 2^-24, summed as uint64) / #mask */
+    SLR_RED_LIVE_COUNT = 2              /* live count (+ on uint64) and any-changed (or) */
+} slr_reduce_op;
+
+typedef enum { SLR_U8 = 0, SLR_BF16 = 1, SLR_F16 = 2, SLR_F32 = 3, SLR_F64 = 4 } slr_dtype;
+
+/* How the loop is driven. */
+typedef enum {
+    SLR_LOOP_AUTO = 0,        /* library choice (currently PERSISTENT) */
+    SLR_LOOP_HOST = 1,        /* plain schema of Fig. 2: one sweep launch, one reduce
+                                 launch and a host-side test per iteration */
+    SLR_LOOP_PERSISTENT = 2   /* one cooperative launch; sweep, reduce, test and buffer
+                                 swap stay on the device, one grid barrier per pass */
+} slr_loop;
+
+/* Precision mode of the floating-point elemental functions. */
+typedef enum {
+    SLR_MATH_EXACT = 0,  /* IEEE ops in the oracle's order, no contraction: bit-exact */
+    SLR_MATH_FAST = 1    /* fused multiply-add and hardware approximations allowed */
+} slr_math;
+
+typedef struct {
+    int32_t stencil;       /* slr_stencil */
+    int32_t storage;       /* slr_dtype of u and aux-f: J2D5/J3D7 F64, F32, BF16, F16
+                              (BF16/F16 store the state, arithmetic is binary32);
+                              LIFE U8; RESTORE8 F32 */
+    int32_t reduce;        /* slr_reduce_op; must be the one of the stencil */
+    int32_t boundary;      /* slr_boundary */
+    int64_t nx, ny, nz;    /* extents, nz = 1 for 2D stencils; each >= 1 */
+    double ghost;          /* Dirichlet ghost value (Jacobi) */
+    double tol;            /* convergence: stop when reduced value < tol (delta reduces);
+                              Life stops when no cell changed */
+    double sigma;          /* Helmholtz sigma */
+    double h;              /* mesh width; <= 0 selects 1/(nx + 1) */
+    float alpha;           /* restoration constant (100) */
+    int32_t loop;          /* slr_loop */
+    int32_t math;          /* slr_math */
+    int32_t temporal_k;    /* sweeps per HBM pass for Life (1, 2, 4, ...); 0 = library choice */
+    int64_t wait_limit_ns; /* device-side barrier wait limit; <= 0 selects 2 s */
+} slr_desc;
+
+/* Fill *d with defaults for a stencil: the matching reduce operator and
+ * storage, Dirichlet ghost 0, tol 1e-6 (Jacobi), 1e-3 (restoration), sigma 1,
+ * h = 1/(nx+1), alpha 100, AUTO loop, EXACT math. */
+void slr_desc_init(slr_desc *d, int32_t stencil, int64_t nx, int64_t ny, int64_t nz);
+
+/* Bytes of device workspace a handle for *d needs (second state buffer,
+ * reduce slots, control block).  Returns 0 for an invalid descriptor. */
+size_t slr_workspace_size(const slr_desc *d);
+
+/* Create a handle (constructor of Sec. 3.2: elemental function, combinator
+ * with identity, iteration condition and sizes).
+ *   u          device state, in/out; holds the result after each run.
+ *   aux        device f (Jacobi), mask (restoration) or NULL (Life); read-only.
+ *   workspace  device buffer of at least slr_workspace_size(d) bytes, 256-byte
+ *              aligned, owned by the caller, not touched by anyone else while
+ *              the handle lives.
+ *   stream     cudaStream_t for all work of this handle.
+ * The iteration counter starts at 0.  Enqueues a small workspace reset. */
+slr_status slr_create(const slr_desc *d, void *u, const void *aux, void *workspace,
+                      size_t workspace_bytes, void *stream, slr_handle *out);
+
+/* Enqueue the loop until the test passes or the TOTAL iteration count of the
+ * handle reaches max_iters (a call with a higher cap resumes from the state
+ * left in u).  Asynchronous.  A converged handle returns at once. */
+slr_status slr_run_until(slr_handle h, int64_t max_iters);
+
+/* Wait for the handle's stream and read the result of the last iteration:
+ * reduced value (max or mean |delta|; live count for Life), total iterations,
+ * converged flag (1 when the test stopped the loop) and the integer count
+ * (live cells for Life, masked pixels for the restoration, else 0).  Any
+ * output pointer may be NULL.  Returns SLR_OK when converged,
+ * SLR_NOT_CONVERGED when stopped by the cap, or an error (SLR_ERR_TIMEOUT if
+ * a device barrier wait ran out). */
+slr_status slr_reduce_value(slr_handle h, double *value, int64_t *iters,
+                            int32_t *converged, uint64_t *count);
+
+/* Release the handle (host memory only; waits for nothing). */
+slr_status slr_destroy(slr_handle h);
+
+/* Message of the last error on h (or of the last failed create when h is
+ * NULL).  Never NULL. */
+const char *slr_last_error(slr_handle h);
+
+/* Library build string (architecture, version). */
+const char *slr_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SLR_H */

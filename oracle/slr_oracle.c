@@ -236,8 +236,8 @@ int orc_j2d5_f32(float *u, const float *f, int64_t nx, int64_t ny, double sigma,
                  int64_t max_iters, orc_result *res)
 {
     if (nx < 1 || ny < 1 || max_iters < 1) return -1;
-    double hh = mesh_h(h, nx);
-    float h2 = (float)(hh * hh), d = (float)(4.0 + sigma * hh * hh);
+    double hh = mesh_h(h, nx), h2d = hh * hh;
+    float h2 = (float)h2d, d = (float)(4.0 + sigma * h2d);   /* same constants as FP64, rounded */
     size_t n = (size_t)(nx * ny);
     float *v = (float *)malloc(n * sizeof(float));
     if (!v) return -2;
@@ -320,8 +320,8 @@ int orc_j3d7_f32(float *u, const float *f, int64_t nx, int64_t ny, int64_t nz,
                  double tol, int64_t max_iters, orc_result *res)
 {
     if (nx < 1 || ny < 1 || nz < 1 || max_iters < 1) return -1;
-    double hh = mesh_h(h, nx);
-    float h2 = (float)(hh * hh), d = (float)(6.0 + sigma * hh * hh);
+    double hh = mesh_h(h, nx), h2d = hh * hh;
+    float h2 = (float)h2d, d = (float)(6.0 + sigma * h2d);   /* same constants as FP64, rounded */
     size_t n = (size_t)(nx * ny * nz);
     float *v = (float *)malloc(n * sizeof(float));
     if (!v) return -2;
