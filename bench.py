@@ -1,0 +1,364 @@
+#!/usr/bin/env python3
+"""Benchmark of the Loop-of-stencil-reduce hot path on one GB300 (or N replicas).
+
+A step is one complete solve of the workload through the C ABI: reset the
+state to the seeded input, create a handle, run the device loop to its stop
+rule, and (at the end of the timed region) read the reduced value.  The
+default workload is the 8192 x 8192 Game of Life torus, uint8 cells,
+Bernoulli(0.3), B3/S23, live-count + any-changed reduce, stop at a still state
+or 2000 generations (it always runs the 2000).
+
+Metric: Gcell-updates/s = cells x generations / device time.
+
+Output: ONE JSON line on rank 0 with value (device-resident inputs), e2e (host
+buffers, copies inside the timed region), roofline of the dominant kernel
+(algorithmic bytes / CUDA-event time vs the measured HBM copy bandwidth),
+cpu_baseline (the plain C oracle on the host cores, bounded sample), clocks
+sampled during the timed region, and the plain one-launch-per-sweep path for
+comparison.
+
+--impl reference times the oracle itself (the CPU program that defines the
+method) on the host cores for the same metric.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+WORKLOADS = {
+    "life": dict(name="life_8192x8192_u8_torus_b3s23_2000gens", nx=8192, ny=8192, gens=2000,
+                 bytes_per_cell_sweep=2.0),
+}
+PROFILE_TRAFFIC = os.path.join(ROOT, "profiles", "traffic.json")
+KERNEL_SOURCES = ["paper_1609_04567_gb300/csrc/life.cu", "paper_1609_04567_gb300/csrc/slr_internal.cuh"]
+
+
+def kernel_hash() -> str:
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def recorded_traffic(workload: str):
+    """DRAM bytes per launch of the dominant kernel from a committed ncu
+    capture, if it was taken on the current kernel source; else None."""
+    if not os.path.exists(PROFILE_TRAFFIC):
+        return None
+    with open(PROFILE_TRAFFIC) as fh:
+        d = json.load(fh)
+    e = d.get(workload)
+    if not e or e.get("kernel_hash") != kernel_hash():
+        return None
+    return float(e["dram_bytes_per_launch"])
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.QUERY,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        out, _ = self.proc.communicate(timeout=10)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        loaded = [x for x in sm if x > 0.5 * max(sm)] or sm
+        return {"sm_mhz": statistics.median(loaded), "sm_max_mhz": max(smax),
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        dist.init_process_group("gloo", rank=rank, world_size=world)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x: float, world: int) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def oracle_life_sample(nx: int, ny: int, budget_s: float):
+    """Time the oracle on the same torus for as many generations as fit in
+    about budget_s seconds (at least one).  Returns (gcells_per_s, gens, secs)."""
+    import oracle
+    from paper_1609_04567_gb300 import inputs
+    cells = inputs.life_cells(ny, nx)
+    t0 = time.perf_counter()
+    state, _ = oracle.life(cells, wrap=True, max_gens=1)
+    one = time.perf_counter() - t0
+    gens = max(1, min(16, int(budget_s / max(one, 1e-9)) - 1))
+    t0 = time.perf_counter()
+    oracle.life(state, wrap=True, max_gens=gens)
+    secs = time.perf_counter() - t0
+    total_gens, total_secs = gens + 1, secs + one
+    return nx * ny * total_gens / total_secs / 1e9, total_gens, total_secs
+
+
+def run_reference(args, wl, world, rank):
+    if rank != 0:
+        return 0
+    import oracle
+    from paper_1609_04567_gb300 import inputs
+    oracle.build()
+    # each step: one generation of an 8192-wide, 2048-row torus through the
+    # oracle (a bounded sample of the 2000-generation 8192 x 8192 workload with
+    # the same per-cell work; the metric is per cell-update)
+    rows = 2048
+    state = inputs.life_cells(rows, wl["nx"])
+    for _ in range(args.warmup):
+        state, _ = oracle.life(state, wrap=True, max_gens=1)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        state, _ = oracle.life(state, wrap=True, max_gens=1)
+    secs = time.perf_counter() - t0
+    value = wl["nx"] * rows * args.steps / secs / 1e9
+    sample = f"1 generation of an {wl['nx']}x{rows} torus per step (same per-cell work), single-threaded plain C"
+    line = {
+        "impl": "reference", "metric": "Gcell-updates/s", "value": value, "unit": "Gcell-updates/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": secs / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+        "config": {"workload": wl["name"], "sample": sample},
+        "cpu_baseline": {"value": value, "unit": "Gcell-updates/s", "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": "Gcell-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args, wl, world, rank, local):
+    import numpy as np
+    import torch
+
+    from paper_1609_04567_gb300 import build as slr_build
+    from paper_1609_04567_gb300 import inputs, slr
+
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    if rank == 0 and not os.path.exists(slr.LIB_PATH):
+        slr_build.build()
+    barrier(world)
+    slr.load()
+    nx, ny, gens = wl["nx"], wl["ny"], wl["gens"]
+    cells = inputs.life_cells(ny, nx)
+    pristine = torch.from_numpy(cells).to(dev)
+    u = torch.empty_like(pristine)
+    stream = torch.cuda.Stream(dev)
+    desc = slr.slr_desc_init(slr.SLR_LIFE, nx, ny, 1, temporal_k=args.k)
+    ws_bytes = slr.slr_workspace_size(desc)
+    ws_t = torch.empty(ws_bytes + 256, dtype=torch.uint8, device=dev)
+    ws = ws_t.data_ptr() + ((-ws_t.data_ptr()) % 256)
+    cell_updates = nx * ny * gens
+
+    def step(launch_events=None, loop=slr.SLR_LOOP_PERSISTENT):
+        u.copy_(pristine, non_blocking=True)
+        desc.loop = loop
+        h = slr.slr_create(desc, u.data_ptr(), 0, ws, ws_bytes, stream.cuda_stream)
+        if launch_events is not None:
+            launch_events[0].record(stream)
+        slr.slr_run_until(h, gens)
+        if launch_events is not None:
+            launch_events[1].record(stream)
+        return h
+
+    handles = []
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            handles.append(step())
+        torch.cuda.synchronize(dev)
+        first = slr.slr_reduce_value(handles[-1])
+        for h in handles:
+            slr.slr_destroy(h)
+        handles = []
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(args.steps)]
+        t_start, t_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        clocks = ClockSampler(local)
+        barrier(world)
+        torch.cuda.synchronize(dev)
+        clocks.start()
+        t_start.record(stream)
+        for i in range(args.steps):
+            handles.append(step(ev[i]))
+        t_end.record(stream)
+        torch.cuda.synchronize(dev)
+        barrier(world)
+        clk = clocks.stop()
+        res = slr.slr_reduce_value(handles[-1])
+        for h in handles:
+            slr.slr_destroy(h)
+    ms_total = t_start.elapsed_time(t_end)
+    ms_step = max_over_ranks(ms_total / args.steps, world)
+    value = world * cell_updates / (ms_step / 1e3) / 1e9
+    kern_ms = statistics.mean(a.elapsed_time(b) for a, b in ev)
+    algo_bytes = wl["bytes_per_cell_sweep"] * nx * ny * gens
+    peak, peak_src = measured_peaks()
+    achieved = algo_bytes / (kern_ms / 1e3) / 1e9
+    traffic = recorded_traffic(wl["name"])
+
+    # plain path: one sweep launch + one reduce launch + host test per generation
+    plain = None
+    if not args.no_plain:
+        with torch.cuda.stream(stream):
+            pe = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+            torch.cuda.synchronize(dev)
+            t0 = time.perf_counter()
+            h = step(pe, loop=slr.SLR_LOOP_HOST)
+            torch.cuda.synchronize(dev)
+            wall = time.perf_counter() - t0
+            pr = slr.slr_reduce_value(h)
+            slr.slr_destroy(h)
+        plain = {"value": cell_updates / wall / 1e9, "unit": "Gcell-updates/s", "ms_per_step": wall * 1e3,
+                 "iters": pr[2], "count": pr[4], "same_result": pr[1:] == res[1:],
+                 "what": "host-driven loop: per generation one sweep launch, one reduce launch, "
+                         "a D2H copy of the reduced value and the test on the host"}
+
+    # end to end through the C ABI with host buffers: pinned H2D of the input,
+    # the solve, D2H of the final state and of the reduced value, every step
+    host_in = torch.from_numpy(cells).pin_memory()
+    host_out = torch.empty_like(host_in).pin_memory()
+    with torch.cuda.stream(stream):
+        e2e_steps = max(1, min(args.steps, 5))
+        barrier(world)
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        for _ in range(e2e_steps):
+            u.copy_(host_in, non_blocking=True)
+            desc.loop = slr.SLR_LOOP_PERSISTENT
+            h = slr.slr_create(desc, u.data_ptr(), 0, ws, ws_bytes, stream.cuda_stream)
+            slr.slr_run_until(h, gens)
+            host_out.copy_(u, non_blocking=True)
+            e2e_res = slr.slr_reduce_value(h)          # waits for the stream
+            slr.slr_destroy(h)
+        wall = max_over_ranks((time.perf_counter() - t0) / e2e_steps, world)
+    assert np.array_equal(host_out.numpy(), u.cpu().numpy())
+    e2e = {"value": world * cell_updates / wall / 1e9, "unit": "Gcell-updates/s",
+           "h2d_bytes_per_step": int(host_in.numel()), "d2h_bytes_per_step": int(host_out.numel()) + 1024,
+           "ms_per_step": wall * 1e3}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        v, g, s = oracle_life_sample(nx, ny, args.cpu_budget)
+        cpu = {"value": v, "unit": "Gcell-updates/s", "cores": 1, "kind": "oracle",
+               "sample": f"{g} generations of the 8192x8192 torus, {s:.1f} s, single-threaded plain C"}
+
+    if rank == 0:
+        line = {
+            "metric": "Gcell-updates/s", "value": value, "unit": "Gcell-updates/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
+            "data": "synthetic",
+            "config": {"workload": wl["name"], "cells": nx * ny, "generations": gens,
+                       "parallelism": f"replicas{world}", "loop": "persistent cooperative kernel",
+                       "temporal_k": args.k,
+                       "l2": "no flush: per-step working set 192 MiB (ping-pong pair 128 MiB + input copy) "
+                             "exceeds the L2"},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": traffic,
+                         "peak_source": peak_src, "kernel_ms": kern_ms,
+                         "algorithmic_bytes_per_launch": algo_bytes,
+                         "kernel": "life persistent loop (all generations in one cooperative launch)"},
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "plain": plain,
+            "gpu_launches": 2 * args.steps,
+            "clocks": clk,
+            "result": {"iters": res[2], "live": res[4], "converged": res[3],
+                       "same_as_warmup": first[1:] == res[1:]},
+        }
+        print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="life", choices=sorted(WORKLOADS))
+    ap.add_argument("--k", type=int, default=0, help="generations per HBM pass (0 = library choice)")
+    ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-budget", type=float, default=12.0)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    wl = WORKLOADS[args.workload]
+    world, rank, local = dist_setup()
+    if args.impl == "reference":
+        return run_reference(args, wl, world, rank)
+    return run_ours(args, wl, world, rank, local)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

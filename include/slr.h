@@ -114,7 +114,15 @@ typedef struct {
     int32_t math;          /* slr_math */
     int32_t temporal_k;    /* sweeps per HBM pass for Life (1, 2, 4, ...); 0 = library choice */
     int64_t wait_limit_ns; /* device-side barrier wait limit; <= 0 selects 2 s */
+    int32_t debug_flags;   /* SLR_DEBUG_* bits; 0 in normal use */
+    int32_t reserved;
 } slr_desc;
+
+/* Fault injection for tests of the device-side wait limit: the last CTA of a
+ * persistent launch leaves before its first barrier arrival, so every other
+ * CTA's wait runs out after wait_limit_ns and the run reports SLR_ERR_TIMEOUT.
+ * The handle is then unusable (create a new one); the GPU context is not. */
+#define SLR_DEBUG_SKIP_ARRIVAL 1
 
 /* Fill *d with defaults for a stencil: the matching reduce operator and
  * storage, Dirichlet ghost 0, tol 1e-6 (Jacobi), 1e-3 (restoration), sigma 1,

@@ -1,0 +1,204 @@
+"""Thin ctypes binding of libslr.so (include/slr.h), plus a torch-tensor wrapper.
+
+The functions ``slr_*`` below carry the C names and only marshal arguments:
+device pointers are passed as integers (``tensor.data_ptr()``), the stream as
+``torch.cuda.Stream.cuda_stream``.  Every sweep, reduce and test runs in the
+CUDA library; there is no CPU path.  If ``libslr.so`` is missing or cannot be
+loaded, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libslr.so")
+
+# enums of slr.h
+SLR_OK, SLR_NOT_CONVERGED = 0, 1
+SLR_ERR_INVALID_ARG, SLR_ERR_WORKSPACE, SLR_ERR_CUDA, SLR_ERR_TIMEOUT, SLR_ERR_UNSUPPORTED = -1, -2, -3, -4, -5
+SLR_J2D5, SLR_J3D7, SLR_LIFE, SLR_RESTORE8 = 0, 1, 2, 3
+SLR_DIRICHLET, SLR_WRAP = 0, 1
+SLR_RED_MAX_ABS_DELTA, SLR_RED_MEAN_ABS_DELTA_MASKED, SLR_RED_LIVE_COUNT = 0, 1, 2
+SLR_U8, SLR_BF16, SLR_F16, SLR_F32, SLR_F64 = 0, 1, 2, 3, 4
+SLR_LOOP_AUTO, SLR_LOOP_HOST, SLR_LOOP_PERSISTENT = 0, 1, 2
+SLR_MATH_EXACT, SLR_MATH_FAST = 0, 1
+SLR_DEBUG_SKIP_ARRIVAL = 1
+
+STATUS_NAMES = {0: "SLR_OK", 1: "SLR_NOT_CONVERGED", -1: "SLR_ERR_INVALID_ARG", -2: "SLR_ERR_WORKSPACE",
+                -3: "SLR_ERR_CUDA", -4: "SLR_ERR_TIMEOUT", -5: "SLR_ERR_UNSUPPORTED"}
+
+
+class slr_desc(ctypes.Structure):
+    _fields_ = [
+        ("stencil", ctypes.c_int32), ("storage", ctypes.c_int32), ("reduce", ctypes.c_int32),
+        ("boundary", ctypes.c_int32),
+        ("nx", ctypes.c_int64), ("ny", ctypes.c_int64), ("nz", ctypes.c_int64),
+        ("ghost", ctypes.c_double), ("tol", ctypes.c_double), ("sigma", ctypes.c_double),
+        ("h", ctypes.c_double), ("alpha", ctypes.c_float),
+        ("loop", ctypes.c_int32), ("math", ctypes.c_int32), ("temporal_k", ctypes.c_int32),
+        ("wait_limit_ns", ctypes.c_int64), ("debug_flags", ctypes.c_int32), ("reserved", ctypes.c_int32),
+    ]
+
+
+EXPORTS = ["slr_desc_init", "slr_workspace_size", "slr_create", "slr_run_until", "slr_reduce_value",
+           "slr_destroy", "slr_last_error", "slr_version"]
+
+_lib = None
+
+
+class SlrError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+def load(path: str = LIB_PATH):
+    """Load libslr.so (raises if it was not built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build it with "
+                           "`python -c 'import __graft_entry__ as g; g.build()'` (nvcc, sm_103a)")
+    import torch  # noqa: F401  -- loads the CUDA runtime the library shares with torch
+    lib = ctypes.CDLL(path)
+    P, i64, i32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32
+    D = ctypes.POINTER(slr_desc)
+    lib.slr_desc_init.argtypes = [D, i32, i64, i64, i64]
+    lib.slr_desc_init.restype = None
+    lib.slr_workspace_size.argtypes = [D]
+    lib.slr_workspace_size.restype = ctypes.c_size_t
+    lib.slr_create.argtypes = [D, P, P, P, ctypes.c_size_t, P, ctypes.POINTER(P)]
+    lib.slr_create.restype = i32
+    lib.slr_run_until.argtypes = [P, i64]
+    lib.slr_run_until.restype = i32
+    lib.slr_reduce_value.argtypes = [P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i64),
+                                     ctypes.POINTER(i32), ctypes.POINTER(ctypes.c_uint64)]
+    lib.slr_reduce_value.restype = i32
+    lib.slr_destroy.argtypes = [P]
+    lib.slr_destroy.restype = i32
+    lib.slr_last_error.argtypes = [P]
+    lib.slr_last_error.restype = ctypes.c_char_p
+    lib.slr_version.argtypes = []
+    lib.slr_version.restype = ctypes.c_char_p
+    _lib = lib
+    return lib
+
+
+# ---- the C calls, one to one ----------------------------------------------
+
+def slr_desc_init(stencil: int, nx: int, ny: int, nz: int = 1, **fields) -> slr_desc:
+    d = slr_desc()
+    load().slr_desc_init(ctypes.byref(d), stencil, nx, ny, nz)
+    for k, v in fields.items():
+        setattr(d, k, v)
+    return d
+
+
+def slr_workspace_size(d: slr_desc) -> int:
+    return int(load().slr_workspace_size(ctypes.byref(d)))
+
+
+def slr_create(d: slr_desc, u_ptr: int, aux_ptr: int, ws_ptr: int, ws_bytes: int, stream: int) -> int:
+    h = ctypes.c_void_p()
+    st = load().slr_create(ctypes.byref(d), u_ptr or None, aux_ptr or None, ws_ptr or None, ws_bytes,
+                           stream or None, ctypes.byref(h))
+    if st != SLR_OK:
+        raise SlrError(st, slr_last_error(None))
+    return h.value
+
+
+def slr_run_until(h: int, max_iters: int) -> int:
+    st = load().slr_run_until(h, max_iters)
+    if st < 0:
+        raise SlrError(st, slr_last_error(h))
+    return st
+
+
+def slr_reduce_value(h: int, check: bool = True):
+    """Returns (status, value, iters, converged, count)."""
+    v, it, c, n = ctypes.c_double(), ctypes.c_int64(), ctypes.c_int32(), ctypes.c_uint64()
+    st = load().slr_reduce_value(h, ctypes.byref(v), ctypes.byref(it), ctypes.byref(c), ctypes.byref(n))
+    if check and st < 0:
+        raise SlrError(st, slr_last_error(h))
+    return st, v.value, it.value, bool(c.value), n.value
+
+
+def slr_destroy(h: int) -> int:
+    return load().slr_destroy(h)
+
+
+def slr_last_error(h) -> str:
+    return load().slr_last_error(h).decode()
+
+
+def slr_version() -> str:
+    return load().slr_version().decode()
+
+
+# ---- torch wrapper ----------------------------------------------------------
+
+@dataclass
+class Result:
+    status: int
+    value: float
+    iters: int
+    converged: bool
+    count: int
+
+
+_TORCH_STORAGE = None
+
+
+def storage_of(dtype) -> int:
+    import torch
+    global _TORCH_STORAGE
+    if _TORCH_STORAGE is None:
+        _TORCH_STORAGE = {torch.uint8: SLR_U8, torch.bfloat16: SLR_BF16, torch.float16: SLR_F16,
+                          torch.float32: SLR_F32, torch.float64: SLR_F64}
+    return _TORCH_STORAGE[dtype]
+
+
+class Solver:
+    """One loop-of-stencil-reduce instance over caller-owned torch tensors.
+
+    ``u`` (state, in/out) and ``aux`` (f or mask) are CUDA tensors; the
+    workspace is allocated here with torch (the library itself never
+    allocates).  ``run(max_iters)`` enqueues the loop on ``stream``;
+    ``result()`` waits and reads the reduced value."""
+
+    def __init__(self, stencil: int, u, aux=None, *, stream=None, **fields):
+        import torch
+        if not u.is_cuda or not u.is_contiguous():
+            raise ValueError("u must be a contiguous CUDA tensor")
+        shape = tuple(u.shape)
+        nz, ny, nx = (1,) * (3 - len(shape)) + shape
+        self.desc = slr_desc_init(stencil, nx, ny, nz, storage=storage_of(u.dtype), **fields)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(u.device)
+        ws = slr_workspace_size(self.desc)
+        if ws == 0:
+            raise SlrError(SLR_ERR_INVALID_ARG, "invalid descriptor")
+        self.ws = torch.empty(ws + 256, dtype=torch.uint8, device=u.device)
+        off = (-self.ws.data_ptr()) % 256
+        self.u, self.aux = u, aux
+        self.handle = slr_create(self.desc, u.data_ptr(), aux.data_ptr() if aux is not None else 0,
+                                 self.ws.data_ptr() + off, ws, self.stream.cuda_stream)
+
+    def run(self, max_iters: int) -> int:
+        return slr_run_until(self.handle, max_iters)
+
+    def result(self, check: bool = True) -> Result:
+        return Result(*slr_reduce_value(self.handle, check))
+
+    def close(self):
+        if getattr(self, "handle", None):
+            slr_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -18,3 +18,26 @@ def orc():
     import oracle
     oracle.build()
     return oracle
+
+
+@pytest.fixture(scope="session")
+def gpu():
+    """Build and load libslr for the GPU tests; skip where no GPU is present.
+    On a GPU machine a missing or broken library fails the test loudly."""
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1609_04567_gb300 import build, slr
+    build.build()
+    slr.load()
+    torch.cuda.set_device(0)
+    return slr
+
+
+def run_solver(slr, stencil, u, aux=None, max_iters=1000, **fields):
+    """Run one solve through the C ABI; returns (state on host, Result)."""
+    s = slr.Solver(stencil, u, aux, **fields)
+    s.run(max_iters)
+    r = s.result()
+    s.close()
+    return u.cpu().numpy(), r

@@ -1,0 +1,93 @@
+"""The C-ABI library builds for sm_103a, loads, and exports every function that
+include/slr.h declares; the binding mirrors the descriptor layout.  No GPU
+needed: nothing here launches a kernel."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    names = []
+    for hdr in os.listdir(os.path.join(ROOT, "include")):
+        if not hdr.endswith(".h"):
+            continue
+        text = open(os.path.join(ROOT, "include", hdr)).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        names += re.findall(r"\b(slr_[a-z0-9_]+)\s*\(", text)
+    return sorted(set(names))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1609_04567_gb300 import build
+    path = build.build()
+    return ctypes.CDLL(path)
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = declared_functions()
+    assert "slr_create" in names and "slr_run_until" in names
+    assert "slr_reduce_value" in names and "slr_destroy" in names
+    for n in names:
+        assert hasattr(lib, n), f"{n} declared in include/ but not exported"
+
+
+def test_binding_covers_declared_functions():
+    from paper_1609_04567_gb300 import slr
+    assert sorted(slr.EXPORTS) == sorted(n for n in declared_functions() if n in slr.EXPORTS)
+    for n in declared_functions():
+        assert n in slr.EXPORTS, f"binding lacks {n}"
+
+
+def test_desc_layout_and_defaults(lib):
+    from paper_1609_04567_gb300 import slr
+    slr.load()
+    d = slr.slr_desc_init(slr.SLR_J2D5, 256, 256, 1)
+    assert d.reduce == slr.SLR_RED_MAX_ABS_DELTA and d.storage == slr.SLR_F64
+    assert d.tol == 1e-6 and d.sigma == 1.0 and d.boundary == slr.SLR_DIRICHLET
+    d = slr.slr_desc_init(slr.SLR_LIFE, 64, 32, 1)
+    assert d.boundary == slr.SLR_WRAP and d.storage == slr.SLR_U8
+    d = slr.slr_desc_init(slr.SLR_RESTORE8, 64, 32, 1)
+    assert d.storage == slr.SLR_F32 and d.alpha == pytest.approx(100.0) and d.tol == 1e-3
+    assert d.reduce == slr.SLR_RED_MEAN_ABS_DELTA_MASKED
+
+
+def test_workspace_size_and_validation(lib):
+    from paper_1609_04567_gb300 import slr
+    d = slr.slr_desc_init(slr.SLR_LIFE, 8192, 8192, 1)
+    ws = slr.slr_workspace_size(d)
+    assert ws >= 8192 * 8192 and ws % 256 == 0
+    bad = slr.slr_desc_init(slr.SLR_LIFE, 0, 8, 1)
+    assert slr.slr_workspace_size(bad) == 0
+    bad = slr.slr_desc_init(slr.SLR_J2D5, 8, 8, 2)          # 2D stencil with nz > 1
+    assert slr.slr_workspace_size(bad) == 0
+    bad = slr.slr_desc_init(slr.SLR_J2D5, 8, 8, 1, reduce=slr.SLR_RED_LIVE_COUNT)
+    assert slr.slr_workspace_size(bad) == 0
+
+
+def test_create_rejects_bad_arguments_without_touching_the_gpu(lib):
+    from paper_1609_04567_gb300 import slr
+    d = slr.slr_desc_init(slr.SLR_J2D5, 8, 8, 1)
+    with pytest.raises(slr.SlrError) as e:
+        slr.slr_create(d, 0x1000, 0x2000, 0x3000, 0, 0)      # workspace too small
+    assert e.value.status == slr.SLR_ERR_WORKSPACE
+    with pytest.raises(slr.SlrError) as e:
+        slr.slr_create(d, 0x1001, 0x2000, 0x3000, 1 << 20, 0)  # misaligned u
+    assert e.value.status == slr.SLR_ERR_INVALID_ARG
+    with pytest.raises(slr.SlrError) as e:
+        slr.slr_create(d, 0x1000, 0, 0x3000, 1 << 20, 0)      # Jacobi needs f
+    assert e.value.status == slr.SLR_ERR_INVALID_ARG
+    r = slr.slr_desc_init(slr.SLR_RESTORE8, 8, 8, 1, boundary=slr.SLR_WRAP)
+    with pytest.raises(slr.SlrError) as e:
+        slr.slr_create(r, 0x1000, 0x2000, 0x3000, 1 << 20, 0)
+    assert e.value.status == slr.SLR_ERR_UNSUPPORTED
+    assert "restoration" in slr.slr_last_error(None)
+
+
+def test_version_names_the_architecture(lib):
+    from paper_1609_04567_gb300 import slr
+    assert "sm_103a" in slr.slr_version()
