@@ -102,15 +102,15 @@ def test_cap_and_resume(gpu, orc):
     from paper_1609_04567_gb300 import inputs
     f = torch.from_numpy(inputs.helmholtz_rhs((128, 128), seed=4)).cuda()
     u = torch.zeros((128, 128), dtype=torch.float64, device="cuda")
-    s = gpu.Solver(gpu.SLR_J2D5, u, f, tol=1e-9)
+    s = gpu.Solver(gpu.SLR_J2D5, u, f, tol=1e-7)
     s.run(10)
     r1 = s.result()
     assert r1.iters == 10 and not r1.converged and r1.status == gpu.SLR_NOT_CONVERGED
-    s.run(5000)
+    s.run(3000)
     r2 = s.result()
     s.close()
-    ref, rr = orc.j2d5(np.zeros((128, 128)), f.cpu().numpy(), tol=1e-9, max_iters=5000)
-    assert r2.iters == rr.iters and r2.converged
+    ref, rr = orc.j2d5(np.zeros((128, 128)), f.cpu().numpy(), tol=1e-7, max_iters=3000)
+    assert (r2.iters, r2.converged, r2.value) == (rr.iters, rr.converged, rr.value)
     assert np.array_equal(u.cpu().numpy(), ref)
 
 
