@@ -140,6 +140,7 @@ slr_status run_persistent(slr_handle h, int64_t max_iters)
     Ctl *ctl = dev_ctl(h);
     cudaError_t e = cudaMemsetAsync(&ctl->bar, 0, sizeof(ctl->bar), h->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(&ctl->slot[0], 0, 2 * sizeof(Slot), h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(&ctl->sub[0][0], 0, 2 * sizeof(ctl->sub[0]), h->stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "reset loop state");
     slr::LoopArgs la;
     la.a = h->u;
@@ -153,7 +154,10 @@ slr_status run_persistent(slr_handle h, int64_t max_iters)
     la.nblocks = 0;
     la.debug_flags = h->desc.debug_flags;
     switch (h->prob.stencil) {
-    case SLR_LIFE: e = slr::life_persistent(h->prob, la, h->stream); break;
+    case SLR_LIFE:
+        e = h->prob.k != 1 && slr::life_tb_supported(h->prob) ? slr::life_tb_persistent(h->prob, la, h->stream)
+                                                             : slr::life_persistent(h->prob, la, h->stream);
+        break;
     case SLR_J2D5:
     case SLR_J3D7: e = slr::jacobi_persistent(h->prob, la, h->stream); break;
     case SLR_RESTORE8: e = slr::restore_persistent(h->prob, la, h->stream); break;

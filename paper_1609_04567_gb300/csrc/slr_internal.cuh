@@ -54,7 +54,7 @@ struct Ctl {
     int changed;                  // any item changed in the last iteration
     int pad;
     Slot slot[kSlots];
-    Slot sub[2][kMaxK];           // per-sub-step slots of temporal-blocked passes
+    Slot sub[kSlots][kMaxK];      // per-sub-step slots of temporal-blocked passes
 };
 
 constexpr size_t kCtlBytes = 4096;            // Ctl padded; state buffer B follows
@@ -313,6 +313,11 @@ struct Problem {
 cudaError_t life_persistent(const Problem &p, LoopArgs la, cudaStream_t st);
 cudaError_t life_sweep(const Problem &p, const void *src, void *dst, cudaStream_t st);
 cudaError_t life_normalize(const Problem &p, void *u, cudaStream_t st);
+// Temporal-blocked Life: k generations per HBM pass (life_tb.cu).  Returns
+// cudaErrorNotSupported when the grid does not fit its tiling rules.
+bool life_tb_supported(const Problem &p);
+int life_tb_default_k(const Problem &p);
+cudaError_t life_tb_persistent(const Problem &p, LoopArgs la, cudaStream_t st);
 cudaError_t jacobi_persistent(const Problem &p, LoopArgs la, cudaStream_t st);
 cudaError_t jacobi_sweep(const Problem &p, const void *src, void *dst, const void *f, cudaStream_t st);
 cudaError_t restore_persistent(const Problem &p, LoopArgs la, cudaStream_t st);

@@ -114,3 +114,53 @@ def test_full_size_2000_generations_properties(gpu):
     rh = s.result()
     s.close()
     assert torch.equal(half, base) and rh.count == r.count == rs.count == rt.count
+
+
+# ---- temporal-blocked path (K generations per HBM pass) ----------------------
+# It serves widths that are multiples of 32 (dead border) or of 128 with
+# heights that are multiples of 32 (torus); tiles own 1024 x 224 cells.
+
+@pytest.mark.parametrize("ny,nx,wrap", [
+    (256, 1024, True), (96, 2176, True), (32, 128, True), (480, 3072, True), (64, 1152, True),
+    (257, 512, False), (70, 2080, False), (500, 1056, False), (33, 32, False),
+])
+@pytest.mark.parametrize("k", [2, 7, 16])
+def test_temporal_blocked_matches_oracle(gpu, orc, ny, nx, wrap, k):
+    from paper_1609_04567_gb300 import inputs
+    cells = inputs.life_cells(ny, nx, seed=ny + nx + k)
+    u = torch.from_numpy(cells).cuda()
+    out, r = run_solver(gpu, gpu.SLR_LIFE, u, None, 45,
+                        boundary=gpu.SLR_WRAP if wrap else gpu.SLR_DIRICHLET, temporal_k=k)
+    ref, rr = orc.life(cells, wrap=wrap, max_gens=45)
+    assert np.array_equal(out, ref)
+    assert (r.iters, r.count, r.converged) == (rr.iters, rr.count, rr.converged)
+
+
+@pytest.mark.parametrize("k", [4, 16])
+def test_temporal_blocked_stops_inside_a_pass(gpu, orc, k):
+    # a blinker and a block that fade into a still state after a few
+    # generations: the stop generation falls inside a K-generation pass
+    cells = np.zeros((256, 1024), np.uint8)
+    cells[100:102, 300:302] = 1                       # block: still
+    cells[10, 10:13] = 1                              # blinker next to ...
+    cells[11, 13] = 1                                 # ... a cell that perturbs it
+    u = torch.from_numpy(cells).cuda()
+    out, r = run_solver(gpu, gpu.SLR_LIFE, u, None, 500, temporal_k=k)
+    ref, rr = orc.life(cells, wrap=True, max_gens=500)
+    assert np.array_equal(out, ref)
+    assert (r.iters, r.count, r.converged) == (rr.iters, rr.count, rr.converged)
+
+
+def test_temporal_blocked_resume_and_cap(gpu, orc):
+    from paper_1609_04567_gb300 import inputs
+    cells = inputs.life_cells(512, 2048, seed=77)
+    a = torch.from_numpy(cells).cuda()
+    s = gpu.Solver(gpu.SLR_LIFE, a, temporal_k=16)
+    s.run(13)
+    r1 = s.result()
+    s.run(61)
+    r2 = s.result()
+    s.close()
+    ref, rr = orc.life(cells, wrap=True, max_gens=61)
+    assert r1.iters == 13 and r2.iters == 61 == rr.iters
+    assert np.array_equal(a.cpu().numpy(), ref) and r2.count == rr.count
