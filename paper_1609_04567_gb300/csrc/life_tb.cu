@@ -178,27 +178,65 @@ __device__ __forceinline__ long long wrap_mod(long long v, long long n)
     return v < 0 ? v + n : v;
 }
 
-// Thread 0: enqueue the ten boxes of chunk c of tile g into staging buffer sb.
+// Box b of a chunk (b < 8: owned columns, 8: left halo, 9: right halo): its
+// column, width and whether any of it lies inside the grid.  On the torus every
+// box is placed at its wrapped coordinate and is always inside; with the dead
+// border a box wholly outside the grid is not loaded at all and reads as zeros
+// (a box partly outside is loaded and the hardware fills the outside with
+// zeros).
+struct Box {
+    long long x;
+    int w;
+    bool in;
+};
+
+__device__ __forceinline__ long long chunk_row(const TbParams &tp, const Tile &g, int c)
+{
+    long long y = g.real0 + (long long)c * kChunkRows;
+    return tp.wrap ? wrap_mod(y, tp.ny) : y;
+}
+
+__device__ __forceinline__ Box box_of(const TbParams &tp, const Tile &g, long long y, int b)
+{
+    Box bx;
+    if (b < kMidBoxes) { bx.x = g.x0 + (long long)b * kMidBoxW; bx.w = kMidBoxW; }
+    else { bx.x = b == kMidBoxes ? g.x0 - kHaloBoxW : g.x0 + kOwnCols; bx.w = kHaloBoxW; }
+    if (tp.wrap) {
+        bx.x = wrap_mod(bx.x, tp.nx);
+        bx.in = true;
+    } else {
+        bx.in = bx.x < tp.nx && bx.x + bx.w > 0 && y < tp.ny && y + kChunkRows > 0;
+    }
+    return bx;
+}
+
+// Thread 0: enqueue the in-grid boxes of chunk c of tile g into a staging buffer.
 __device__ __forceinline__ void issue_chunk(const TbParams &tp, int srcbuf, const Tile &g, int c,
                                            unsigned char *stage, uint64_t *bar)
 {
-    mbar_expect_tx(bar, (uint32_t)kStageBytes);
-    long long y = g.real0 + (long long)c * kChunkRows;
-    if (tp.wrap) y = wrap_mod(y, tp.ny);
-    const CUtensorMap *mid = &tp.mid[srcbuf];
-    const CUtensorMap *halo = &tp.halo[srcbuf];
+    const long long y = chunk_row(tp, g, c);
+    uint32_t bytes = 0;
+    Box bx[kMidBoxes + 2];
 #pragma unroll
-    for (int b = 0; b < kMidBoxes; ++b) {
-        long long x = g.x0 + (long long)b * kMidBoxW;
-        if (tp.wrap) x = wrap_mod(x, tp.nx);
-        tma_load_2d(stage + b * kMidBoxBytes, mid, (int)x, (int)y, bar);
+    for (int b = 0; b < kMidBoxes + 2; ++b) {
+        bx[b] = box_of(tp, g, y, b);
+        if (bx[b].in) bytes += (uint32_t)(bx[b].w * kChunkRows);
     }
-    long long xl = g.x0 - kHaloBoxW, xr = g.x0 + kOwnCols;
-    if (tp.wrap) { xl = wrap_mod(xl, tp.nx); xr = wrap_mod(xr, tp.nx); }
-    tma_load_2d(stage + kMidBoxes * kMidBoxBytes, halo, (int)xl, (int)y, bar);
-    tma_load_2d(stage + kMidBoxes * kMidBoxBytes + kHaloBoxBytes, halo, (int)xr, (int)y, bar);
+    mbar_expect_tx(bar, bytes);
+#pragma unroll
+    for (int b = 0; b < kMidBoxes; ++b)
+        if (bx[b].in) tma_load_2d(stage + b * kMidBoxBytes, &tp.mid[srcbuf], (int)bx[b].x, (int)y, bar);
+#pragma unroll
+    for (int s = 0; s < 2; ++s)
+        if (bx[kMidBoxes + s].in)
+            tma_load_2d(stage + kMidBoxes * kMidBoxBytes + s * kHaloBoxBytes, &tp.halo[srcbuf],
+                        (int)bx[kMidBoxes + s].x, (int)y, bar);
 }
 
+// WRAP: torus (every tile cell is a real, wrapped cell).  !WRAP: dead border;
+// cells of the tile that lie outside the grid are cleared after every
+// generation, because the border stays dead at every step.
+template <bool WRAP>
 __global__ void __launch_bounds__(kThreads, 2) life_tb_kernel(const __grid_constant__ TbParams tp, LoopArgs la)
 {
     extern __shared__ unsigned char smem_raw[];
@@ -275,20 +313,26 @@ __global__ void __launch_bounds__(kThreads, 2) life_tb_kernel(const __grid_const
                 if (!s_ok) return;
                 const unsigned char *sbase = stage + sb * kStageBytes;
                 uint32_t *brow = bits + c * kChunkRows * kBitStride;
+                const long long ychunk = chunk_row(tp, g, c);
 #pragma unroll
                 for (int i = 0; i < (kChunkRows * 64) / kThreads; ++i) {   // 32 rows x 64 groups of 16 cells
                     const int item = tid + i * kThreads;
                     const int rr = item >> 6, gidx = item & 63;
                     const int box = gidx >> 3, qq = gidx & 7;
-                    const uint4 v = *(const uint4 *)(sbase + box * kMidBoxBytes + rr * kMidBoxW + ((qq ^ (rr & 7)) << 4));
-                    ((unsigned short *)(brow + rr * kBitStride + 1 + (gidx >> 1)))[gidx & 1] = (unsigned short)pack16(v);
+                    uint32_t packed = 0u;
+                    if (box_of(tp, g, ychunk, box).in)
+                        packed = pack16(*(const uint4 *)(sbase + box * kMidBoxBytes + rr * kMidBoxW +
+                                                         ((qq ^ (rr & 7)) << 4)));
+                    ((unsigned short *)(brow + rr * kBitStride + 1 + (gidx >> 1)))[gidx & 1] = (unsigned short)packed;
                 }
                 if (tid < kChunkRows * 4) {                                // halo words 0 and 33
                     const int rr = tid >> 2, side = (tid >> 1) & 1, half = tid & 1;
-                    const uint4 v = *(const uint4 *)(sbase + kMidBoxes * kMidBoxBytes + side * kHaloBoxBytes +
-                                                     rr * kHaloBoxW + half * 16);
+                    uint32_t packed = 0u;
+                    if (box_of(tp, g, ychunk, kMidBoxes + side).in)
+                        packed = pack16(*(const uint4 *)(sbase + kMidBoxes * kMidBoxBytes + side * kHaloBoxBytes +
+                                                         rr * kHaloBoxW + half * 16));
                     ((unsigned short *)(brow + rr * kBitStride + (side ? kWords - 1 : 0)))[half] =
-                        (unsigned short)pack16(v);
+                        (unsigned short)packed;
                 }
                 __syncthreads();                                           // staging buffer sb is free again
                 const int nxt = ti * kChunks + c + 2;
@@ -304,6 +348,13 @@ __global__ void __launch_bounds__(kThreads, 2) life_tb_kernel(const __grid_const
             const bool own_row = tid >= kHaloRows && tid < kHaloRows + kOwnRows && frame < tp.ny;
             const long long ocols = tp.nx - g.x0;
             const int own_words = ocols >= kOwnCols ? 32 : (int)(ocols / 32);
+            // dead border: words [wlo, whi] of this row are inside the grid
+            const long long yreal = g.real0 + tid;
+            const bool row_in = WRAP || (yreal >= 0 && yreal < tp.ny);
+            const int wlo = (WRAP || g.x0 > 0) ? 0 : 1;
+            // word w holds columns x0 - 32 + 32w .. x0 + 32w - 1
+            const long long wmax = (tp.nx - g.x0) / 32;
+            const int whi = WRAP ? kWords - 1 : (int)(wmax < kWords - 1 ? wmax : kWords - 1);
             for (int j = 0; j < kp; ++j) {
                 uint32_t *mine_x = xch + ((j & 1) * kWarps + warp) * 2 * kWords;
                 if (lane == 0) {
@@ -333,7 +384,8 @@ __global__ void __launch_bounds__(kThreads, 2) life_tb_kernel(const __grid_const
                         if (lane == 0) Un = upr[w + 1];
                         if (lane == 31) Dn = dnr[w + 1];
                     }
-                    const uint32_t nw = life_word(Um, Uc, Un, Cm, Cc, Cn, Dm, Dc, Dn);
+                    uint32_t nw = life_word(Um, Uc, Un, Cm, Cc, Cn, Dm, Dc, Dn);
+                    if (!WRAP && !(row_in && w >= wlo && w <= whi)) nw = 0u;
                     if (w >= 1 && w <= 32 && own_row && w <= own_words) {
                         changed |= nw ^ Cc;
                         cnt += (uint32_t)__popc(nw);
@@ -469,9 +521,10 @@ cudaError_t life_tb_persistent(const Problem &p, LoopArgs la, cudaStream_t st)
     tp.K = p.k > 0 ? (p.k > kHaloRows ? kHaloRows : p.k) : life_tb_default_k(p);
     tp.tiles_x = (int)((p.nx + kOwnCols - 1) / kOwnCols);
     tp.tiles_y = (int)((p.ny + kOwnRows - 1) / kOwnRows);
-    cudaError_t e = cudaFuncSetAttribute(life_tb_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes);
+    auto kern = tp.wrap ? life_tb_kernel<true> : life_tb_kernel<false>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes);
     if (e != cudaSuccess) return e;
-    return launch_cooperative(life_tb_kernel, kThreads, kSmemBytes, 2, la, &tp, st);
+    return launch_cooperative(kern, kThreads, kSmemBytes, 2, la, &tp, st);
 }
 
 }  // namespace slr
