@@ -170,6 +170,38 @@ const char *slr_last_error(slr_handle h);
 /* Library build string (architecture, version). */
 const char *slr_version(void);
 
+/* ---- A Jacobi solve that allocates nothing ---------------------------------
+ * The paper has no counterpart to this call; it serves callers that cannot
+ * allocate device memory when they need a solve (a device-memory budget owned
+ * by another framework's allocator, a real-time loop that forbids allocation
+ * after start-up, or a host thread where cudaMalloc/cudaFree would synchronise
+ * the device and stall other streams).  The second state buffer and the
+ * control block live in one static device array inside the library, of
+ * SLR_STATIC_STATE_BYTES + 4 KiB, which every GPU that loads the library keeps
+ * until the process exits.  The call makes no cudaMalloc, cudaFree or other
+ * allocating call.
+ *
+ * Runs d's loop (SLR_J2D5 or SLR_J3D7, any storage, persistent device loop)
+ * from the state in u with right-hand side f (both device pointers owned by
+ * the caller, layout as for slr_create) until the test passes or max_iters
+ * iterations, on `stream`, then waits for the stream and returns the reduced
+ * value, the iterations run and the converged flag (NULL outputs are
+ * skipped).  Returns SLR_OK / SLR_NOT_CONVERGED like slr_reduce_value,
+ * SLR_ERR_INVALID_ARG for a grid whose state exceeds SLR_STATIC_STATE_BYTES
+ * (message from slr_static_last_error()), SLR_ERR_UNSUPPORTED for other
+ * stencils.
+ *
+ * The first call on each device looks up the array's device address (once per
+ * device, with that device current); make that first call before any stream
+ * capture begins.  Every call shares the one array: each call clears the
+ * control block before it starts, and calls whose GPU work overlaps (several
+ * streams or host threads on one device) race on it. */
+#define SLR_STATIC_STATE_BYTES (4u << 20)
+slr_status slr_run_static(const slr_desc *d, void *u, const void *f, int64_t max_iters, void *stream,
+                          double *value, int64_t *iters, int32_t *converged);
+/* Message of the last failed slr_run_static on this host thread. */
+const char *slr_static_last_error(void);
+
 #ifdef __cplusplus
 }
 #endif

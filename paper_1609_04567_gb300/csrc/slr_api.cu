@@ -223,6 +223,12 @@ slr_status run_host(slr_handle h, int64_t max_iters)
 
 }  // namespace
 
+namespace slr {
+// Validation and problem set-up shared with entry points in other files.
+std::string describe_invalid(const slr_desc *d, bool *unsupported) { return check_desc(d, unsupported); }
+Problem problem_of(const slr_desc *d) { return make_problem(d); }
+}  // namespace slr
+
 extern "C" {
 
 void slr_desc_init(slr_desc *d, int32_t stencil, int64_t nx, int64_t ny, int64_t nz)

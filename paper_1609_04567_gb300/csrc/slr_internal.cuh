@@ -9,6 +9,8 @@
 #include <cuda_fp16.h>
 #include <stdint.h>
 
+#include <string>
+
 #include "slr.h"
 
 // __longlong_as_double exists only in device code; this works on both sides.
@@ -326,6 +328,10 @@ cudaError_t restore_sweep(const Problem &p, const void *src, void *dst, const vo
 // states (and the mask), reduced into *slot.
 cudaError_t reduce_states(const Problem &p, const void *src, const void *dst, const void *aux,
                           Slot *slot, cudaStream_t st);
+
+// Descriptor checks and problem set-up (slr_api.cu), for other entry points.
+std::string describe_invalid(const slr_desc *d, bool *unsupported);
+Problem problem_of(const slr_desc *d);
 
 // Cooperative launch of a persistent kernel with as many CTAs as can be
 // co-resident (at most `max_per_sm` per SM).  Fills la.nblocks.

@@ -43,7 +43,8 @@ class slr_desc(ctypes.Structure):
 
 
 EXPORTS = ["slr_desc_init", "slr_workspace_size", "slr_create", "slr_run_until", "slr_reduce_value",
-           "slr_destroy", "slr_last_error", "slr_version"]
+           "slr_destroy", "slr_last_error", "slr_version", "slr_run_static", "slr_static_last_error"]
+SLR_STATIC_STATE_BYTES = 4 << 20
 
 _lib = None
 
@@ -83,6 +84,11 @@ def load(path: str = LIB_PATH):
     lib.slr_last_error.restype = ctypes.c_char_p
     lib.slr_version.argtypes = []
     lib.slr_version.restype = ctypes.c_char_p
+    lib.slr_run_static.argtypes = [D, P, P, i64, P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i64),
+                                   ctypes.POINTER(i32)]
+    lib.slr_run_static.restype = i32
+    lib.slr_static_last_error.argtypes = []
+    lib.slr_static_last_error.restype = ctypes.c_char_p
     _lib = lib
     return lib
 
@@ -136,6 +142,20 @@ def slr_last_error(h) -> str:
 
 def slr_version() -> str:
     return load().slr_version().decode()
+
+
+def slr_run_static(d: slr_desc, u_ptr: int, f_ptr: int, max_iters: int, stream: int, check: bool = True):
+    """The allocation-free Jacobi solve; returns (status, value, iters, converged)."""
+    v, it, c = ctypes.c_double(), ctypes.c_int64(), ctypes.c_int32()
+    st = load().slr_run_static(ctypes.byref(d), u_ptr or None, f_ptr or None, max_iters, stream or None,
+                               ctypes.byref(v), ctypes.byref(it), ctypes.byref(c))
+    if check and st < 0:
+        raise SlrError(st, slr_static_last_error())
+    return st, v.value, it.value, bool(c.value)
+
+
+def slr_static_last_error() -> str:
+    return load().slr_static_last_error().decode()
 
 
 # ---- torch wrapper ----------------------------------------------------------
