@@ -36,11 +36,19 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 WORKLOADS = {
-    "life": dict(name="life_8192x8192_u8_torus_b3s23_2000gens", nx=8192, ny=8192, gens=2000,
-                 bytes_per_cell_sweep=2.0),
+    "life": dict(name="life_8192x8192_u8_torus_b3s23_{gens}gens", nx=8192, ny=8192, gens=2000,
+                 bytes_per_cell_pass=2.0),
 }
+# Logic operations per 32 cells per generation in the bit-sliced update of the
+# temporal-blocked kernel: 6 funnel shifts, 12 three-input logic operations for
+# the adder tree and the rule, and 3 for the two reduces (popcount, add, or).
+ALU_OPS_PER_CELL_GEN = 21.0 / 32.0
+# Integer/logic lanes per SM per clock on sm_103 (4 sub-partitions x 32 lanes)
+ALU_LANES_PER_SM = 128
+SMS = 152
 PROFILE_TRAFFIC = os.path.join(ROOT, "profiles", "traffic.json")
-KERNEL_SOURCES = ["paper_1609_04567_gb300/csrc/life.cu", "paper_1609_04567_gb300/csrc/slr_internal.cuh"]
+KERNEL_SOURCES = ["paper_1609_04567_gb300/csrc/life.cu", "paper_1609_04567_gb300/csrc/life_tb.cu",
+                  "paper_1609_04567_gb300/csrc/slr_internal.cuh"]
 
 
 def kernel_hash() -> str:
@@ -60,17 +68,19 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
-def recorded_traffic(workload: str):
-    """DRAM bytes per launch of the dominant kernel from a committed ncu
-    capture, if it was taken on the current kernel source; else None."""
+def recorded_traffic(workload: str, k: int):
+    """DRAM bytes per launch of the dominant kernel, scaled from a committed ncu
+    capture of a shorter run of the same kernel (bytes per pass x passes), if
+    it was taken on the current kernel source; else None."""
     if not os.path.exists(PROFILE_TRAFFIC):
         return None
     with open(PROFILE_TRAFFIC) as fh:
         d = json.load(fh)
-    e = d.get(workload)
+    e = d.get(f"life_8192_k{k}")
     if not e or e.get("kernel_hash") != kernel_hash():
         return None
-    return float(e["dram_bytes_per_launch"])
+    gens = int(workload.rsplit("_", 1)[-1].replace("gens", ""))
+    return float(e["dram_bytes_per_pass"]) * (-(-gens // k))
 
 
 class ClockSampler:
@@ -187,7 +197,7 @@ def run_reference(args, wl, world, rank):
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": secs / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "u8", "data": "synthetic",
-        "config": {"workload": wl["name"], "sample": sample},
+        "config": {"workload": wl["name"].format(gens=wl["gens"]), "sample": sample},
         "cpu_baseline": {"value": value, "unit": "Gcell-updates/s", "cores": 1, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": "Gcell-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -208,7 +218,7 @@ def run_ours(args, wl, world, rank, local):
         slr_build.build()
     barrier(world)
     slr.load()
-    nx, ny, gens = wl["nx"], wl["ny"], wl["gens"]
+    nx, ny, gens = wl["nx"], wl["ny"], args.gens
     cells = inputs.life_cells(ny, nx)
     pristine = torch.from_numpy(cells).to(dev)
     u = torch.empty_like(pristine)
@@ -260,10 +270,29 @@ def run_ours(args, wl, world, rank, local):
     ms_step = max_over_ranks(ms_total / args.steps, world)
     value = world * cell_updates / (ms_step / 1e3) / 1e9
     kern_ms = statistics.mean(a.elapsed_time(b) for a, b in ev)
-    algo_bytes = wl["bytes_per_cell_sweep"] * nx * ny * gens
+    # generations per HBM pass: the library runs the temporal-blocked kernel
+    # with 16 generations per pass unless k = 1 is asked for
+    k_eff = 1 if args.k == 1 else (args.k if args.k > 0 else 16)
+    passes = -(-gens // k_eff)
+    algo_bytes = wl["bytes_per_cell_pass"] * nx * ny * passes
     peak, peak_src = measured_peaks()
     achieved = algo_bytes / (kern_ms / 1e3) / 1e9
-    traffic = recorded_traffic(wl["name"])
+    traffic = recorded_traffic(wl["name"].format(gens=gens), k_eff)
+    hbm = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+           "traffic": traffic, "peak_source": peak_src, "kernel_ms": kern_ms,
+           "algorithmic_bytes_per_launch": algo_bytes, "passes_per_launch": passes,
+           "generations_per_pass": k_eff}
+    alu_ops = ALU_OPS_PER_CELL_GEN * nx * ny * gens
+    alu_peak = ALU_LANES_PER_SM * SMS * (clk.get("sm_mhz") or 2070.0) * 1e6 / 1e12
+    alu = {"bound": "alu", "achieved": alu_ops / (kern_ms / 1e3) / 1e12, "peak": alu_peak, "unit": "Tops/s",
+           "frac": alu_ops / (kern_ms / 1e3) / 1e12 / alu_peak, "traffic": traffic,
+           "peak_source": f"{ALU_LANES_PER_SM} lanes/SM x {SMS} SMs x median SM clock under load",
+           "kernel_ms": kern_ms, "algorithmic_ops_per_launch": alu_ops}
+    if k_eff == 1:
+        roof = dict(hbm, kernel="life persistent loop, one generation per pass (all generations in one launch)")
+    else:
+        roof = dict(alu, kernel=f"life temporal-blocked persistent loop, {k_eff} generations per HBM pass",
+                    hbm_per_pass=hbm)
 
     # plain path: one sweep launch + one reduce launch + host test per generation
     plain = None
@@ -317,16 +346,12 @@ def run_ours(args, wl, world, rank, local):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
             "data": "synthetic",
-            "config": {"workload": wl["name"], "cells": nx * ny, "generations": gens,
+            "config": {"workload": wl["name"].format(gens=gens), "cells": nx * ny, "generations": gens,
                        "parallelism": f"replicas{world}", "loop": "persistent cooperative kernel",
                        "temporal_k": args.k,
                        "l2": "no flush: per-step working set 192 MiB (ping-pong pair 128 MiB + input copy) "
                              "exceeds the L2"},
-            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": traffic,
-                         "peak_source": peak_src, "kernel_ms": kern_ms,
-                         "algorithmic_bytes_per_launch": algo_bytes,
-                         "kernel": "life persistent loop (all generations in one cooperative launch)"},
+            "roofline": roof,
             "cpu_baseline": cpu,
             "e2e": e2e,
             "plain": plain,
@@ -347,6 +372,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="life", choices=sorted(WORKLOADS))
     ap.add_argument("--k", type=int, default=0, help="generations per HBM pass (0 = library choice)")
+    ap.add_argument("--gens", type=int, default=2000,
+                    help="generations per solve (the workload has 2000; shorter runs are for profiler captures "
+                         "and are named as such in config.workload)")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=12.0)
