@@ -40,11 +40,13 @@ WORKLOADS = {
                  bytes_per_cell_pass=2.0),
 }
 # Logic operations per 32 cells per generation in the bit-sliced update of the
-# temporal-blocked kernel: 6 funnel shifts, 12 three-input logic operations for
-# the adder tree and the rule, and 3 for the two reduces (popcount, add, or).
-ALU_OPS_PER_CELL_GEN = 21.0 / 32.0
-# Integer/logic lanes per SM per clock on sm_103 (4 sub-partitions x 32 lanes)
-ALU_LANES_PER_SM = 128
+# temporal-blocked kernel: 2 funnel shifts and 4 logic operations for the row's
+# horizontal 2-bit sums, 6 for the vertical combination and the rule, and 3 for
+# the two reduces (popcount, add, or).
+ALU_OPS_PER_CELL_GEN = 15.0 / 32.0
+# Logic/shift lanes per SM per clock on sm_103: 4 sub-partitions x 16 lanes
+# (ncu: one pipe_alu warp instruction per sub-partition every other cycle)
+ALU_LANES_PER_SM = 64
 SMS = 152
 PROFILE_TRAFFIC = os.path.join(ROOT, "profiles", "traffic.json")
 KERNEL_SOURCES = ["paper_1609_04567_gb300/csrc/life.cu", "paper_1609_04567_gb300/csrc/life_tb.cu",
@@ -270,11 +272,17 @@ def run_ours(args, wl, world, rank, local):
     ms_step = max_over_ranks(ms_total / args.steps, world)
     value = world * cell_updates / (ms_step / 1e3) / 1e9
     kern_ms = statistics.mean(a.elapsed_time(b) for a, b in ev)
-    # generations per HBM pass: the library runs the temporal-blocked kernel
-    # with 16 generations per pass unless k = 1 is asked for
-    k_eff = 1 if args.k == 1 else (args.k if args.k > 0 else 16)
+    # generations per pass: the library's choice for 8192 x 8192 on 152 SMs is
+    # 12 (the largest k up to 16 whose 1024 x (242 - 2k) tiles fit 304 CTAs)
+    k_eff = 1 if args.k == 1 else (args.k if args.k > 0 else 12)
     passes = -(-gens // k_eff)
-    algo_bytes = wl["bytes_per_cell_pass"] * nx * ny * passes
+    # k = 1 moves every cell as uint8 per pass; the temporal-blocked path reads
+    # and writes the uint8 grid once per launch and the bit-packed grid once
+    # per pass (1/8 byte per cell each way)
+    if k_eff == 1:
+        algo_bytes = wl["bytes_per_cell_pass"] * nx * ny * passes
+    else:
+        algo_bytes = 2.0 * nx * ny + (0.25 * nx * ny) * (passes + 1)
     peak, peak_src = measured_peaks()
     achieved = algo_bytes / (kern_ms / 1e3) / 1e9
     traffic = recorded_traffic(wl["name"].format(gens=gens), k_eff)

@@ -170,6 +170,44 @@ const char *slr_last_error(slr_handle h);
 /* Library build string (architecture, version). */
 const char *slr_version(void);
 
+/* ---- Batches: many instances in one persistent launch -----------------------
+ * A batch holds up to max_instances independent loops (SLR_J2D5, SLR_J3D7 in
+ * any storage, SLR_RESTORE8 in EXACT math), each with its own grid, tolerance
+ * and iteration cap.  slr_batch_run enqueues ONE cooperative launch that runs
+ * up to `sweeps` more sweeps of every running instance with one grid barrier
+ * per sweep for the whole batch; an instance stops when its test passes or
+ * its cap is reached (the per-instance -d/-s tests of Sec. 3.1), and its
+ * result is then in its u.  Instances may be added and removed between runs,
+ * which is how a serving loop admits new work while earlier work is still
+ * running (continuous batching).  Results are identical to slr_create runs of
+ * the same descriptors.
+ *
+ * Ownership: the caller owns u, aux and a scratch buffer per instance
+ * (slr_batch_scratch_size bytes, the second state buffer), and the batch
+ * workspace (slr_batch_workspace_size bytes, 256-byte aligned).  None of them
+ * may be freed or reused while the instance is in the batch and a run may be
+ * in flight.  The batch handle owns host metadata only. */
+typedef struct slr_batch_ctx *slr_batch;
+size_t slr_batch_workspace_size(int32_t max_instances);       /* 0 if out of [1, 2048] */
+size_t slr_batch_scratch_size(const slr_desc *d);             /* 0 for an invalid/unsupported d */
+slr_status slr_batch_create(int32_t max_instances, void *workspace, size_t workspace_bytes, void *stream,
+                            slr_batch *out);
+/* Add an instance with its own absolute iteration cap; returns its slot. */
+slr_status slr_batch_add(slr_batch b, const slr_desc *d, void *u, const void *aux, void *scratch,
+                         int64_t max_iters, int32_t *slot);
+/* Enqueue up to `sweeps` sweeps of all running instances (asynchronous). */
+slr_status slr_batch_run(slr_batch b, int64_t sweeps);
+/* Wait for the batch's stream; list (up to max_finished) slots that finished
+ * since the last poll, and count the instances still running. */
+slr_status slr_batch_poll(slr_batch b, int32_t *finished, int32_t max_finished, int32_t *n_finished,
+                          int32_t *n_running);
+/* Result of a slot as of the last poll (same meaning as slr_reduce_value). */
+slr_status slr_batch_result(slr_batch b, int32_t slot, double *value, int64_t *iters, int32_t *converged,
+                            uint64_t *count);
+slr_status slr_batch_remove(slr_batch b, int32_t slot);
+slr_status slr_batch_destroy(slr_batch b);
+const char *slr_batch_last_error(slr_batch b);
+
 /* ---- A Jacobi solve that allocates nothing ---------------------------------
  * The paper has no counterpart to this call; it serves callers that cannot
  * allocate device memory when they need a solve (a device-memory budget owned

@@ -1,0 +1,631 @@
+// batch.cu -- many loop-of-stencil-reduce instances in one persistent launch.
+//
+// Each instance is its own loop of Sec. 3.1 (its own grid, stencil, storage,
+// reduce, tolerance and iteration cap); one cooperative launch runs a budget
+// of sweeps over all instances still running, with one bounded grid barrier
+// per sweep for the whole batch.  Work is cut into warp units (a 64 x 16 tile
+// of one plane of one instance); the units of all running instances form one
+// index space that every warp walks with a grid stride, so small grids no
+// longer pay a launch or a barrier each, and large and small grids share the
+// machine.  After each sweep every CTA reads the per-instance reduce slots and
+// takes the same per-instance decision (test passed, or the instance's cap
+// reached); stopped instances drop out of the index space.  At the end of a
+// run the state of every stopped instance is in its caller buffer u.
+//
+// The elemental functions and the evaluation order are those of jacobi.cu and
+// restore.cu (EXACT math), so every instance gets the same result alone, in a
+// batch, or through slr_create.
+#include <stdio.h>
+#include <string.h>
+
+#include <new>
+#include <string>
+#include <vector>
+
+#include "slr_internal.cuh"
+
+namespace slr {
+namespace {
+
+constexpr int kBThreads = 256;
+constexpr int kTileW = 64, kTileH = 16;
+constexpr int kMaxBatch = 2048;
+
+// One instance as the kernel sees it.  Host-written fields first; the kernel
+// writes the results at the end of a run (and value/count/converged when the
+// instance stops).
+struct BInst {
+    int stencil, storage, wrap, reduce;
+    long long nx, ny, nz;
+    double ghost, h2, d, tol;
+    float ghostf, h2f, df, alpha;
+    void *a, *b;
+    const void *aux;
+    long long max_iters;
+    long long tiles_x, tiles_y, units;
+    // results
+    long long iters;
+    int parity;       // 0: current state in a, 1: in b
+    int done;         // stopped (converged or capped)
+    int converged;
+    int pad;
+    double value;
+    unsigned long long count;
+};
+
+struct BatchArgs {
+    BInst *inst;
+    Slot *slots;               // [kMaxBatch][kSlots]
+    const int *act;            // indices of the running instances
+    const long long *prefix;   // unit offsets of act[] (nact + 1 entries)
+    int nact;
+    long long sweeps;
+    Ctl *ctl;                  // barrier counter and error word (reduce slots unused)
+    long long limit_ns;
+    int nblocks;
+};
+
+// ---- per-cell elemental functions (same order as jacobi.cu / restore.cu) -----
+template <class T> struct St;
+template <> struct St<double> {
+    using C = double;
+    __device__ static C ld(const void *p, long long i) { return __ldcg((const double *)p + i); }
+    __device__ static C ldf(const void *p, long long i) { return __ldg((const double *)p + i); }
+    __device__ static C put(void *p, long long i, C v) { ((double *)p)[i] = v; return v; }
+};
+template <> struct St<float> {
+    using C = float;
+    __device__ static C ld(const void *p, long long i) { return __ldcg((const float *)p + i); }
+    __device__ static C ldf(const void *p, long long i) { return __ldg((const float *)p + i); }
+    __device__ static C put(void *p, long long i, C v) { ((float *)p)[i] = v; return v; }
+};
+template <> struct St<__nv_bfloat16> {
+    using C = float;
+    __device__ static C ld(const void *p, long long i)
+    {
+        return __uint_as_float((uint32_t)__ldcg((const unsigned short *)p + i) << 16);
+    }
+    __device__ static C ldf(const void *p, long long i)
+    {
+        return __uint_as_float((uint32_t)__ldg((const unsigned short *)p + i) << 16);
+    }
+    __device__ static C put(void *p, long long i, C v)
+    {
+        const __nv_bfloat16 s = __float2bfloat16_rn(v);
+        ((__nv_bfloat16 *)p)[i] = s;
+        return __bfloat162float(s);
+    }
+};
+template <> struct St<__half> {
+    using C = float;
+    __device__ static C ld(const void *p, long long i)
+    {
+        return __half2float(__ushort_as_half(__ldcg((const unsigned short *)p + i)));
+    }
+    __device__ static C ldf(const void *p, long long i)
+    {
+        return __half2float(__ushort_as_half(__ldg((const unsigned short *)p + i)));
+    }
+    __device__ static C put(void *p, long long i, C v)
+    {
+        const __half s = __float2half_rn(v);
+        ((__half *)p)[i] = s;
+        return __half2float(s);
+    }
+};
+
+__device__ __forceinline__ double add_rn(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ double div_rn(double a, double b) { return __ddiv_rn(a, b); }
+__device__ __forceinline__ double sub_rn(double a, double b) { return __dsub_rn(a, b); }
+__device__ __forceinline__ float add_rn(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ float div_rn(float a, float b) { return __fdiv_rn(a, b); }
+__device__ __forceinline__ float sub_rn(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ unsigned long long abs_bits(double v) { return (unsigned long long)__double_as_longlong(fabs(v)); }
+__device__ __forceinline__ unsigned long long abs_bits(float v) { return (unsigned long long)__double_as_longlong((double)fabsf(v)); }
+
+template <class T>
+__device__ __forceinline__ typename St<T>::C at(const BInst &I, const void *u, long long k, long long i, long long j,
+                                                typename St<T>::C ghost)
+{
+    if (i < 0 || i >= I.ny || j < 0 || j >= I.nx || k < 0 || k >= I.nz) {
+        if (!I.wrap) return ghost;
+        i = i < 0 ? i + I.ny : (i >= I.ny ? i - I.ny : i);
+        j = j < 0 ? j + I.nx : (j >= I.nx ? j - I.nx : j);
+        k = k < 0 ? k + I.nz : (k >= I.nz ? k - I.nz : k);
+    }
+    return St<T>::ld(u, (k * I.ny + i) * I.nx + j);
+}
+
+// One warp unit of a Jacobi instance; returns the unit's max |delta| bits.
+template <class T, int DIM>
+__device__ unsigned long long jacobi_unit(const BInst &I, long long unit, const void *u, void *v)
+{
+    using C = typename St<T>::C;
+    const int lane = threadIdx.x & 31;
+    const long long per_plane = I.tiles_x * I.tiles_y;
+    const long long k = unit / per_plane, rem = unit - k * per_plane;
+    const long long ty = rem / I.tiles_x, tx = rem - ty * I.tiles_x;
+    const C ghost = sizeof(C) == 8 ? (C)I.ghost : (C)I.ghostf;
+    const C h2 = sizeof(C) == 8 ? (C)I.h2 : (C)I.h2f;
+    const C d = sizeof(C) == 8 ? (C)I.d : (C)I.df;
+    unsigned long long mx = 0ull;
+    for (int r = 0; r < kTileH; ++r) {
+        const long long i = ty * kTileH + r;
+        if (i >= I.ny) break;
+        for (int c = lane; c < kTileW; c += 32) {
+            const long long j = tx * kTileW + c;
+            if (j >= I.nx) continue;
+            const long long idx = (k * I.ny + i) * I.nx + j;
+            const C uc = St<T>::ld(u, idx);
+            C s;
+            if (DIM == 2) {
+                s = add_rn(add_rn(add_rn(at<T>(I, u, k, i - 1, j, ghost), at<T>(I, u, k, i + 1, j, ghost)),
+                                  at<T>(I, u, k, i, j - 1, ghost)),
+                           at<T>(I, u, k, i, j + 1, ghost));
+            } else {
+                s = add_rn(add_rn(add_rn(add_rn(add_rn(at<T>(I, u, k, i, j - 1, ghost), at<T>(I, u, k, i, j + 1, ghost)),
+                                                at<T>(I, u, k, i - 1, j, ghost)),
+                                         at<T>(I, u, k, i + 1, j, ghost)),
+                                  at<T>(I, u, k - 1, i, j, ghost)),
+                           at<T>(I, u, k + 1, i, j, ghost));
+            }
+            const C t = mul_rn(h2, St<T>::ldf(I.aux, idx));
+            const C stored = St<T>::put(v, idx, div_rn(add_rn(t, s), d));
+            const unsigned long long b = abs_bits(sub_rn(stored, uc));
+            mx = b > mx ? b : mx;
+        }
+    }
+    return mx;
+}
+
+// One warp unit of a restoration instance; returns (fixed-point sum, masked count).
+__device__ void restore_unit(const BInst &I, long long unit, const void *uv, void *vv, unsigned long long &sum,
+                             unsigned long long &cnt)
+{
+    const float *u = (const float *)uv;
+    float *v = (float *)vv;
+    const unsigned char *mask = (const unsigned char *)I.aux;
+    const int lane = threadIdx.x & 31;
+    const long long ty = unit / I.tiles_x, tx = unit - ty * I.tiles_x;
+    for (int r = 0; r < kTileH; ++r) {
+        const long long i = ty * kTileH + r;
+        if (i >= I.ny) break;
+        for (int c = lane; c < kTileW; c += 32) {
+            const long long j = tx * kTileW + c;
+            if (j >= I.nx) continue;
+            const long long idx = i * I.nx + j;
+            const float uc = __ldcg(u + idx);
+            if (!__ldg(mask + idx)) { v[idx] = uc; continue; }
+            float num = 0.0f, den = 0.0f;
+            for (int di = -1; di <= 1; ++di)
+                for (int dj = -1; dj <= 1; ++dj) {
+                    if (di == 0 && dj == 0) continue;
+                    const long long y = i + di, x = j + dj;
+                    if (y < 0 || y >= I.ny || x < 0 || x >= I.nx) continue;
+                    const float uj = __ldcg(u + y * I.nx + x);
+                    const float t = __fsub_rn(uc, uj);
+                    const float w = __fdiv_rn(1.0f, __fsqrt_rn(__fadd_rn(I.alpha, __fmul_rn(t, t))));
+                    num = __fadd_rn(num, __fmul_rn(w, uj));
+                    den = __fadd_rn(den, w);
+                }
+            const float nv = den > 0.0f ? __fdiv_rn(num, den) : uc;
+            v[idx] = nv;
+            sum += (unsigned long long)__double2ull_rz((double)fabsf(__fsub_rn(nv, uc)) * 16777216.0);
+            cnt += 1ull;
+        }
+    }
+}
+
+__device__ void unit_copy(const BInst &I, long long unit, const void *src, void *dst)
+{
+    const int lane = threadIdx.x & 31;
+    const size_t es = I.storage == SLR_F64 ? 8 : (I.storage == SLR_F32 ? 4 : 2);
+    const long long per_plane = I.tiles_x * I.tiles_y;
+    const long long k = unit / per_plane, rem = unit - k * per_plane;
+    const long long ty = rem / I.tiles_x, tx = rem - ty * I.tiles_x;
+    for (int r = 0; r < kTileH; ++r) {
+        const long long i = ty * kTileH + r;
+        if (i >= I.ny) break;
+        for (int c = lane; c < kTileW; c += 32) {
+            const long long j = tx * kTileW + c;
+            if (j >= I.nx) continue;
+            const long long idx = (k * I.ny + i) * I.nx + j;
+            if (es == 8) ((double *)dst)[idx] = __ldcg((const double *)src + idx);
+            else if (es == 4) ((float *)dst)[idx] = __ldcg((const float *)src + idx);
+            else ((unsigned short *)dst)[idx] = __ldcg((const unsigned short *)src + idx);
+        }
+    }
+}
+
+__device__ __forceinline__ int find_instance(const long long *prefix, int n, long long u)
+{
+    int lo = 0, hi = n;     // prefix[lo] <= u < prefix[hi]
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (prefix[mid] <= u) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
+__global__ void __launch_bounds__(kBThreads) batch_kernel(BatchArgs ba)
+{
+    extern __shared__ unsigned char smem_raw[];
+    long long *s_prefix = (long long *)smem_raw;             // [nact + 1]
+    long long *s_iters0 = s_prefix + (ba.nact + 1);           // [nact]
+    int *s_stop = (int *)(s_iters0 + ba.nact);                // [nact]: sweep index of the stop, -1 running
+    unsigned char *s_par0 = (unsigned char *)(s_stop + ba.nact);  // [nact]
+    __shared__ int s_alive;
+
+    const int tid = threadIdx.x, lane = tid & 31;
+    const int n = ba.nact;
+    for (int i = tid; i <= n; i += kBThreads) s_prefix[i] = ba.prefix[i];
+    for (int i = tid; i < n; i += kBThreads) {
+        const BInst &I = ba.inst[ba.act[i]];
+        s_iters0[i] = I.iters;
+        s_par0[i] = (unsigned char)I.parity;
+        s_stop[i] = I.done ? -2 : -1;
+    }
+    __syncthreads();
+    const long long U = s_prefix[n];
+    const long long warps = (long long)gridDim.x * (kBThreads / 32);
+    const long long gw = (long long)blockIdx.x * (kBThreads / 32) + (tid >> 5);
+    long long s = 0;
+    for (; s < ba.sweeps; ++s) {
+        for (long long u = gw; u < U; u += warps) {
+            const int ai = find_instance(s_prefix, n, u);
+            if (s_stop[ai] != -1) continue;
+            const BInst &I = ba.inst[ba.act[ai]];
+            const long long unit = u - s_prefix[ai];
+            const int par = (s_par0[ai] + (int)s) & 1;
+            const void *src = par ? I.b : I.a;
+            void *dst = par ? I.a : I.b;
+            Slot *slot = &ba.slots[(size_t)ba.act[ai] * kSlots + (size_t)(s % kSlots)];
+            if (I.stencil == SLR_RESTORE8) {
+                unsigned long long sum = 0ull, cnt = 0ull;
+                restore_unit(I, unit, src, dst, sum, cnt);
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    sum += __shfl_xor_sync(0xffffffffu, sum, o);
+                    cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+                }
+                if (lane == 0) {
+                    if (sum) atomicAdd(&slot->sum, sum);
+                    if (cnt) atomicAdd(&slot->cnt, cnt);
+                    if (sum) atomicOr(&slot->changed, 1u);
+                }
+            } else {
+                unsigned long long mx = 0ull;
+                const bool d3 = I.stencil == SLR_J3D7;
+                switch (I.storage) {
+                case SLR_F64: mx = d3 ? jacobi_unit<double, 3>(I, unit, src, dst) : jacobi_unit<double, 2>(I, unit, src, dst); break;
+                case SLR_F32: mx = d3 ? jacobi_unit<float, 3>(I, unit, src, dst) : jacobi_unit<float, 2>(I, unit, src, dst); break;
+                case SLR_BF16:
+                    mx = d3 ? jacobi_unit<__nv_bfloat16, 3>(I, unit, src, dst) : jacobi_unit<__nv_bfloat16, 2>(I, unit, src, dst);
+                    break;
+                default: mx = d3 ? jacobi_unit<__half, 3>(I, unit, src, dst) : jacobi_unit<__half, 2>(I, unit, src, dst); break;
+                }
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    const unsigned long long m2 = __shfl_xor_sync(0xffffffffu, mx, o);
+                    mx = m2 > mx ? m2 : mx;
+                }
+                if (lane == 0 && mx) {
+                    atomicMax(&slot->maxbits, mx);
+                    atomicOr(&slot->changed, 1u);
+                }
+            }
+        }
+        if (!grid_barrier(ba.ctl, (unsigned long long)(s + 1) * (unsigned long long)ba.nblocks, ba.limit_ns))
+            return;
+        // every CTA takes the same per-instance decision
+        if (tid == 0) s_alive = 0;
+        __syncthreads();
+        int alive = 0;
+        for (int i = tid; i < n; i += kBThreads) {
+            if (s_stop[i] != -1) continue;
+            const int gi = ba.act[i];
+            const Slot sl = read_slot(&ba.slots[(size_t)gi * kSlots + (size_t)(s % kSlots)]);
+            BInst &I = ba.inst[gi];
+            const Decision dcs = decide(I.reduce, sl, I.tol);
+            const long long it = s_iters0[i] + s + 1;
+            if (dcs.converged || it >= I.max_iters) {
+                s_stop[i] = (int)s;
+                if (blockIdx.x == 0) {
+                    I.value = dcs.value;
+                    I.count = dcs.count;
+                    I.converged = dcs.converged;
+                }
+            } else {
+                alive = 1;
+            }
+            if (blockIdx.x == 0) zero_slot(&ba.slots[(size_t)gi * kSlots + (size_t)((s + 2) % kSlots)]);
+        }
+        if (alive) s_alive = 1;
+        __syncthreads();
+        if (!s_alive) { ++s; break; }
+    }
+    const long long ran = s < ba.sweeps ? s : ba.sweeps;
+    // results (CTA 0) and the write-back of stopped instances whose state is in b
+    if (blockIdx.x == 0) {
+        for (int i = tid; i < n; i += kBThreads) {
+            if (s_stop[i] == -2) continue;
+            BInst &I = ba.inst[ba.act[i]];
+            const long long done_sweeps = s_stop[i] >= 0 ? s_stop[i] + 1 : ran;
+            I.iters = s_iters0[i] + done_sweeps;
+            I.parity = (s_par0[i] + (int)done_sweeps) & 1;
+            I.done = s_stop[i] >= 0;
+        }
+    }
+    for (long long u = gw; u < U; u += warps) {
+        const int ai = find_instance(s_prefix, n, u);
+        if (s_stop[ai] < 0) continue;
+        if (((s_par0[ai] + s_stop[ai] + 1) & 1) == 0) continue;   // final state already in a
+        const BInst &I = ba.inst[ba.act[ai]];
+        unit_copy(I, u - s_prefix[ai], I.b, I.a);
+    }
+}
+
+}  // namespace
+}  // namespace slr
+
+using slr::BInst;
+
+struct slr_batch_ctx {
+    int max_inst;
+    unsigned char *ws;
+    cudaStream_t stream;
+    std::vector<BInst> inst;     // host mirror
+    std::vector<int> used;       // slot in use
+    std::vector<int> reported;   // finished and already returned by poll
+    std::string err;
+    bool dirty;                  // host mirror newer than the device table
+};
+
+namespace {
+
+thread_local std::string g_batch_create_error = "no error";
+
+size_t rup(size_t x, size_t a) { return (x + a - 1) / a * a; }
+size_t off_inst() { return rup(sizeof(slr::Ctl), 256); }
+size_t off_slots(int m) { return off_inst() + rup((size_t)m * sizeof(BInst), 256); }
+size_t off_act(int m) { return off_slots(m) + rup((size_t)m * slr::kSlots * sizeof(slr::Slot), 256); }
+size_t off_prefix(int m) { return off_act(m) + rup((size_t)m * sizeof(int), 256); }
+size_t ws_total(int m) { return off_prefix(m) + rup((size_t)(m + 1) * sizeof(long long), 256); }
+
+slr_status bfail(slr_batch b, slr_status s, const std::string &m)
+{
+    if (b) b->err = m; else g_batch_create_error = m;
+    return s;
+}
+
+slr_status bcuda(slr_batch b, cudaError_t e, const char *where)
+{
+    return bfail(b, SLR_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+// Bring the host mirror up to date with the device results.
+slr_status sync_mirror(slr_batch b)
+{
+    cudaError_t e = cudaMemcpyAsync(b->inst.data(), b->ws + off_inst(), (size_t)b->max_inst * sizeof(BInst),
+                                    cudaMemcpyDeviceToHost, b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) return bcuda(b, e, "read batch table");
+    return SLR_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t slr_batch_workspace_size(int32_t max_instances)
+{
+    if (max_instances < 1 || max_instances > slr::kMaxBatch) return 0;
+    return ws_total(max_instances);
+}
+
+size_t slr_batch_scratch_size(const slr_desc *d)
+{
+    bool unsup = false;
+    if (!slr::describe_invalid(d, &unsup).empty()) return 0;
+    if (d->stencil == SLR_LIFE) return 0;
+    return rup(slr::problem_of(d).state_bytes, 256);
+}
+
+slr_status slr_batch_create(int32_t max_instances, void *workspace, size_t workspace_bytes, void *stream,
+                            slr_batch *out)
+{
+    if (!out) return bfail(nullptr, SLR_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (max_instances < 1 || max_instances > slr::kMaxBatch)
+        return bfail(nullptr, SLR_ERR_INVALID_ARG, "max_instances must be in [1, 2048]");
+    if (!workspace || ((uintptr_t)workspace & 255u))
+        return bfail(nullptr, SLR_ERR_INVALID_ARG, "workspace must be a 256-byte aligned device pointer");
+    if (workspace_bytes < ws_total(max_instances)) return bfail(nullptr, SLR_ERR_WORKSPACE, "workspace too small");
+    slr_batch_ctx *b = new (std::nothrow) slr_batch_ctx();
+    if (!b) return bfail(nullptr, SLR_ERR_INVALID_ARG, "host allocation failed");
+    b->max_inst = max_instances;
+    b->ws = (unsigned char *)workspace;
+    b->stream = (cudaStream_t)stream;
+    b->inst.assign((size_t)max_instances, BInst());
+    memset(b->inst.data(), 0, sizeof(BInst) * (size_t)max_instances);
+    b->used.assign((size_t)max_instances, 0);
+    b->reported.assign((size_t)max_instances, 0);
+    b->err = "no error";
+    b->dirty = true;
+    cudaError_t e = cudaMemsetAsync(b->ws, 0, ws_total(max_instances), b->stream);
+    if (e != cudaSuccess) {
+        delete b;
+        return bcuda(nullptr, e, "clear batch workspace");
+    }
+    *out = b;
+    return SLR_OK;
+}
+
+slr_status slr_batch_add(slr_batch b, const slr_desc *d, void *u, const void *aux, void *scratch, int64_t max_iters,
+                         int32_t *slot)
+{
+    if (!b) return bfail(nullptr, SLR_ERR_INVALID_ARG, "batch is NULL");
+    bool unsup = false;
+    const std::string why = slr::describe_invalid(d, &unsup);
+    if (!why.empty()) return bfail(b, unsup ? SLR_ERR_UNSUPPORTED : SLR_ERR_INVALID_ARG, why);
+    if (d->stencil == SLR_LIFE) return bfail(b, SLR_ERR_UNSUPPORTED, "batches run the Jacobi and restoration stencils");
+    if (d->stencil == SLR_RESTORE8 && d->math != SLR_MATH_EXACT)
+        return bfail(b, SLR_ERR_UNSUPPORTED, "batched restoration runs EXACT math");
+    if (!u || !aux || !scratch || ((uintptr_t)u & 15u) || ((uintptr_t)scratch & 15u))
+        return bfail(b, SLR_ERR_INVALID_ARG, "u, aux and scratch must be device pointers (u, scratch 16-byte aligned)");
+    if (max_iters < 1) return bfail(b, SLR_ERR_INVALID_ARG, "max_iters must be >= 1");
+    int s = -1;
+    for (int i = 0; i < b->max_inst; ++i)
+        if (!b->used[(size_t)i]) { s = i; break; }
+    if (s < 0) return bfail(b, SLR_ERR_WORKSPACE, "batch is full");
+    if (!b->dirty) {
+        slr_status st = sync_mirror(b);
+        if (st != SLR_OK) return st;
+    }
+    const slr::Problem p = slr::problem_of(d);
+    BInst I;
+    memset(&I, 0, sizeof(I));
+    I.stencil = p.stencil; I.storage = p.storage; I.wrap = p.wrap; I.reduce = p.reduce;
+    I.nx = p.nx; I.ny = p.ny; I.nz = p.nz;
+    I.ghost = p.ghost; I.h2 = p.h2; I.d = p.d; I.tol = p.tol;
+    I.ghostf = p.ghostf; I.h2f = p.h2f; I.df = p.df; I.alpha = p.alpha;
+    I.a = u; I.b = scratch; I.aux = aux;
+    I.max_iters = max_iters;
+    I.tiles_x = (p.nx + slr::kTileW - 1) / slr::kTileW;
+    I.tiles_y = (p.ny + slr::kTileH - 1) / slr::kTileH;
+    I.units = I.tiles_x * I.tiles_y * p.nz;
+    b->inst[(size_t)s] = I;
+    b->used[(size_t)s] = 1;
+    b->reported[(size_t)s] = 0;
+    b->dirty = true;
+    if (slot) *slot = s;
+    return SLR_OK;
+}
+
+slr_status slr_batch_remove(slr_batch b, int32_t slot)
+{
+    if (!b || slot < 0 || slot >= b->max_inst || !b->used[(size_t)slot])
+        return bfail(b, SLR_ERR_INVALID_ARG, "no such slot");
+    if (!b->dirty) {
+        slr_status st = sync_mirror(b);
+        if (st != SLR_OK) return st;
+    }
+    b->used[(size_t)slot] = 0;
+    memset(&b->inst[(size_t)slot], 0, sizeof(BInst));
+    b->dirty = true;
+    return SLR_OK;
+}
+
+slr_status slr_batch_run(slr_batch b, int64_t sweeps)
+{
+    if (!b) return bfail(nullptr, SLR_ERR_INVALID_ARG, "batch is NULL");
+    if (sweeps < 1) return bfail(b, SLR_ERR_INVALID_ARG, "sweeps must be >= 1");
+    if (!b->dirty) {
+        slr_status st = sync_mirror(b);
+        if (st != SLR_OK) return st;
+    }
+    std::vector<int> act;
+    std::vector<long long> prefix(1, 0);
+    for (int i = 0; i < b->max_inst; ++i) {
+        const BInst &I = b->inst[(size_t)i];
+        if (!b->used[(size_t)i] || I.done || I.iters >= I.max_iters) continue;
+        act.push_back(i);
+        prefix.push_back(prefix.back() + I.units);
+    }
+    cudaError_t e = cudaMemcpyAsync(b->ws + off_inst(), b->inst.data(), (size_t)b->max_inst * sizeof(BInst),
+                                    cudaMemcpyHostToDevice, b->stream);
+    b->dirty = false;
+    if (e != cudaSuccess) return bcuda(b, e, "write batch table");
+    if (act.empty()) return cudaStreamSynchronize(b->stream) == cudaSuccess ? SLR_OK : bcuda(b, cudaGetLastError(), "sync");
+    e = cudaMemcpyAsync(b->ws + off_act(b->max_inst), act.data(), act.size() * sizeof(int), cudaMemcpyHostToDevice,
+                        b->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(b->ws + off_prefix(b->max_inst), prefix.data(), prefix.size() * sizeof(long long),
+                            cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess)
+        e = cudaMemsetAsync(b->ws + off_slots(b->max_inst), 0, (size_t)b->max_inst * slr::kSlots * sizeof(slr::Slot),
+                            b->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->ws, 0, sizeof(slr::Ctl), b->stream);
+    // the host vectors must outlive the asynchronous copies
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) return bcuda(b, e, "stage batch run");
+    slr::BatchArgs ba;
+    ba.inst = (BInst *)(b->ws + off_inst());
+    ba.slots = (slr::Slot *)(b->ws + off_slots(b->max_inst));
+    ba.act = (const int *)(b->ws + off_act(b->max_inst));
+    ba.prefix = (const long long *)(b->ws + off_prefix(b->max_inst));
+    ba.nact = (int)act.size();
+    ba.sweeps = sweeps;
+    ba.ctl = (slr::Ctl *)b->ws;
+    ba.limit_ns = 2000000000ll;
+    const size_t smem = (size_t)(ba.nact + 1) * 8 + (size_t)ba.nact * 8 + (size_t)ba.nact * 4 + (size_t)ba.nact;
+    e = cudaFuncSetAttribute(slr::batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return bcuda(b, e, "batch kernel attributes");
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, slr::batch_kernel, slr::kBThreads, smem);
+    if (e != cudaSuccess || per_sm < 1) return bcuda(b, e == cudaSuccess ? cudaErrorCooperativeLaunchTooLarge : e, "occupancy");
+    if (per_sm > 4) per_sm = 4;
+    ba.nblocks = sms * per_sm;
+    void *args[] = {&ba};
+    e = cudaLaunchCooperativeKernel((const void *)slr::batch_kernel, dim3(ba.nblocks), dim3(slr::kBThreads), args,
+                                    smem, b->stream);
+    if (e != cudaSuccess) return bcuda(b, e, "batch kernel launch");
+    return SLR_OK;
+}
+
+slr_status slr_batch_poll(slr_batch b, int32_t *finished, int32_t max_finished, int32_t *n_finished,
+                          int32_t *n_running)
+{
+    if (!b) return bfail(nullptr, SLR_ERR_INVALID_ARG, "batch is NULL");
+    slr_status st = sync_mirror(b);
+    if (st != SLR_OK) return st;
+    slr::Ctl c;
+    cudaError_t e = cudaMemcpyAsync(&c, b->ws, sizeof(c), cudaMemcpyDeviceToHost, b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) return bcuda(b, e, "read batch control");
+    int nf = 0, nr = 0;
+    for (int i = 0; i < b->max_inst; ++i) {
+        if (!b->used[(size_t)i]) continue;
+        const BInst &I = b->inst[(size_t)i];
+        const bool fin = I.done || I.iters >= I.max_iters;
+        if (fin && !b->reported[(size_t)i]) {
+            if (finished && nf < max_finished) {
+                finished[nf++] = i;
+                b->reported[(size_t)i] = 1;
+            }
+        } else if (!fin) {
+            ++nr;
+        }
+    }
+    if (n_finished) *n_finished = nf;
+    if (n_running) *n_running = nr;
+    if (c.err & slr::DEV_ERR_TIMEOUT) return bfail(b, SLR_ERR_TIMEOUT, "a device-side grid barrier wait ran out its limit");
+    return SLR_OK;
+}
+
+slr_status slr_batch_result(slr_batch b, int32_t slot, double *value, int64_t *iters, int32_t *converged,
+                            uint64_t *count)
+{
+    if (!b || slot < 0 || slot >= b->max_inst || !b->used[(size_t)slot])
+        return bfail(b, SLR_ERR_INVALID_ARG, "no such slot");
+    const BInst &I = b->inst[(size_t)slot];
+    if (value) *value = I.value;
+    if (iters) *iters = I.iters;
+    if (converged) *converged = I.converged;
+    if (count) *count = I.count;
+    return I.converged ? SLR_OK : SLR_NOT_CONVERGED;
+}
+
+slr_status slr_batch_destroy(slr_batch b)
+{
+    delete b;
+    return SLR_OK;
+}
+
+const char *slr_batch_last_error(slr_batch b) { return b ? b->err.c_str() : g_batch_create_error.c_str(); }
+
+}  // extern "C"

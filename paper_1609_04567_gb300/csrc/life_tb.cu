@@ -1,38 +1,38 @@
-// life_tb.cu -- temporal-blocked Game of Life: K generations per HBM pass.
+// life_tb.cu -- temporal-blocked Game of Life: K generations per pass over a
+// bit-packed grid.
 //
 // The loop-of-stencil-reduce of Sec. 3.1 with the Fig. 1 elemental function
-// (B3/S23) on a uint8 grid, restructured for GB300: every pass reads each cell
-// from HBM once, runs up to K generations on chip, and writes each cell once,
-// so HBM traffic per generation is 2/K bytes per cell instead of 2.
+// (B3/S23), restructured for GB300.  One cooperative persistent launch does:
 //
-// Tile: 256 rows x 1088 columns loaded (1024 owned columns plus one 32-cell
-// word of halo on each side; 224 owned rows plus 16 halo rows above and
-// below), so up to 16 generations stay exact inside the owned region (each
-// generation invalidates one more cell ring from the outside).
-//
-//  1. Load: the tile arrives in 8 chunks of 32 rows, each chunk as ten TMA
-//     boxes (cp.async.bulk.tensor.2d) into a double-buffered staging area:
-//     eight 128-byte-wide boxes with the 128B swizzle (so that the packing
-//     reads below are bank-conflict free) and two 32-byte halo boxes.  An
-//     out-of-range box reads zeros (the dead border for free); on the torus
-//     every box is placed at its wrapped coordinate (tiles are laid out so no
-//     box straddles the grid edge).  Threads pack the bytes into a bit-tile in
-//     shared memory, 32 cells per 32-bit word, bit b = column b.
-//  2. Evolve: thread t takes tile row t into 34 registers.  Vertical
-//     neighbours come from the adjacent lanes by shuffle (and from the adjacent
-//     warps through a small shared exchange row, one barrier per generation);
-//     horizontal neighbours by funnel shifts across the word boundary.  The
-//     8-neighbour count is a bit-sliced adder tree of 18 logic operations per
-//     32 cells.  The two reduces of the generation (live count, any cell
-//     changed) are taken over the owned region only, per generation.
-//  3. Store: rows go back through the bit-tile, are expanded to bytes and
-//     written with coalesced 16-byte stores.
+//  P. Pack: the caller's uint8 grid is staged through shared memory by TMA
+//     (cp.async.bulk.tensor.2d, 32-row x 128-byte boxes with the 128B swizzle,
+//     double buffered) and packed to 1 bit per cell (bit b of word w = column
+//     32w + b) into a workspace buffer.  Boxes wholly outside the grid are not
+//     loaded; the hardware fills the outside of partly-outside boxes with
+//     zeros.
+//  G. Passes: each pass reads the packed grid, runs up to K generations on
+//     chip, and writes the packed grid to the other workspace buffer.  A tile
+//     is 1024 owned columns (plus one 32-cell word of halo on each side) by
+//     242 - 2K owned rows (plus K halo rows above and below); K generations
+//     stay exact inside it.  Thread (w, l) of the 8 warps holds tile row
+//     30w + l as 34 words in registers, so warps overlap by two rows: lanes
+//     1..30 are the warp's own rows, lanes 0 and 31 are copies of the
+//     neighbour warps' edge rows, refreshed through shared memory after every
+//     generation.  Per generation every thread forms its row's horizontal
+//     2-bit sums (left + self + right, and left + right) with two funnel shifts
+//     and four logic operations, takes the rows above and below by shuffle,
+//     and finishes the B3/S23 rule with six more logic operations: twelve per
+//     32 cells.  Live count and "any cell changed" are reduced per generation
+//     over the owned cells.
+//  U. Unpack: the final packed grid is expanded back into the caller's uint8
+//     grid.
 //
 // After each pass a bounded grid barrier publishes the per-generation
-// reduces; every CTA takes the same decision: stop at the first generation
-// that changed nothing (a still state is a fixed point, so the stored state
-// after the pass equals that generation) or at the iteration cap (the last
-// pass runs only the generations left).
+// reduces and every CTA takes the same decision: stop at the first generation
+// that changed nothing (a still state is a fixed point, so the packed state at
+// the end of the pass equals it), or at the iteration cap (the last pass runs
+// only the generations left).  The dead border stays dead: cells of a tile
+// outside the grid are cleared after every generation.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
@@ -43,38 +43,31 @@ namespace {
 
 constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
-constexpr int kTileRows = 256;
-constexpr int kHaloRows = 16;
-constexpr int kOwnRows = kTileRows - 2 * kHaloRows;  // 224
+constexpr int kRowsPerWarp = 30;                      // own rows of a warp (lanes 1..30)
+constexpr int kTileRows = kWarps * kRowsPerWarp + 2;  // 242 distinct tile rows
 constexpr int kWords = 34;                            // 1 halo + 32 owned + 1 halo
-constexpr int kOwnCols = 1024;
-constexpr int kBitStride = 35;                        // odd: conflict-free row loads
-constexpr int kChunkRows = 32;
-constexpr int kChunks = kTileRows / kChunkRows;       // 8
-constexpr int kMidBoxW = 128;                         // bytes (= cells) per swizzled box row
-constexpr int kMidBoxes = kOwnCols / kMidBoxW;        // 8
-constexpr int kMidBoxBytes = kMidBoxW * kChunkRows;   // 4096
-constexpr int kHaloBoxW = 32;
-constexpr int kHaloBoxBytes = kHaloBoxW * kChunkRows; // 1024
-constexpr int kStageBytes = kMidBoxes * kMidBoxBytes + 2 * kHaloBoxBytes;  // 34816 = 34 KiB
-constexpr int kBitsBytes = kTileRows * kBitStride * 4;                      // 35840
-constexpr int kXchWords = 2 * kWarps * 2 * kWords;    // [parity][warp][top,bottom][word]
-constexpr size_t kSmemBytes = 1024 /*alignment slack*/ + 2 * kStageBytes + kBitsBytes + kXchWords * 4 +
-                              kWords * 4 /*zero row*/ + 2 * 8 /*mbarriers*/ + kMaxK * 8 + kMaxK * 4;
-static_assert(kStageBytes % 1024 == 0, "staging buffers must keep 1024-byte alignment for the swizzle");
+constexpr int kOwnWords = 32;
+constexpr int kOwnCols = 32 * kOwnWords;              // 1024
+constexpr int kXchWords = kWarps * 2 * kWords;        // [warp][lane 1 row, lane 30 row][word]
+// pack phase: 32 rows x 1024 columns per unit, 8 swizzled boxes of 128 bytes
+constexpr int kPackRows = 32;
+constexpr int kBoxW = 128;
+constexpr int kBoxes = kOwnCols / kBoxW;              // 8
+constexpr int kBoxBytes = kBoxW * kPackRows;          // 4096
+constexpr int kStageBytes = kBoxes * kBoxBytes;       // 32768
+constexpr size_t kSmemBytes = 1024 + 2 * kStageBytes + kXchWords * 4 + 2 * 8 + kMaxK * 8 + kMaxK * 4;
+static_assert((kXchWords * 4) % 8 == 0, "mbarriers must stay 8-byte aligned");
 
 struct TbParams {
-    CUtensorMap mid[2];   // [0] reads buffer A (the caller's u), [1] reads buffer B
-    CUtensorMap halo[2];
-    long long nx, ny;
-    int wrap, K, tiles_x, tiles_y;
+    CUtensorMap cells;           // uint8 view of the caller's grid (box 128 x 32, 128B swizzle)
+    unsigned int *bits[2];       // packed ping-pong buffers (workspace)
+    long long nx, ny;            // grid extents (nx % 32 == 0)
+    long long nxw, pitch;        // words per row, row pitch in words (multiple of 4)
+    int wrap, K, own_rows, tiles_x, tiles_y;
 };
 
 // ---- PTX wrappers -----------------------------------------------------------
-__device__ __forceinline__ uint32_t smem_u32(const void *p)
-{
-    return (uint32_t)__cvta_generic_to_shared(p);
-}
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
 __device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
 {
@@ -108,14 +101,9 @@ __device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, i
         : "memory");
 }
 
-__device__ __forceinline__ void fence_proxy_async_global()
-{
-    asm volatile("fence.proxy.async.global;" ::: "memory");
-}
-
 // ---- cell packing -----------------------------------------------------------
-// Four 0/1 bytes -> 4 bits (byte i -> bit i): the products land on distinct bit
-// positions 24..27, so the multiply adds no carries.
+// Four 0/1 bytes -> 4 bits (byte i -> bit i): the partial products land on
+// distinct bit positions 24..27, so the multiply adds no carries.
 __device__ __forceinline__ uint32_t pack4(uint32_t w) { return (w * 0x01020408u) >> 24; }
 
 __device__ __forceinline__ uint32_t pack16(const uint4 v)
@@ -132,128 +120,227 @@ __device__ __forceinline__ uint4 unpack16(uint32_t h)
     return make_uint4(unpack4(h & 15u), unpack4((h >> 4) & 15u), unpack4((h >> 8) & 15u), unpack4((h >> 12) & 15u));
 }
 
-// ---- the B3/S23 step on 32 cells --------------------------------------------
-// U*, C*, D*: the row above, the row itself, the row below; m/c/n: the word to
-// the left, the word, the word to the right.  Bit b of a word is column b, so
-// the left neighbour of bit b is bit b-1 (or bit 31 of the word to the left).
-__device__ __forceinline__ uint32_t life_word(uint32_t Um, uint32_t Uc, uint32_t Un, uint32_t Cm, uint32_t Cc,
-                                              uint32_t Cn, uint32_t Dm, uint32_t Dc, uint32_t Dn)
-{
-    const uint32_t UL = __funnelshift_l(Um, Uc, 1), UR = __funnelshift_r(Uc, Un, 1);
-    const uint32_t CL = __funnelshift_l(Cm, Cc, 1), CR = __funnelshift_r(Cc, Cn, 1);
-    const uint32_t DL = __funnelshift_l(Dm, Dc, 1), DR = __funnelshift_r(Dc, Dn, 1);
-    // 2-bit sums: above (a1 a0) = UL+Uc+UR, below (b1 b0), middle (m1 m0) = CL+CR
-    const uint32_t a0 = UL ^ Uc ^ UR, a1 = (UL & Uc) | (UL & UR) | (Uc & UR);
-    const uint32_t b0 = DL ^ Dc ^ DR, b1 = (DL & Dc) | (DL & DR) | (Dc & DR);
-    const uint32_t m0 = CL ^ CR, m1 = CL & CR;
-    // n = bit0 + 2*H with H = c0 + a1 + m1 + b1; alive next <=> H == 1 and (bit0 or self)
-    const uint32_t bit0 = a0 ^ m0 ^ b0, c0 = (a0 & m0) | (a0 & b0) | (m0 & b0);
-    const uint32_t x = a1 ^ m1 ^ b1, y = (a1 & m1) | (a1 & b1) | (m1 & b1);
-    const uint32_t one = (x ^ c0) & ~y;  // exactly one of {a1, m1, b1, c0}
-    return one & (Cc | bit0);
-}
-
-// ---- tile geometry ----------------------------------------------------------
-struct Tile {
-    long long x0;        // first owned column
-    long long frame0;    // frame row of tile row 0 (owned frame rows: [frame0 + 16, frame0 + 240))
-    long long real0;     // real (unwrapped) row of tile row 0
-};
-
-__device__ __forceinline__ Tile tile_of(const TbParams &tp, int t)
-{
-    Tile g;
-    const int tx = t % tp.tiles_x, ty = t / tp.tiles_x;
-    g.x0 = (long long)tx * kOwnCols;
-    g.frame0 = (long long)ty * kOwnRows - kHaloRows;
-    // on the torus the frame is rotated by 16 rows so that every 32-row chunk
-    // starts on a multiple of 32 and never straddles the grid edge
-    g.real0 = g.frame0 - (tp.wrap ? kHaloRows : 0);
-    return g;
-}
-
 __device__ __forceinline__ long long wrap_mod(long long v, long long n)
 {
     v %= n;
     return v < 0 ? v + n : v;
 }
 
-// Box b of a chunk (b < 8: owned columns, 8: left halo, 9: right halo): its
-// column, width and whether any of it lies inside the grid.  On the torus every
-// box is placed at its wrapped coordinate and is always inside; with the dead
-// border a box wholly outside the grid is not loaded at all and reads as zeros
-// (a box partly outside is loaded and the hardware fills the outside with
-// zeros).
-struct Box {
-    long long x;
-    int w;
-    bool in;
-};
-
-__device__ __forceinline__ long long chunk_row(const TbParams &tp, const Tile &g, int c)
+__device__ __forceinline__ bool bounded_wait(uint64_t *bar, uint32_t parity, long long limit_ns, int *err)
 {
-    long long y = g.real0 + (long long)c * kChunkRows;
-    return tp.wrap ? wrap_mod(y, tp.ny) : y;
-}
-
-__device__ __forceinline__ Box box_of(const TbParams &tp, const Tile &g, long long y, int b)
-{
-    Box bx;
-    if (b < kMidBoxes) { bx.x = g.x0 + (long long)b * kMidBoxW; bx.w = kMidBoxW; }
-    else { bx.x = b == kMidBoxes ? g.x0 - kHaloBoxW : g.x0 + kOwnCols; bx.w = kHaloBoxW; }
-    if (tp.wrap) {
-        bx.x = wrap_mod(bx.x, tp.nx);
-        bx.in = true;
-    } else {
-        bx.in = bx.x < tp.nx && bx.x + bx.w > 0 && y < tp.ny && y + kChunkRows > 0;
+    long long t0 = 0;
+    unsigned spins = 0;
+    while (!mbar_try_wait(bar, parity)) {
+        if ((++spins & 255u) == 0u) {
+            const long long t = global_timer_ns();
+            if (t0 == 0) t0 = t;
+            else if (t - t0 > limit_ns) { atomicOr(err, DEV_ERR_TIMEOUT); return false; }
+        }
     }
-    return bx;
+    return true;
 }
 
-// Thread 0: enqueue the in-grid boxes of chunk c of tile g into a staging buffer.
-__device__ __forceinline__ void issue_chunk(const TbParams &tp, int srcbuf, const Tile &g, int c,
-                                           unsigned char *stage, uint64_t *bar)
+// ---- phase P: uint8 -> bits ---------------------------------------------------
+__device__ __forceinline__ void issue_pack_unit(const TbParams &tp, int unit, unsigned char *stage, uint64_t *bar)
 {
-    const long long y = chunk_row(tp, g, c);
+    const int cbs = (int)((tp.nx + kOwnCols - 1) / kOwnCols);
+    const long long y = (long long)(unit / cbs) * kPackRows;
+    const long long x0 = (long long)(unit % cbs) * kOwnCols;
     uint32_t bytes = 0;
-    Box bx[kMidBoxes + 2];
-#pragma unroll
-    for (int b = 0; b < kMidBoxes + 2; ++b) {
-        bx[b] = box_of(tp, g, y, b);
-        if (bx[b].in) bytes += (uint32_t)(bx[b].w * kChunkRows);
-    }
+    for (int b = 0; b < kBoxes; ++b)
+        if (x0 + (long long)b * kBoxW < tp.nx) bytes += kBoxBytes;
     mbar_expect_tx(bar, bytes);
-#pragma unroll
-    for (int b = 0; b < kMidBoxes; ++b)
-        if (bx[b].in) tma_load_2d(stage + b * kMidBoxBytes, &tp.mid[srcbuf], (int)bx[b].x, (int)y, bar);
-#pragma unroll
-    for (int s = 0; s < 2; ++s)
-        if (bx[kMidBoxes + s].in)
-            tma_load_2d(stage + kMidBoxes * kMidBoxBytes + s * kHaloBoxBytes, &tp.halo[srcbuf],
-                        (int)bx[kMidBoxes + s].x, (int)y, bar);
+    for (int b = 0; b < kBoxes; ++b)
+        if (x0 + (long long)b * kBoxW < tp.nx)
+            tma_load_2d(stage + b * kBoxBytes, &tp.cells, (int)(x0 + (long long)b * kBoxW), (int)y, bar);
 }
 
-// WRAP: torus (every tile cell is a real, wrapped cell).  !WRAP: dead border;
-// cells of the tile that lie outside the grid are cleared after every
-// generation, because the border stays dead at every step.
+__device__ bool pack_phase(const TbParams &tp, unsigned char *stage, uint64_t *mbar, int *s_ok, long long limit_ns,
+                           int *err)
+{
+    const int tid = threadIdx.x;
+    const int cbs = (int)((tp.nx + kOwnCols - 1) / kOwnCols);
+    const int units = (int)((tp.ny + kPackRows - 1) / kPackRows) * cbs;
+    const int mine = (int)blockIdx.x < units ? (units - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+    unsigned int *dst = tp.bits[0];
+    // unit i of this CTA uses staging buffer i & 1, phase (i >> 1) & 1 of its mbarrier
+    if (tid == 0)
+        for (int i = 0; i < 2 && i < mine; ++i)
+            issue_pack_unit(tp, (int)blockIdx.x + i * (int)gridDim.x, stage + (i & 1) * kStageBytes, &mbar[i & 1]);
+    for (int i = 0; i < mine; ++i) {
+        const int unit = (int)blockIdx.x + i * (int)gridDim.x;
+        const int sb = i & 1;
+        if (tid == 0) *s_ok = bounded_wait(&mbar[sb], (uint32_t)(i >> 1) & 1u, limit_ns, err);
+        __syncthreads();
+        if (!*s_ok) return false;
+        const long long y0 = (long long)(unit / cbs) * kPackRows;
+        const long long xw0 = (long long)(unit % cbs) * kOwnWords;
+        const unsigned char *sbase = stage + sb * kStageBytes;
+#pragma unroll
+        for (int it = 0; it < (kPackRows * kOwnWords) / kThreads; ++it) {   // 32 rows x 32 words
+            const int item = tid + it * kThreads;
+            const int rr = item >> 5, w = item & 31;                        // one warp = one row
+            const int box = w >> 2, c0 = (w & 3) * 2;                       // 4 words per 128-byte box row
+            const long long y = y0 + rr, xw = xw0 + w;
+            if (y >= tp.ny || xw >= tp.nxw) continue;
+            const unsigned char *row = sbase + box * kBoxBytes + rr * kBoxW;
+            const uint4 lo = *(const uint4 *)(row + ((c0 ^ (rr & 7)) << 4));
+            const uint4 hi = *(const uint4 *)(row + (((c0 + 1) ^ (rr & 7)) << 4));
+            dst[y * tp.pitch + xw] = pack16(lo) | (pack16(hi) << 16);
+        }
+        __syncthreads();
+        const int nxt = i + 2;
+        if (tid == 0 && nxt < mine)
+            issue_pack_unit(tp, (int)blockIdx.x + nxt * (int)gridDim.x, stage + sb * kStageBytes, &mbar[sb]);
+    }
+    return true;
+}
+
+// ---- phase G: one tile of one pass ---------------------------------------------
+// Word xw of a packed row, with wrap-around or the dead border in x.
+__device__ __forceinline__ uint32_t load_word(const TbParams &tp, const unsigned int *row, long long xw)
+{
+    if (xw < 0 || xw >= tp.nxw) {
+        if (!tp.wrap) return 0u;
+        xw = wrap_mod(xw, tp.nxw);
+    }
+    return __ldcg(row + xw);
+}
+
+template <bool WRAP>
+__device__ __forceinline__ void run_tile(const TbParams &tp, int tile, int kp, const unsigned int *src,
+                                         unsigned int *dst, uint32_t *xch, unsigned long long *s_cnt,
+                                         unsigned int *s_ch)
+{
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int tx = tile % tp.tiles_x, ty = tile / tp.tiles_x;
+    const long long xw0 = (long long)tx * kOwnWords;
+    const int trow = warp * kRowsPerWarp + lane;                     // tile row of this thread
+    const long long yf = (long long)ty * tp.own_rows - tp.K + trow;  // grid row before wrapping
+    long long y = yf;
+    bool row_in = true;
+    if (WRAP) y = wrap_mod(yf, tp.ny);
+    else row_in = yf >= 0 && yf < tp.ny;
+
+    // load the row: 32 owned words and one halo word on each side
+    uint32_t cur[kWords];
+    if (row_in) {
+        const unsigned int *row = src + y * tp.pitch;
+        if (xw0 + kOwnWords <= tp.nxw) {
+            const uint4 *v = (const uint4 *)(row + xw0);
+#pragma unroll
+            for (int i = 0; i < kOwnWords / 4; ++i) {
+                const uint4 q4 = __ldcg(v + i);
+                cur[1 + 4 * i] = q4.x; cur[2 + 4 * i] = q4.y; cur[3 + 4 * i] = q4.z; cur[4 + 4 * i] = q4.w;
+            }
+        } else {
+#pragma unroll
+            for (int w = 1; w <= kOwnWords; ++w) cur[w] = load_word(tp, row, xw0 + w - 1);
+        }
+        cur[0] = load_word(tp, row, xw0 - 1);
+        cur[kWords - 1] = load_word(tp, row, xw0 + kOwnWords);
+    } else {
+#pragma unroll
+        for (int w = 0; w < kWords; ++w) cur[w] = 0u;
+    }
+    // word w of the tile holds grid word xw0 + w - 1; with the dead border only
+    // words [wlo, whi] lie inside the grid
+    const long long wmax = tp.nxw - xw0;
+    const int wlo = (WRAP || xw0 > 0) ? 0 : 1;
+    const int whi = WRAP ? kWords - 1 : (int)(wmax < kWords - 1 ? wmax : kWords - 1);
+    // reduce and store ownership: the warp's own lanes, owned tile rows, rows
+    // inside the grid (the last band of tiles may reach past it)
+    const bool own = lane >= 1 && lane <= kRowsPerWarp && trow >= tp.K && trow < kTileRows - tp.K &&
+                     (long long)ty * tp.own_rows + (trow - tp.K) < tp.ny;
+    const int own_words = (int)(wmax < kOwnWords ? wmax : kOwnWords);
+
+    for (int j = 0; j < kp; ++j) {
+        uint32_t changed = 0u, cnt = 0u;
+        uint32_t prevC = 0u, C = cur[0];
+#pragma unroll
+        for (int w = 0; w < kWords; ++w) {
+            const uint32_t nextC = w + 1 < kWords ? cur[w + 1] : 0u;
+            const uint32_t L = __funnelshift_l(prevC, C, 1);   // left neighbours (bit b-1)
+            const uint32_t R = __funnelshift_r(C, nextC, 1);   // right neighbours (bit b+1)
+            const uint32_t s0 = L ^ C ^ R, s1 = (L & C) | (L & R) | (C & R);   // L + C + R
+            const uint32_t m0 = L ^ R, m1 = L & R;                              // L + R
+            const uint32_t u0 = __shfl_up_sync(0xffffffffu, s0, 1), u1 = __shfl_up_sync(0xffffffffu, s1, 1);
+            const uint32_t d0 = __shfl_down_sync(0xffffffffu, s0, 1), d1 = __shfl_down_sync(0xffffffffu, s1, 1);
+            // n = (u0 + m0 + d0) + 2 (u1 + m1 + d1) = bit0 + 2 (c0 + u1 + m1 + d1)
+            const uint32_t bit0 = u0 ^ m0 ^ d0, c0 = (u0 & m0) | (u0 & d0) | (m0 & d0);
+            const uint32_t x = u1 ^ m1 ^ d1, yy = (u1 & m1) | (u1 & d1) | (m1 & d1);
+            uint32_t nw = ((x ^ c0) & ~yy) & (C | bit0);       // n == 3, or n == 2 and alive
+            if (!WRAP && !(row_in && w >= wlo && w <= whi)) nw = 0u;
+            if (w >= 1 && w <= own_words && own) {
+                changed |= nw ^ C;
+                cnt += (uint32_t)__popc(nw);
+            }
+            prevC = C;
+            cur[w] = nw;
+            C = nextC;
+        }
+        // refresh the two copied rows from the neighbour warps
+        uint32_t *mine = xch + warp * 2 * kWords;
+        if (lane == 1) {
+#pragma unroll
+            for (int w = 0; w < kWords; ++w) mine[w] = cur[w];
+        }
+        if (lane == kRowsPerWarp) {
+#pragma unroll
+            for (int w = 0; w < kWords; ++w) mine[kWords + w] = cur[w];
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+            changed |= __shfl_xor_sync(0xffffffffu, changed, o);
+        }
+        if (lane == 0) {
+            if (cnt) atomicAdd(&s_cnt[j], (unsigned long long)cnt);
+            if (changed) atomicOr(&s_ch[j], 1u);
+        }
+        __syncthreads();
+        if (lane == 0 && warp > 0) {
+            const uint32_t *up = xch + (warp - 1) * 2 * kWords + kWords;   // lane 30 of the warp above
+#pragma unroll
+            for (int w = 0; w < kWords; ++w) cur[w] = up[w];
+        }
+        if (lane == 31 && warp < kWarps - 1) {
+            const uint32_t *dn = xch + (warp + 1) * 2 * kWords;            // lane 1 of the warp below
+#pragma unroll
+            for (int w = 0; w < kWords; ++w) cur[w] = dn[w];
+        }
+        __syncthreads();
+    }
+    // store the owned words of the owned rows
+    if (own) {
+        unsigned int *row = dst + y * tp.pitch + xw0;
+        if (own_words == kOwnWords) {
+            uint4 *v = (uint4 *)row;
+#pragma unroll
+            for (int i = 0; i < kOwnWords / 4; ++i)
+                v[i] = make_uint4(cur[1 + 4 * i], cur[2 + 4 * i], cur[3 + 4 * i], cur[4 + 4 * i]);
+        } else {
+#pragma unroll
+            for (int w = 1; w <= kOwnWords; ++w)
+                if (w <= own_words) row[w - 1] = cur[w];
+        }
+    }
+}
+
 template <bool WRAP>
 __global__ void __launch_bounds__(kThreads, 2) life_tb_kernel(const __grid_constant__ TbParams tp, LoopArgs la)
 {
     extern __shared__ unsigned char smem_raw[];
     unsigned char *base = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     unsigned char *stage = base;                                   // [2][kStageBytes]
-    uint32_t *bits = (uint32_t *)(base + 2 * kStageBytes);         // [256][35]
-    uint32_t *xch = bits + kTileRows * kBitStride;                 // [2][8][2][34]
-    uint32_t *zrow = xch + kXchWords;                              // [34] zeros
-    uint64_t *mbar = (uint64_t *)(zrow + kWords);                  // [2] (8-byte aligned: offsets are even words)
+    uint32_t *xch = (uint32_t *)(base + 2 * kStageBytes);          // [8][2][34]
+    uint64_t *mbar = (uint64_t *)(xch + kXchWords);                // [2]
     unsigned long long *s_cnt = (unsigned long long *)(mbar + 2);  // [kMaxK]
     unsigned int *s_ch = (unsigned int *)(s_cnt + kMaxK);          // [kMaxK]
-    __shared__ int s_ok, s_stop, s_conv;
+    __shared__ int s_ok, s_stop;
     __shared__ long long s_it;
-    __shared__ double s_val;
-    __shared__ unsigned long long s_count;
 
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int tid = threadIdx.x;
     Ctl *ctl = la.ctl;
     const long long it0 = ctl->iters;
     if (ctl->converged || it0 >= la.max_iters || ctl->err) return;
@@ -265,161 +352,23 @@ __global__ void __launch_bounds__(kThreads, 2) life_tb_kernel(const __grid_const
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
-    if (tid < kWords) zrow[tid] = 0u;
     if (tid < kMaxK) { s_cnt[tid] = 0ull; s_ch[tid] = 0u; }
     __syncthreads();
 
-    const int ntiles = tp.tiles_x * tp.tiles_y;
-    const int mine = (int)blockIdx.x < ntiles ? (ntiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
-    const int nchunks = mine * kChunks;
-    // chunks consumed so far by this CTA; chunk q uses staging buffer q & 1 and
-    // completes phase (q >> 1) & 1 of that buffer's mbarrier
-    uint32_t q = 0;
-    long long it = it0;
+    // ---- P: pack the caller's cells into bits[0]
+    if (!pack_phase(tp, stage, mbar, &s_ok, la.limit_ns, &ctl->err)) return;
+    unsigned long long bar_target = (unsigned long long)la.nblocks;
+    if (!grid_barrier(ctl, bar_target, la.limit_ns)) return;
 
+    // ---- G: passes
+    const int ntiles = tp.tiles_x * tp.tiles_y;
+    long long it = it0;
+    int cur = 0;
     for (long long p = 0;; ++p) {
-        const int srcbuf = (int)(p & 1);                         // pass p reads A (p even) or B
-        unsigned char *dst = (unsigned char *)(srcbuf ? la.a : la.b);
         const long long left = la.max_iters - it;
         const int kp = (int)((long long)tp.K < left ? (long long)tp.K : left);
-
-        if (tid == 0) {
-            // after the grid barrier: make other CTAs' generic stores of the
-            // previous pass visible to this CTA's TMA (async proxy) reads
-            fence_proxy_async_global();
-            for (int ci = 0; ci < 2 && ci < nchunks; ++ci)
-                issue_chunk(tp, srcbuf, tile_of(tp, (int)blockIdx.x + (ci / kChunks) * (int)gridDim.x),
-                            ci % kChunks, stage + ((q + ci) & 1u) * kStageBytes, &mbar[(q + ci) & 1u]);
-        }
-        for (int ti = 0; ti < mine; ++ti) {
-            const Tile g = tile_of(tp, (int)blockIdx.x + ti * (int)gridDim.x);
-            // ---- 1. load: wait for each chunk, pack it into the bit-tile -----------
-            for (int c = 0; c < kChunks; ++c, ++q) {
-                const uint32_t sb = q & 1u;
-                if (tid == 0) {
-                    int ok = 1;
-                    long long t0 = 0;
-                    unsigned spins = 0;
-                    while (!mbar_try_wait(&mbar[sb], (q >> 1) & 1u)) {
-                        if ((++spins & 255u) == 0u) {
-                            const long long t = global_timer_ns();
-                            if (t0 == 0) t0 = t;
-                            else if (t - t0 > la.limit_ns) { atomicOr(&ctl->err, DEV_ERR_TIMEOUT); ok = 0; break; }
-                        }
-                    }
-                    s_ok = ok;
-                }
-                __syncthreads();
-                if (!s_ok) return;
-                const unsigned char *sbase = stage + sb * kStageBytes;
-                uint32_t *brow = bits + c * kChunkRows * kBitStride;
-                const long long ychunk = chunk_row(tp, g, c);
-#pragma unroll
-                for (int i = 0; i < (kChunkRows * 64) / kThreads; ++i) {   // 32 rows x 64 groups of 16 cells
-                    const int item = tid + i * kThreads;
-                    const int rr = item >> 6, gidx = item & 63;
-                    const int box = gidx >> 3, qq = gidx & 7;
-                    uint32_t packed = 0u;
-                    if (box_of(tp, g, ychunk, box).in)
-                        packed = pack16(*(const uint4 *)(sbase + box * kMidBoxBytes + rr * kMidBoxW +
-                                                         ((qq ^ (rr & 7)) << 4)));
-                    ((unsigned short *)(brow + rr * kBitStride + 1 + (gidx >> 1)))[gidx & 1] = (unsigned short)packed;
-                }
-                if (tid < kChunkRows * 4) {                                // halo words 0 and 33
-                    const int rr = tid >> 2, side = (tid >> 1) & 1, half = tid & 1;
-                    uint32_t packed = 0u;
-                    if (box_of(tp, g, ychunk, kMidBoxes + side).in)
-                        packed = pack16(*(const uint4 *)(sbase + kMidBoxes * kMidBoxBytes + side * kHaloBoxBytes +
-                                                         rr * kHaloBoxW + half * 16));
-                    ((unsigned short *)(brow + rr * kBitStride + (side ? kWords - 1 : 0)))[half] =
-                        (unsigned short)packed;
-                }
-                __syncthreads();                                           // staging buffer sb is free again
-                const int nxt = ti * kChunks + c + 2;
-                if (tid == 0 && nxt < nchunks)
-                    issue_chunk(tp, srcbuf, tile_of(tp, (int)blockIdx.x + (nxt / kChunks) * (int)gridDim.x),
-                                nxt % kChunks, stage + sb * kStageBytes, &mbar[sb]);
-            }
-            // ---- 2. evolve kp generations in registers ------------------------------
-            uint32_t cur[kWords];
-#pragma unroll
-            for (int w = 0; w < kWords; ++w) cur[w] = bits[tid * kBitStride + w];
-            const long long frame = g.frame0 + tid;
-            const bool own_row = tid >= kHaloRows && tid < kHaloRows + kOwnRows && frame < tp.ny;
-            const long long ocols = tp.nx - g.x0;
-            const int own_words = ocols >= kOwnCols ? 32 : (int)(ocols / 32);
-            // dead border: words [wlo, whi] of this row are inside the grid
-            const long long yreal = g.real0 + tid;
-            const bool row_in = WRAP || (yreal >= 0 && yreal < tp.ny);
-            const int wlo = (WRAP || g.x0 > 0) ? 0 : 1;
-            // word w holds columns x0 - 32 + 32w .. x0 + 32w - 1
-            const long long wmax = (tp.nx - g.x0) / 32;
-            const int whi = WRAP ? kWords - 1 : (int)(wmax < kWords - 1 ? wmax : kWords - 1);
-            for (int j = 0; j < kp; ++j) {
-                uint32_t *mine_x = xch + ((j & 1) * kWarps + warp) * 2 * kWords;
-                if (lane == 0) {
-#pragma unroll
-                    for (int w = 0; w < kWords; ++w) mine_x[w] = cur[w];
-                }
-                if (lane == 31) {
-#pragma unroll
-                    for (int w = 0; w < kWords; ++w) mine_x[kWords + w] = cur[w];
-                }
-                __syncthreads();
-                const uint32_t *upr = warp > 0 ? xch + (((j & 1) * kWarps + warp - 1) * 2 + 1) * kWords : zrow;
-                const uint32_t *dnr = warp < kWarps - 1 ? xch + (((j & 1) * kWarps + warp + 1) * 2) * kWords : zrow;
-                uint32_t Um = 0u, Cm = 0u, Dm = 0u;
-                uint32_t Cc = cur[0];
-                uint32_t Uc = __shfl_up_sync(0xffffffffu, Cc, 1), Dc = __shfl_down_sync(0xffffffffu, Cc, 1);
-                if (lane == 0) Uc = upr[0];
-                if (lane == 31) Dc = dnr[0];
-                uint32_t changed = 0u, cnt = 0u;
-#pragma unroll
-                for (int w = 0; w < kWords; ++w) {
-                    uint32_t Un = 0u, Cn = 0u, Dn = 0u;
-                    if (w + 1 < kWords) {
-                        Cn = cur[w + 1];
-                        Un = __shfl_up_sync(0xffffffffu, Cn, 1);
-                        Dn = __shfl_down_sync(0xffffffffu, Cn, 1);
-                        if (lane == 0) Un = upr[w + 1];
-                        if (lane == 31) Dn = dnr[w + 1];
-                    }
-                    uint32_t nw = life_word(Um, Uc, Un, Cm, Cc, Cn, Dm, Dc, Dn);
-                    if (!WRAP && !(row_in && w >= wlo && w <= whi)) nw = 0u;
-                    if (w >= 1 && w <= 32 && own_row && w <= own_words) {
-                        changed |= nw ^ Cc;
-                        cnt += (uint32_t)__popc(nw);
-                    }
-                    cur[w] = nw;
-                    Um = Uc; Uc = Un; Cm = Cc; Cc = Cn; Dm = Dc; Dc = Dn;
-                }
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) {
-                    cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
-                    changed |= __shfl_xor_sync(0xffffffffu, changed, o);
-                }
-                if (lane == 0) {
-                    if (cnt) atomicAdd(&s_cnt[j], (unsigned long long)cnt);
-                    if (changed) atomicOr(&s_ch[j], 1u);
-                }
-            }
-            // ---- 3. store the owned region ----------------------------------------
-            __syncthreads();
-#pragma unroll
-            for (int w = 1; w <= 32; ++w) bits[tid * kBitStride + w] = cur[w];
-            __syncthreads();
-            for (int i = 0; i < (kOwnRows * 64) / kThreads; ++i) {        // 224 rows x 64 groups
-                const int item = tid + i * kThreads;
-                const int rr = kHaloRows + (item >> 6), gidx = item & 63;
-                const long long col = g.x0 + 16ll * gidx;
-                if (col >= tp.nx || g.frame0 + rr >= tp.ny) continue;
-                long long y = g.real0 + rr;
-                if (tp.wrap) y = wrap_mod(y, tp.ny);
-                const uint32_t word = bits[rr * kBitStride + 1 + (gidx >> 1)];
-                *(uint4 *)(dst + y * tp.nx + col) = unpack16((gidx & 1) ? (word >> 16) : (word & 0xFFFFu));
-            }
-        }
-        // ---- publish this CTA's per-generation reduces, then the grid barrier -------
+        for (int t = (int)blockIdx.x; t < ntiles; t += (int)gridDim.x)
+            run_tile<WRAP>(tp, t, kp, tp.bits[cur], tp.bits[cur ^ 1], xch, s_cnt, s_ch);
         __syncthreads();
         if (tid < kp) {
             Slot *s = &ctl->sub[p % kSlots][tid];
@@ -428,8 +377,9 @@ __global__ void __launch_bounds__(kThreads, 2) life_tb_kernel(const __grid_const
             s_cnt[tid] = 0ull;
             s_ch[tid] = 0u;
         }
-        fence_proxy_async_global();
-        if (!grid_barrier(ctl, (unsigned long long)(p + 1) * (unsigned long long)la.nblocks, la.limit_ns)) return;
+        bar_target += (unsigned long long)la.nblocks;
+        if (!grid_barrier(ctl, bar_target, la.limit_ns)) return;
+        cur ^= 1;
         if (tid == 0) {
             if (blockIdx.x == 0)
                 for (int j = 0; j < kMaxK; ++j) zero_slot(&ctl->sub[(p + 2) % kSlots][j]);
@@ -443,9 +393,6 @@ __global__ void __launch_bounds__(kThreads, 2) life_tb_kernel(const __grid_const
             const int conv = jstop >= 0;
             s_stop = conv || itn >= la.max_iters;
             s_it = itn;
-            s_conv = conv;
-            s_val = (double)sj.cnt;
-            s_count = sj.cnt;
             if (s_stop && blockIdx.x == 0) {
                 ctl->iters = itn;
                 ctl->value = (double)sj.cnt;
@@ -456,74 +403,100 @@ __global__ void __launch_bounds__(kThreads, 2) life_tb_kernel(const __grid_const
         }
         __syncthreads();
         it = s_it;
-        if (s_stop) {
-            if ((p & 1) == 0) grid_copy(la.b, la.a, (size_t)tp.nx * (size_t)tp.ny);
-            return;
-        }
+        if (s_stop) break;
+    }
+
+    // ---- U: unpack bits[cur] into the caller's cells
+    const unsigned int *fin = tp.bits[cur];
+    unsigned char *cells = (unsigned char *)la.a;
+    const long long total = tp.ny * tp.nxw;
+    for (long long i = (long long)blockIdx.x * kThreads + tid; i < total; i += (long long)gridDim.x * kThreads) {
+        const long long y = i / tp.nxw, xw = i - y * tp.nxw;
+        const uint32_t word = __ldcg(fin + y * tp.pitch + xw);
+        uint4 *o = (uint4 *)(cells + y * tp.nx + 32 * xw);
+        o[0] = unpack16(word & 0xFFFFu);
+        o[1] = unpack16(word >> 16);
     }
 }
-
 
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
 {
     static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
     if (!fn) {
         void *p = nullptr;
-        cudaDriverEntryPointQueryResult q;
-        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+        cudaDriverEntryPointQueryResult qr;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &qr) ==
                 cudaSuccess &&
-            q == cudaDriverEntryPointSuccess)
+            qr == cudaDriverEntryPointSuccess)
             fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
     }
     return fn;
 }
 
-// 2D uint8 tensor map over an nx x ny row-major grid with the given box.
-bool make_map(CUtensorMap *m, void *base, long long nx, long long ny, uint32_t box_w, uint32_t box_h,
-              CUtensorMapSwizzle swz)
+bool make_cells_map(CUtensorMap *m, void *base, long long nx, long long ny)
 {
     auto fn = encode_fn();
     if (!fn) return false;
     cuuint64_t dims[2] = {(cuuint64_t)nx, (cuuint64_t)ny};
     cuuint64_t strides[1] = {(cuuint64_t)nx};
-    cuuint32_t box[2] = {box_w, box_h};
+    cuuint32_t box[2] = {(cuuint32_t)kBoxW, (cuuint32_t)kPackRows};
     cuuint32_t estr[2] = {1, 1};
     return fn(m, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-              swz, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+              CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
+
+long long pitch_words(long long nx) { return ((nx / 32) + 3) / 4 * 4; }
 
 }  // namespace
 
 bool life_tb_supported(const Problem &p)
 {
     if (p.nx % 32 != 0 || p.nx < 32 || p.ny < 1) return false;
-    if (p.wrap && (p.nx % kMidBoxW != 0 || p.ny % kChunkRows != 0)) return false;
     if (p.nx >= (1ll << 31) || p.ny >= (1ll << 31)) return false;
     return encode_fn() != nullptr;
 }
 
-int life_tb_default_k(const Problem &) { return 16; }
+size_t life_tb_bits_bytes(long long nx, long long ny) { return (size_t)(pitch_words(nx) * ny * 4); }
 
-cudaError_t life_tb_persistent(const Problem &p, LoopArgs la, cudaStream_t st)
+// Generations per pass when the caller leaves it to the library: the largest K
+// (up to 16) whose tiling needs no more tiles than the CTAs resident at once.
+int life_tb_default_k(const Problem &p, int nblocks)
+{
+    const long long tx = (p.nx + kOwnCols - 1) / kOwnCols;
+    for (int k = 16; k >= 4; --k) {
+        const long long own = kTileRows - 2 * k;
+        if (tx * ((p.ny + own - 1) / own) <= nblocks) return k;
+    }
+    return 16;
+}
+
+cudaError_t life_tb_persistent(const Problem &p, LoopArgs la, void *bits0, void *bits1, cudaStream_t st)
 {
     if (!life_tb_supported(p)) return cudaErrorNotSupported;
     TbParams tp;
     memset(&tp, 0, sizeof(tp));
-    void *bufs[2] = {la.a, la.b};
-    for (int i = 0; i < 2; ++i) {
-        if (!make_map(&tp.mid[i], bufs[i], p.nx, p.ny, kMidBoxW, kChunkRows, CU_TENSOR_MAP_SWIZZLE_128B) ||
-            !make_map(&tp.halo[i], bufs[i], p.nx, p.ny, kHaloBoxW, kChunkRows, CU_TENSOR_MAP_SWIZZLE_NONE))
-            return cudaErrorInvalidValue;
-    }
+    if (!make_cells_map(&tp.cells, la.a, p.nx, p.ny)) return cudaErrorInvalidValue;
+    tp.bits[0] = (unsigned int *)bits0;
+    tp.bits[1] = (unsigned int *)bits1;
     tp.nx = p.nx;
     tp.ny = p.ny;
+    tp.nxw = p.nx / 32;
+    tp.pitch = pitch_words(p.nx);
     tp.wrap = p.wrap;
-    tp.K = p.k > 0 ? (p.k > kHaloRows ? kHaloRows : p.k) : life_tb_default_k(p);
-    tp.tiles_x = (int)((p.nx + kOwnCols - 1) / kOwnCols);
-    tp.tiles_y = (int)((p.ny + kOwnRows - 1) / kOwnRows);
-    auto kern = tp.wrap ? life_tb_kernel<true> : life_tb_kernel<false>;
+    auto kern = p.wrap ? life_tb_kernel<true> : life_tb_kernel<false>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes);
     if (e != cudaSuccess) return e;
+    int dev = 0, sms = 0, per_sm = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, kSmemBytes)) != cudaSuccess)
+        return e;
+    const int nblocks = sms * (per_sm > 2 ? 2 : per_sm);
+    tp.K = p.k > 1 ? (p.k > kMaxK ? kMaxK : p.k) : life_tb_default_k(p, nblocks);
+    tp.own_rows = kTileRows - 2 * tp.K;
+    tp.tiles_x = (int)((p.nx + kOwnCols - 1) / kOwnCols);
+    tp.tiles_y = (int)((p.ny + tp.own_rows - 1) / tp.own_rows);
     return launch_cooperative(kern, kThreads, kSmemBytes, 2, la, &tp, st);
 }
 

@@ -134,6 +134,12 @@ slr_status cuda_fail(slr_handle h, cudaError_t e, const char *where)
 
 Ctl *dev_ctl(slr_handle h) { return (Ctl *)h->ws; }
 void *dev_b(slr_handle h) { return h->ws + slr::kCtlBytes; }
+// Life only: the two bit-packed buffers of the temporal-blocked path
+void *dev_bits(slr_handle h, int i)
+{
+    const size_t b = round_up(slr::life_tb_bits_bytes(h->prob.nx, h->prob.ny), 256);
+    return h->ws + slr::kCtlBytes + round_up(h->prob.state_bytes, 256) + (size_t)i * b;
+}
 
 slr_status run_persistent(slr_handle h, int64_t max_iters)
 {
@@ -155,8 +161,9 @@ slr_status run_persistent(slr_handle h, int64_t max_iters)
     la.debug_flags = h->desc.debug_flags;
     switch (h->prob.stencil) {
     case SLR_LIFE:
-        e = h->prob.k != 1 && slr::life_tb_supported(h->prob) ? slr::life_tb_persistent(h->prob, la, h->stream)
-                                                             : slr::life_persistent(h->prob, la, h->stream);
+        e = h->prob.k != 1 && slr::life_tb_supported(h->prob)
+                ? slr::life_tb_persistent(h->prob, la, dev_bits(h, 0), dev_bits(h, 1), h->stream)
+                : slr::life_persistent(h->prob, la, h->stream);
         break;
     case SLR_J2D5:
     case SLR_J3D7: e = slr::jacobi_persistent(h->prob, la, h->stream); break;
@@ -256,7 +263,9 @@ size_t slr_workspace_size(const slr_desc *d)
     bool unsup = false;
     if (!check_desc(d, &unsup).empty()) return 0;
     const Problem p = make_problem(d);
-    return slr::kCtlBytes + round_up(p.state_bytes, 256);
+    size_t bytes = slr::kCtlBytes + round_up(p.state_bytes, 256);
+    if (p.stencil == SLR_LIFE) bytes += 2 * round_up(slr::life_tb_bits_bytes(p.nx, p.ny), 256);
+    return bytes;
 }
 
 slr_status slr_create(const slr_desc *d, void *u, const void *aux, void *workspace, size_t workspace_bytes,

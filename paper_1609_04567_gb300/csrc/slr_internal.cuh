@@ -43,7 +43,7 @@ struct Slot {
 };
 
 constexpr int kSlots = 3;         // reduce slots cycled by sweep number (see loop)
-constexpr int kMaxK = 16;         // most sweeps a temporal-blocked pass may fuse
+constexpr int kMaxK = 32;         // most sweeps a temporal-blocked pass may fuse
 
 // Control block at the start of the workspace.  Written by device and host.
 struct Ctl {
@@ -315,11 +315,13 @@ struct Problem {
 cudaError_t life_persistent(const Problem &p, LoopArgs la, cudaStream_t st);
 cudaError_t life_sweep(const Problem &p, const void *src, void *dst, cudaStream_t st);
 cudaError_t life_normalize(const Problem &p, void *u, cudaStream_t st);
-// Temporal-blocked Life: k generations per HBM pass (life_tb.cu).  Returns
+// Temporal-blocked Life: k generations per pass over a bit-packed copy of the
+// grid kept in two workspace buffers (life_tb.cu).  Returns
 // cudaErrorNotSupported when the grid does not fit its tiling rules.
 bool life_tb_supported(const Problem &p);
-int life_tb_default_k(const Problem &p);
-cudaError_t life_tb_persistent(const Problem &p, LoopArgs la, cudaStream_t st);
+int life_tb_default_k(const Problem &p, int nblocks);
+size_t life_tb_bits_bytes(long long nx, long long ny);
+cudaError_t life_tb_persistent(const Problem &p, LoopArgs la, void *bits0, void *bits1, cudaStream_t st);
 cudaError_t jacobi_persistent(const Problem &p, LoopArgs la, cudaStream_t st);
 cudaError_t jacobi_sweep(const Problem &p, const void *src, void *dst, const void *f, cudaStream_t st);
 cudaError_t restore_persistent(const Problem &p, LoopArgs la, cudaStream_t st);

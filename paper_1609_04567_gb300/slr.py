@@ -43,7 +43,10 @@ class slr_desc(ctypes.Structure):
 
 
 EXPORTS = ["slr_desc_init", "slr_workspace_size", "slr_create", "slr_run_until", "slr_reduce_value",
-           "slr_destroy", "slr_last_error", "slr_version", "slr_run_static", "slr_static_last_error"]
+           "slr_destroy", "slr_last_error", "slr_version", "slr_run_static", "slr_static_last_error",
+           "slr_batch_workspace_size", "slr_batch_scratch_size", "slr_batch_create", "slr_batch_add",
+           "slr_batch_run", "slr_batch_poll", "slr_batch_result", "slr_batch_remove", "slr_batch_destroy",
+           "slr_batch_last_error"]
 SLR_STATIC_STATE_BYTES = 4 << 20
 
 _lib = None
@@ -89,6 +92,27 @@ def load(path: str = LIB_PATH):
     lib.slr_run_static.restype = i32
     lib.slr_static_last_error.argtypes = []
     lib.slr_static_last_error.restype = ctypes.c_char_p
+    lib.slr_batch_workspace_size.argtypes = [i32]
+    lib.slr_batch_workspace_size.restype = ctypes.c_size_t
+    lib.slr_batch_scratch_size.argtypes = [D]
+    lib.slr_batch_scratch_size.restype = ctypes.c_size_t
+    lib.slr_batch_create.argtypes = [i32, P, ctypes.c_size_t, P, ctypes.POINTER(P)]
+    lib.slr_batch_create.restype = i32
+    lib.slr_batch_add.argtypes = [P, D, P, P, P, i64, ctypes.POINTER(i32)]
+    lib.slr_batch_add.restype = i32
+    lib.slr_batch_run.argtypes = [P, i64]
+    lib.slr_batch_run.restype = i32
+    lib.slr_batch_poll.argtypes = [P, ctypes.POINTER(i32), i32, ctypes.POINTER(i32), ctypes.POINTER(i32)]
+    lib.slr_batch_poll.restype = i32
+    lib.slr_batch_result.argtypes = [P, i32, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i64),
+                                     ctypes.POINTER(i32), ctypes.POINTER(ctypes.c_uint64)]
+    lib.slr_batch_result.restype = i32
+    lib.slr_batch_remove.argtypes = [P, i32]
+    lib.slr_batch_remove.restype = i32
+    lib.slr_batch_destroy.argtypes = [P]
+    lib.slr_batch_destroy.restype = i32
+    lib.slr_batch_last_error.argtypes = [P]
+    lib.slr_batch_last_error.restype = ctypes.c_char_p
     _lib = lib
     return lib
 
@@ -156,6 +180,120 @@ def slr_run_static(d: slr_desc, u_ptr: int, f_ptr: int, max_iters: int, stream: 
 
 def slr_static_last_error() -> str:
     return load().slr_static_last_error().decode()
+
+
+def _bcheck(st: int, b) -> int:
+    if st < 0:
+        raise SlrError(st, load().slr_batch_last_error(b).decode())
+    return st
+
+
+def slr_batch_workspace_size(max_instances: int) -> int:
+    return int(load().slr_batch_workspace_size(max_instances))
+
+
+def slr_batch_scratch_size(d: slr_desc) -> int:
+    return int(load().slr_batch_scratch_size(ctypes.byref(d)))
+
+
+def slr_batch_create(max_instances: int, ws_ptr: int, ws_bytes: int, stream: int) -> int:
+    h = ctypes.c_void_p()
+    _bcheck(load().slr_batch_create(max_instances, ws_ptr or None, ws_bytes, stream or None, ctypes.byref(h)), None)
+    return h.value
+
+
+def slr_batch_add(b: int, d: slr_desc, u_ptr: int, aux_ptr: int, scratch_ptr: int, max_iters: int) -> int:
+    slot = ctypes.c_int32()
+    _bcheck(load().slr_batch_add(b, ctypes.byref(d), u_ptr or None, aux_ptr or None, scratch_ptr or None,
+                                 max_iters, ctypes.byref(slot)), b)
+    return slot.value
+
+
+def slr_batch_run(b: int, sweeps: int) -> int:
+    return _bcheck(load().slr_batch_run(b, sweeps), b)
+
+
+def slr_batch_poll(b: int, max_finished: int = 4096):
+    """Returns (finished slots, number still running)."""
+    arr = (ctypes.c_int32 * max_finished)()
+    nf, nr = ctypes.c_int32(), ctypes.c_int32()
+    _bcheck(load().slr_batch_poll(b, arr, max_finished, ctypes.byref(nf), ctypes.byref(nr)), b)
+    return [arr[i] for i in range(nf.value)], nr.value
+
+
+def slr_batch_result(b: int, slot: int):
+    """Returns (status, value, iters, converged, count)."""
+    v, it, c, n = ctypes.c_double(), ctypes.c_int64(), ctypes.c_int32(), ctypes.c_uint64()
+    st = _bcheck(load().slr_batch_result(b, slot, ctypes.byref(v), ctypes.byref(it), ctypes.byref(c),
+                                         ctypes.byref(n)), b)
+    return st, v.value, it.value, bool(c.value), n.value
+
+
+def slr_batch_remove(b: int, slot: int) -> int:
+    return _bcheck(load().slr_batch_remove(b, slot), b)
+
+
+def slr_batch_destroy(b: int) -> int:
+    return load().slr_batch_destroy(b)
+
+
+def slr_batch_last_error(b) -> str:
+    return load().slr_batch_last_error(b).decode()
+
+
+class Batch:
+    """A resident batch of instances over torch tensors (the library's
+    batched persistent launch).  ``add`` allocates the instance's scratch with
+    torch and keeps references until ``remove``."""
+
+    def __init__(self, max_instances: int, *, device=None, stream=None):
+        import torch
+        self.device = torch.device(device or "cuda")
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        ws = slr_batch_workspace_size(max_instances)
+        if ws == 0:
+            raise SlrError(SLR_ERR_INVALID_ARG, "max_instances out of range")
+        self.ws = torch.empty(ws + 256, dtype=torch.uint8, device=self.device)
+        off = (-self.ws.data_ptr()) % 256
+        self.handle = slr_batch_create(max_instances, self.ws.data_ptr() + off, ws, self.stream.cuda_stream)
+        self.held = {}
+
+    def add(self, stencil: int, u, aux, max_iters: int, **fields) -> int:
+        import torch
+        shape = tuple(u.shape)
+        nz, ny, nx = (1,) * (3 - len(shape)) + shape
+        d = slr_desc_init(stencil, nx, ny, nz, storage=storage_of(u.dtype), **fields)
+        nbytes = slr_batch_scratch_size(d)
+        if nbytes == 0:
+            raise SlrError(SLR_ERR_INVALID_ARG, "descriptor not accepted for batches")
+        scratch = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
+        slot = slr_batch_add(self.handle, d, u.data_ptr(), aux.data_ptr(), scratch.data_ptr(), max_iters)
+        self.held[slot] = (u, aux, scratch)
+        return slot
+
+    def run(self, sweeps: int) -> None:
+        slr_batch_run(self.handle, sweeps)
+
+    def poll(self):
+        return slr_batch_poll(self.handle)
+
+    def result(self, slot: int) -> Result:
+        return Result(*slr_batch_result(self.handle, slot))
+
+    def remove(self, slot: int) -> None:
+        slr_batch_remove(self.handle, slot)
+        self.held.pop(slot, None)
+
+    def close(self) -> None:
+        if getattr(self, "handle", None):
+            slr_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 # ---- torch wrapper ----------------------------------------------------------

@@ -1,0 +1,147 @@
+"""Batched persistent launch: many uneven instances (2D and 3D Helmholtz
+Jacobi in several storage precisions, restoration frames) in one launch, each
+with its own test and cap.  Every instance must match the oracle exactly as it
+does when run alone, and instances added while others are running (the
+continuous-batching use) must give the same results."""
+import numpy as np
+import pytest
+import torch
+
+pytestmark = pytest.mark.gpu
+
+TORCH = {"f64": torch.float64, "f32": torch.float32, "bf16": torch.bfloat16, "f16": torch.float16}
+
+
+def jacobi_instance(shape, storage, seed, **kw):
+    from paper_1609_04567_gb300 import inputs
+    f64 = inputs.helmholtz_rhs(shape, seed=seed)
+    if storage == "f64":
+        ft, fo = torch.from_numpy(f64), f64
+    else:
+        ft = torch.from_numpy(f64.astype(np.float32)).to(TORCH[storage])
+        fo = ft.float().numpy()
+    u = torch.zeros(shape, dtype=TORCH[storage], device="cuda")
+    return dict(kind="j", shape=shape, storage=storage, u=u, aux=ft.cuda(), f_oracle=fo, kw=kw)
+
+
+def restore_instance(ny, nx, seed, **kw):
+    from paper_1609_04567_gb300 import inputs
+    frame, _ = inputs.noisy_frame(ny, nx, seed=seed)
+    mask = inputs.noise_mask(frame)
+    u = torch.from_numpy(frame.astype(np.float32)).cuda()
+    return dict(kind="r", u=u, aux=torch.from_numpy(mask).cuda(), frame=frame, mask=mask, kw=kw)
+
+
+def oracle_of(orc, inst, cap):
+    kw = dict(inst["kw"])
+    if inst["kind"] == "r":
+        out, r = orc.restore8(inst["frame"].astype(np.float32), inst["mask"], tol=kw.get("tol", 1e-3), max_iters=cap)
+        return out, r
+    shape = inst["shape"]
+    fn = orc.j3d7 if len(shape) == 3 else orc.j2d5
+    wrap = kw.pop("boundary", 0) == 1
+    out, r = fn(np.zeros(shape, dtype=inst["f_oracle"].dtype), inst["f_oracle"], wrap=wrap,
+                storage=None if inst["storage"] == "f64" else inst["storage"], max_iters=cap, **kw)
+    return out, r
+
+
+def state(inst):
+    u = inst["u"]
+    return u.float().cpu().numpy() if u.dtype in (torch.bfloat16, torch.float16) else u.cpu().numpy()
+
+
+def add(slr, batch, inst, cap):
+    stencil = slr.SLR_RESTORE8 if inst["kind"] == "r" else (slr.SLR_J3D7 if len(inst["shape"]) == 3 else slr.SLR_J2D5)
+    return batch.add(stencil, inst["u"], inst["aux"], cap, **inst["kw"])
+
+
+def make_mix():
+    insts = [
+        (jacobi_instance((64, 64), "f64", 1, tol=1e-6), 5000),
+        (jacobi_instance((33, 17), "f64", 2, tol=1e-9), 5000),
+        (jacobi_instance((100, 130), "f64", 3, tol=1e-6, boundary=1), 5000),
+        (jacobi_instance((48, 80), "f64", 4, tol=1e-8, ghost=0.5), 5000),
+        (jacobi_instance((96, 80), "bf16", 5, tol=1e-6), 3000),
+        (jacobi_instance((70, 70), "f16", 6, tol=1e-6), 3000),
+        (jacobi_instance((40, 56), "f32", 7, tol=1e-7), 3000),
+        (jacobi_instance((12, 20, 24), "f64", 8, tol=1e-6), 2000),
+        (jacobi_instance((9, 10, 11), "bf16", 9, tol=1e-6), 2000),
+        (jacobi_instance((256, 256), "f64", 10, tol=1e-6), 17),      # stopped by its cap
+        (restore_instance(128, 200, 11), 5000),
+        (restore_instance(37, 1, 12), 5000),
+    ]
+    return insts
+
+
+def test_mixed_batch_matches_oracle_and_solo_runs(gpu, orc):
+    b = gpu.Batch(64)
+    mix = make_mix()
+    slots = [add(gpu, b, inst, cap) for inst, cap in mix]
+    b.run(100000)
+    finished, running = b.poll()
+    assert running == 0 and sorted(finished) == sorted(slots)
+    for (inst, cap), s in zip(mix, slots):
+        r = b.result(s)
+        ref, rr = oracle_of(orc, inst, cap)
+        got = state(inst)
+        assert (r.iters, r.converged) == (rr.iters, rr.converged), (inst["kw"], r, rr)
+        assert np.array_equal(got, ref.astype(got.dtype)), inst["kw"]
+        assert r.value == rr.value
+    b.close()
+
+
+def test_instances_added_while_others_run(gpu, orc):
+    # continuous batching: a run stops on its sweep budget with work still in
+    # flight, new instances join, finished ones leave; every result is still
+    # the one of the instance alone
+    b = gpu.Batch(16)
+    first = [(jacobi_instance((64, 64), "f64", 21, tol=1e-7), 5000),
+             (restore_instance(64, 96, 22), 5000)]
+    later = [(jacobi_instance((50, 40), "bf16", 23, tol=1e-6), 3000),
+             (jacobi_instance((30, 30), "f64", 24, tol=1e-9), 5000)]
+    slots = {add(gpu, b, inst, cap): (inst, cap) for inst, cap in first}
+    b.run(7)
+    done, running = b.poll()
+    assert running >= 1
+    for inst, cap in later:
+        slots[add(gpu, b, inst, cap)] = (inst, cap)
+    seen = set(done)
+    for _ in range(2000):
+        b.run(50)
+        done, running = b.poll()
+        seen.update(done)
+        if running == 0:
+            break
+    assert seen == set(slots)
+    for s, (inst, cap) in slots.items():
+        r = b.result(s)
+        ref, rr = oracle_of(orc, inst, cap)
+        got = state(inst)
+        assert (r.iters, r.converged) == (rr.iters, rr.converged)
+        assert np.array_equal(got, ref.astype(got.dtype))
+    # a freed slot is reused by a new instance
+    s0 = next(iter(slots))
+    b.remove(s0)
+    inst, cap = jacobi_instance((20, 20), "f64", 25, tol=1e-9), 5000
+    s_new = add(gpu, b, inst, cap)
+    assert s_new == s0
+    b.run(10000)
+    done, running = b.poll()
+    assert s_new in done and running == 0
+    ref, rr = oracle_of(orc, inst, cap)
+    assert np.array_equal(state(inst), ref) and b.result(s_new).iters == rr.iters
+    b.close()
+
+
+def test_batch_rejects_life_and_full_batches(gpu):
+    b = gpu.Batch(1)
+    u = torch.zeros((8, 8), dtype=torch.uint8, device="cuda")
+    with pytest.raises(gpu.SlrError):
+        b.add(gpu.SLR_LIFE, u, u, 10)
+    inst = jacobi_instance((8, 8), "f64", 1)
+    add(gpu, b, inst, 10)
+    inst2 = jacobi_instance((8, 8), "f64", 2)
+    with pytest.raises(gpu.SlrError) as e:
+        add(gpu, b, inst2, 10)
+    assert e.value.status == gpu.SLR_ERR_WORKSPACE
+    b.close()

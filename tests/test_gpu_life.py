@@ -116,15 +116,16 @@ def test_full_size_2000_generations_properties(gpu):
     assert torch.equal(half, base) and rh.count == r.count == rs.count == rt.count
 
 
-# ---- temporal-blocked path (K generations per HBM pass) ----------------------
-# It serves widths that are multiples of 32 (dead border) or of 128 with
-# heights that are multiples of 32 (torus); tiles own 1024 x 224 cells.
+# ---- temporal-blocked path (K generations per pass over a bit-packed grid) ----
+# It serves widths that are multiples of 32; tiles own 1024 columns and
+# 242 - 2K rows.
 
 @pytest.mark.parametrize("ny,nx,wrap", [
     (256, 1024, True), (96, 2176, True), (32, 128, True), (480, 3072, True), (64, 1152, True),
-    (257, 512, False), (70, 2080, False), (500, 1056, False), (33, 32, False),
+    (257, 1024, True), (1, 32, True), (7, 96, True), (450, 2048, True),
+    (257, 512, False), (70, 2080, False), (500, 1056, False), (33, 32, False), (1, 64, False),
 ])
-@pytest.mark.parametrize("k", [2, 7, 16])
+@pytest.mark.parametrize("k", [2, 7, 16, 32])
 def test_temporal_blocked_matches_oracle(gpu, orc, ny, nx, wrap, k):
     from paper_1609_04567_gb300 import inputs
     cells = inputs.life_cells(ny, nx, seed=ny + nx + k)
