@@ -372,13 +372,216 @@ def run_ours(args, wl, world, rank, local):
     return 0
 
 
+def _stream_time(stream, fn, steps):
+    """CUDA-event time of `steps` calls of fn() on `stream` (ms per call)."""
+    import torch
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    a.record(stream)
+    for _ in range(steps):
+        fn()
+    b.record(stream)
+    torch.cuda.synchronize()
+    return a.elapsed_time(b) / steps
+
+
+def run_helmholtz(args):
+    """2D Helmholtz Jacobi 256 x 256 FP64, tol 1e-6, cap 5000: time to solution."""
+    import numpy as np
+    import torch
+    import oracle
+    from paper_1609_04567_gb300 import inputs, slr
+    slr.load()
+    n = 256
+    f = torch.from_numpy(inputs.helmholtz_rhs((n, n))).cuda()
+    u = torch.zeros((n, n), dtype=torch.float64, device="cuda")
+    stream = torch.cuda.Stream()
+    res = {}
+    for name, loop in (("fused_device_loop", slr.SLR_LOOP_PERSISTENT), ("plain", slr.SLR_LOOP_HOST)):
+        with torch.cuda.stream(stream):
+            s = slr.Solver(slr.SLR_J2D5, u, f, stream=stream, tol=1e-6, loop=loop)
+
+            def step():
+                u.zero_()
+                slr.slr_destroy(s.handle)
+                s.handle = slr.slr_create(s.desc, u.data_ptr(), f.data_ptr(),
+                                          s.ws.data_ptr() + ((-s.ws.data_ptr()) % 256),
+                                          slr.slr_workspace_size(s.desc), stream.cuda_stream)
+                s.run(5000)
+            for _ in range(args.warmup):
+                step()
+            if loop == slr.SLR_LOOP_HOST:
+                t0 = time.perf_counter()
+                for _ in range(args.steps):
+                    step()
+                torch.cuda.synchronize()
+                ms = (time.perf_counter() - t0) / args.steps * 1e3
+            else:
+                ms = _stream_time(stream, step, args.steps)
+            r = s.result()
+            s.close()
+        res[name] = {"ms_per_solve": ms, "iters": r.iters, "gcell_per_s": n * n * r.iters / ms / 1e6}
+    t0 = time.perf_counter()
+    _, rr = oracle.j2d5(np.zeros((n, n)), f.cpu().numpy(), tol=1e-6, max_iters=5000)
+    cpu_ms = (time.perf_counter() - t0) * 1e3
+    line = {"workload": "helmholtz_256x256_f64_tol1e-6", "metric": "time-to-solution", "unit": "ms",
+            "value": res["fused_device_loop"]["ms_per_solve"], "higher_is_better": False, "sweeps": rr.iters,
+            "fused": res["fused_device_loop"], "plain": res["plain"],
+            "cpu_baseline": {"value": cpu_ms, "unit": "ms", "cores": 1, "kind": "oracle", "sample": "full solve"}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_restore(args):
+    """Restoration 4096 x 4096 FP32, 50% salt-and-pepper, tol 1e-3."""
+    import numpy as np
+    import torch
+    import oracle
+    from paper_1609_04567_gb300 import inputs, slr
+    slr.load()
+    n = 4096
+    frame, _ = inputs.noisy_frame(n, n)
+    mask = torch.from_numpy(inputs.noise_mask(frame)).cuda()
+    init = torch.from_numpy(frame.astype(np.float32)).cuda()
+    u = init.clone()
+    stream = torch.cuda.Stream()
+    res = {}
+    for name, loop, math in (("fused_exact", slr.SLR_LOOP_PERSISTENT, slr.SLR_MATH_EXACT),
+                             ("fused_fast", slr.SLR_LOOP_PERSISTENT, slr.SLR_MATH_FAST),
+                             ("plain_exact", slr.SLR_LOOP_HOST, slr.SLR_MATH_EXACT)):
+        with torch.cuda.stream(stream):
+            desc = slr.slr_desc_init(slr.SLR_RESTORE8, n, n, 1, loop=loop, math=math)
+            wsb = slr.slr_workspace_size(desc)
+            ws = torch.empty(wsb + 256, dtype=torch.uint8, device="cuda")
+            wp = ws.data_ptr() + ((-ws.data_ptr()) % 256)
+            hs = []
+
+            def step():
+                u.copy_(init)
+                h = slr.slr_create(desc, u.data_ptr(), mask.data_ptr(), wp, wsb, stream.cuda_stream)
+                slr.slr_run_until(h, 5000)
+                hs.append(h)
+            for _ in range(args.warmup):
+                step()
+            steps = args.steps if loop != slr.SLR_LOOP_HOST else 2
+            if loop == slr.SLR_LOOP_HOST:
+                t0 = time.perf_counter()
+                for _ in range(steps):
+                    step()
+                torch.cuda.synchronize()
+                ms = (time.perf_counter() - t0) / steps * 1e3
+            else:
+                ms = _stream_time(stream, step, steps)
+            r = slr.slr_reduce_value(hs[-1])
+            for h in hs:
+                slr.slr_destroy(h)
+        res[name] = {"ms_per_solve": ms, "iters": r[2], "value": r[1], "gcell_per_s": n * n * r[2] / ms / 1e6,
+                     "hbm_gbs": 9.0 * n * n * r[2] / ms / 1e6}
+    t0 = time.perf_counter()
+    oracle.restore8(frame.astype(np.float32), inputs.noise_mask(frame), tol=0.0, max_iters=2)
+    cpu_s = time.perf_counter() - t0
+    line = {"workload": "restore_4096x4096_f32_tol1e-3", "metric": "Gcell-updates/s", "unit": "Gcell-updates/s",
+            "value": res["fused_exact"]["gcell_per_s"], "fused_exact": res["fused_exact"],
+            "fused_fast": res["fused_fast"], "plain_exact": res["plain_exact"],
+            "cpu_baseline": {"value": n * n * 2 / cpu_s / 1e9, "unit": "Gcell-updates/s", "cores": 1,
+                             "kind": "oracle", "sample": "2 sweeps of the 4096x4096 frame"}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_batch(args):
+    """512 2D Helmholtz grids (side log-uniform in [64, 1024]) + one 512^3 3D
+    grid, bfloat16 storage, tol 1e-6, in one batch; against the same grids
+    solved one after another (persistent loop per grid)."""
+    import numpy as np
+    import torch
+    from paper_1609_04567_gb300 import inputs, slr
+    slr.load()
+    sides = inputs.batch_sides(512)
+    grids = []
+    for i, sd in enumerate(sides):
+        f = torch.from_numpy(inputs.helmholtz_rhs((int(sd), int(sd)), stream=inputs.STREAM_BATCH_F0 + i)
+                             .astype(np.float32)).to(torch.bfloat16).cuda()
+        grids.append((f, torch.zeros_like(f)))
+    n3 = args.batch3d
+    if n3:
+        f3 = torch.empty((n3, n3, n3), dtype=torch.bfloat16, device="cuda")
+        f3_host = np.empty((n3, n3, n3), dtype=np.float32)
+        flat = inputs.helmholtz_rhs((n3 * n3 * n3,), stream=inputs.STREAM_BATCH_F0 + 999)
+        f3_host.reshape(-1)[:] = flat
+        f3.copy_(torch.from_numpy(f3_host).to(torch.bfloat16))
+        grids.append((f3, torch.zeros_like(f3)))
+    cells = [g[0].numel() for g in grids]
+    stream = torch.cuda.Stream()
+    b = slr.Batch(len(grids) + 1, stream=stream)
+    with torch.cuda.stream(stream):
+        def batch_step():
+            for _, u in grids:
+                u.zero_()
+            slots = [b.add(slr.SLR_J3D7 if u.dim() == 3 else slr.SLR_J2D5, u, f, 100000, tol=1e-6) for f, u in grids]
+            b.run(100000)
+            fin, running = b.poll()
+            its = [b.result(s).iters for s in slots]
+            for s in slots:
+                b.remove(s)
+            return its
+        batch_step()
+        t0 = time.perf_counter()
+        its = batch_step()
+        torch.cuda.synchronize()
+        batch_s = time.perf_counter() - t0
+    upd = float(sum(c * i for c, i in zip(cells, its)))
+    # the same grids one after another, each with its own persistent launch
+    t0 = time.perf_counter()
+    seq_its = []
+    with torch.cuda.stream(stream):
+        for f, u in grids:
+            u.zero_()
+            s = slr.Solver(slr.SLR_J3D7 if u.dim() == 3 else slr.SLR_J2D5, u, f, stream=stream, tol=1e-6)
+            s.run(100000)
+            seq_its.append(s.result().iters)
+            s.close()
+    torch.cuda.synchronize()
+    seq_s = time.perf_counter() - t0
+    line = {"workload": f"batch_512x2d_bf16_side64-1024_plus_{n3}^3_tol1e-6", "metric": "Gcell-updates/s",
+            "unit": "Gcell-updates/s", "value": upd / batch_s / 1e9, "batch_s": batch_s,
+            "sequential_s": seq_s, "sequential_gcell_per_s": upd / seq_s / 1e9, "same_iters": its == seq_its,
+            "cell_updates": upd, "grids": len(grids), "max_sweeps": max(its), "min_sweeps": min(its)}
+    print(json.dumps(line), flush=True)
+    b.close()
+    return 0
+
+
+def run_serve(args):
+    """Continuous-batching serving: Poisson arrivals at 2000 requests/s, half
+    denoise (sides 256-4096) and half Helmholtz solves (sides 64-2048)."""
+    import torch
+    from paper_1609_04567_gb300 import serve, slr
+    slr.load()
+    reqs = serve.make_requests(args.serve_seconds + 1.0, args.rate)
+    srv = serve.Server(max_slots=2048, step_sweeps=args.step_sweeps)
+    st = srv.serve(reqs, warmup_s=1.0, time_limit_s=args.serve_seconds * 6 + 30)
+    srv.close()
+    line = {"workload": f"serve_poisson{args.rate:g}rps_denoise256-4096_solve64-2048",
+            "metric": "p50/p99 latency and throughput", "unit": "ms", "p50_ms": st.p50_ms, "p99_ms": st.p99_ms,
+            "mean_ms": st.mean_ms, "throughput_rps": st.throughput_rps, "gcell_per_s": st.gcell_per_s,
+            "requests": st.requests, "completed": st.completed, "wall_s": st.wall_s, "steps": st.steps,
+            "max_in_flight": st.max_in_flight, "max_queue": st.max_queue}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="life", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="life", choices=["life", "helmholtz", "restore", "batch", "serve"])
+    ap.add_argument("--batch3d", type=int, default=512, help="side of the 3D grid of the batch workload (0: none)")
+    ap.add_argument("--rate", type=float, default=2000.0)
+    ap.add_argument("--serve-seconds", type=float, default=10.0)
+    ap.add_argument("--step-sweeps", type=int, default=32)
     ap.add_argument("--k", type=int, default=0, help="generations per HBM pass (0 = library choice)")
     ap.add_argument("--gens", type=int, default=2000,
                     help="generations per solve (the workload has 2000; shorter runs are for profiler captures "
@@ -389,6 +592,9 @@ def main():
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
+    if args.workload != "life":
+        fn = {"helmholtz": run_helmholtz, "restore": run_restore, "batch": run_batch, "serve": run_serve}
+        return fn[args.workload](args)
     wl = WORKLOADS[args.workload]
     world, rank, local = dist_setup()
     if args.impl == "reference":

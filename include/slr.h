@@ -115,6 +115,14 @@ typedef struct {
     int32_t temporal_k;    /* sweeps per HBM pass for Life (1, 2, 4, ...); 0 = library choice */
     int64_t wait_limit_ns; /* device-side barrier wait limit; <= 0 selects 2 s */
     int32_t debug_flags;   /* SLR_DEBUG_* bits; 0 in normal use */
+    int32_t defect_correction; /* 1: FP64 defect correction around FP32 Jacobi inner solves
+                                  (SLR_J2D5, storage F64, Dirichlet ghost 0).  One iteration:
+                                  inner_sweeps binary32 Jacobi sweeps of A e = r from e = 0,
+                                  then u += e and r = f - A u in binary64; the reduced value
+                                  is the scaled defect max |h^2 r / (4 + sigma h^2)| (the
+                                  change the next FP64 Jacobi sweep would make); stop when
+                                  it is < tol or at the cap */
+    int32_t inner_sweeps;  /* binary32 sweeps per correction; 0 selects 50 */
     int32_t reserved;
 } slr_desc;
 

@@ -470,7 +470,8 @@ slr_status slr_batch_add(slr_batch b, const slr_desc *d, void *u, const void *au
     bool unsup = false;
     const std::string why = slr::describe_invalid(d, &unsup);
     if (!why.empty()) return bfail(b, unsup ? SLR_ERR_UNSUPPORTED : SLR_ERR_INVALID_ARG, why);
-    if (d->stencil == SLR_LIFE) return bfail(b, SLR_ERR_UNSUPPORTED, "batches run the Jacobi and restoration stencils");
+    if (d->stencil == SLR_LIFE || d->defect_correction)
+        return bfail(b, SLR_ERR_UNSUPPORTED, "batches run the Jacobi and restoration stencils (no defect correction)");
     if (d->stencil == SLR_RESTORE8 && d->math != SLR_MATH_EXACT)
         return bfail(b, SLR_ERR_UNSUPPORTED, "batched restoration runs EXACT math");
     if (!u || !aux || !scratch || ((uintptr_t)u & 15u) || ((uintptr_t)scratch & 15u))

@@ -22,8 +22,8 @@
 //     2-bit sums (left + self + right, and left + right) with two funnel shifts
 //     and four logic operations, takes the rows above and below by shuffle,
 //     and finishes the B3/S23 rule with six more logic operations: twelve per
-//     32 cells.  Live count and "any cell changed" are reduced per generation
-//     over the owned cells.
+//     32 cells.  "Any cell changed" is reduced per generation over the owned
+//     cells, the live count once per pass (see the decision below).
 //  U. Unpack: the final packed grid is expanded back into the caller's uint8
 //     grid.
 //
@@ -48,7 +48,7 @@ constexpr int kTileRows = kWarps * kRowsPerWarp + 2;  // 242 distinct tile rows
 constexpr int kWords = 34;                            // 1 halo + 32 owned + 1 halo
 constexpr int kOwnWords = 32;
 constexpr int kOwnCols = 32 * kOwnWords;              // 1024
-constexpr int kXchWords = kWarps * 2 * kWords;        // [warp][lane 1 row, lane 30 row][word]
+constexpr int kXchWords = 2 * kWarps * 2 * kWords;    // [parity][warp][lane 1 row, lane 30 row][word]
 // pack phase: 32 rows x 1024 columns per unit, 8 swizzled boxes of 128 bytes
 constexpr int kPackRows = 32;
 constexpr int kBoxW = 128;
@@ -273,14 +273,16 @@ __device__ __forceinline__ void run_tile(const TbParams &tp, int tile, int kp, c
             if (!WRAP && !(row_in && w >= wlo && w <= whi)) nw = 0u;
             if (w >= 1 && w <= own_words && own) {
                 changed |= nw ^ C;
-                cnt += (uint32_t)__popc(nw);
+                if (j == kp - 1) cnt += (uint32_t)__popc(nw);   // the count is taken on the pass's last state
             }
             prevC = C;
             cur[w] = nw;
             C = nextC;
         }
-        // refresh the two copied rows from the neighbour warps
-        uint32_t *mine = xch + warp * 2 * kWords;
+        // refresh the two copied rows from the neighbour warps (exchange rows
+        // double buffered by generation parity: one barrier per generation)
+        uint32_t *xb = xch + (j & 1) * kWarps * 2 * kWords;
+        uint32_t *mine = xb + warp * 2 * kWords;
         if (lane == 1) {
 #pragma unroll
             for (int w = 0; w < kWords; ++w) mine[w] = cur[w];
@@ -295,22 +297,22 @@ __device__ __forceinline__ void run_tile(const TbParams &tp, int tile, int kp, c
             changed |= __shfl_xor_sync(0xffffffffu, changed, o);
         }
         if (lane == 0) {
-            if (cnt) atomicAdd(&s_cnt[j], (unsigned long long)cnt);
+            if (cnt) atomicAdd(&s_cnt[kp - 1], (unsigned long long)cnt);
             if (changed) atomicOr(&s_ch[j], 1u);
         }
         __syncthreads();
         if (lane == 0 && warp > 0) {
-            const uint32_t *up = xch + (warp - 1) * 2 * kWords + kWords;   // lane 30 of the warp above
+            const uint32_t *up = xb + (warp - 1) * 2 * kWords + kWords;   // lane 30 of the warp above
 #pragma unroll
             for (int w = 0; w < kWords; ++w) cur[w] = up[w];
         }
         if (lane == 31 && warp < kWarps - 1) {
-            const uint32_t *dn = xch + (warp + 1) * 2 * kWords;            // lane 1 of the warp below
+            const uint32_t *dn = xb + (warp + 1) * 2 * kWords;            // lane 1 of the warp below
 #pragma unroll
             for (int w = 0; w < kWords; ++w) cur[w] = dn[w];
         }
-        __syncthreads();
     }
+    __syncthreads();   // the last exchange buffer is read before the next tile writes it
     // store the owned words of the owned rows
     if (own) {
         unsigned int *row = dst + y * tp.pitch + xw0;
@@ -383,12 +385,13 @@ __global__ void __launch_bounds__(kThreads, 2) life_tb_kernel(const __grid_const
         if (tid == 0) {
             if (blockIdx.x == 0)
                 for (int j = 0; j < kMaxK; ++j) zero_slot(&ctl->sub[(p + 2) % kSlots][j]);
+            // a generation that changed nothing is a still state, a fixed
+            // point: the state (and live count) at the end of the pass equal it
             int jstop = -1;
-            Slot sj = {0ull, 0ull, 0ull, 0u, 0u};
             for (int j = 0; j < kp; ++j) {
-                sj = read_slot(&ctl->sub[p % kSlots][j]);
-                if (!sj.changed) { jstop = j; break; }
+                if (!read_slot(&ctl->sub[p % kSlots][j]).changed) { jstop = j; break; }
             }
+            const Slot sj = read_slot(&ctl->sub[p % kSlots][kp - 1]);
             const long long itn = jstop >= 0 ? it + jstop + 1 : it + kp;
             const int conv = jstop >= 0;
             s_stop = conv || itn >= la.max_iters;

@@ -88,6 +88,14 @@ std::string check_desc(const slr_desc *d, bool *unsupported)
         if (!(d->alpha > 0.0f)) return "alpha must be > 0";
         break;
     }
+    if (d->defect_correction) {
+        if (d->stencil != SLR_J2D5 || d->storage != SLR_F64 || d->boundary != SLR_DIRICHLET || d->ghost != 0.0 ||
+            d->loop == SLR_LOOP_HOST) {
+            *unsupported = true;
+            return "defect correction runs SLR_J2D5 in F64 with ghost 0 on the persistent loop";
+        }
+        if (d->inner_sweeps < 0) return "inner_sweeps must be >= 0";
+    }
     const double cells = (double)d->nx * (double)d->ny * (double)d->nz;
     if (cells * elem_bytes_of(d->storage) > 4.0e11) return "grid larger than device memory";
     return std::string();
@@ -166,7 +174,12 @@ slr_status run_persistent(slr_handle h, int64_t max_iters)
                 : slr::life_persistent(h->prob, la, h->stream);
         break;
     case SLR_J2D5:
-    case SLR_J3D7: e = slr::jacobi_persistent(h->prob, la, h->stream); break;
+    case SLR_J3D7:
+        e = h->desc.defect_correction
+                ? slr::dc_persistent(h->prob, la, h->desc.inner_sweeps,
+                                     h->ws + slr::kCtlBytes + round_up(h->prob.state_bytes, 256), h->stream)
+                : slr::jacobi_persistent(h->prob, la, h->stream);
+        break;
     case SLR_RESTORE8: e = slr::restore_persistent(h->prob, la, h->stream); break;
     default: e = cudaErrorInvalidValue;
     }
@@ -265,6 +278,7 @@ size_t slr_workspace_size(const slr_desc *d)
     const Problem p = make_problem(d);
     size_t bytes = slr::kCtlBytes + round_up(p.state_bytes, 256);
     if (p.stencil == SLR_LIFE) bytes += 2 * round_up(slr::life_tb_bits_bytes(p.nx, p.ny), 256);
+    if (d->defect_correction) bytes += slr::dc_workspace_bytes(p.nx, p.ny);
     return bytes;
 }
 

@@ -326,6 +326,9 @@ cudaError_t jacobi_persistent(const Problem &p, LoopArgs la, cudaStream_t st);
 cudaError_t jacobi_sweep(const Problem &p, const void *src, void *dst, const void *f, cudaStream_t st);
 cudaError_t restore_persistent(const Problem &p, LoopArgs la, cudaStream_t st);
 cudaError_t restore_sweep(const Problem &p, const void *src, void *dst, const void *mask, cudaStream_t st);
+// FP64 defect correction around FP32 Jacobi inner solves (dc.cu).
+size_t dc_workspace_bytes(long long nx, long long ny);
+cudaError_t dc_persistent(const Problem &p, LoopArgs la, int inner, void *fp32_area, cudaStream_t st);
 // The separate reduce kernel of the host-driven loop: delta between two
 // states (and the mask), reduced into *slot.
 cudaError_t reduce_states(const Problem &p, const void *src, const void *dst, const void *aux,

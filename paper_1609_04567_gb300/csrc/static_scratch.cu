@@ -68,7 +68,7 @@ slr_status slr_run_static(const slr_desc *d, void *u, const void *f, int64_t max
     bool unsup = false;
     const std::string why = slr::describe_invalid(d, &unsup);
     if (!why.empty()) return static_fail(unsup ? SLR_ERR_UNSUPPORTED : SLR_ERR_INVALID_ARG, why);
-    if (d->stencil != SLR_J2D5 && d->stencil != SLR_J3D7)
+    if ((d->stencil != SLR_J2D5 && d->stencil != SLR_J3D7) || d->defect_correction)
         return static_fail(SLR_ERR_UNSUPPORTED, "slr_run_static runs the Jacobi stencils (SLR_J2D5, SLR_J3D7) only");
     if (!u || ((uintptr_t)u & 15u)) return static_fail(SLR_ERR_INVALID_ARG, "u must be a 16-byte aligned device pointer");
     if (!f) return static_fail(SLR_ERR_INVALID_ARG, "f is required");

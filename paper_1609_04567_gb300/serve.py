@@ -1,0 +1,216 @@
+"""Continuous-batching serving loop over the batched persistent launch.
+
+Requests (restoration "denoise" jobs and 2D Helmholtz "solve" jobs of mixed
+sizes) arrive as a Poisson process.  The server keeps ONE resident batch
+(``slr.Batch``): each loop iteration admits every request that has arrived,
+for which device memory and a batch slot are free, runs a bounded number of
+sweeps of everything in the batch (one persistent launch), and retires the
+requests whose loops stopped.  A request that arrives while others are on the
+GPU joins them at the next iteration; its work overlaps theirs in the same
+launch.  This is the stream composition of Sec. 4.3 (read, restore, write over
+a stream of frames) served on one GPU, with latency measured per request.
+
+Admission is by device memory: a request needs its state, its auxiliary input
+(f or mask) and one scratch buffer; it is admitted only while the sum of the
+footprints of admitted requests stays inside the budget (by default a fraction
+of the free memory reported by the driver at start-up).
+"""
+from __future__ import annotations
+
+import math
+import time
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from . import inputs, slr
+
+KIND_DENOISE, KIND_SOLVE = "denoise", "solve"
+
+
+@dataclass
+class Request:
+    rid: int
+    kind: str
+    side: int
+    arrival: float                 # seconds after the start of the run
+    seed: int = 0
+    admitted: float | None = None
+    finished: float | None = None
+    iters: int = 0
+    converged: bool = False
+    value: float = 0.0
+    slot: int = -1
+    tensors: tuple = field(default=(), repr=False)
+
+
+def bucket_sides(lo: int, hi: int, n: int) -> list[int]:
+    """n log-spaced sides in [lo, hi] (rounded to multiples of 8)."""
+    return sorted({int(round(math.exp(math.log(lo) + i * (math.log(hi) - math.log(lo)) / (n - 1)) / 8.0)) * 8
+                   for i in range(n)})
+
+
+def make_requests(duration_s: float, rate: float, *, seed: int = inputs.DEFAULT_SEED, denoise_share: float = 0.5,
+                  denoise_sides=(256, 4096), solve_sides=(64, 2048), buckets: int = 8) -> list[Request]:
+    """Poisson arrivals at `rate` per second for `duration_s` seconds; each
+    request is a denoise job with probability `denoise_share`, else a solve;
+    sides are log-uniform over a set of `buckets` log-spaced sizes."""
+    n_max = int(rate * duration_s * 1.5) + 16
+    gaps = inputs.exp_gaps(n_max, rate, seed=seed)
+    arrivals = np.cumsum(gaps)
+    arrivals = arrivals[arrivals < duration_s]
+    u = inputs.uniform01(seed, inputs.STREAM_ARRIVALS + 1, 2 * len(arrivals)).reshape(-1, 2)
+    dsides, ssides = bucket_sides(*denoise_sides, buckets), bucket_sides(*solve_sides, buckets)
+    reqs = []
+    for i, t in enumerate(arrivals):
+        if u[i, 0] < denoise_share:
+            reqs.append(Request(i, KIND_DENOISE, dsides[min(int(u[i, 1] * len(dsides)), len(dsides) - 1)], float(t)))
+        else:
+            reqs.append(Request(i, KIND_SOLVE, ssides[min(int(u[i, 1] * len(ssides)), len(ssides) - 1)], float(t)))
+    return reqs
+
+
+class InputPool:
+    """Pinned host inputs per (kind, side): the synthetic frames and
+    right-hand sides of the workload, generated once."""
+
+    def __init__(self, seed: int = inputs.DEFAULT_SEED):
+        self.seed = seed
+        self.cache = {}
+
+    def get(self, kind: str, side: int):
+        import torch
+        key = (kind, side)
+        if key not in self.cache:
+            if kind == KIND_DENOISE:
+                frame, _ = inputs.noisy_frame(side, side, seed=self.seed + side)
+                mask = inputs.noise_mask(frame)
+                self.cache[key] = (torch.from_numpy(frame.astype(np.float32)).pin_memory(),
+                                   torch.from_numpy(mask).pin_memory())
+            else:
+                f = inputs.helmholtz_rhs((side, side), seed=self.seed + side)
+                self.cache[key] = (torch.zeros((side, side), dtype=torch.float64).pin_memory(),
+                                   torch.from_numpy(f).pin_memory())
+        return self.cache[key]
+
+
+def footprint(kind: str, side: int) -> int:
+    cells = side * side
+    return cells * (4 + 1 + 4) if kind == KIND_DENOISE else cells * (8 + 8 + 8)
+
+
+@dataclass
+class ServeStats:
+    requests: int
+    completed: int
+    wall_s: float
+    p50_ms: float
+    p99_ms: float
+    mean_ms: float
+    throughput_rps: float
+    cell_updates: float
+    gcell_per_s: float
+    steps: int
+    max_in_flight: int
+    max_queue: int
+    budget_bytes: int
+
+
+class Server:
+    """One resident batch served with continuous batching."""
+
+    def __init__(self, *, max_slots: int = 1024, budget_bytes: int | None = None, step_sweeps: int = 32,
+                 denoise_tol: float = 1e-3, solve_tol: float = 1e-6, cap: int = 5000, device=None):
+        import torch
+        self.torch = torch
+        self.device = torch.device(device or "cuda")
+        self.stream = torch.cuda.Stream(self.device)
+        self.batch = slr.Batch(max_slots, device=self.device, stream=self.stream)
+        self.max_slots = max_slots
+        if budget_bytes is None:
+            free, _ = torch.cuda.mem_get_info(self.device)
+            budget_bytes = int(free * 0.6)
+        self.budget = budget_bytes
+        self.in_use = 0
+        self.step_sweeps = step_sweeps
+        self.tol = {KIND_DENOISE: denoise_tol, KIND_SOLVE: solve_tol}
+        self.cap = cap
+        self.pool = InputPool()
+        self.active = {}
+
+    def admit(self, r: Request, now: float) -> bool:
+        need = footprint(r.kind, r.side)
+        if len(self.active) >= self.max_slots or self.in_use + need > self.budget:
+            return False
+        torch = self.torch
+        host_u, host_aux = self.pool.get(r.kind, r.side)
+        with torch.cuda.stream(self.stream):
+            u = torch.empty(host_u.shape, dtype=host_u.dtype, device=self.device)
+            aux = torch.empty(host_aux.shape, dtype=host_aux.dtype, device=self.device)
+            u.copy_(host_u, non_blocking=True)
+            aux.copy_(host_aux, non_blocking=True)
+            stencil = slr.SLR_RESTORE8 if r.kind == KIND_DENOISE else slr.SLR_J2D5
+            r.slot = self.batch.add(stencil, u, aux, self.cap, tol=self.tol[r.kind])
+        r.tensors = (u, aux)
+        r.admitted = now
+        self.in_use += need
+        self.active[r.slot] = r
+        return True
+
+    def retire(self, slot: int, now: float, keep: bool) -> Request:
+        r = self.active.pop(slot)
+        res = self.batch.result(slot)
+        r.finished, r.iters, r.converged, r.value = now, res.iters, res.converged, res.value
+        self.batch.remove(slot)
+        self.in_use -= footprint(r.kind, r.side)
+        if not keep:
+            r.tensors = ()
+        return r
+
+    def serve(self, requests: list[Request], *, warmup_s: float = 0.0, keep_results: bool = False,
+              time_limit_s: float | None = None) -> ServeStats:
+        """Serve `requests` in real time (arrival offsets from now).  Latency
+        is arrival -> the poll that sees the request's loop stopped."""
+        for r in requests:
+            self.pool.get(r.kind, r.side)          # inputs ready before the clock starts
+        pending = sorted(requests, key=lambda r: r.arrival)
+        done: list[Request] = []
+        qi = 0
+        queue: list[Request] = []
+        steps = max_in_flight = max_queue = 0
+        t0 = time.perf_counter()
+        while qi < len(pending) or queue or self.active:
+            now = time.perf_counter() - t0
+            if time_limit_s is not None and now > time_limit_s:
+                break
+            while qi < len(pending) and pending[qi].arrival <= now:
+                queue.append(pending[qi])
+                qi += 1
+            while queue and self.admit(queue[0], now):
+                queue.pop(0)
+            max_queue = max(max_queue, len(queue))
+            max_in_flight = max(max_in_flight, len(self.active))
+            if not self.active:
+                if qi < len(pending):
+                    time.sleep(max(0.0, min(pending[qi].arrival - now, 0.001)))
+                continue
+            self.batch.run(self.step_sweeps)
+            finished, _ = self.batch.poll()
+            steps += 1
+            now = time.perf_counter() - t0
+            for s in finished:
+                done.append(self.retire(s, now, keep_results))
+        wall = time.perf_counter() - t0
+        self.done = done
+        measured = [r for r in done if r.arrival >= warmup_s]
+        lat = np.array([(r.finished - r.arrival) * 1e3 for r in measured]) if measured else np.zeros(1)
+        cells = float(sum(r.side * r.side * r.iters for r in done))
+        span = max(wall - warmup_s, 1e-9)
+        return ServeStats(
+            requests=len(requests), completed=len(done), wall_s=wall,
+            p50_ms=float(np.percentile(lat, 50)), p99_ms=float(np.percentile(lat, 99)), mean_ms=float(lat.mean()),
+            throughput_rps=len(measured) / span, cell_updates=cells, gcell_per_s=cells / wall / 1e9,
+            steps=steps, max_in_flight=max_in_flight, max_queue=max_queue, budget_bytes=self.budget)
+
+    def close(self):
+        self.batch.close()

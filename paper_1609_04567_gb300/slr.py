@@ -38,7 +38,8 @@ class slr_desc(ctypes.Structure):
         ("ghost", ctypes.c_double), ("tol", ctypes.c_double), ("sigma", ctypes.c_double),
         ("h", ctypes.c_double), ("alpha", ctypes.c_float),
         ("loop", ctypes.c_int32), ("math", ctypes.c_int32), ("temporal_k", ctypes.c_int32),
-        ("wait_limit_ns", ctypes.c_int64), ("debug_flags", ctypes.c_int32), ("reserved", ctypes.c_int32),
+        ("wait_limit_ns", ctypes.c_int64), ("debug_flags", ctypes.c_int32),
+        ("defect_correction", ctypes.c_int32), ("inner_sweeps", ctypes.c_int32), ("reserved", ctypes.c_int32),
     ]
 
 

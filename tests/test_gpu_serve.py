@@ -1,0 +1,58 @@
+"""Continuous-batching serving loop: requests that arrive while others run are
+admitted into the resident batch as memory and slots free up; every result
+must equal the result of the same request solved alone."""
+import numpy as np
+import pytest
+import torch
+
+pytestmark = pytest.mark.gpu
+
+
+def solve_alone(slr, r, server):
+    host_u, host_aux = server.pool.get(r.kind, r.side)
+    u = host_u.clone().cuda()
+    aux = host_aux.clone().cuda()
+    stencil = slr.SLR_RESTORE8 if r.kind == "denoise" else slr.SLR_J2D5
+    s = slr.Solver(stencil, u, aux, tol=server.tol[r.kind])
+    s.run(server.cap)
+    res = s.result()
+    s.close()
+    return u, res
+
+
+def test_results_alone_equal_results_in_the_mix(gpu):
+    from paper_1609_04567_gb300 import serve
+    reqs = serve.make_requests(0.4, 300.0, seed=3, denoise_sides=(32, 256), solve_sides=(16, 128), buckets=5)
+    assert len(reqs) > 60
+    srv = serve.Server(max_slots=64, step_sweeps=8)
+    stats = srv.serve(reqs, keep_results=True)
+    assert stats.completed == len(reqs)
+    assert stats.max_in_flight > 1                     # work really overlapped in the batch
+    done = {r.rid: r for r in srv.done}
+    for r in list(done.values())[::7]:
+        u_alone, res = solve_alone(gpu, r, srv)
+        assert (r.iters, r.converged) == (res.iters, res.converged)
+        assert torch.equal(r.tensors[0], u_alone)
+        assert r.value == res.value
+    srv.close()
+
+
+def test_admission_respects_the_memory_budget(gpu):
+    from paper_1609_04567_gb300 import serve
+    reqs = serve.make_requests(0.2, 400.0, seed=4, denoise_sides=(64, 256), solve_sides=(32, 128), buckets=4)
+    budget = 2 * serve.footprint("denoise", 256)
+    srv = serve.Server(max_slots=32, step_sweeps=16, budget_bytes=budget)
+    peak = 0
+    orig = srv.admit
+
+    def watched(r, now):
+        nonlocal peak
+        ok = orig(r, now)
+        peak = max(peak, srv.in_use)
+        return ok
+    srv.admit = watched
+    stats = srv.serve(reqs)
+    assert stats.completed == len(reqs)
+    assert 0 < peak <= budget
+    assert stats.p99_ms >= stats.p50_ms > 0
+    srv.close()
