@@ -82,7 +82,7 @@ def recorded_traffic(workload: str, k: int):
     if not e or e.get("kernel_hash") != kernel_hash():
         return None
     gens = int(workload.rsplit("_", 1)[-1].replace("gens", ""))
-    return float(e["dram_bytes_per_pass"]) * (-(-gens // k))
+    return float(e.get("fixed_bytes", 0.0)) + float(e["dram_bytes_per_pass"]) * (-(-gens // k))
 
 
 class ClockSampler:
@@ -319,6 +319,26 @@ def run_ours(args, wl, world, rank, local):
                  "what": "host-driven loop: per generation one sweep launch, one reduce launch, "
                          "a D2H copy of the reduced value and the test on the host"}
 
+    # the same fused kernel family with one generation per pass (k = 1): the
+    # "fused + device loop" column next to "fused + k-blocking" (the default)
+    fused_k1 = None
+    if not args.no_plain and args.k != 1:
+        with torch.cuda.stream(stream):
+            saved_k = desc.temporal_k
+            desc.temporal_k = 1
+            k1_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(2)]
+            step()                                     # warm-up of the k = 1 kernel
+            hs = [step(k1_ev[i]) for i in range(2)]
+            torch.cuda.synchronize(dev)
+            k1_ms = statistics.mean(a.elapsed_time(b) for a, b in k1_ev)
+            k1r = slr.slr_reduce_value(hs[-1])
+            for h in hs:
+                slr.slr_destroy(h)
+            desc.temporal_k = saved_k
+        fused_k1 = {"value": cell_updates / (k1_ms / 1e3) / 1e9, "unit": "Gcell-updates/s", "kernel_ms": k1_ms,
+                    "same_result": k1r[1:] == res[1:],
+                    "what": "one generation per pass: uint8 grid read and written every generation"}
+
     # end to end through the C ABI with host buffers: pinned H2D of the input,
     # the solve, D2H of the final state and of the reduced value, every step
     host_in = torch.from_numpy(cells).pin_memory()
@@ -363,6 +383,7 @@ def run_ours(args, wl, world, rank, local):
             "cpu_baseline": cpu,
             "e2e": e2e,
             "plain": plain,
+            "fused_k1": fused_k1,
             "gpu_launches": 2 * args.steps,
             "clocks": clk,
             "result": {"iters": res[2], "live": res[4], "converged": res[3],

@@ -57,6 +57,7 @@ constexpr int kBoxBytes = kBoxW * kPackRows;          // 4096
 constexpr int kStageBytes = kBoxes * kBoxBytes;       // 32768
 constexpr size_t kSmemBytes = 1024 + 2 * kStageBytes + kXchWords * 4 + 2 * 8 + kMaxK * 8 + kMaxK * 4;
 static_assert((kXchWords * 4) % 8 == 0, "mbarriers must stay 8-byte aligned");
+static_assert(kMaxK == 32, "one lane per generation in the per-pass decision");
 
 struct TbParams {
     CUtensorMap cells;           // uint8 view of the caller's grid (box 128 x 32, 128B swizzle)
@@ -382,26 +383,27 @@ __global__ void __launch_bounds__(kThreads, 2) life_tb_kernel(const __grid_const
         bar_target += (unsigned long long)la.nblocks;
         if (!grid_barrier(ctl, bar_target, la.limit_ns)) return;
         cur ^= 1;
-        if (tid == 0) {
-            if (blockIdx.x == 0)
-                for (int j = 0; j < kMaxK; ++j) zero_slot(&ctl->sub[(p + 2) % kSlots][j]);
+        if (tid < 32) {
+            if (blockIdx.x == 0) zero_slot(&ctl->sub[(p + 2) % kSlots][tid]);
             // a generation that changed nothing is a still state, a fixed
-            // point: the state (and live count) at the end of the pass equal it
-            int jstop = -1;
-            for (int j = 0; j < kp; ++j) {
-                if (!read_slot(&ctl->sub[p % kSlots][j]).changed) { jstop = j; break; }
-            }
-            const Slot sj = read_slot(&ctl->sub[p % kSlots][kp - 1]);
+            // point: the state (and live count) at the end of the pass equal it.
+            // Lane j reads generation j's flag; the first unchanged one wins.
+            const bool unchanged = tid < kp && ld_relaxed_u32(&ctl->sub[p % kSlots][tid].changed) == 0u;
+            const unsigned still = __ballot_sync(0xffffffffu, unchanged);
+            const int jstop = still ? __ffs(still) - 1 : -1;
+            const unsigned long long cnt = ld_relaxed_u64(&ctl->sub[p % kSlots][kp - 1].cnt);
             const long long itn = jstop >= 0 ? it + jstop + 1 : it + kp;
             const int conv = jstop >= 0;
-            s_stop = conv || itn >= la.max_iters;
-            s_it = itn;
-            if (s_stop && blockIdx.x == 0) {
-                ctl->iters = itn;
-                ctl->value = (double)sj.cnt;
-                ctl->count = sj.cnt;
-                ctl->changed = !conv;
-                ctl->converged = conv;
+            if (tid == 0) {
+                s_stop = conv || itn >= la.max_iters;
+                s_it = itn;
+                if ((conv || itn >= la.max_iters) && blockIdx.x == 0) {
+                    ctl->iters = itn;
+                    ctl->value = (double)cnt;
+                    ctl->count = cnt;
+                    ctl->changed = !conv;
+                    ctl->converged = conv;
+                }
             }
         }
         __syncthreads();

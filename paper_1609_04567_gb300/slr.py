@@ -338,6 +338,9 @@ class Solver:
         self.stream = stream if stream is not None else torch.cuda.current_stream(u.device)
         ws = slr_workspace_size(self.desc)
         if ws == 0:
+            # the library's own checks name the problem (invalid or unsupported)
+            slr_create(self.desc, u.data_ptr(), aux.data_ptr() if aux is not None else 0, 0, 0,
+                       self.stream.cuda_stream)
             raise SlrError(SLR_ERR_INVALID_ARG, "invalid descriptor")
         self.ws = torch.empty(ws + 256, dtype=torch.uint8, device=u.device)
         off = (-self.ws.data_ptr()) % 256
