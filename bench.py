@@ -384,7 +384,7 @@ def run_ours(args, wl, world, rank, local):
             "e2e": e2e,
             "plain": plain,
             "fused_k1": fused_k1,
-            "gpu_launches": 2 * args.steps,
+            "gpu_launches": args.steps,
             "clocks": clk,
             "result": {"iters": res[2], "live": res[4], "converged": res[3],
                        "same_as_warmup": first[1:] == res[1:]},
@@ -539,16 +539,17 @@ def run_batch(args):
         def batch_step():
             for _, u in grids:
                 u.zero_()
-            slots = [b.add(slr.SLR_J3D7 if u.dim() == 3 else slr.SLR_J2D5, u, f, 100000, tol=1e-6) for f, u in grids]
+            slots = [b.add(slr.SLR_J3D7 if u.dim() == 3 else slr.SLR_J2D5, u, f, 5000, tol=1e-6) for f, u in grids]
             b.run(100000)
             fin, running = b.poll()
             its = [b.result(s).iters for s in slots]
+            conv = [b.result(s).converged for s in slots]
             for s in slots:
                 b.remove(s)
-            return its
+            return its, conv
         batch_step()
         t0 = time.perf_counter()
-        its = batch_step()
+        its, conv = batch_step()
         torch.cuda.synchronize()
         batch_s = time.perf_counter() - t0
     upd = float(sum(c * i for c, i in zip(cells, its)))
@@ -559,7 +560,7 @@ def run_batch(args):
         for f, u in grids:
             u.zero_()
             s = slr.Solver(slr.SLR_J3D7 if u.dim() == 3 else slr.SLR_J2D5, u, f, stream=stream, tol=1e-6)
-            s.run(100000)
+            s.run(5000)
             seq_its.append(s.result().iters)
             s.close()
     torch.cuda.synchronize()
@@ -567,7 +568,9 @@ def run_batch(args):
     line = {"workload": f"batch_512x2d_bf16_side64-1024_plus_{n3}^3_tol1e-6", "metric": "Gcell-updates/s",
             "unit": "Gcell-updates/s", "value": upd / batch_s / 1e9, "batch_s": batch_s,
             "sequential_s": seq_s, "sequential_gcell_per_s": upd / seq_s / 1e9, "same_iters": its == seq_its,
-            "cell_updates": upd, "grids": len(grids), "max_sweeps": max(its), "min_sweeps": min(its)}
+            "cell_updates": upd, "grids": len(grids), "max_sweeps": max(its), "min_sweeps": min(its),
+            "converged": int(sum(conv)), "capped_at_5000": int(len(conv) - sum(conv)),
+            "note": "bfloat16 storage can trap Jacobi in a +-1 ulp cycle that never meets tol; such grids stop at the cap"}
     print(json.dumps(line), flush=True)
     b.close()
     return 0

@@ -138,9 +138,27 @@ __device__ __forceinline__ typename St<T>::C at(const BInst &I, const void *u, l
     return St<T>::ld(u, (k * I.ny + i) * I.nx + j);
 }
 
+// Per-warp staging of a unit's plane tile with a one-cell halo: (kTileH + 2)
+// rows x (kTileW + 2) columns in the compute type, boundary values applied
+// while loading (ghost or wrapped neighbour).  Every lane issues its loads
+// before any is used, so one warp keeps ~36 loads in flight.
+constexpr int kSW = kTileW + 2, kSH = kTileH + 2;
+
+template <class T>
+__device__ __forceinline__ void stage_tile(const BInst &I, const void *u, long long k, long long y0, long long x0,
+                                           typename St<T>::C *tile, typename St<T>::C ghost)
+{
+    const int lane = threadIdx.x & 31;
+    for (int r = 0; r < kSH; ++r) {
+        const long long i = y0 - 1 + r;
+        for (int c = lane; c < kSW; c += 32) tile[r * kSW + c] = at<T>(I, u, k, i, x0 - 1 + c, ghost);
+    }
+    __syncwarp();
+}
+
 // One warp unit of a Jacobi instance; returns the unit's max |delta| bits.
 template <class T, int DIM>
-__device__ unsigned long long jacobi_unit(const BInst &I, long long unit, const void *u, void *v)
+__device__ unsigned long long jacobi_unit(const BInst &I, long long unit, const void *u, void *v, void *stage)
 {
     using C = typename St<T>::C;
     const int lane = threadIdx.x & 31;
@@ -150,6 +168,8 @@ __device__ unsigned long long jacobi_unit(const BInst &I, long long unit, const 
     const C ghost = sizeof(C) == 8 ? (C)I.ghost : (C)I.ghostf;
     const C h2 = sizeof(C) == 8 ? (C)I.h2 : (C)I.h2f;
     const C d = sizeof(C) == 8 ? (C)I.d : (C)I.df;
+    C *tile = (C *)stage;
+    stage_tile<T>(I, u, k, ty * kTileH, tx * kTileW, tile, ghost);
     unsigned long long mx = 0ull;
     for (int r = 0; r < kTileH; ++r) {
         const long long i = ty * kTileH + r;
@@ -158,64 +178,90 @@ __device__ unsigned long long jacobi_unit(const BInst &I, long long unit, const 
             const long long j = tx * kTileW + c;
             if (j >= I.nx) continue;
             const long long idx = (k * I.ny + i) * I.nx + j;
-            const C uc = St<T>::ld(u, idx);
+            const C *t = tile + (r + 1) * kSW + (c + 1);
+            const C uc = t[0];
             C s;
             if (DIM == 2) {
-                s = add_rn(add_rn(add_rn(at<T>(I, u, k, i - 1, j, ghost), at<T>(I, u, k, i + 1, j, ghost)),
-                                  at<T>(I, u, k, i, j - 1, ghost)),
-                           at<T>(I, u, k, i, j + 1, ghost));
+                s = add_rn(add_rn(add_rn(t[-kSW], t[kSW]), t[-1]), t[1]);
             } else {
-                s = add_rn(add_rn(add_rn(add_rn(add_rn(at<T>(I, u, k, i, j - 1, ghost), at<T>(I, u, k, i, j + 1, ghost)),
-                                                at<T>(I, u, k, i - 1, j, ghost)),
-                                         at<T>(I, u, k, i + 1, j, ghost)),
-                                  at<T>(I, u, k - 1, i, j, ghost)),
+                s = add_rn(add_rn(add_rn(add_rn(add_rn(t[-1], t[1]), t[-kSW]), t[kSW]), at<T>(I, u, k - 1, i, j, ghost)),
                            at<T>(I, u, k + 1, i, j, ghost));
             }
-            const C t = mul_rn(h2, St<T>::ldf(I.aux, idx));
-            const C stored = St<T>::put(v, idx, div_rn(add_rn(t, s), d));
+            const C tt = mul_rn(h2, St<T>::ldf(I.aux, idx));
+            const C stored = St<T>::put(v, idx, div_rn(add_rn(tt, s), d));
             const unsigned long long b = abs_bits(sub_rn(stored, uc));
             mx = b > mx ? b : mx;
         }
     }
+    __syncwarp();                                   // the stage is reused by the warp's next unit
     return mx;
 }
 
-// One warp unit of a restoration instance; returns (fixed-point sum, masked count).
-__device__ void restore_unit(const BInst &I, long long unit, const void *uv, void *vv, unsigned long long &sum,
-                             unsigned long long &cnt)
+// One warp unit of a restoration instance; returns (fixed-point sum, masked
+// count).  Clean pixels are copied; the noisy pixels of each 4-row band are
+// gathered with ballots and processed 32 at a time, so the weight arithmetic
+// runs on full warps.
+__device__ void restore_unit(const BInst &I, long long unit, const void *uv, void *vv, void *stage,
+                             unsigned long long &sum, unsigned long long &cnt)
 {
-    const float *u = (const float *)uv;
     float *v = (float *)vv;
     const unsigned char *mask = (const unsigned char *)I.aux;
     const int lane = threadIdx.x & 31;
     const long long ty = unit / I.tiles_x, tx = unit - ty * I.tiles_x;
-    for (int r = 0; r < kTileH; ++r) {
-        const long long i = ty * kTileH + r;
-        if (i >= I.ny) break;
-        for (int c = lane; c < kTileW; c += 32) {
-            const long long j = tx * kTileW + c;
-            if (j >= I.nx) continue;
-            const long long idx = i * I.nx + j;
-            const float uc = __ldcg(u + idx);
-            if (!__ldg(mask + idx)) { v[idx] = uc; continue; }
+    const long long y0 = ty * kTileH, x0 = tx * kTileW;
+    float *tile = (float *)stage;
+    stage_tile<float>(I, uv, 0, y0, x0, tile, 0.0f);
+    for (int band = 0; band < kTileH / 4; ++band) {
+        unsigned masks[8];
+#pragma unroll
+        for (int h = 0; h < 8; ++h) {
+            const int rr = band * 4 + (h >> 1), cc = (h & 1) * 32 + lane;
+            const long long y = y0 + rr, x = x0 + cc;
+            const bool valid = y < I.ny && x < I.nx;
+            const bool noisy = valid && __ldg(mask + y * I.nx + x) != 0;
+            if (valid && !noisy) v[y * I.nx + x] = tile[(rr + 1) * kSW + cc + 1];
+            masks[h] = __ballot_sync(0xffffffffu, noisy);
+        }
+        int total = 0;
+#pragma unroll
+        for (int h = 0; h < 8; ++h) total += __popc(masks[h]);
+        for (int first = 0; first < total; first += 32) {
+            const int t = first + lane;
+            if (t >= total) continue;
+            int h = 0, before = 0;
+#pragma unroll
+            for (int g = 0; g < 7; ++g) {
+                const int c = __popc(masks[g]);
+                if (h == g && t >= before + c) { before += c; h = g + 1; }
+            }
+            unsigned mh = 0u;
+#pragma unroll
+            for (int g = 0; g < 8; ++g)
+                if (g == h) mh = masks[g];
+            const unsigned fb = __fns(mh, 0u, t - before + 1);   // bit of the (t - before)-th noisy pixel
+            if (fb > 31u) continue;                                // cannot happen: t < total
+            const int bit = (int)fb;
+            const int rr = band * 4 + (h >> 1), cc = (h & 1) * 32 + bit;
+            const long long y = y0 + rr, x = x0 + cc;
+            const float uc = tile[(rr + 1) * kSW + cc + 1];
             float num = 0.0f, den = 0.0f;
             for (int di = -1; di <= 1; ++di)
                 for (int dj = -1; dj <= 1; ++dj) {
                     if (di == 0 && dj == 0) continue;
-                    const long long y = i + di, x = j + dj;
-                    if (y < 0 || y >= I.ny || x < 0 || x >= I.nx) continue;
-                    const float uj = __ldcg(u + y * I.nx + x);
-                    const float t = __fsub_rn(uc, uj);
-                    const float w = __fdiv_rn(1.0f, __fsqrt_rn(__fadd_rn(I.alpha, __fmul_rn(t, t))));
+                    if (y + di < 0 || y + di >= I.ny || x + dj < 0 || x + dj >= I.nx) continue;
+                    const float uj = tile[(rr + 1 + di) * kSW + cc + 1 + dj];
+                    const float tt = __fsub_rn(uc, uj);
+                    const float w = __fdiv_rn(1.0f, __fsqrt_rn(__fadd_rn(I.alpha, __fmul_rn(tt, tt))));
                     num = __fadd_rn(num, __fmul_rn(w, uj));
                     den = __fadd_rn(den, w);
                 }
             const float nv = den > 0.0f ? __fdiv_rn(num, den) : uc;
-            v[idx] = nv;
+            v[y * I.nx + x] = nv;
             sum += (unsigned long long)__double2ull_rz((double)fabsf(__fsub_rn(nv, uc)) * 16777216.0);
             cnt += 1ull;
         }
     }
+    __syncwarp();
 }
 
 __device__ void unit_copy(const BInst &I, long long unit, const void *src, void *dst)
@@ -244,23 +290,26 @@ __device__ __forceinline__ int find_instance(const long long *prefix, int n, lon
     int lo = 0, hi = n;     // prefix[lo] <= u < prefix[hi]
     while (hi - lo > 1) {
         const int mid = (lo + hi) >> 1;
-        if (prefix[mid] <= u) lo = mid; else hi = mid;
+        if (__ldg(prefix + mid) <= u) lo = mid; else hi = mid;
     }
     return lo;
 }
 
-__global__ void __launch_bounds__(kBThreads) batch_kernel(BatchArgs ba)
+constexpr size_t kStageBytesPerWarp = (size_t)kSW * kSH * 8;      // binary64 worst case
+
+__global__ void __launch_bounds__(kBThreads, 2) batch_kernel(BatchArgs ba)
 {
     extern __shared__ unsigned char smem_raw[];
-    long long *s_prefix = (long long *)smem_raw;             // [nact + 1]
-    long long *s_iters0 = s_prefix + (ba.nact + 1);           // [nact]
-    int *s_stop = (int *)(s_iters0 + ba.nact);                // [nact]: sweep index of the stop, -1 running
+    unsigned char *stage = smem_raw + (size_t)(threadIdx.x >> 5) * kStageBytesPerWarp;
+    unsigned char *tail = smem_raw + (size_t)(kBThreads / 32) * kStageBytesPerWarp;
+    long long *s_iters0 = (long long *)tail;                      // [nact]
+    int *s_stop = (int *)(s_iters0 + ba.nact);                    // [nact]: sweep index of the stop, -1 running
     unsigned char *s_par0 = (unsigned char *)(s_stop + ba.nact);  // [nact]
+    const long long *s_prefix = ba.prefix;                         // read-only during the launch
     __shared__ int s_alive;
 
     const int tid = threadIdx.x, lane = tid & 31;
     const int n = ba.nact;
-    for (int i = tid; i <= n; i += kBThreads) s_prefix[i] = ba.prefix[i];
     for (int i = tid; i < n; i += kBThreads) {
         const BInst &I = ba.inst[ba.act[i]];
         s_iters0[i] = I.iters;
@@ -268,7 +317,7 @@ __global__ void __launch_bounds__(kBThreads) batch_kernel(BatchArgs ba)
         s_stop[i] = I.done ? -2 : -1;
     }
     __syncthreads();
-    const long long U = s_prefix[n];
+    const long long U = __ldg(s_prefix + n);
     const long long warps = (long long)gridDim.x * (kBThreads / 32);
     const long long gw = (long long)blockIdx.x * (kBThreads / 32) + (tid >> 5);
     long long s = 0;
@@ -277,14 +326,14 @@ __global__ void __launch_bounds__(kBThreads) batch_kernel(BatchArgs ba)
             const int ai = find_instance(s_prefix, n, u);
             if (s_stop[ai] != -1) continue;
             const BInst &I = ba.inst[ba.act[ai]];
-            const long long unit = u - s_prefix[ai];
+            const long long unit = u - __ldg(s_prefix + ai);
             const int par = (s_par0[ai] + (int)s) & 1;
             const void *src = par ? I.b : I.a;
             void *dst = par ? I.a : I.b;
             Slot *slot = &ba.slots[(size_t)ba.act[ai] * kSlots + (size_t)(s % kSlots)];
             if (I.stencil == SLR_RESTORE8) {
                 unsigned long long sum = 0ull, cnt = 0ull;
-                restore_unit(I, unit, src, dst, sum, cnt);
+                restore_unit(I, unit, src, dst, stage, sum, cnt);
 #pragma unroll
                 for (int o = 16; o > 0; o >>= 1) {
                     sum += __shfl_xor_sync(0xffffffffu, sum, o);
@@ -299,12 +348,12 @@ __global__ void __launch_bounds__(kBThreads) batch_kernel(BatchArgs ba)
                 unsigned long long mx = 0ull;
                 const bool d3 = I.stencil == SLR_J3D7;
                 switch (I.storage) {
-                case SLR_F64: mx = d3 ? jacobi_unit<double, 3>(I, unit, src, dst) : jacobi_unit<double, 2>(I, unit, src, dst); break;
-                case SLR_F32: mx = d3 ? jacobi_unit<float, 3>(I, unit, src, dst) : jacobi_unit<float, 2>(I, unit, src, dst); break;
+                case SLR_F64: mx = d3 ? jacobi_unit<double, 3>(I, unit, src, dst, stage) : jacobi_unit<double, 2>(I, unit, src, dst, stage); break;
+                case SLR_F32: mx = d3 ? jacobi_unit<float, 3>(I, unit, src, dst, stage) : jacobi_unit<float, 2>(I, unit, src, dst, stage); break;
                 case SLR_BF16:
-                    mx = d3 ? jacobi_unit<__nv_bfloat16, 3>(I, unit, src, dst) : jacobi_unit<__nv_bfloat16, 2>(I, unit, src, dst);
+                    mx = d3 ? jacobi_unit<__nv_bfloat16, 3>(I, unit, src, dst, stage) : jacobi_unit<__nv_bfloat16, 2>(I, unit, src, dst, stage);
                     break;
-                default: mx = d3 ? jacobi_unit<__half, 3>(I, unit, src, dst) : jacobi_unit<__half, 2>(I, unit, src, dst); break;
+                default: mx = d3 ? jacobi_unit<__half, 3>(I, unit, src, dst, stage) : jacobi_unit<__half, 2>(I, unit, src, dst, stage); break;
                 }
 #pragma unroll
                 for (int o = 16; o > 0; o >>= 1) {
@@ -363,7 +412,7 @@ __global__ void __launch_bounds__(kBThreads) batch_kernel(BatchArgs ba)
         if (s_stop[ai] < 0) continue;
         if (((s_par0[ai] + s_stop[ai] + 1) & 1) == 0) continue;   // final state already in a
         const BInst &I = ba.inst[ba.act[ai]];
-        unit_copy(I, u - s_prefix[ai], I.b, I.a);
+        unit_copy(I, u - __ldg(s_prefix + ai), I.b, I.a);
     }
 }
 
@@ -561,7 +610,8 @@ slr_status slr_batch_run(slr_batch b, int64_t sweeps)
     ba.sweeps = sweeps;
     ba.ctl = (slr::Ctl *)b->ws;
     ba.limit_ns = 2000000000ll;
-    const size_t smem = (size_t)(ba.nact + 1) * 8 + (size_t)ba.nact * 8 + (size_t)ba.nact * 4 + (size_t)ba.nact;
+    const size_t smem = (size_t)(slr::kBThreads / 32) * slr::kStageBytesPerWarp + (size_t)ba.nact * 8 +
+                        (size_t)ba.nact * 4 + (size_t)ba.nact;
     e = cudaFuncSetAttribute(slr::batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return bcuda(b, e, "batch kernel attributes");
     int dev = 0, sms = 0, per_sm = 0;

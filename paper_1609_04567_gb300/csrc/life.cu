@@ -190,10 +190,27 @@ __global__ void __launch_bounds__(kLifeThreads, 1) life_sweep_kernel(Op op, cons
     op.template sweep<false>(src, dst, nullptr);
 }
 
+// Any non-zero byte becomes 1 (16 bytes per thread and step where aligned).
 __global__ void life_normalize_kernel(unsigned char *u, size_t n)
 {
     const size_t tid = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    for (size_t i = tid; i < n; i += (size_t)gridDim.x * blockDim.x) u[i] = u[i] != 0;
+    const size_t nthr = (size_t)gridDim.x * blockDim.x;
+    const size_t n16 = ((uintptr_t)u & 15u) ? 0 : n / 16;
+    uint4 *u4 = (uint4 *)u;
+    for (size_t i = tid; i < n16; i += nthr) {
+        uint4 v = u4[i];
+        uint32_t *w = &v.x;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            uint32_t x = w[k];
+            x |= x >> 4;
+            x |= x >> 2;
+            x |= x >> 1;
+            w[k] = x & 0x01010101u;
+        }
+        u4[i] = v;
+    }
+    for (size_t i = n16 * 16 + tid; i < n; i += nthr) u[i] = u[i] != 0;
 }
 
 bool fast_ok(const Problem &p) { return p.nx % 16 == 0; }

@@ -4,7 +4,8 @@
 // The loop-of-stencil-reduce of Sec. 3.1 with the Fig. 1 elemental function
 // (B3/S23), restructured for GB300.  One cooperative persistent launch does:
 //
-//  P. Pack: the caller's uint8 grid is staged through shared memory by TMA
+//  P. Pack: the caller's uint8 grid (any non-zero byte is a live cell) is
+//     staged through shared memory by TMA
 //     (cp.async.bulk.tensor.2d, 32-row x 128-byte boxes with the 128B swizzle,
 //     double buffered) and packed to 1 bit per cell (bit b of word w = column
 //     32w + b) into a workspace buffer.  Boxes wholly outside the grid are not
@@ -107,9 +108,20 @@ __device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, i
 // distinct bit positions 24..27, so the multiply adds no carries.
 __device__ __forceinline__ uint32_t pack4(uint32_t w) { return (w * 0x01020408u) >> 24; }
 
+// Any non-zero byte reads as a live cell: fold each byte's bits into its bit 0
+// (shifts by 4, 2, 1 stay inside the byte for the low bits kept).
+__device__ __forceinline__ uint32_t nonzero_bytes(uint32_t w)
+{
+    w |= w >> 4;
+    w |= w >> 2;
+    w |= w >> 1;
+    return w & 0x01010101u;
+}
+
 __device__ __forceinline__ uint32_t pack16(const uint4 v)
 {
-    return pack4(v.x) | (pack4(v.y) << 4) | (pack4(v.z) << 8) | (pack4(v.w) << 12);
+    return pack4(nonzero_bytes(v.x)) | (pack4(nonzero_bytes(v.y)) << 4) | (pack4(nonzero_bytes(v.z)) << 8) |
+           (pack4(nonzero_bytes(v.w)) << 12);
 }
 
 // 4 bits -> four 0/1 bytes (bit i -> byte i): copies of the nibble at shifts

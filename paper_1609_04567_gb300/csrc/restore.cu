@@ -15,7 +15,17 @@
 // EXACT math: IEEE-rounded sqrt and divisions, no contraction (bit-identical
 // to a sequential evaluation).  FAST math: the weight is the hardware
 // reciprocal square root and products fuse into FMAs.
+//
+// Two sweep implementations: RestoreTma (rows a multiple of 16 bytes) streams
+// 32 x 64 tiles through shared memory, each tile arriving as two TMA boxes
+// (state with a 1-pixel halo, mask) double buffered per CTA, and compacts the
+// noisy pixels of each warp with ballots so the weight arithmetic runs on full
+// warps; RestoreOp is the plain per-pixel form for other widths and for the
+// host-driven loop.
+#include <string.h>
+
 #include "slr_internal.cuh"
+#include "tma.cuh"
 
 namespace slr {
 namespace {
@@ -29,6 +39,7 @@ struct RestoreOp {
     const unsigned char *mask;
 
     __device__ __forceinline__ size_t state_bytes() const { return (size_t)nx * ny * sizeof(float); }
+    __device__ __forceinline__ void prologue() const {}
 
     template <bool REDUCE>
     __device__ __forceinline__ void sweep(const void *src_v, void *dst_v, Slot *slot) const
@@ -78,6 +89,172 @@ struct RestoreOp {
     }
 };
 
+
+// ---- TMA-tiled sweep -----------------------------------------------------------
+constexpr int kTH = 32, kTW = 64;                 // tile of pixels
+constexpr int kUBoxW = kTW + 8;                   // floats from x0 - 4 (16-byte aligned start)
+constexpr int kMBoxW = kTW + 32;                  // mask bytes from x0 - 16
+constexpr int kBoxH = kTH + 2;                    // rows y0 - 1 .. y0 + 32
+// every TMA destination in shared memory must be 128-byte aligned
+constexpr int kUBytes = (kUBoxW * kBoxH * 4 + 127) / 128 * 128;   // 9792 -> 9856
+constexpr int kMBytes = (kMBoxW * kBoxH + 127) / 128 * 128;       // 3264 -> 3328
+constexpr int kStage = kUBytes + kMBytes;                         // 13184
+constexpr uint32_t kTxBytes = kUBoxW * kBoxH * 4 + kMBoxW * kBoxH; // bytes the two boxes deliver
+constexpr int kTThreads = 256;                    // 8 warps x 4 tile rows
+constexpr size_t kTSmem = 128 + 2 * (size_t)kStage + 32;   // stages, 2 mbarriers, tile counter
+static_assert(kStage % 128 == 0 && kUBytes % 128 == 0, "TMA destinations must be 128-byte aligned");
+
+__device__ __forceinline__ float weight(float uc, float uj, float alpha, bool fast)
+{
+    if (fast) {
+        const float t = uc - uj;
+        return rsqrtf(fmaf(t, t, alpha));
+    }
+    const float t = __fsub_rn(uc, uj);
+    return __fdiv_rn(1.0f, __fsqrt_rn(__fadd_rn(alpha, __fmul_rn(t, t))));
+}
+
+template <bool FAST>
+struct RestoreTma {
+    CUtensorMap umap[2];      // state maps over buffer A and buffer B
+    CUtensorMap mmap;         // mask map
+    const void *base[2];      // A and B, to pick the map of a sweep's source
+    int *err;                 // control-block error word
+    long long nx, ny;
+    float alpha;
+    int tiles_x, tiles_y;
+
+    __device__ __forceinline__ size_t state_bytes() const { return (size_t)nx * ny * sizeof(float); }
+
+    // dynamic shared memory: [stage 0][stage 1][mbarrier 0, 1][tile counter]
+    __device__ __forceinline__ unsigned char *stages() const
+    {
+        extern __shared__ unsigned char smem_dyn[];
+        return (unsigned char *)(((uintptr_t)smem_dyn + 127) & ~(uintptr_t)127);
+    }
+    __device__ __forceinline__ uint64_t *bars() const { return (uint64_t *)(stages() + 2 * kStage); }
+    // tiles consumed by this CTA so far: tile q uses stage q & 1, phase (q >> 1) & 1
+    __device__ __forceinline__ unsigned *counter() const { return (unsigned *)(bars() + 2); }
+
+    __device__ __forceinline__ void prologue() const
+    {
+        if (threadIdx.x == 0) {
+            tma::mbar_init(&bars()[0], 1);
+            tma::mbar_init(&bars()[1], 1);
+            tma::mbar_init_fence();
+            *counter() = 0u;
+        }
+        __syncthreads();
+    }
+
+    __device__ __forceinline__ void issue(int tile, int mi, int sb) const
+    {
+        const int tx = tile % tiles_x, ty = tile / tiles_x;
+        const int x0 = tx * kTW, y0 = ty * kTH;
+        unsigned char *st = stages() + sb * kStage;
+        tma::mbar_expect_tx(&bars()[sb], kTxBytes);
+        tma::load_2d(st, &umap[mi], x0 - 4, y0 - 1, &bars()[sb]);
+        tma::load_2d(st + kUBytes, &mmap, x0 - 16, y0 - 1, &bars()[sb]);
+    }
+
+    template <bool REDUCE>
+    __device__ __forceinline__ void sweep(const void *src_v, void *dst_v, Slot *slot) const
+    {
+        __shared__ int s_ok;
+        float *dst = (float *)dst_v;
+        const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+        const int mi = src_v == base[0] ? 0 : 1;
+        const int ntiles = tiles_x * tiles_y;
+        const int mine = (int)blockIdx.x < ntiles ? (ntiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+        const unsigned q0 = *counter();
+        __syncthreads();                                        // everyone has read the counter
+        if (tid == 0) {
+            tma::fence_proxy_async_global();   // the previous sweep's stores, published by the grid barrier
+            for (int i = 0; i < 2 && i < mine; ++i)
+                issue((int)blockIdx.x + i * (int)gridDim.x, mi, (int)((q0 + (unsigned)i) & 1u));
+        }
+        unsigned long long sum = 0ull, cnt = 0ull;
+        for (int i = 0; i < mine; ++i) {
+            const unsigned qn = q0 + (unsigned)i;
+            const int sb = (int)(qn & 1u);
+            if (tid == 0) s_ok = tma::bounded_wait(&bars()[sb], (qn >> 1) & 1u, 2000000000ll, err);
+            __syncthreads();
+            if (!s_ok) break;
+            const int tile = (int)blockIdx.x + i * (int)gridDim.x;
+            const long long x0 = (long long)(tile % tiles_x) * kTW, y0 = (long long)(tile / tiles_x) * kTH;
+            const float *U = (const float *)(stages() + sb * kStage);   // [34][72]: row y0-1+r, column x0-4+c
+            const unsigned char *M = stages() + sb * kStage + kUBytes;  // [34][96]: row y0-1+r, column x0-16+c
+            // clean pixels are copied; the noisy ones of this warp's 4 x 64
+            // cells are collected as 8 ballots and then processed 32 at a time
+            unsigned masks[8];
+#pragma unroll
+            for (int h = 0; h < 8; ++h) {
+                const int rr = warp * 4 + (h >> 1), cc = (h & 1) * 32 + lane;
+                const long long y = y0 + rr, x = x0 + cc;
+                const bool valid = y < ny && x < nx;
+                const bool noisy = valid && M[(rr + 1) * kMBoxW + cc + 16] != 0;
+                if (valid && !noisy) dst[y * nx + x] = U[(rr + 1) * kUBoxW + cc + 4];
+                masks[h] = __ballot_sync(0xffffffffu, noisy);
+            }
+            int total = 0;
+#pragma unroll
+            for (int h = 0; h < 8; ++h) total += __popc(masks[h]);
+            for (int first = 0; first < total; first += 32) {
+                const int t = first + lane;
+                if (t >= total) continue;
+                // which ballot holds noisy pixel number t of the warp, and its bit
+                int h = 0, before = 0;
+#pragma unroll
+                for (int g = 0; g < 7; ++g) {
+                    const int c = __popc(masks[g]);
+                    if (h == g && t >= before + c) { before += c; h = g + 1; }
+                }
+                unsigned mh = 0u;
+#pragma unroll
+                for (int g = 0; g < 8; ++g)
+                    if (g == h) mh = masks[g];
+                const unsigned fb = __fns(mh, 0u, t - before + 1);   // bit of the (t - before)-th noisy pixel
+            if (fb > 31u) continue;                                // cannot happen: t < total
+            const int bit = (int)fb;
+                const int rr = warp * 4 + (h >> 1), cc = (h & 1) * 32 + bit;
+                const long long y = y0 + rr, x = x0 + cc;
+                const float uc = U[(rr + 1) * kUBoxW + cc + 4];
+                float num = 0.0f, den = 0.0f;
+#pragma unroll
+                for (int di = -1; di <= 1; ++di) {
+#pragma unroll
+                    for (int dj = -1; dj <= 1; ++dj) {
+                        if (di == 0 && dj == 0) continue;
+                        if (y + di < 0 || y + di >= ny || x + dj < 0 || x + dj >= nx) continue;
+                        const float uj = U[(rr + 1 + di) * kUBoxW + cc + 4 + dj];
+                        const float w = weight(uc, uj, alpha, FAST);
+                        if (FAST) { num = fmaf(w, uj, num); den += w; }
+                        else { num = __fadd_rn(num, __fmul_rn(w, uj)); den = __fadd_rn(den, w); }
+                    }
+                }
+                const float nv = den > 0.0f ? __fdiv_rn(num, den) : uc;
+                dst[y * nx + x] = nv;
+                if (REDUCE) {
+                    sum += (unsigned long long)__double2ull_rz((double)fabsf(__fsub_rn(nv, uc)) * 16777216.0);
+                    cnt += 1ull;
+                }
+            }
+            __syncthreads();                                   // stage sb is free again
+            if (tid == 0 && i + 2 < mine) issue((int)blockIdx.x + (i + 2) * (int)gridDim.x, mi, sb);
+        }
+        if (tid == 0) *counter() = q0 + (unsigned)mine;
+        tma::fence_proxy_async_global();                       // this sweep's stores before the next TMA reads
+        if (REDUCE) block_to_slot(slot, 0ull, sum, cnt, sum != 0ull);
+    }
+};
+
+template <class Op>
+__global__ void __launch_bounds__(kTThreads, 4) restore_tma_kernel(const __grid_constant__ Op op, LoopArgs la)
+{
+    op.prologue();
+    persistent_loop_body(op, la);
+}
+
 template <class Op>
 __global__ void __launch_bounds__(kRThreads, 1) restore_persistent_kernel(Op op, LoopArgs la)
 {
@@ -98,10 +275,39 @@ int sm_count()
     return sms > 0 ? sms : 1;
 }
 
+
+template <bool FAST>
+cudaError_t launch_tma(const Problem &p, LoopArgs la, cudaStream_t st)
+{
+    RestoreTma<FAST> op;
+    memset(&op, 0, sizeof(op));
+    if (!tma::make_map_2d(&op.umap[0], la.a, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, p.nx, p.ny, kUBoxW, kBoxH) ||
+        !tma::make_map_2d(&op.umap[1], la.b, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, p.nx, p.ny, kUBoxW, kBoxH) ||
+        !tma::make_map_2d(&op.mmap, la.aux, CU_TENSOR_MAP_DATA_TYPE_UINT8, 1, p.nx, p.ny, kMBoxW, kBoxH))
+        return cudaErrorInvalidValue;
+    op.base[0] = la.a;
+    op.base[1] = la.b;
+    op.err = &la.ctl->err;
+    op.nx = p.nx;
+    op.ny = p.ny;
+    op.alpha = p.alpha;
+    op.tiles_x = (int)((p.nx + kTW - 1) / kTW);
+    op.tiles_y = (int)((p.ny + kTH - 1) / kTH);
+    auto kern = restore_tma_kernel<RestoreTma<FAST>>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTSmem);
+    if (e != cudaSuccess) return e;
+    return launch_cooperative(kern, kTThreads, kTSmem, 4, la, &op, st);
+}
+
+// The TMA path needs 16-byte row strides for the state (nx % 4) and the mask
+// (nx % 16), and the tensor-map encoder of the driver.
+bool tma_ok(const Problem &p) { return p.nx % 16 == 0 && p.nx < (1ll << 31) && p.ny < (1ll << 31) && tma::encode_fn(); }
+
 }  // namespace
 
 cudaError_t restore_persistent(const Problem &p, LoopArgs la, cudaStream_t st)
 {
+    if (tma_ok(p)) return p.math == SLR_MATH_FAST ? launch_tma<true>(p, la, st) : launch_tma<false>(p, la, st);
     if (p.math == SLR_MATH_FAST) {
         RestoreOp<true> op{p.nx, p.ny, p.alpha, (const unsigned char *)la.aux};
         return launch_cooperative(restore_persistent_kernel<RestoreOp<true>>, kRThreads, 0, 1, la, &op, st);

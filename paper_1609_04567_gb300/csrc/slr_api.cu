@@ -326,7 +326,11 @@ slr_status slr_run_until(slr_handle h, int64_t max_iters)
 {
     if (!h) return fail(nullptr, SLR_ERR_INVALID_ARG, "handle is NULL");
     if (max_iters < 0) return fail(h, SLR_ERR_INVALID_ARG, "max_iters must be >= 0");
-    if (h->prob.stencil == SLR_LIFE) {
+    // Life reads any non-zero byte as alive; the temporal-blocked path folds
+    // that into its pack phase, the other paths normalise the cells first
+    const bool life_tb = h->prob.stencil == SLR_LIFE && h->desc.loop != SLR_LOOP_HOST && h->prob.k != 1 &&
+                         slr::life_tb_supported(h->prob);
+    if (h->prob.stencil == SLR_LIFE && !life_tb) {
         cudaError_t e = slr::life_normalize(h->prob, h->u, h->stream);
         if (e != cudaSuccess) return cuda_fail(h, e, "normalize cells");
     }
