@@ -583,7 +583,7 @@ def run_serve(args):
     from paper_1609_04567_gb300 import serve, slr
     slr.load()
     reqs = serve.make_requests(args.serve_seconds + 1.0, args.rate)
-    srv = serve.Server(max_slots=2048, step_sweeps=args.step_sweeps)
+    srv = serve.Server(max_slots=1024, step_sweeps=args.step_sweeps)
     st = srv.serve(reqs, warmup_s=1.0, time_limit_s=args.serve_seconds * 6 + 30)
     srv.close()
     line = {"workload": f"serve_poisson{args.rate:g}rps_denoise256-4096_solve64-2048",

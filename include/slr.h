@@ -196,7 +196,7 @@ const char *slr_version(void);
  * may be freed or reused while the instance is in the batch and a run may be
  * in flight.  The batch handle owns host metadata only. */
 typedef struct slr_batch_ctx *slr_batch;
-size_t slr_batch_workspace_size(int32_t max_instances);       /* 0 if out of [1, 2048] */
+size_t slr_batch_workspace_size(int32_t max_instances);       /* 0 if out of [1, 1024] */
 size_t slr_batch_scratch_size(const slr_desc *d);             /* 0 for an invalid/unsupported d */
 slr_status slr_batch_create(int32_t max_instances, void *workspace, size_t workspace_bytes, void *stream,
                             slr_batch *out);

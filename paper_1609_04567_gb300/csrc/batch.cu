@@ -29,7 +29,7 @@ namespace {
 
 constexpr int kBThreads = 256;
 constexpr int kTileW = 64, kTileH = 16;
-constexpr int kMaxBatch = 2048;
+constexpr int kMaxBatch = 1024;
 
 // One instance as the kernel sees it.  Host-written fields first; the kernel
 // writes the results at the end of a run (and value/count/converged when the
@@ -245,13 +245,16 @@ __device__ void restore_unit(const BInst &I, long long unit, const void *uv, voi
             const long long y = y0 + rr, x = x0 + cc;
             const float uc = tile[(rr + 1) * kSW + cc + 1];
             float num = 0.0f, den = 0.0f;
+            const bool inner = y > 0 && y + 1 < I.ny && x > 0 && x + 1 < I.nx;
+#pragma unroll
             for (int di = -1; di <= 1; ++di)
+#pragma unroll
                 for (int dj = -1; dj <= 1; ++dj) {
                     if (di == 0 && dj == 0) continue;
-                    if (y + di < 0 || y + di >= I.ny || x + dj < 0 || x + dj >= I.nx) continue;
+                    if (!inner && (y + di < 0 || y + di >= I.ny || x + dj < 0 || x + dj >= I.nx)) continue;
                     const float uj = tile[(rr + 1 + di) * kSW + cc + 1 + dj];
                     const float tt = __fsub_rn(uc, uj);
-                    const float w = __fdiv_rn(1.0f, __fsqrt_rn(__fadd_rn(I.alpha, __fmul_rn(tt, tt))));
+                    const float w = __frcp_rn(__fsqrt_rn(__fadd_rn(I.alpha, __fmul_rn(tt, tt))));
                     num = __fadd_rn(num, __fmul_rn(w, uj));
                     den = __fadd_rn(den, w);
                 }
@@ -297,36 +300,100 @@ __device__ __forceinline__ int find_instance(const long long *prefix, int n, lon
 
 constexpr size_t kStageBytesPerWarp = (size_t)kSW * kSH * 8;      // binary64 worst case
 
+// Rebuild this CTA's list of running instances (s_aidx) and the exclusive
+// prefix of their unit counts (s_upref, n_run + 1 entries) from s_stop; every
+// CTA holds the same decisions, so every CTA builds the same list.  Returns
+// the number of running instances.
+__device__ int compact_running(int n, const int *s_stop, const int *s_units, int *s_aidx, int *s_upref)
+{
+    __shared__ int s_wsum_n[kBThreads / 32], s_wsum_u[kBThreads / 32];
+    __shared__ int s_total_n;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int per = (n + kBThreads - 1) / kBThreads;
+    const int lo = tid * per, hi = lo + per < n ? lo + per : n;
+    int cn = 0, cu = 0;
+    for (int i = lo; i < hi; ++i)
+        if (s_stop[i] == -1) { ++cn; cu += s_units[i]; }
+    // block exclusive scan of (cn, cu)
+    int sn = cn, su = cu;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int tn = __shfl_up_sync(0xffffffffu, sn, o), tu = __shfl_up_sync(0xffffffffu, su, o);
+        if (lane >= o) { sn += tn; su += tu; }
+    }
+    if (lane == 31) { s_wsum_n[warp] = sn; s_wsum_u[warp] = su; }
+    __syncthreads();
+    if (warp == 0) {
+        int wn = lane < kBThreads / 32 ? s_wsum_n[lane] : 0, wu = lane < kBThreads / 32 ? s_wsum_u[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int tn = __shfl_up_sync(0xffffffffu, wn, o), tu = __shfl_up_sync(0xffffffffu, wu, o);
+            if (lane >= o) { wn += tn; wu += tu; }
+        }
+        if (lane < kBThreads / 32) { s_wsum_n[lane] = wn; s_wsum_u[lane] = wu; }
+        if (lane == kBThreads / 32 - 1) s_total_n = wn;
+    }
+    __syncthreads();
+    int pn = sn - cn + (warp > 0 ? s_wsum_n[warp - 1] : 0);
+    int pu = su - cu + (warp > 0 ? s_wsum_u[warp - 1] : 0);
+    for (int i = lo; i < hi; ++i)
+        if (s_stop[i] == -1) {
+            s_aidx[pn] = i;
+            s_upref[pn] = pu;
+            ++pn;
+            pu += s_units[i];
+        }
+    const int total = s_total_n;
+    if (tid == kBThreads - 1) s_upref[total] = pu;   // the last thread ends on the total
+    __syncthreads();
+    return total;
+}
+
+__device__ __forceinline__ int find_running(const int *s_upref, int nrun, int u)
+{
+    int lo = 0, hi = nrun;     // s_upref[lo] <= u < s_upref[hi]
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (s_upref[mid] <= u) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
 __global__ void __launch_bounds__(kBThreads, 2) batch_kernel(BatchArgs ba)
 {
     extern __shared__ unsigned char smem_raw[];
     unsigned char *stage = smem_raw + (size_t)(threadIdx.x >> 5) * kStageBytesPerWarp;
     unsigned char *tail = smem_raw + (size_t)(kBThreads / 32) * kStageBytesPerWarp;
-    long long *s_iters0 = (long long *)tail;                      // [nact]
-    int *s_stop = (int *)(s_iters0 + ba.nact);                    // [nact]: sweep index of the stop, -1 running
-    unsigned char *s_par0 = (unsigned char *)(s_stop + ba.nact);  // [nact]
-    const long long *s_prefix = ba.prefix;                         // read-only during the launch
+    const int n = ba.nact;
+    long long *s_iters0 = (long long *)tail;                      // [n]
+    int *s_stop = (int *)(s_iters0 + n);                          // [n]: sweep index of the stop, -1 running
+    int *s_units = s_stop + n;                                    // [n]
+    int *s_aidx = s_units + n;                                    // [n]: running instances (positions in act)
+    int *s_upref = s_aidx + n;                                    // [n + 1]: unit prefix of s_aidx
+    unsigned char *s_par0 = (unsigned char *)(s_upref + n + 1);   // [n]
     __shared__ int s_alive;
 
     const int tid = threadIdx.x, lane = tid & 31;
-    const int n = ba.nact;
     for (int i = tid; i < n; i += kBThreads) {
         const BInst &I = ba.inst[ba.act[i]];
         s_iters0[i] = I.iters;
         s_par0[i] = (unsigned char)I.parity;
         s_stop[i] = I.done ? -2 : -1;
+        s_units[i] = (int)I.units;
     }
     __syncthreads();
-    const long long U = __ldg(s_prefix + n);
-    const long long warps = (long long)gridDim.x * (kBThreads / 32);
-    const long long gw = (long long)blockIdx.x * (kBThreads / 32) + (tid >> 5);
+    int nrun = compact_running(n, s_stop, s_units, s_aidx, s_upref);
+    // warps interleave across CTAs so that consecutive units land on different SMs
+    const int warps = (int)gridDim.x * (kBThreads / 32);
+    const int gw = (tid >> 5) * (int)gridDim.x + (int)blockIdx.x;
     long long s = 0;
     for (; s < ba.sweeps; ++s) {
-        for (long long u = gw; u < U; u += warps) {
-            const int ai = find_instance(s_prefix, n, u);
-            if (s_stop[ai] != -1) continue;
+        const int U = s_upref[nrun];
+        for (int u = gw; u < U; u += warps) {
+            const int ri = find_running(s_upref, nrun, u);
+            const int ai = s_aidx[ri];
             const BInst &I = ba.inst[ba.act[ai]];
-            const long long unit = u - __ldg(s_prefix + ai);
+            const long long unit = u - s_upref[ri];
             const int par = (s_par0[ai] + (int)s) & 1;
             const void *src = par ? I.b : I.a;
             void *dst = par ? I.a : I.b;
@@ -372,8 +439,8 @@ __global__ void __launch_bounds__(kBThreads, 2) batch_kernel(BatchArgs ba)
         if (tid == 0) s_alive = 0;
         __syncthreads();
         int alive = 0;
-        for (int i = tid; i < n; i += kBThreads) {
-            if (s_stop[i] != -1) continue;
+        for (int r = tid; r < nrun; r += kBThreads) {
+            const int i = s_aidx[r];
             const int gi = ba.act[i];
             const Slot sl = read_slot(&ba.slots[(size_t)gi * kSlots + (size_t)(s % kSlots)]);
             BInst &I = ba.inst[gi];
@@ -394,6 +461,7 @@ __global__ void __launch_bounds__(kBThreads, 2) batch_kernel(BatchArgs ba)
         if (alive) s_alive = 1;
         __syncthreads();
         if (!s_alive) { ++s; break; }
+        nrun = compact_running(n, s_stop, s_units, s_aidx, s_upref);
     }
     const long long ran = s < ba.sweeps ? s : ba.sweeps;
     // results (CTA 0) and the write-back of stopped instances whose state is in b
@@ -407,12 +475,13 @@ __global__ void __launch_bounds__(kBThreads, 2) batch_kernel(BatchArgs ba)
             I.done = s_stop[i] >= 0;
         }
     }
-    for (long long u = gw; u < U; u += warps) {
-        const int ai = find_instance(s_prefix, n, u);
+    const long long U0 = __ldg(ba.prefix + n);
+    for (long long u = gw; u < U0; u += warps) {
+        const int ai = find_instance(ba.prefix, n, u);
         if (s_stop[ai] < 0) continue;
         if (((s_par0[ai] + s_stop[ai] + 1) & 1) == 0) continue;   // final state already in a
         const BInst &I = ba.inst[ba.act[ai]];
-        unit_copy(I, u - __ldg(s_prefix + ai), I.b, I.a);
+        unit_copy(I, u - __ldg(ba.prefix + ai), I.b, I.a);
     }
 }
 
@@ -488,7 +557,7 @@ slr_status slr_batch_create(int32_t max_instances, void *workspace, size_t works
     if (!out) return bfail(nullptr, SLR_ERR_INVALID_ARG, "out is NULL");
     *out = nullptr;
     if (max_instances < 1 || max_instances > slr::kMaxBatch)
-        return bfail(nullptr, SLR_ERR_INVALID_ARG, "max_instances must be in [1, 2048]");
+        return bfail(nullptr, SLR_ERR_INVALID_ARG, "max_instances must be in [1, 1024]");
     if (!workspace || ((uintptr_t)workspace & 255u))
         return bfail(nullptr, SLR_ERR_INVALID_ARG, "workspace must be a 256-byte aligned device pointer");
     if (workspace_bytes < ws_total(max_instances)) return bfail(nullptr, SLR_ERR_WORKSPACE, "workspace too small");
@@ -611,7 +680,7 @@ slr_status slr_batch_run(slr_batch b, int64_t sweeps)
     ba.ctl = (slr::Ctl *)b->ws;
     ba.limit_ns = 2000000000ll;
     const size_t smem = (size_t)(slr::kBThreads / 32) * slr::kStageBytesPerWarp + (size_t)ba.nact * 8 +
-                        (size_t)ba.nact * 4 + (size_t)ba.nact;
+                        (size_t)ba.nact * 4 * 4 + 4 + (size_t)ba.nact;
     e = cudaFuncSetAttribute(slr::batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return bcuda(b, e, "batch kernel attributes");
     int dev = 0, sms = 0, per_sm = 0;

@@ -49,7 +49,8 @@ constexpr int kTileRows = kWarps * kRowsPerWarp + 2;  // 242 distinct tile rows
 constexpr int kWords = 34;                            // 1 halo + 32 owned + 1 halo
 constexpr int kOwnWords = 32;
 constexpr int kOwnCols = 32 * kOwnWords;              // 1024
-constexpr int kXchWords = 2 * kWarps * 2 * kWords;    // [parity][warp][lane 1 row, lane 30 row][word]
+constexpr int kXchStride = 36;                        // exchange row stride in words (16-byte aligned rows)
+constexpr int kXchWords = 2 * kWarps * 2 * kXchStride; // [parity][warp][lane 1 row, lane 30 row][word]
 // pack phase: 32 rows x 1024 columns per unit, 8 swizzled boxes of 128 bytes
 constexpr int kPackRows = 32;
 constexpr int kBoxW = 128;
@@ -57,7 +58,7 @@ constexpr int kBoxes = kOwnCols / kBoxW;              // 8
 constexpr int kBoxBytes = kBoxW * kPackRows;          // 4096
 constexpr int kStageBytes = kBoxes * kBoxBytes;       // 32768
 constexpr size_t kSmemBytes = 1024 + 2 * kStageBytes + kXchWords * 4 + 2 * 8 + kMaxK * 8 + kMaxK * 4;
-static_assert((kXchWords * 4) % 8 == 0, "mbarriers must stay 8-byte aligned");
+static_assert((kXchWords * 4) % 16 == 0 && (2 * kStageBytes) % 16 == 0, "exchange rows and mbarriers stay aligned");
 static_assert(kMaxK == 32, "one lane per generation in the per-pass decision");
 
 struct TbParams {
@@ -293,16 +294,15 @@ __device__ __forceinline__ void run_tile(const TbParams &tp, int tile, int kp, c
             C = nextC;
         }
         // refresh the two copied rows from the neighbour warps (exchange rows
-        // double buffered by generation parity: one barrier per generation)
-        uint32_t *xb = xch + (j & 1) * kWarps * 2 * kWords;
-        uint32_t *mine = xb + warp * 2 * kWords;
-        if (lane == 1) {
+        // double buffered by generation parity: one barrier per generation;
+        // 16-byte shared-memory accesses)
+        uint32_t *xb = xch + (j & 1) * kWarps * 2 * kXchStride;
+        if (lane == 1 || lane == kRowsPerWarp) {
+            uint32_t *row = xb + (warp * 2 + (lane == 1 ? 0 : 1)) * kXchStride;
 #pragma unroll
-            for (int w = 0; w < kWords; ++w) mine[w] = cur[w];
-        }
-        if (lane == kRowsPerWarp) {
-#pragma unroll
-            for (int w = 0; w < kWords; ++w) mine[kWords + w] = cur[w];
+            for (int i = 0; i < 8; ++i)
+                ((uint4 *)row)[i] = make_uint4(cur[4 * i], cur[4 * i + 1], cur[4 * i + 2], cur[4 * i + 3]);
+            ((uint2 *)row)[16] = make_uint2(cur[32], cur[33]);
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
@@ -314,15 +314,17 @@ __device__ __forceinline__ void run_tile(const TbParams &tp, int tile, int kp, c
             if (changed) atomicOr(&s_ch[j], 1u);
         }
         __syncthreads();
-        if (lane == 0 && warp > 0) {
-            const uint32_t *up = xb + (warp - 1) * 2 * kWords + kWords;   // lane 30 of the warp above
+        if ((lane == 0 && warp > 0) || (lane == 31 && warp < kWarps - 1)) {
+            // lane 0 takes lane 30 of the warp above, lane 31 lane 1 of the warp below
+            const uint32_t *row = xb + (lane == 0 ? (warp - 1) * 2 + 1 : (warp + 1) * 2) * kXchStride;
 #pragma unroll
-            for (int w = 0; w < kWords; ++w) cur[w] = up[w];
-        }
-        if (lane == 31 && warp < kWarps - 1) {
-            const uint32_t *dn = xb + (warp + 1) * 2 * kWords;            // lane 1 of the warp below
-#pragma unroll
-            for (int w = 0; w < kWords; ++w) cur[w] = dn[w];
+            for (int i = 0; i < 8; ++i) {
+                const uint4 v = ((const uint4 *)row)[i];
+                cur[4 * i] = v.x; cur[4 * i + 1] = v.y; cur[4 * i + 2] = v.z; cur[4 * i + 3] = v.w;
+            }
+            const uint2 t = ((const uint2 *)row)[16];
+            cur[32] = t.x;
+            cur[33] = t.y;
         }
     }
     __syncthreads();   // the last exchange buffer is read before the next tile writes it
@@ -348,7 +350,7 @@ __global__ void __launch_bounds__(kThreads, 2) life_tb_kernel(const __grid_const
     extern __shared__ unsigned char smem_raw[];
     unsigned char *base = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     unsigned char *stage = base;                                   // [2][kStageBytes]
-    uint32_t *xch = (uint32_t *)(base + 2 * kStageBytes);          // [8][2][34]
+    uint32_t *xch = (uint32_t *)(base + 2 * kStageBytes);          // [2][8][2][36]
     uint64_t *mbar = (uint64_t *)(xch + kXchWords);                // [2]
     unsigned long long *s_cnt = (unsigned long long *)(mbar + 2);  // [kMaxK]
     unsigned int *s_ch = (unsigned int *)(s_cnt + kMaxK);          // [kMaxK]

@@ -72,7 +72,7 @@ struct RestoreOp {
                         den += w;
                     } else {
                         const float t = __fsub_rn(uc, uj);
-                        const float w = __fdiv_rn(1.0f, __fsqrt_rn(__fadd_rn(alpha, __fmul_rn(t, t))));
+                        const float w = __frcp_rn(__fsqrt_rn(__fadd_rn(alpha, __fmul_rn(t, t))));
                         num = __fadd_rn(num, __fmul_rn(w, uj));
                         den = __fadd_rn(den, w);
                     }
@@ -110,8 +110,9 @@ __device__ __forceinline__ float weight(float uc, float uj, float alpha, bool fa
         const float t = uc - uj;
         return rsqrtf(fmaf(t, t, alpha));
     }
+    // 1/s rounded once: the IEEE reciprocal equals the IEEE division 1.0f / s
     const float t = __fsub_rn(uc, uj);
-    return __fdiv_rn(1.0f, __fsqrt_rn(__fadd_rn(alpha, __fmul_rn(t, t))));
+    return __frcp_rn(__fsqrt_rn(__fadd_rn(alpha, __fmul_rn(t, t))));
 }
 
 template <bool FAST>
@@ -161,6 +162,8 @@ struct RestoreTma {
     __device__ __forceinline__ void sweep(const void *src_v, void *dst_v, Slot *slot) const
     {
         __shared__ int s_ok;
+        __shared__ unsigned s_masks[64];
+        __shared__ int s_pref[65];
         float *dst = (float *)dst_v;
         const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
         const int mi = src_v == base[0] ? 0 : 1;
@@ -184,9 +187,10 @@ struct RestoreTma {
             const long long x0 = (long long)(tile % tiles_x) * kTW, y0 = (long long)(tile / tiles_x) * kTH;
             const float *U = (const float *)(stages() + sb * kStage);   // [34][72]: row y0-1+r, column x0-4+c
             const unsigned char *M = stages() + sb * kStage + kUBytes;  // [34][96]: row y0-1+r, column x0-16+c
-            // clean pixels are copied; the noisy ones of this warp's 4 x 64
-            // cells are collected as 8 ballots and then processed 32 at a time
-            unsigned masks[8];
+            // clean pixels are copied; the noisy ones of the whole tile are
+            // listed as 64 ballots (8 warps x 8 row halves) with a prefix sum,
+            // then split evenly over the 8 warps, 32 at a time, so every warp
+            // does the same share of the weight arithmetic
 #pragma unroll
             for (int h = 0; h < 8; ++h) {
                 const int rr = warp * 4 + (h >> 1), cc = (h & 1) * 32 + lane;
@@ -194,38 +198,49 @@ struct RestoreTma {
                 const bool valid = y < ny && x < nx;
                 const bool noisy = valid && M[(rr + 1) * kMBoxW + cc + 16] != 0;
                 if (valid && !noisy) dst[y * nx + x] = U[(rr + 1) * kUBoxW + cc + 4];
-                masks[h] = __ballot_sync(0xffffffffu, noisy);
+                const unsigned m = __ballot_sync(0xffffffffu, noisy);
+                if (lane == 0) s_masks[warp * 8 + h] = m;
             }
-            int total = 0;
+            __syncthreads();
+            if (warp == 0) {
+                // exclusive prefix of the 64 ballot counts (two per lane)
+                const int c0 = __popc(s_masks[2 * lane]), c1 = __popc(s_masks[2 * lane + 1]);
+                int incl = c0 + c1;
 #pragma unroll
-            for (int h = 0; h < 8; ++h) total += __popc(masks[h]);
-            for (int first = 0; first < total; first += 32) {
-                const int t = first + lane;
-                if (t >= total) continue;
-                // which ballot holds noisy pixel number t of the warp, and its bit
-                int h = 0, before = 0;
-#pragma unroll
-                for (int g = 0; g < 7; ++g) {
-                    const int c = __popc(masks[g]);
-                    if (h == g && t >= before + c) { before += c; h = g + 1; }
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int t2 = __shfl_up_sync(0xffffffffu, incl, o);
+                    if (lane >= o) incl += t2;
                 }
-                unsigned mh = 0u;
-#pragma unroll
-                for (int g = 0; g < 8; ++g)
-                    if (g == h) mh = masks[g];
-                const unsigned fb = __fns(mh, 0u, t - before + 1);   // bit of the (t - before)-th noisy pixel
-            if (fb > 31u) continue;                                // cannot happen: t < total
-            const int bit = (int)fb;
-                const int rr = warp * 4 + (h >> 1), cc = (h & 1) * 32 + bit;
+                const int excl = incl - c0 - c1;
+                s_pref[2 * lane] = excl;
+                s_pref[2 * lane + 1] = excl + c0;
+                if (lane == 31) s_pref[64] = incl;
+            }
+            __syncthreads();
+            const int total = s_pref[64];
+            const int share = (total + 8 * 32 - 1) / (8 * 32) * 32;   // multiple of 32 per warp
+            const int lo = warp * share, hi = lo + share < total ? lo + share : total;
+            for (int first = lo; first < hi; first += 32) {
+                const int t = first + lane;
+                if (t >= hi) continue;
+                int a = 0, b = 64;                                 // s_pref[a] <= t < s_pref[b]
+                while (b - a > 1) {
+                    const int mid = (a + b) >> 1;
+                    if (s_pref[mid] <= t) a = mid; else b = mid;
+                }
+                const unsigned fb = __fns(s_masks[a], 0u, t - s_pref[a] + 1);   // bit of that noisy pixel
+                if (fb > 31u) continue;                                          // cannot happen: t < total
+                const int rr = (a >> 3) * 4 + ((a & 7) >> 1), cc = (a & 1) * 32 + (int)fb;
                 const long long y = y0 + rr, x = x0 + cc;
                 const float uc = U[(rr + 1) * kUBoxW + cc + 4];
                 float num = 0.0f, den = 0.0f;
+                const bool inner = y > 0 && y + 1 < ny && x > 0 && x + 1 < nx;   // all 8 neighbours exist
 #pragma unroll
                 for (int di = -1; di <= 1; ++di) {
 #pragma unroll
                     for (int dj = -1; dj <= 1; ++dj) {
                         if (di == 0 && dj == 0) continue;
-                        if (y + di < 0 || y + di >= ny || x + dj < 0 || x + dj >= nx) continue;
+                        if (!inner && (y + di < 0 || y + di >= ny || x + dj < 0 || x + dj >= nx)) continue;
                         const float uj = U[(rr + 1 + di) * kUBoxW + cc + 4 + dj];
                         const float w = weight(uc, uj, alpha, FAST);
                         if (FAST) { num = fmaf(w, uj, num); den += w; }
