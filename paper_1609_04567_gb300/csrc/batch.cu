@@ -122,8 +122,25 @@ __device__ __forceinline__ float add_rn(float a, float b) { return __fadd_rn(a, 
 __device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
 __device__ __forceinline__ float div_rn(float a, float b) { return __fdiv_rn(a, b); }
 __device__ __forceinline__ float sub_rn(float a, float b) { return __fsub_rn(a, b); }
-__device__ __forceinline__ unsigned long long abs_bits(double v) { return (unsigned long long)__double_as_longlong(fabs(v)); }
-__device__ __forceinline__ unsigned long long abs_bits(float v) { return (unsigned long long)__double_as_longlong((double)fabsf(v)); }
+// Running max of |delta| as bit patterns (unsigned order = numeric order for
+// non-negative values); binary32 deltas stay 32-bit and widen once per unit.
+__device__ __forceinline__ void max_bits(unsigned long long &m, double v)
+{
+    const unsigned long long b = (unsigned long long)__double_as_longlong(fabs(v));
+    m = b > m ? b : m;
+}
+__device__ __forceinline__ void max_bits(unsigned int &m, float v)
+{
+    const unsigned int b = __float_as_uint(fabsf(v));
+    m = b > m ? b : m;
+}
+__device__ __forceinline__ unsigned long long widen_bits(unsigned long long m) { return m; }
+__device__ __forceinline__ unsigned long long widen_bits(unsigned int m)
+{
+    return (unsigned long long)__double_as_longlong((double)__uint_as_float(m));
+}
+template <class C> struct MaxBits { using type = unsigned long long; };
+template <> struct MaxBits<float> { using type = unsigned int; };
 
 template <class T>
 __device__ __forceinline__ typename St<T>::C at(const BInst &I, const void *u, long long k, long long i, long long j,
@@ -170,7 +187,7 @@ __device__ unsigned long long jacobi_unit(const BInst &I, long long unit, const 
     const C d = sizeof(C) == 8 ? (C)I.d : (C)I.df;
     C *tile = (C *)stage;
     stage_tile<T>(I, u, k, ty * kTileH, tx * kTileW, tile, ghost);
-    unsigned long long mx = 0ull;
+    typename MaxBits<C>::type mx = 0;
     for (int r = 0; r < kTileH; ++r) {
         const long long i = ty * kTileH + r;
         if (i >= I.ny) break;
@@ -189,12 +206,11 @@ __device__ unsigned long long jacobi_unit(const BInst &I, long long unit, const 
             }
             const C tt = mul_rn(h2, St<T>::ldf(I.aux, idx));
             const C stored = St<T>::put(v, idx, div_rn(add_rn(tt, s), d));
-            const unsigned long long b = abs_bits(sub_rn(stored, uc));
-            mx = b > mx ? b : mx;
+            max_bits(mx, sub_rn(stored, uc));
         }
     }
     __syncwarp();                                   // the stage is reused by the warp's next unit
-    return mx;
+    return widen_bits(mx);
 }
 
 // One warp unit of a restoration instance; returns (fixed-point sum, masked
@@ -260,7 +276,7 @@ __device__ void restore_unit(const BInst &I, long long unit, const void *uv, voi
                 }
             const float nv = den > 0.0f ? __fdiv_rn(num, den) : uc;
             v[y * I.nx + x] = nv;
-            sum += (unsigned long long)__double2ull_rz((double)fabsf(__fsub_rn(nv, uc)) * 16777216.0);
+            sum += fixed_2m24(__fsub_rn(nv, uc));
             cnt += 1ull;
         }
     }

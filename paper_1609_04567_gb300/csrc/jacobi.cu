@@ -74,8 +74,26 @@ __device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, 
 __device__ __forceinline__ float div_rn(float a, float b) { return __fdiv_rn(a, b); }
 __device__ __forceinline__ float sub_rn(float a, float b) { return __fsub_rn(a, b); }
 
-__device__ __forceinline__ unsigned long long delta_bits(double d) { return (unsigned long long)__double_as_longlong(fabs(d)); }
-__device__ __forceinline__ unsigned long long delta_bits(float d) { return (unsigned long long)__double_as_longlong((double)fabsf(d)); }
+// Running max of |delta| as bit patterns: for non-negative IEEE values the
+// unsigned order of the bits is the numeric order (and a NaN stays the max).
+// binary32 deltas keep 32-bit patterns and are widened once, at the end.
+__device__ __forceinline__ void max_bits(unsigned long long &m, double d)
+{
+    const unsigned long long b = (unsigned long long)__double_as_longlong(fabs(d));
+    m = b > m ? b : m;
+}
+__device__ __forceinline__ void max_bits(unsigned int &m, float d)
+{
+    const unsigned int b = __float_as_uint(fabsf(d));
+    m = b > m ? b : m;
+}
+__device__ __forceinline__ unsigned long long widen_bits(unsigned long long m) { return m; }
+__device__ __forceinline__ unsigned long long widen_bits(unsigned int m)
+{
+    return (unsigned long long)__double_as_longlong((double)__uint_as_float(m));
+}
+template <class C> struct MaxBits { using type = unsigned long long; };
+template <> struct MaxBits<float> { using type = unsigned int; };
 
 template <class T, int DIM>
 struct JacobiOp {
@@ -106,7 +124,7 @@ struct JacobiOp {
         T *v = (T *)dst_v;
         const long long chunks = (nx + blockDim.x - 1) / blockDim.x;
         const long long units = ny * nz * chunks;
-        unsigned long long mx = 0ull;
+        typename MaxBits<C>::type mx = 0;
         for (long long un = blockIdx.x; un < units; un += gridDim.x) {
             const long long row = un / chunks;
             const long long j = (un - row * chunks) * blockDim.x + threadIdx.x;
@@ -126,12 +144,9 @@ struct JacobiOp {
             const C t = mul_rn(h2, Store<T>::ldf(f + c));
             const T nv = Store<T>::st(div_rn(add_rn(t, s), d));
             v[c] = nv;
-            if (REDUCE) {
-                const unsigned long long b = delta_bits(sub_rn(Store<T>::back(nv), uc));
-                mx = b > mx ? b : mx;
-            }
+            if (REDUCE) max_bits(mx, sub_rn(Store<T>::back(nv), uc));
         }
-        if (REDUCE) block_to_slot(slot, mx, 0ull, 0ull, mx != 0ull);
+        if (REDUCE) block_to_slot(slot, widen_bits(mx), 0ull, 0ull, mx != 0);
     }
 };
 

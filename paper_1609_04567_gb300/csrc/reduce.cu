@@ -38,7 +38,7 @@ __global__ void reduce_masked_mean(const float *a, const float *b, const unsigne
     unsigned long long sum = 0ull, cnt = 0ull;
     for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
         if (!mask[i]) continue;
-        sum += (unsigned long long)__double2ull_rz((double)fabsf(__fsub_rn(__ldcg(b + i), __ldcg(a + i))) * 16777216.0);
+        sum += fixed_2m24(__fsub_rn(__ldcg(b + i), __ldcg(a + i)));
         cnt += 1ull;
     }
     block_to_slot(slot, 0ull, sum, cnt, sum != 0ull);

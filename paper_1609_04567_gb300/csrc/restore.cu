@@ -81,7 +81,7 @@ struct RestoreOp {
             const float nv = den > 0.0f ? __fdiv_rn(num, den) : uc;
             v[c] = nv;
             if (REDUCE) {
-                sum += (unsigned long long)__double2ull_rz((double)fabsf(__fsub_rn(nv, uc)) * 16777216.0);
+                sum += fixed_2m24(__fsub_rn(nv, uc));
                 cnt += 1ull;
             }
         }
@@ -184,7 +184,9 @@ struct RestoreTma {
             __syncthreads();
             if (!s_ok) break;
             const int tile = (int)blockIdx.x + i * (int)gridDim.x;
-            const long long x0 = (long long)(tile % tiles_x) * kTW, y0 = (long long)(tile / tiles_x) * kTH;
+            // coordinates in 32 bits (extents are below 2^31 on this path)
+            const int x0 = (tile % tiles_x) * kTW, y0 = (tile / tiles_x) * kTH;
+            const int nxi = (int)nx, nyi = (int)ny;
             const float *U = (const float *)(stages() + sb * kStage);   // [34][72]: row y0-1+r, column x0-4+c
             const unsigned char *M = stages() + sb * kStage + kUBytes;  // [34][96]: row y0-1+r, column x0-16+c
             // clean pixels are copied; the noisy ones of the whole tile are
@@ -194,10 +196,10 @@ struct RestoreTma {
 #pragma unroll
             for (int h = 0; h < 8; ++h) {
                 const int rr = warp * 4 + (h >> 1), cc = (h & 1) * 32 + lane;
-                const long long y = y0 + rr, x = x0 + cc;
-                const bool valid = y < ny && x < nx;
+                const int y = y0 + rr, x = x0 + cc;
+                const bool valid = y < nyi && x < nxi;
                 const bool noisy = valid && M[(rr + 1) * kMBoxW + cc + 16] != 0;
-                if (valid && !noisy) dst[y * nx + x] = U[(rr + 1) * kUBoxW + cc + 4];
+                if (valid && !noisy) dst[(size_t)y * (size_t)nxi + x] = U[(rr + 1) * kUBoxW + cc + 4];
                 const unsigned m = __ballot_sync(0xffffffffu, noisy);
                 if (lane == 0) s_masks[warp * 8 + h] = m;
             }
@@ -231,16 +233,16 @@ struct RestoreTma {
                 const unsigned fb = __fns(s_masks[a], 0u, t - s_pref[a] + 1);   // bit of that noisy pixel
                 if (fb > 31u) continue;                                          // cannot happen: t < total
                 const int rr = (a >> 3) * 4 + ((a & 7) >> 1), cc = (a & 1) * 32 + (int)fb;
-                const long long y = y0 + rr, x = x0 + cc;
+                const int y = y0 + rr, x = x0 + cc;
                 const float uc = U[(rr + 1) * kUBoxW + cc + 4];
                 float num = 0.0f, den = 0.0f;
-                const bool inner = y > 0 && y + 1 < ny && x > 0 && x + 1 < nx;   // all 8 neighbours exist
+                const bool inner = y > 0 && y + 1 < nyi && x > 0 && x + 1 < nxi;   // all 8 neighbours exist
 #pragma unroll
                 for (int di = -1; di <= 1; ++di) {
 #pragma unroll
                     for (int dj = -1; dj <= 1; ++dj) {
                         if (di == 0 && dj == 0) continue;
-                        if (!inner && (y + di < 0 || y + di >= ny || x + dj < 0 || x + dj >= nx)) continue;
+                        if (!inner && (y + di < 0 || y + di >= nyi || x + dj < 0 || x + dj >= nxi)) continue;
                         const float uj = U[(rr + 1 + di) * kUBoxW + cc + 4 + dj];
                         const float w = weight(uc, uj, alpha, FAST);
                         if (FAST) { num = fmaf(w, uj, num); den += w; }
@@ -248,9 +250,9 @@ struct RestoreTma {
                     }
                 }
                 const float nv = den > 0.0f ? __fdiv_rn(num, den) : uc;
-                dst[y * nx + x] = nv;
+                dst[(size_t)y * (size_t)nxi + x] = nv;
                 if (REDUCE) {
-                    sum += (unsigned long long)__double2ull_rz((double)fabsf(__fsub_rn(nv, uc)) * 16777216.0);
+                    sum += fixed_2m24(__fsub_rn(nv, uc));
                     cnt += 1ull;
                 }
             }

@@ -161,6 +161,17 @@ __device__ __forceinline__ void block_to_slot(Slot *slot, unsigned long long max
     __syncthreads();
 }
 
+// |delta| truncated to a multiple of 2^-24, as an integer: trunc(|d| * 2^24).
+// Scaling by 2^24 is exact in binary32, so for |d| < 256 (the product below
+// 2^32) a binary32 multiply and an unsigned 32-bit truncation give the same
+// integer as the binary64 route, without binary64 arithmetic.
+__device__ __forceinline__ unsigned long long fixed_2m24(float d)
+{
+    const float a = fabsf(d);
+    if (a < 256.0f) return (unsigned long long)__float2uint_rz(a * 16777216.0f);
+    return (unsigned long long)__double2ull_rz((double)a * 16777216.0);
+}
+
 // What every stencil's loop needs to decide after a sweep.
 struct Decision {
     double value;
