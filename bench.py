@@ -225,11 +225,20 @@ def run_ours(args, wl, world, rank, local):
     pristine = torch.from_numpy(cells).to(dev)
     u = torch.empty_like(pristine)
     stream = torch.cuda.Stream(dev)
-    desc = slr.slr_desc_init(slr.SLR_LIFE, nx, ny, 1, temporal_k=args.k)
+    desc = slr.slr_desc_init(slr.SLR_LIFE, nx, ny, 1, temporal_k=args.k, grid_ctas=args.grid_ctas)
     ws_bytes = slr.slr_workspace_size(desc)
     ws_t = torch.empty(ws_bytes + 256, dtype=torch.uint8, device=dev)
     ws = ws_t.data_ptr() + ((-ws_t.data_ptr()) % 256)
     cell_updates = nx * ny * gens
+    # autotune the launch choices left to the library (untimed set-up: the
+    # tuner's cache then feeds every slr_create below)
+    tuned = None
+    if not args.no_tune:
+        t0 = time.perf_counter()
+        with torch.cuda.stream(stream):
+            tuned = slr.tune(slr.SLR_LIFE, pristine, stream=stream, trial_iters=args.tune_iters,
+                             loop=slr.SLR_LOOP_PERSISTENT, temporal_k=args.k, grid_ctas=args.grid_ctas)
+        tuned["seconds"] = time.perf_counter() - t0
 
     def step(launch_events=None, loop=slr.SLR_LOOP_PERSISTENT):
         u.copy_(pristine, non_blocking=True)
@@ -272,9 +281,13 @@ def run_ours(args, wl, world, rank, local):
     ms_step = max_over_ranks(ms_total / args.steps, world)
     value = world * cell_updates / (ms_step / 1e3) / 1e9
     kern_ms = statistics.mean(a.elapsed_time(b) for a, b in ev)
-    # generations per pass: the library's choice for 8192 x 8192 on 152 SMs is
-    # 12 (the largest k up to 16 whose 1024 x (242 - 2k) tiles fit 304 CTAs)
-    k_eff = 1 if args.k == 1 else (args.k if args.k > 0 else 12)
+    # generations per pass: the tuner's choice, else the built-in default for
+    # 8192 x 8192 on 152 SMs, 12 (the largest k up to 16 whose 1024 x (242 - 2k)
+    # tiles fit 304 CTAs)
+    if tuned is not None:
+        k_eff = tuned["temporal_k"]
+    else:
+        k_eff = 1 if args.k == 1 else (args.k if args.k > 0 else 12)
     passes = -(-gens // k_eff)
     # k = 1 moves every cell as uint8 per pass; the temporal-blocked path reads
     # and writes the uint8 grid once per launch and the bit-packed grid once
@@ -376,7 +389,8 @@ def run_ours(args, wl, world, rank, local):
             "data": "synthetic",
             "config": {"workload": wl["name"].format(gens=gens), "cells": nx * ny, "generations": gens,
                        "parallelism": f"replicas{world}", "loop": "persistent cooperative kernel",
-                       "temporal_k": args.k,
+                       "temporal_k": k_eff, "grid_ctas": tuned["grid_ctas"] if tuned else args.grid_ctas,
+                       "tuned": tuned,
                        "l2": "no flush: per-step working set 192 MiB (ping-pong pair 128 MiB + input copy) "
                              "exceeds the L2"},
             "roofline": roof,
@@ -418,7 +432,16 @@ def run_helmholtz(args):
     u = torch.zeros((n, n), dtype=torch.float64, device="cuda")
     stream = torch.cuda.Stream()
     res = {}
-    for name, loop in (("fused_device_loop", slr.SLR_LOOP_PERSISTENT), ("plain", slr.SLR_LOOP_HOST)):
+    tuned = None
+    runs = [("fused_device_loop", slr.SLR_LOOP_PERSISTENT), ("plain", slr.SLR_LOOP_HOST)]
+    if not args.no_tune:
+        runs.append(("fused_tuned", slr.SLR_LOOP_AUTO))
+    for name, loop in runs:
+        if loop == slr.SLR_LOOP_AUTO:
+            t0 = time.perf_counter()
+            with torch.cuda.stream(stream):
+                tuned = slr.tune(slr.SLR_J2D5, u, f, stream=stream, trial_iters=64, tol=1e-6)
+            tuned["seconds"] = time.perf_counter() - t0
         with torch.cuda.stream(stream):
             s = slr.Solver(slr.SLR_J2D5, u, f, stream=stream, tol=1e-6, loop=loop)
 
@@ -445,9 +468,11 @@ def run_helmholtz(args):
     t0 = time.perf_counter()
     _, rr = oracle.j2d5(np.zeros((n, n)), f.cpu().numpy(), tol=1e-6, max_iters=5000)
     cpu_ms = (time.perf_counter() - t0) * 1e3
+    best = res.get("fused_tuned", res["fused_device_loop"])
     line = {"workload": "helmholtz_256x256_f64_tol1e-6", "metric": "time-to-solution", "unit": "ms",
-            "value": res["fused_device_loop"]["ms_per_solve"], "higher_is_better": False, "sweeps": rr.iters,
-            "fused": res["fused_device_loop"], "plain": res["plain"],
+            "value": best["ms_per_solve"], "higher_is_better": False, "sweeps": rr.iters,
+            "fused": res["fused_device_loop"], "plain": res["plain"], "tuned": res.get("fused_tuned"),
+            "tuner": tuned,
             "cpu_baseline": {"value": cpu_ms, "unit": "ms", "cores": 1, "kind": "oracle", "sample": "full solve"}}
     print(json.dumps(line), flush=True)
     return 0
@@ -467,9 +492,18 @@ def run_restore(args):
     u = init.clone()
     stream = torch.cuda.Stream()
     res = {}
-    for name, loop, math in (("fused_exact", slr.SLR_LOOP_PERSISTENT, slr.SLR_MATH_EXACT),
-                             ("fused_fast", slr.SLR_LOOP_PERSISTENT, slr.SLR_MATH_FAST),
-                             ("plain_exact", slr.SLR_LOOP_HOST, slr.SLR_MATH_EXACT)):
+    tuned = None
+    runs = [("fused_exact", slr.SLR_LOOP_PERSISTENT, slr.SLR_MATH_EXACT),
+            ("fused_fast", slr.SLR_LOOP_PERSISTENT, slr.SLR_MATH_FAST),
+            ("plain_exact", slr.SLR_LOOP_HOST, slr.SLR_MATH_EXACT)]
+    if not args.no_tune:
+        runs.append(("tuned_exact", slr.SLR_LOOP_AUTO, slr.SLR_MATH_EXACT))
+    for name, loop, math in runs:
+        if loop == slr.SLR_LOOP_AUTO:
+            t0 = time.perf_counter()
+            with torch.cuda.stream(stream):
+                tuned = slr.tune(slr.SLR_RESTORE8, init, mask, stream=stream, trial_iters=16)
+            tuned["seconds"] = time.perf_counter() - t0
         with torch.cuda.stream(stream):
             desc = slr.slr_desc_init(slr.SLR_RESTORE8, n, n, 1, loop=loop, math=math)
             wsb = slr.slr_workspace_size(desc)
@@ -502,8 +536,9 @@ def run_restore(args):
     oracle.restore8(frame.astype(np.float32), inputs.noise_mask(frame), tol=0.0, max_iters=2)
     cpu_s = time.perf_counter() - t0
     line = {"workload": "restore_4096x4096_f32_tol1e-3", "metric": "Gcell-updates/s", "unit": "Gcell-updates/s",
-            "value": res["fused_exact"]["gcell_per_s"], "fused_exact": res["fused_exact"],
-            "fused_fast": res["fused_fast"], "plain_exact": res["plain_exact"],
+            "value": res.get("tuned_exact", res["fused_exact"])["gcell_per_s"], "fused_exact": res["fused_exact"],
+            "fused_fast": res["fused_fast"], "plain_exact": res["plain_exact"], "tuned_exact": res.get("tuned_exact"),
+            "tuner": tuned,
             "cpu_baseline": {"value": n * n * 2 / cpu_s / 1e9, "unit": "Gcell-updates/s", "cores": 1,
                              "kind": "oracle", "sample": "2 sweeps of the 4096x4096 frame"}}
     print(json.dumps(line), flush=True)
@@ -610,6 +645,9 @@ def main():
     ap.add_argument("--gens", type=int, default=2000,
                     help="generations per solve (the workload has 2000; shorter runs are for profiler captures "
                          "and are named as such in config.workload)")
+    ap.add_argument("--no-tune", action="store_true", help="skip the autotuner (built-in launch defaults)")
+    ap.add_argument("--grid-ctas", type=int, default=0, help="CTAs of the persistent launch (0 = library choice)")
+    ap.add_argument("--tune-iters", type=int, default=240, help="iterations per autotuner trial")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=12.0)

@@ -83,7 +83,7 @@ typedef enum { SLR_U8 = 0, SLR_BF16 = 1, SLR_F16 = 2, SLR_F32 = 3, SLR_F64 = 4 }
 
 /* How the loop is driven. */
 typedef enum {
-    SLR_LOOP_AUTO = 0,        /* library choice (currently PERSISTENT) */
+    SLR_LOOP_AUTO = 0,        /* library choice: the autotuner's, else PERSISTENT */
     SLR_LOOP_HOST = 1,        /* plain schema of Fig. 2: one sweep launch, one reduce
                                  launch and a host-side test per iteration */
     SLR_LOOP_PERSISTENT = 2   /* one cooperative launch; sweep, reduce, test and buffer
@@ -112,7 +112,9 @@ typedef struct {
     float alpha;           /* restoration constant (100) */
     int32_t loop;          /* slr_loop */
     int32_t math;          /* slr_math */
-    int32_t temporal_k;    /* sweeps per HBM pass for Life (1, 2, 4, ...); 0 = library choice */
+    int32_t temporal_k;    /* sweeps per HBM pass for Life (1, 2, 4, ..., 32); 0 = library
+                              choice (the autotuner's, else the largest k in [4, 16] whose
+                              tiles fit the co-resident CTAs) */
     int64_t wait_limit_ns; /* device-side barrier wait limit; <= 0 selects 2 s */
     int32_t debug_flags;   /* SLR_DEBUG_* bits; 0 in normal use */
     int32_t defect_correction; /* 1: FP64 defect correction around FP32 Jacobi inner solves
@@ -123,8 +125,20 @@ typedef struct {
                                   change the next FP64 Jacobi sweep would make); stop when
                                   it is < tol or at the cap */
     int32_t inner_sweeps;  /* binary32 sweeps per correction; 0 selects 50 */
-    int32_t reserved;
+    int32_t grid_ctas;     /* CTAs of the persistent launch, capped at the number that can
+                              be co-resident; 0 = library choice (all co-resident CTAs).
+                              Results do not depend on it. */
+    int32_t tiling;        /* slr_tiling of the RESTORE8 sweep; other stencils ignore it */
+    int32_t reserved;      /* 0 */
 } slr_desc;
+
+/* How the RESTORE8 sweep stages its input.  Results do not depend on it. */
+typedef enum {
+    SLR_TILING_AUTO = 0,   /* library choice (TMA when nx is a multiple of 16) */
+    SLR_TILING_NONE = 1,   /* each thread reads its 3x3 neighbourhood from global memory */
+    SLR_TILING_TMA = 2     /* 32x64 tiles with halo staged in shared memory by TMA
+                              (needs nx a multiple of 16; falls back to NONE otherwise) */
+} slr_tiling;
 
 /* Fault injection for tests of the device-side wait limit: the last CTA of a
  * persistent launch leaves before its first barrier arrival, so every other
@@ -247,6 +261,62 @@ slr_status slr_run_static(const slr_desc *d, void *u, const void *f, int64_t max
                           double *value, int64_t *iters, int32_t *converged);
 /* Message of the last failed slr_run_static on this host thread. */
 const char *slr_static_last_error(void);
+
+/* ---- Autotuner -------------------------------------------------------------
+ * The paper sizes its OpenCL work-groups with fixed heuristics (Sec. 3.3); this
+ * library instead times the launch choices that do not change results on the
+ * caller's own data and keeps the fastest in a process-wide cache.
+ *
+ * slr_tune searches the fields of *d left at their library-choice value:
+ *   loop        (SLR_LOOP_AUTO: persistent device loop or the host-driven loop;
+ *                defect correction keeps the persistent loop),
+ *   temporal_k  (0, Life only: generations per HBM pass, 1 = none),
+ *   tiling      (SLR_TILING_AUTO, RESTORE8 only: TMA tiles or none),
+ *   grid_ctas   (0: CTAs of the persistent launch),
+ * first loop x temporal_k x tiling with all co-resident CTAs, then grid_ctas
+ * for the winner.  Fields set explicitly are held fixed.  Each candidate runs
+ * trial_iters iterations (<= 0 selects 64, or 4 with defect correction) from a
+ * copy of u taken into `scratch`, with the convergence test disabled (Life
+ * still stops at a still state), once untimed and twice timed with CUDA events
+ * on `stream`; its score is the shorter time per iteration run.  A candidate
+ * replaces the best so far only when it is more than 1% faster, so the library
+ * default (timed first) is kept on a tie.  u and aux are only read.
+ *   scratch     device buffer of slr_tune_scratch_size(d) bytes, 256-byte
+ *               aligned, owned by the caller; free to reuse after return.
+ *   out         receives the choice with every searched field explicit (loop
+ *               HOST or PERSISTENT, temporal_k >= 1 for Life, tiling NONE or TMA
+ *               for RESTORE8, grid_ctas >= 0 where 0 kept the default), the
+ *               number of candidates timed and the two scores; may be NULL.
+ * The call waits for `stream`.  It stores the choice under (device, SM count,
+ * stencil, storage, boundary, math, defect correction, nx, ny, nz) and under
+ * the same key with each extent replaced by its power-of-two bucket
+ * (floor(log2)).  slr_create then fills the library-choice fields of a
+ * descriptor from the exact entry, else from the bucket entry, else from the
+ * built-in defaults; grid_ctas only when the descriptor then names the
+ * choice's loop, temporal_k (Life) and tiling (RESTORE8), the kernel that
+ * grid size was timed with.  Returns SLR_OK, SLR_ERR_INVALID_ARG / UNSUPPORTED for a
+ * descriptor slr_create would refuse or a NULL/misaligned pointer,
+ * SLR_ERR_WORKSPACE for a short scratch, or the error of a failed trial
+ * (message from slr_tune_last_error()), and leaves the cache unchanged then.  The
+ * cache is guarded by a mutex; concurrent slr_tune calls on one device time
+ * each other's work and should be avoided. */
+typedef struct {
+    int32_t loop, temporal_k, tiling, grid_ctas;  /* the choice */
+    int32_t trials;                               /* candidates timed */
+    int32_t reserved;
+    double ms_per_iter;                           /* score of the choice */
+    double default_ms_per_iter;                   /* score of the library default */
+} slr_tune_result;
+size_t slr_tune_scratch_size(const slr_desc *d);  /* 0 for an invalid descriptor */
+slr_status slr_tune(const slr_desc *d, const void *u, const void *aux, void *scratch, size_t scratch_bytes,
+                    void *stream, int64_t trial_iters, slr_tune_result *out);
+/* Copy the cached choice for *d (exact key, else bucket) into *out; returns 1
+ * when one exists, 0 otherwise.  Needs no GPU work. */
+int32_t slr_tune_lookup(const slr_desc *d, slr_tune_result *out);
+/* Empty the cache. */
+void slr_tune_clear(void);
+/* Message of the last failed slr_tune on this host thread. */
+const char *slr_tune_last_error(void);
 
 #ifdef __cplusplus
 }

@@ -177,7 +177,7 @@ cudaError_t dc_persistent(const Problem &p, LoopArgs la, int inner, void *fp32_a
     if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, dc_kernel, kDThreads, 0);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorCooperativeLaunchTooLarge;
-    la.nblocks = sms;
+    la.nblocks = grid_ctas(sms, 1, la.nblocks);
     void *args[] = {&a, &la};
     return cudaLaunchCooperativeKernel((const void *)dc_kernel, dim3(la.nblocks), dim3(kDThreads), args, 0, st);
 }

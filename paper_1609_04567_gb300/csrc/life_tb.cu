@@ -490,6 +490,33 @@ int life_tb_default_k(const Problem &p, int nblocks)
     return 16;
 }
 
+// CTAs of the persistent launch (at most 2 per SM, capped by `request`).
+static cudaError_t tb_grid(const Problem &p, int request, int *nblocks)
+{
+    auto kern = p.wrap ? life_tb_kernel<true> : life_tb_kernel<false>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes);
+    if (e != cudaSuccess) return e;
+    int dev = 0, sms = 0, per_sm = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, kSmemBytes)) != cudaSuccess)
+        return e;
+    if (per_sm < 1) return cudaErrorCooperativeLaunchTooLarge;
+    *nblocks = grid_ctas(sms, per_sm > 2 ? 2 : per_sm, request);
+    return cudaSuccess;
+}
+
+int life_tb_resolve_k(const Problem &p, int grid_request)
+{
+    if (p.k > 1) return p.k > kMaxK ? kMaxK : p.k;
+    int nblocks = 0;
+    if (tb_grid(p, grid_request, &nblocks) != cudaSuccess) {
+        cudaGetLastError();
+        return 1;
+    }
+    return life_tb_default_k(p, nblocks);
+}
+
 cudaError_t life_tb_persistent(const Problem &p, LoopArgs la, void *bits0, void *bits1, cudaStream_t st)
 {
     if (!life_tb_supported(p)) return cudaErrorNotSupported;
@@ -504,14 +531,9 @@ cudaError_t life_tb_persistent(const Problem &p, LoopArgs la, void *bits0, void 
     tp.pitch = pitch_words(p.nx);
     tp.wrap = p.wrap;
     auto kern = p.wrap ? life_tb_kernel<true> : life_tb_kernel<false>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes);
+    int nblocks = 0;
+    cudaError_t e = tb_grid(p, la.nblocks, &nblocks);
     if (e != cudaSuccess) return e;
-    int dev = 0, sms = 0, per_sm = 0;
-    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
-    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, kSmemBytes)) != cudaSuccess)
-        return e;
-    const int nblocks = sms * (per_sm > 2 ? 2 : per_sm);
     tp.K = p.k > 1 ? (p.k > kMaxK ? kMaxK : p.k) : life_tb_default_k(p, nblocks);
     tp.own_rows = kTileRows - 2 * tp.K;
     tp.tiles_x = (int)((p.nx + kOwnCols - 1) / kOwnCols);

@@ -322,9 +322,12 @@ bool tma_ok(const Problem &p) { return p.nx % 16 == 0 && p.nx < (1ll << 31) && p
 
 }  // namespace
 
+bool restore_tma_ok(const Problem &p) { return tma_ok(p); }
+
 cudaError_t restore_persistent(const Problem &p, LoopArgs la, cudaStream_t st)
 {
-    if (tma_ok(p)) return p.math == SLR_MATH_FAST ? launch_tma<true>(p, la, st) : launch_tma<false>(p, la, st);
+    if (p.tiling != SLR_TILING_NONE && tma_ok(p))
+        return p.math == SLR_MATH_FAST ? launch_tma<true>(p, la, st) : launch_tma<false>(p, la, st);
     if (p.math == SLR_MATH_FAST) {
         RestoreOp<true> op{p.nx, p.ny, p.alpha, (const unsigned char *)la.aux};
         return launch_cooperative(restore_persistent_kernel<RestoreOp<true>>, kRThreads, 0, 1, la, &op, st);

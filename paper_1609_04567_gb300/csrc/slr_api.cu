@@ -69,6 +69,8 @@ std::string check_desc(const slr_desc *d, bool *unsupported)
     if (d->loop < SLR_LOOP_AUTO || d->loop > SLR_LOOP_PERSISTENT) return "unknown loop mode";
     if (d->math != SLR_MATH_EXACT && d->math != SLR_MATH_FAST) return "unknown math mode";
     if (d->temporal_k < 0 || d->temporal_k > slr::kMaxK) return "temporal_k out of range";
+    if (d->grid_ctas < 0) return "grid_ctas must be >= 0";
+    if (d->tiling < SLR_TILING_AUTO || d->tiling > SLR_TILING_TMA) return "unknown tiling";
     switch (d->stencil) {
     case SLR_J2D5:
     case SLR_J3D7:
@@ -111,6 +113,7 @@ Problem make_problem(const slr_desc *d)
     p.wrap = d->boundary == SLR_WRAP;
     p.math = d->math;
     p.k = d->temporal_k;
+    p.tiling = d->tiling;
     p.nx = d->nx; p.ny = d->ny; p.nz = d->nz;
     p.ghost = d->ghost;
     p.tol = d->tol;
@@ -165,7 +168,7 @@ slr_status run_persistent(slr_handle h, int64_t max_iters)
     la.limit_ns = h->desc.wait_limit_ns > 0 ? h->desc.wait_limit_ns : 2000000000ll;
     la.tol = h->prob.tol;
     la.reduce = h->prob.reduce;
-    la.nblocks = 0;
+    la.nblocks = h->desc.grid_ctas;
     la.debug_flags = h->desc.debug_flags;
     switch (h->prob.stencil) {
     case SLR_LIFE:
@@ -247,6 +250,53 @@ namespace slr {
 // Validation and problem set-up shared with entry points in other files.
 std::string describe_invalid(const slr_desc *d, bool *unsupported) { return check_desc(d, unsupported); }
 Problem problem_of(const slr_desc *d) { return make_problem(d); }
+
+// slr_create without the autotuner's cache: the descriptor's library-choice
+// fields keep the built-in defaults.  The tuner creates its trial handles
+// with it.
+slr_status create_handle(const slr_desc *d, void *u, const void *aux, void *workspace, size_t workspace_bytes,
+                         void *stream, slr_handle *out, bool use_cache)
+{
+    if (!out) return fail(nullptr, SLR_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    bool unsup = false;
+    std::string why = check_desc(d, &unsup);
+    if (!why.empty()) return fail(nullptr, unsup ? SLR_ERR_UNSUPPORTED : SLR_ERR_INVALID_ARG, why);
+    if (!u || ((uintptr_t)u & 15u)) return fail(nullptr, SLR_ERR_INVALID_ARG, "u must be a 16-byte aligned device pointer");
+    if (d->stencil != SLR_LIFE && !aux) return fail(nullptr, SLR_ERR_INVALID_ARG, "aux (f or mask) is required");
+    if (!workspace || ((uintptr_t)workspace & 255u))
+        return fail(nullptr, SLR_ERR_INVALID_ARG, "workspace must be a 256-byte aligned device pointer");
+    const size_t need = slr_workspace_size(d);
+    if (workspace_bytes < need) {
+        char buf[128];
+        snprintf(buf, sizeof buf, "workspace too small: %zu < %zu bytes", workspace_bytes, need);
+        return fail(nullptr, SLR_ERR_WORKSPACE, buf);
+    }
+    slr_ctx *h = new (std::nothrow) slr_ctx();
+    if (!h) return fail(nullptr, SLR_ERR_INVALID_ARG, "host allocation failed");
+    h->desc = *d;
+    if (use_cache) tune_fill(&h->desc);
+    if (h->desc.loop == SLR_LOOP_AUTO) h->desc.loop = SLR_LOOP_PERSISTENT;
+    h->prob = make_problem(&h->desc);
+    h->u = u;
+    h->aux = aux;
+    h->ws = (unsigned char *)workspace;
+    h->ws_bytes = workspace_bytes;
+    h->stream = (cudaStream_t)stream;
+    memset(&h->host_ctl, 0, sizeof(Ctl));
+    h->err = "no error";
+    cudaError_t e = cudaMemsetAsync(h->ws, 0, sizeof(Ctl), h->stream);
+    if (e != cudaSuccess) {
+        cuda_fail(nullptr, e, "workspace reset");
+        delete h;
+        return SLR_ERR_CUDA;
+    }
+    *out = h;
+    return SLR_OK;
+}
+
+// The descriptor a handle runs (library-choice fields resolved).
+const slr_desc *handle_desc(slr_handle h) { return &h->desc; }
 }  // namespace slr
 
 extern "C" {
@@ -285,41 +335,7 @@ size_t slr_workspace_size(const slr_desc *d)
 slr_status slr_create(const slr_desc *d, void *u, const void *aux, void *workspace, size_t workspace_bytes,
                       void *stream, slr_handle *out)
 {
-    if (!out) return fail(nullptr, SLR_ERR_INVALID_ARG, "out is NULL");
-    *out = nullptr;
-    bool unsup = false;
-    std::string why = check_desc(d, &unsup);
-    if (!why.empty()) return fail(nullptr, unsup ? SLR_ERR_UNSUPPORTED : SLR_ERR_INVALID_ARG, why);
-    if (!u || ((uintptr_t)u & 15u)) return fail(nullptr, SLR_ERR_INVALID_ARG, "u must be a 16-byte aligned device pointer");
-    if (d->stencil != SLR_LIFE && !aux) return fail(nullptr, SLR_ERR_INVALID_ARG, "aux (f or mask) is required");
-    if (!workspace || ((uintptr_t)workspace & 255u))
-        return fail(nullptr, SLR_ERR_INVALID_ARG, "workspace must be a 256-byte aligned device pointer");
-    const size_t need = slr_workspace_size(d);
-    if (workspace_bytes < need) {
-        char buf[128];
-        snprintf(buf, sizeof buf, "workspace too small: %zu < %zu bytes", workspace_bytes, need);
-        return fail(nullptr, SLR_ERR_WORKSPACE, buf);
-    }
-    slr_ctx *h = new (std::nothrow) slr_ctx();
-    if (!h) return fail(nullptr, SLR_ERR_INVALID_ARG, "host allocation failed");
-    h->desc = *d;
-    if (h->desc.loop == SLR_LOOP_AUTO) h->desc.loop = SLR_LOOP_PERSISTENT;
-    h->prob = make_problem(&h->desc);
-    h->u = u;
-    h->aux = aux;
-    h->ws = (unsigned char *)workspace;
-    h->ws_bytes = workspace_bytes;
-    h->stream = (cudaStream_t)stream;
-    memset(&h->host_ctl, 0, sizeof(Ctl));
-    h->err = "no error";
-    cudaError_t e = cudaMemsetAsync(h->ws, 0, sizeof(Ctl), h->stream);
-    if (e != cudaSuccess) {
-        cuda_fail(nullptr, e, "workspace reset");
-        delete h;
-        return SLR_ERR_CUDA;
-    }
-    *out = h;
-    return SLR_OK;
+    return slr::create_handle(d, u, aux, workspace, workspace_bytes, stream, out, true);
 }
 
 slr_status slr_run_until(slr_handle h, int64_t max_iters)

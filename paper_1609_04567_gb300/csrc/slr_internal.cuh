@@ -209,7 +209,8 @@ struct LoopArgs {
     long long limit_ns;      // barrier wait limit
     double tol;
     int reduce;
-    int nblocks;             // grid size of the persistent launch
+    int nblocks;             // grid size of the persistent launch; on entry to a launcher,
+                             // the requested CTAs (0 = all that can be co-resident)
     int debug_flags;         // SLR_DEBUG_* (fault injection for tests)
 };
 
@@ -314,6 +315,7 @@ namespace slr {
 // from an slr_desc.
 struct Problem {
     int stencil, storage, reduce, wrap, math, k;
+    int tiling;                      // slr_tiling (RESTORE8)
     long long nx, ny, nz;
     double ghost, h2, d, tol;        // Jacobi constants in binary64: h2 = h*h, d = 2n + sigma*h2
     float ghostf, h2f, df, alpha;    // the same rounded to binary32
@@ -331,11 +333,16 @@ cudaError_t life_normalize(const Problem &p, void *u, cudaStream_t st);
 // cudaErrorNotSupported when the grid does not fit its tiling rules.
 bool life_tb_supported(const Problem &p);
 int life_tb_default_k(const Problem &p, int nblocks);
+// The k a temporal-blocked launch of p would run with `grid_request` CTAs
+// requested (p.k when > 1, else the default for the grid).
+int life_tb_resolve_k(const Problem &p, int grid_request);
 size_t life_tb_bits_bytes(long long nx, long long ny);
 cudaError_t life_tb_persistent(const Problem &p, LoopArgs la, void *bits0, void *bits1, cudaStream_t st);
 cudaError_t jacobi_persistent(const Problem &p, LoopArgs la, cudaStream_t st);
 cudaError_t jacobi_sweep(const Problem &p, const void *src, void *dst, const void *f, cudaStream_t st);
 cudaError_t restore_persistent(const Problem &p, LoopArgs la, cudaStream_t st);
+// Whether the TMA-tiled restoration sweep accepts p (nx % 16 == 0).
+bool restore_tma_ok(const Problem &p);
 cudaError_t restore_sweep(const Problem &p, const void *src, void *dst, const void *mask, cudaStream_t st);
 // FP64 defect correction around FP32 Jacobi inner solves (dc.cu).
 size_t dc_workspace_bytes(long long nx, long long ny);
@@ -348,9 +355,24 @@ cudaError_t reduce_states(const Problem &p, const void *src, const void *dst, co
 // Descriptor checks and problem set-up (slr_api.cu), for other entry points.
 std::string describe_invalid(const slr_desc *d, bool *unsupported);
 Problem problem_of(const slr_desc *d);
+// slr_create with (use_cache) or without the autotuner's cache.
+slr_status create_handle(const slr_desc *d, void *u, const void *aux, void *workspace, size_t workspace_bytes,
+                         void *stream, slr_handle *out, bool use_cache);
+const slr_desc *handle_desc(slr_handle h);
+// Fill the library-choice fields of *d from the autotuner's cache (tune.cu).
+void tune_fill(slr_desc *d);
+
+// CTAs of a persistent launch: the co-resident capacity (sms * per_sm), or
+// the request when it is smaller and positive.
+inline int grid_ctas(int sms, int per_sm, int request)
+{
+    const int cap = sms * per_sm;
+    return request > 0 && request < cap ? request : cap;
+}
 
 // Cooperative launch of a persistent kernel with as many CTAs as can be
-// co-resident (at most `max_per_sm` per SM).  Fills la.nblocks.
+// co-resident (at most `max_per_sm` per SM), or la.nblocks if that is
+// smaller and positive.  Sets la.nblocks to the grid launched.
 template <class K>
 cudaError_t launch_cooperative(K kernel, int threads, size_t smem, int max_per_sm, LoopArgs &la,
                                const void *op, cudaStream_t st)
@@ -364,7 +386,7 @@ cudaError_t launch_cooperative(K kernel, int threads, size_t smem, int max_per_s
     if (e != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorCooperativeLaunchTooLarge;
     if (per_sm > max_per_sm) per_sm = max_per_sm;
-    la.nblocks = sms * per_sm;
+    la.nblocks = grid_ctas(sms, per_sm, la.nblocks);
     void *args[] = {const_cast<void *>(op), (void *)&la};
     return cudaLaunchCooperativeKernel((const void *)kernel, dim3(la.nblocks), dim3(threads), args, smem, st);
 }

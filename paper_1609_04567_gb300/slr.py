@@ -24,6 +24,7 @@ SLR_RED_MAX_ABS_DELTA, SLR_RED_MEAN_ABS_DELTA_MASKED, SLR_RED_LIVE_COUNT = 0, 1,
 SLR_U8, SLR_BF16, SLR_F16, SLR_F32, SLR_F64 = 0, 1, 2, 3, 4
 SLR_LOOP_AUTO, SLR_LOOP_HOST, SLR_LOOP_PERSISTENT = 0, 1, 2
 SLR_MATH_EXACT, SLR_MATH_FAST = 0, 1
+SLR_TILING_AUTO, SLR_TILING_NONE, SLR_TILING_TMA = 0, 1, 2
 SLR_DEBUG_SKIP_ARRIVAL = 1
 
 STATUS_NAMES = {0: "SLR_OK", 1: "SLR_NOT_CONVERGED", -1: "SLR_ERR_INVALID_ARG", -2: "SLR_ERR_WORKSPACE",
@@ -39,15 +40,28 @@ class slr_desc(ctypes.Structure):
         ("h", ctypes.c_double), ("alpha", ctypes.c_float),
         ("loop", ctypes.c_int32), ("math", ctypes.c_int32), ("temporal_k", ctypes.c_int32),
         ("wait_limit_ns", ctypes.c_int64), ("debug_flags", ctypes.c_int32),
-        ("defect_correction", ctypes.c_int32), ("inner_sweeps", ctypes.c_int32), ("reserved", ctypes.c_int32),
+        ("defect_correction", ctypes.c_int32), ("inner_sweeps", ctypes.c_int32), ("grid_ctas", ctypes.c_int32),
+        ("tiling", ctypes.c_int32), ("reserved", ctypes.c_int32),
     ]
+
+
+class slr_tune_result(ctypes.Structure):
+    _fields_ = [
+        ("loop", ctypes.c_int32), ("temporal_k", ctypes.c_int32), ("tiling", ctypes.c_int32),
+        ("grid_ctas", ctypes.c_int32), ("trials", ctypes.c_int32), ("reserved", ctypes.c_int32),
+        ("ms_per_iter", ctypes.c_double), ("default_ms_per_iter", ctypes.c_double),
+    ]
+
+    def as_dict(self) -> dict:
+        return {name: getattr(self, name) for name, _ in self._fields_ if name != "reserved"}
 
 
 EXPORTS = ["slr_desc_init", "slr_workspace_size", "slr_create", "slr_run_until", "slr_reduce_value",
            "slr_destroy", "slr_last_error", "slr_version", "slr_run_static", "slr_static_last_error",
            "slr_batch_workspace_size", "slr_batch_scratch_size", "slr_batch_create", "slr_batch_add",
            "slr_batch_run", "slr_batch_poll", "slr_batch_result", "slr_batch_remove", "slr_batch_destroy",
-           "slr_batch_last_error"]
+           "slr_batch_last_error", "slr_tune_scratch_size", "slr_tune", "slr_tune_lookup", "slr_tune_clear",
+           "slr_tune_last_error"]
 SLR_STATIC_STATE_BYTES = 4 << 20
 
 _lib = None
@@ -114,6 +128,17 @@ def load(path: str = LIB_PATH):
     lib.slr_batch_destroy.restype = i32
     lib.slr_batch_last_error.argtypes = [P]
     lib.slr_batch_last_error.restype = ctypes.c_char_p
+    R = ctypes.POINTER(slr_tune_result)
+    lib.slr_tune_scratch_size.argtypes = [D]
+    lib.slr_tune_scratch_size.restype = ctypes.c_size_t
+    lib.slr_tune.argtypes = [D, P, P, P, ctypes.c_size_t, P, i64, R]
+    lib.slr_tune.restype = i32
+    lib.slr_tune_lookup.argtypes = [D, R]
+    lib.slr_tune_lookup.restype = i32
+    lib.slr_tune_clear.argtypes = []
+    lib.slr_tune_clear.restype = None
+    lib.slr_tune_last_error.argtypes = []
+    lib.slr_tune_last_error.restype = ctypes.c_char_p
     _lib = lib
     return lib
 
@@ -240,6 +265,54 @@ def slr_batch_destroy(b: int) -> int:
 
 def slr_batch_last_error(b) -> str:
     return load().slr_batch_last_error(b).decode()
+
+
+def slr_tune_scratch_size(d: slr_desc) -> int:
+    return int(load().slr_tune_scratch_size(ctypes.byref(d)))
+
+
+def slr_tune(d: slr_desc, u_ptr: int, aux_ptr: int, scratch_ptr: int, scratch_bytes: int, stream: int,
+             trial_iters: int = 0) -> slr_tune_result:
+    r = slr_tune_result()
+    st = load().slr_tune(ctypes.byref(d), u_ptr or None, aux_ptr or None, scratch_ptr or None, scratch_bytes,
+                         stream or None, trial_iters, ctypes.byref(r))
+    if st != SLR_OK:
+        raise SlrError(st, slr_tune_last_error())
+    return r
+
+
+def slr_tune_lookup(d: slr_desc):
+    """The cached choice for d, or None."""
+    r = slr_tune_result()
+    return r if load().slr_tune_lookup(ctypes.byref(d), ctypes.byref(r)) else None
+
+
+def slr_tune_clear() -> None:
+    load().slr_tune_clear()
+
+
+def slr_tune_last_error() -> str:
+    return load().slr_tune_last_error().decode()
+
+
+def tune(stencil: int, u, aux=None, *, stream=None, trial_iters: int = 0, **fields) -> dict:
+    """Autotune the launch choices for a problem shaped like ``u`` on its
+    own data (u and aux are only read); later Solvers of the same shape pick
+    the choice up.  Returns the choice as a dict."""
+    import torch
+    shape = tuple(u.shape)
+    nz, ny, nx = (1,) * (3 - len(shape)) + shape
+    d = slr_desc_init(stencil, nx, ny, nz, storage=storage_of(u.dtype), **fields)
+    stream = stream if stream is not None else torch.cuda.current_stream(u.device)
+    nbytes = slr_tune_scratch_size(d)
+    if nbytes == 0:
+        slr_tune(d, u.data_ptr(), aux.data_ptr() if aux is not None else 0, 0, 0, stream.cuda_stream)
+        raise SlrError(SLR_ERR_INVALID_ARG, "invalid descriptor")
+    scratch = torch.empty(nbytes + 256, dtype=torch.uint8, device=u.device)
+    off = (-scratch.data_ptr()) % 256
+    r = slr_tune(d, u.data_ptr(), aux.data_ptr() if aux is not None else 0, scratch.data_ptr() + off, nbytes,
+                 stream.cuda_stream, trial_iters)
+    return r.as_dict()
 
 
 class Batch:

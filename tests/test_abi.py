@@ -91,3 +91,55 @@ def test_create_rejects_bad_arguments_without_touching_the_gpu(lib):
 def test_version_names_the_architecture(lib):
     from paper_1609_04567_gb300 import slr
     assert "sm_103a" in slr.slr_version()
+
+
+def _c_layout(struct, fields, tmp_path):
+    """sizeof and field offsets of a C struct of slr.h, from gcc."""
+    src = tmp_path / "layout.c"
+    body = "".join(f'    printf("%zu\\n", offsetof({struct}, {f}));\n' for f in fields)
+    src.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "slr.h"\nint main(void) {\n'
+                   f'    printf("%zu\\n", sizeof({struct}));\n{body}    return 0;\n}}\n')
+    exe = tmp_path / "layout"
+    import subprocess
+    subprocess.run(["gcc", "-std=c99", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split()
+    return [int(x) for x in out]
+
+
+@pytest.mark.parametrize("struct", ["slr_desc", "slr_tune_result"])
+def test_binding_struct_layout_matches_the_header(struct, tmp_path):
+    from paper_1609_04567_gb300 import slr
+    cls = getattr(slr, struct)
+    fields = [name for name, _ in cls._fields_]
+    got = _c_layout(struct, fields, tmp_path)
+    assert got[0] == ctypes.sizeof(cls)
+    assert got[1:] == [getattr(cls, f).offset for f in fields]
+
+
+def test_tuning_fields_are_validated(lib):
+    from paper_1609_04567_gb300 import slr
+    d = slr.slr_desc_init(slr.SLR_J2D5, 64, 64, 1)
+    assert d.grid_ctas == 0 and d.tiling == slr.SLR_TILING_AUTO
+    assert slr.slr_workspace_size(d) > 0
+    assert slr.slr_workspace_size(slr.slr_desc_init(slr.SLR_J2D5, 64, 64, 1, grid_ctas=-1)) == 0
+    assert slr.slr_workspace_size(slr.slr_desc_init(slr.SLR_RESTORE8, 64, 64, 1, tiling=3)) == 0
+    assert slr.slr_workspace_size(slr.slr_desc_init(slr.SLR_J2D5, 64, 64, 1, grid_ctas=7)) > 0
+
+
+def test_tune_scratch_size_and_argument_checks(lib):
+    from paper_1609_04567_gb300 import slr
+    d = slr.slr_desc_init(slr.SLR_LIFE, 8192, 8192, 1)
+    assert slr.slr_tune_scratch_size(d) == 8192 * 8192 + slr.slr_workspace_size(d)
+    assert slr.slr_tune_scratch_size(slr.slr_desc_init(slr.SLR_LIFE, 0, 8, 1)) == 0
+    assert slr.slr_tune_lookup(d) is None          # nothing tuned in this process
+    with pytest.raises(slr.SlrError) as e:
+        slr.slr_tune(d, 0x1000, 0, 0x3000, 16, 0)   # scratch too small
+    assert e.value.status == slr.SLR_ERR_WORKSPACE
+    with pytest.raises(slr.SlrError) as e:
+        slr.slr_tune(d, 0x1000, 0, 0x3001, 1 << 30, 0)  # misaligned scratch
+    assert e.value.status == slr.SLR_ERR_INVALID_ARG
+    j = slr.slr_desc_init(slr.SLR_J2D5, 8, 8, 1)
+    with pytest.raises(slr.SlrError) as e:
+        slr.slr_tune(j, 0x1000, 0, 0x3000, 1 << 20, 0)  # Jacobi needs f
+    assert "aux" in slr.slr_tune_last_error()
+    slr.slr_tune_clear()

@@ -29,12 +29,13 @@ def prepare(f64, storage):
 
 
 def jacobi_case(slr, orc, shape, storage="f64", tol=1e-6, max_iters=5000, wrap=False, ghost=0.0,
-                sigma=1.0, h=0.0, loop=None, seed=1):
+                sigma=1.0, h=0.0, loop=None, seed=1, **extra):
     from paper_1609_04567_gb300 import inputs
     f64 = inputs.helmholtz_rhs(shape, seed=seed)
     ft, fo = prepare(f64, storage)
     u = torch.zeros(shape, dtype=TORCH[storage], device="cuda")
-    fields = dict(tol=tol, boundary=slr.SLR_WRAP if wrap else slr.SLR_DIRICHLET, ghost=ghost, sigma=sigma, h=h)
+    fields = dict(tol=tol, boundary=slr.SLR_WRAP if wrap else slr.SLR_DIRICHLET, ghost=ghost, sigma=sigma, h=h,
+                  **extra)
     if loop is not None:
         fields["loop"] = loop
     stencil = slr.SLR_J3D7 if len(shape) == 3 else slr.SLR_J2D5

@@ -9,11 +9,11 @@ from conftest import run_solver
 pytestmark = pytest.mark.gpu
 
 
-def life_case(slr, orc, cells, wrap, gens, loop):
+def life_case(slr, orc, cells, wrap, gens, loop, **extra):
     from paper_1609_04567_gb300 import slr as S
     u = torch.from_numpy(cells).cuda()
     out, r = run_solver(slr, S.SLR_LIFE, u, None, gens,
-                        boundary=S.SLR_WRAP if wrap else S.SLR_DIRICHLET, loop=loop)
+                        boundary=S.SLR_WRAP if wrap else S.SLR_DIRICHLET, loop=loop, **extra)
     ref, rr = orc.life(cells, wrap=wrap, max_gens=gens)
     assert np.array_equal(out, ref)
     assert (r.iters, r.count, r.converged) == (rr.iters, rr.count, rr.converged)

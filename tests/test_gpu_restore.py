@@ -8,13 +8,13 @@ import torch
 pytestmark = pytest.mark.gpu
 
 
-def restore_case(slr, orc, ny, nx, tol=1e-3, max_iters=5000, math=0, loop=None, seed=1):
+def restore_case(slr, orc, ny, nx, tol=1e-3, max_iters=5000, math=0, loop=None, seed=1, **extra):
     from paper_1609_04567_gb300 import inputs
     frame, _ = inputs.noisy_frame(ny, nx, seed=seed)
     mask = inputs.noise_mask(frame)
     u = torch.from_numpy(frame.astype(np.float32)).cuda()
     m = torch.from_numpy(mask).cuda()
-    fields = dict(tol=tol, math=math)
+    fields = dict(tol=tol, math=math, **extra)
     if loop is not None:
         fields["loop"] = loop
     s = slr.Solver(slr.SLR_RESTORE8, u, m, **fields)

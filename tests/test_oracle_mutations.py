@@ -1,0 +1,115 @@
+"""The oracle's pins catch plausible mistakes.
+
+Each case plants one mistake in a copy of oracle/slr_oracle.c (a dropped term,
+a wrong sign, a shifted index, a changed rule, a wrong rounding or a moved
+convergence test), rebuilds the copy with gcc and runs the oracle pin tests
+against it in a subprocess; the pins must fail.  The unmutated copy must pass.
+Only the copy under pytest's temporary directory is touched.  CPU only."""
+import os
+import shutil
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+# (name, exact text in slr_oracle.c, replacement)
+MUTATIONS = [
+    ("J2D5 drops the east neighbour",
+     "            double s = ((uN + uS) + uW) + uE;",
+     "            double s = ((uN + uS) + uW);"),
+    ("J2D5 sigma term with the wrong sign",
+     "    double hh = mesh_h(h, nx), h2 = hh * hh, d = 4.0 + sigma * h2;\n    size_t n = (size_t)(nx * ny);\n"
+     "    double *v = (double *)malloc(n * sizeof(double));",
+     "    double hh = mesh_h(h, nx), h2 = hh * hh, d = 4.0 - sigma * h2;\n    size_t n = (size_t)(nx * ny);\n"
+     "    double *v = (double *)malloc(n * sizeof(double));"),
+    ("J2D5 h instead of h squared",
+     "            double t = h2 * f[i * nx + j];",
+     "            double t = sqrt(h2) * f[i * nx + j];"),
+    ("J2D5 south neighbour two rows down",
+     "            double uS = at2_f64(u, nx, ny, i + 1, j, wrap, ghost);",
+     "            double uS = at2_f64(u, nx, ny, i + 2, j, wrap, ghost);"),
+    ("J3D7 drops the z+ neighbour",
+     "                               at3_f64(u, nx, ny, nz, k + 1, i, j, wrap, ghost);\n"
+     "                    size_t c = (size_t)((k * ny + i) * nx + j);\n                    double nv",
+     "                               0.0;\n"
+     "                    size_t c = (size_t)((k * ny + i) * nx + j);\n                    double nv"),
+    ("J2D5 counts one sweep too few",
+     "        memcpy(u, v, n * sizeof(double));   /* a = fst(b) */\n        it += 1;\n"
+     "        conv = val < tol;\n    } while (!conv && it < max_iters);\n    free(v);\n"
+     "    res->iters = it;",
+     "        memcpy(u, v, n * sizeof(double));   /* a = fst(b) */\n        it += 1;\n"
+     "        conv = val < tol;\n    } while (!conv && it < max_iters);\n    free(v);\n"
+     "    res->iters = it - (it > 1);"),
+    ("Life rule S23 becomes S3",
+     "                int next = (alive_nbrs == 3) || (self && alive_nbrs == 2);",
+     "                int next = (alive_nbrs == 3);"),
+    ("Life wrap-around off by one to the west",
+     "                        if (wrap) { y = wrap_index(y, ny); x = wrap_index(x, nx); }",
+     "                        if (wrap) { y = wrap_index(y, ny); x = wrap_index(x + (x < 0), nx); }"),
+    ("restoration skips a neighbour",
+     "                        if (di == 0 && dj == 0) continue;\n                        int64_t y = i + di, x = j + dj;\n"
+     "                        if (y < 0 || y >= ny || x < 0 || x >= nx) continue;\n                        float uj",
+     "                        if (di == 0 && dj >= 0) continue;\n                        int64_t y = i + di, x = j + dj;\n"
+     "                        if (y < 0 || y >= ny || x < 0 || x >= nx) continue;\n                        float uj"),
+    ("restoration weight without the square root",
+     "                        float w = 1.0f / sqrtf(alpha + t * t);",
+     "                        float w = 1.0f / (alpha + t * t);"),
+    ("restoration weight with alpha 1",
+     "                        float w = 1.0f / sqrtf(alpha + t * t);",
+     "                        float w = 1.0f / sqrtf(1.0f + t * t);"),
+    ("restoration mean over every pixel",
+     "        mean = nmask ? ((double)sum * 0x1p-24) / (double)nmask : 0.0;",
+     "        mean = nmask ? ((double)sum * 0x1p-24) / (double)n : 0.0;"),
+    ("defect correction with the defect's sign flipped",
+     "            double rv = f[i * nx + j] - au;",
+     "            double rv = au - f[i * nx + j];"),
+    ("bfloat16 rounds half up instead of to even",
+     "    if (rest > 0x8000u || (rest == 0x8000u && (keep & 1u)))\n        keep += 1u;",
+     "    if (rest >= 0x8000u)\n        keep += 1u;"),
+    ("binary16 subnormal shift off by one",
+     "    int32_t shift = -(e + 1);                        /* >= 14 */",
+     "    int32_t shift = -(e + 2);                        /* >= 14 */"),
+]
+
+
+def run_pins(tmp_path, source: str) -> subprocess.CompletedProcess:
+    """Run the oracle pin tests against `source` as oracle/slr_oracle.c."""
+    work = tmp_path / "copy"
+    shutil.copytree(os.path.join(ROOT, "oracle"), work / "oracle",
+                    ignore=shutil.ignore_patterns("*.so", "*.tmp", "__pycache__"))
+    (work / "oracle" / "slr_oracle.c").write_text(source)
+    (work / "tests").mkdir()
+    for name in os.listdir(os.path.join(ROOT, "tests")):
+        if name == "conftest.py" or (name.startswith("test_oracle_") and name.endswith(".py")
+                                     and name != os.path.basename(__file__)):
+            shutil.copy(os.path.join(ROOT, "tests", name), work / "tests" / name)
+    shutil.copytree(os.path.join(ROOT, "tests", "golden"), work / "tests" / "golden")
+    shutil.copy(os.path.join(ROOT, "pytest.ini"), work / "pytest.ini")
+    env = dict(os.environ, PYTHONPATH=ROOT)     # the input generators come from the package
+    return subprocess.run([sys.executable, "-m", "pytest", "-q", "-x", "-m", "not gpu", "tests"],
+                          cwd=work, env=env, capture_output=True, text=True, timeout=300)
+
+
+def oracle_source() -> str:
+    with open(os.path.join(ROOT, "oracle", "slr_oracle.c")) as fh:
+        return fh.read()
+
+
+def test_unmutated_copy_passes(tmp_path):
+    p = run_pins(tmp_path, oracle_source())
+    assert p.returncode == 0, p.stdout[-2000:]
+
+
+@pytest.mark.parametrize("name,old,new", MUTATIONS, ids=[m[0] for m in MUTATIONS])
+def test_pins_catch_the_mistake(tmp_path, name, old, new):
+    src = oracle_source()
+    assert src.count(old) == 1, f"mutation site of '{name}' not found once in slr_oracle.c"
+    mutated = src.replace(old, new)
+    # the mutant must build: a compile error would fail the pins for the wrong reason
+    c = tmp_path / "mutant.c"
+    c.write_text(mutated)
+    subprocess.run(["gcc", "-std=c11", "-fsyntax-only", str(c)], check=True)
+    p = run_pins(tmp_path, mutated)
+    assert p.returncode != 0, f"'{name}' was not caught by any pin:\n{p.stdout[-1500:]}"
