@@ -545,6 +545,48 @@ def run_restore(args):
     return 0
 
 
+def run_jacobi(args):
+    """Large single Jacobi grids, HBM-bound: 2D 5-point 8192 x 8192 in FP32 and
+    BF16 storage, 3D 7-point 512^3 in BF16 storage; a fixed number of sweeps
+    (convergence test never met) in one persistent launch; HBM GB/s from the
+    algorithmic bytes per cell per sweep (read u and f, write u')."""
+    import torch
+    from paper_1609_04567_gb300 import inputs, slr
+    slr.load()
+    peak, peak_src = measured_peaks()
+    stream = torch.cuda.Stream()
+    cases = [("j2d5_8192x8192_f32", slr.SLR_J2D5, (8192, 8192), torch.float32, 200),
+             ("j2d5_8192x8192_bf16", slr.SLR_J2D5, (8192, 8192), torch.bfloat16, 200),
+             ("j3d7_512x512x512_bf16", slr.SLR_J3D7, (512, 512, 512), torch.bfloat16, 50)]
+    out = {}
+    for name, stencil, shape, dt, sweeps in cases:
+        f = torch.from_numpy(inputs.helmholtz_rhs(shape)).to(torch.float32).to(dt).cuda()
+        u = torch.zeros(shape, dtype=dt, device="cuda")
+        with torch.cuda.stream(stream):
+            s = slr.Solver(stencil, u, f, stream=stream, tol=0.0)
+
+            def step():
+                slr.slr_destroy(s.handle)
+                s.handle = slr.slr_create(s.desc, u.data_ptr(), f.data_ptr(),
+                                          s.ws.data_ptr() + ((-s.ws.data_ptr()) % 256),
+                                          slr.slr_workspace_size(s.desc), stream.cuda_stream)
+                s.run(sweeps)
+            for _ in range(args.warmup):
+                step()
+            ms = _stream_time(stream, step, args.steps)
+            r = s.result(check=False)
+            s.close()
+        cells = u.numel()
+        bpc = 3 * u.element_size()
+        gbs = bpc * cells * r.iters / (ms / 1e3) / 1e9
+        out[name] = {"ms": ms, "sweeps": r.iters, "gcell_per_s": cells * r.iters / ms / 1e6,
+                     "hbm_gbs": gbs, "frac": gbs / peak, "bytes_per_cell_sweep": bpc}
+    line = {"workload": "jacobi_large_grids", "metric": "HBM GB/s per sweep", "unit": "GB/s",
+            "peak": peak, "peak_source": peak_src, "cases": out}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_batch(args):
     """512 2D Helmholtz grids (side log-uniform in [64, 1024]) + one 512^3 3D
     grid, bfloat16 storage, tol 1e-6, in one batch; against the same grids
@@ -636,7 +678,8 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="life", choices=["life", "helmholtz", "restore", "batch", "serve"])
+    ap.add_argument("--workload", default="life",
+                    choices=["life", "helmholtz", "restore", "jacobi", "batch", "serve"])
     ap.add_argument("--batch3d", type=int, default=512, help="side of the 3D grid of the batch workload (0: none)")
     ap.add_argument("--rate", type=float, default=2000.0)
     ap.add_argument("--serve-seconds", type=float, default=10.0)
@@ -655,7 +698,8 @@ def main():
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     if args.workload != "life":
-        fn = {"helmholtz": run_helmholtz, "restore": run_restore, "batch": run_batch, "serve": run_serve}
+        fn = {"helmholtz": run_helmholtz, "restore": run_restore, "jacobi": run_jacobi, "batch": run_batch,
+              "serve": run_serve}
         return fn[args.workload](args)
     wl = WORKLOADS[args.workload]
     world, rank, local = dist_setup()

@@ -318,6 +318,32 @@ void slr_tune_clear(void);
 /* Message of the last failed slr_tune on this host thread. */
 const char *slr_tune_last_error(void);
 
+/* ---- Self-check of the restoration's EXACT arithmetic ----------------------
+ * EXACT RESTORE8 sweeps form each weight 1 / sqrt(alpha + t*t) with the two
+ * IEEE roundings of a sequential 1.0f / sqrtf(x), from the hardware estimates
+ * plus one fused-multiply-add correction each (Markstein's method).  This
+ * call checks that arithmetic on the device against CUDA's IEEE operations
+ * __frcp_rn(__fsqrt_rn(x)) for every non-negative binary32 x (2^31 inputs):
+ * mismatches[0] counts inputs whose weight bits differ, mismatches[1] and
+ * mismatches[2] the square roots and reciprocals on the inputs that take the
+ * estimate route; *checked receives the number of inputs (2^31).  All three
+ * counts are 0 on a correct build.  Waits for `stream`; the counters live in a
+ * static device array (no allocation).  Either pointer may be NULL. */
+slr_status slr_check_exact_math(uint64_t *mismatches, uint64_t *checked, void *stream);
+
+/* Self-check of the Jacobi sweeps' division by the constant d = 2n + sigma h^2:
+ * EXACT sweeps form RN(a / d) from the correctly rounded reciprocal of d and
+ * two fused-multiply-add corrections (Markstein's method) when |a| and |d|
+ * lie in [2^-40, 2^40) (binary32) or [2^-400, 2^400) (binary64), and call the
+ * IEEE division otherwise.  For the given d this compares that quotient with
+ * CUDA's __fdiv_rn for every binary32 numerator (2^32) and with __ddiv_rn for
+ * 2^26 binary64 numerators spread over exponents -600..600; mismatches[0]
+ * and [1] count differing quotients (binary32, binary64; NaN quotients agree
+ * as NaNs), checked[0] and [1] the numerators tried.  Both counts are 0 on a
+ * correct build.  Returns SLR_ERR_INVALID_ARG when d (or (float)d) is outside
+ * the range above.  Waits for `stream`; static device counters. */
+slr_status slr_check_exact_division(double d, uint64_t *mismatches, uint64_t *checked, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -22,6 +22,7 @@
 #include <string>
 #include <vector>
 
+#include "crmath.cuh"
 #include "slr_internal.cuh"
 
 namespace slr {
@@ -270,7 +271,7 @@ __device__ void restore_unit(const BInst &I, long long unit, const void *uv, voi
                     if (!inner && (y + di < 0 || y + di >= I.ny || x + dj < 0 || x + dj >= I.nx)) continue;
                     const float uj = tile[(rr + 1 + di) * kSW + cc + 1 + dj];
                     const float tt = __fsub_rn(uc, uj);
-                    const float w = __frcp_rn(__fsqrt_rn(__fadd_rn(I.alpha, __fmul_rn(tt, tt))));
+                    const float w = inv_sqrt_rn2(__fadd_rn(I.alpha, __fmul_rn(tt, tt)));
                     num = __fadd_rn(num, __fmul_rn(w, uj));
                     den = __fadd_rn(den, w);
                 }

@@ -12,12 +12,17 @@
 // operation is an explicitly rounded IEEE operation (no contraction into
 // fused multiply-adds), in the order above, so results are bit-identical to a
 // sequential evaluation of the same formula.
+#include <string.h>
+
+#include <type_traits>
+
+#include "crmath.cuh"
 #include "slr_internal.cuh"
 
 namespace slr {
 namespace {
 
-constexpr int kJThreads = 1024;
+constexpr int kJThreads = 256;
 
 // ---- storage types --------------------------------------------------------
 template <class T> struct Store;
@@ -95,85 +100,241 @@ __device__ __forceinline__ unsigned long long widen_bits(unsigned int m)
 template <class C> struct MaxBits { using type = unsigned long long; };
 template <> struct MaxBits<float> { using type = unsigned int; };
 
-template <class T, int DIM>
-struct JacobiOp {
+// ---- streaming sweep ----------------------------------------------------------
+// A warp owns a segment of 32*V consecutive cells of a row (V cells per lane,
+// one 16-byte access when the row allows it) and marches along the slowest
+// axis (y in 2D, z in 3D) over a run of rows or planes, keeping a window of
+// rows of its segment in registers and loading the next few rows (and their
+// f) together before computing them: each cell of u
+// is loaded from memory about once per sweep in 2D (the 3D sweep also loads
+// the rows y - 1 and y + 1 of the current plane, which the neighbouring warps
+// have just brought into L2).  x-neighbours come from the adjacent lanes by
+// shuffles; the segment's two outer neighbours, and those beyond the grid,
+// by single loads with the boundary rule.
+// V consecutive cells of a row in their storage format, packed in 32-bit
+// words (4 words for a 16-byte group), widened to the compute type on use; a
+// row past a Dirichlet edge is flagged instead (its cells read as the ghost).
+template <class T, int V>
+struct Packed {
+    static constexpr int kWords = (V * (int)sizeof(T) + 3) / 4;
+    uint32_t w[kWords];
+    bool ghost;
+
+    __device__ __forceinline__ void load(const T *p, bool readonly)
+    {
+        ghost = false;
+        if constexpr (V * sizeof(T) == 16) {
+            const uint4 r = readonly ? __ldg((const uint4 *)p) : __ldcg((const uint4 *)p);
+            w[0] = r.x; w[1] = r.y; w[2] = r.z; w[3] = r.w;
+        } else if constexpr (sizeof(T) == 8) {
+            const unsigned long long r = readonly ? __ldg((const unsigned long long *)p)
+                                                  : __ldcg((const unsigned long long *)p);
+            w[0] = (uint32_t)r; w[1] = (uint32_t)(r >> 32);
+        } else if constexpr (sizeof(T) == 4) {
+            w[0] = readonly ? __ldg((const unsigned int *)p) : __ldcg((const unsigned int *)p);
+        } else {
+            w[0] = readonly ? __ldg((const unsigned short *)p) : __ldcg((const unsigned short *)p);
+        }
+    }
+
+    // cell k widened (exact: every storage value is a compute-type value)
+    __device__ __forceinline__ typename Store<T>::C raw(int k) const
+    {
+        if constexpr (sizeof(T) == 8) {
+            return __hiloint2double((int)w[2 * k + 1], (int)w[2 * k]);
+        } else if constexpr (sizeof(T) == 4) {
+            return __uint_as_float(w[k]);
+        } else {
+            const uint32_t h = (k & 1) ? (w[k >> 1] >> 16) : (w[k >> 1] & 0xFFFFu);
+            if constexpr (std::is_same<T, __nv_bfloat16>::value) return __uint_as_float(h << 16);
+            else return __half2float(__ushort_as_half((unsigned short)h));
+        }
+    }
+
+    __device__ __forceinline__ typename Store<T>::C at(int k, typename Store<T>::C g) const
+    {
+        return ghost ? g : raw(k);
+    }
+};
+
+// storage bits of one value, in the low bits of a 32-bit word (2-byte types)
+__device__ __forceinline__ uint32_t bits16(__nv_bfloat16 h) { return (uint32_t)__bfloat16_as_ushort(h); }
+__device__ __forceinline__ uint32_t bits16(__half h) { return (uint32_t)__half_as_ushort(h); }
+
+// ---- streaming sweep ----------------------------------------------------------
+// A warp owns a segment of 32*V consecutive cells of a row (V cells per lane,
+// one 16-byte access when the row allows it) and marches along the slowest
+// axis (y in 2D, z in 3D) over a run of rows or planes, keeping a window of
+// rows of its segment in registers and loading the next few rows (and their
+// f) together before computing them: each cell of u
+// is loaded from memory about once per sweep in 2D (the 3D sweep also loads
+// the rows y - 1 and y + 1 of the current plane, which the neighbouring warps
+// have just brought into L2).  x-neighbours come from the adjacent lanes by
+// shuffles; the segment's two outer neighbours, and those beyond the grid,
+// by single loads with the boundary rule.
+template <class T, int DIM, int V>
+struct JacobiStream {
     using C = typename Store<T>::C;
-    long long nx, ny, nz;
+    using Row = Packed<T, V>;
+    static constexpr int kSeg = 32 * V;   // cells per warp segment
+    int nx, ny, nz;                       // extents, each below 2^31 - 4096
+    int nseg;                             // segments per row
+    int run;                              // rows (2D) or planes (3D) one warp marches per unit
     int wrap;
     C ghost, h2, d;
+    C yd;                                 // RN(1 / d)
+    int dconst;                           // d in the range of div_const_rn
     const T *f;
 
     __device__ __forceinline__ size_t state_bytes() const { return (size_t)nx * ny * nz * sizeof(T); }
+    __device__ __forceinline__ void prologue() const {}
 
-    // value at (k, i, j) with the boundary rule
-    __device__ __forceinline__ C at(const T *u, long long k, long long i, long long j) const
+    __device__ __forceinline__ C divide(C a) const { return dconst ? div_const_rn(a, d, yd) : div_rn(a, d); }
+
+    __device__ __forceinline__ size_t off(int y, int z, int x) const { return ((size_t)z * ny + y) * nx + x; }
+
+    // the segment of row (y, z) starting at x, or a ghost row past a Dirichlet edge
+    __device__ __forceinline__ void row(const T *u, int y, int z, int x, bool ok, Row &r) const
     {
-        if (i < 0 || i >= ny || j < 0 || j >= nx || k < 0 || k >= nz) {
-            if (!wrap) return ghost;
-            i = i < 0 ? i + ny : (i >= ny ? i - ny : i);
-            j = j < 0 ? j + nx : (j >= nx ? j - nx : j);
-            k = k < 0 ? k + nz : (k >= nz ? k - nz : k);
+        if (y < 0 || y >= ny || z < 0 || z >= nz) {
+            if (!wrap) {
+                r.ghost = true;
+                return;
+            }
+            y = y < 0 ? y + ny : (y >= ny ? y - ny : y);
+            z = z < 0 ? z + nz : (z >= nz ? z - nz : z);
         }
-        return Store<T>::ld(u + (k * ny + i) * nx + j);
+        if (ok) r.load(u + off(y, z, x), false);
+        else r.ghost = true;
+    }
+
+    // cell (y, z, x) of an in-range row, x possibly -1 or nx
+    __device__ __forceinline__ C cell(const T *u, int y, int z, int x) const
+    {
+        if (x < 0 || x >= nx) {
+            if (!wrap) return ghost;
+            x = x < 0 ? x + nx : x - nx;
+        }
+        return Store<T>::ld(u + off(y, z, x));
+    }
+
+    // new values of the lane's V cells of row (y, z): c = this row, a/b = the
+    // rows before/after along the march (y in 2D, z in 3D), n/s = the rows
+    // y - 1 / y + 1 of the same plane (3D)
+    template <bool REDUCE>
+    __device__ __forceinline__ void update(const T *u, T *v, int y, int z, int x, bool ok, int lane, const Row &a,
+                                           const Row &c, const Row &b, const Row &fr, const Row &n, const Row &s,
+                                           typename MaxBits<C>::type &mx) const
+    {
+        C left = __shfl_up_sync(0xffffffffu, c.raw(V - 1), 1);
+        C right = __shfl_down_sync(0xffffffffu, c.raw(0), 1);
+        if (!ok) return;                                   // past the end of the row
+        if (lane == 0) left = cell(u, y, z, x - 1);
+        if (lane == 31 || x + V >= nx) right = cell(u, y, z, x + V);   // x + V <= nx here
+        uint32_t ow[Row::kWords];                          // the new values, packed like a Row
+#pragma unroll
+        for (int k = 0; k < V; ++k) {
+            const C w = k > 0 ? c.raw(k - 1) : left, e = k < V - 1 ? c.raw(k + 1) : right;
+            C sum;
+            if (DIM == 2) sum = add_rn(add_rn(add_rn(a.at(k, ghost), b.at(k, ghost)), w), e);
+            else sum = add_rn(add_rn(add_rn(add_rn(add_rn(w, e), n.at(k, ghost)), s.at(k, ghost)), a.at(k, ghost)),
+                              b.at(k, ghost));
+            const T o = Store<T>::st(divide(add_rn(mul_rn(h2, fr.raw(k)), sum)));
+            if (REDUCE) max_bits(mx, sub_rn(Store<T>::back(o), c.raw(k)));
+            if constexpr (sizeof(T) == 8) {
+                ow[2 * k] = (uint32_t)__double2loint((double)o);
+                ow[2 * k + 1] = (uint32_t)__double2hiint((double)o);
+            } else if constexpr (sizeof(T) == 4) {
+                ow[k] = __float_as_uint((float)o);
+            } else {
+                if (k & 1) ow[k >> 1] |= bits16(o) << 16;
+                else ow[k >> 1] = bits16(o);
+            }
+        }
+        T *dst = v + off(y, z, x);
+        if constexpr (V * sizeof(T) == 16) *(uint4 *)dst = make_uint4(ow[0], ow[1], ow[2], ow[3]);
+        else if constexpr (sizeof(T) == 8) *(unsigned long long *)dst = (unsigned long long)ow[1] << 32 | ow[0];
+        else if constexpr (sizeof(T) == 4) *(unsigned int *)dst = ow[0];
+        else *(unsigned short *)dst = (unsigned short)ow[0];
     }
 
     template <bool REDUCE>
     __device__ __forceinline__ void sweep(const void *src_v, void *dst_v, Slot *slot) const
     {
+        constexpr int P = DIM == 2 ? 4 : 2;                    // rows computed per batch of loads
         const T *u = (const T *)src_v;
         T *v = (T *)dst_v;
-        const long long chunks = (nx + blockDim.x - 1) / blockDim.x;
-        const long long units = ny * nz * chunks;
+        const int lane = threadIdx.x & 31;
+        const long long nw = (long long)gridDim.x * (blockDim.x >> 5);
+        const int mlen = DIM == 2 ? ny : nz;                   // extent of the march axis
+        const int runs = (mlen + run - 1) / run;
+        const long long units = (long long)runs * (DIM == 2 ? 1 : ny) * nseg;
         typename MaxBits<C>::type mx = 0;
-        for (long long un = blockIdx.x; un < units; un += gridDim.x) {
-            const long long row = un / chunks;
-            const long long j = (un - row * chunks) * blockDim.x + threadIdx.x;
-            if (j >= nx) continue;
-            const long long k = row / ny, i = row - k * ny;
-            const long long c = row * nx + j;
-            const C uc = Store<T>::ld(u + c);
-            C s;
+        // consecutive units (neighbouring segments, then rows) go to the same
+        // warp slot of consecutive CTAs, which run at the same time
+        for (long long un = (long long)(threadIdx.x >> 5) * gridDim.x + blockIdx.x; un < units; un += nw) {
+            const int seg = (int)(un % nseg);
+            const long long rest = un / nseg;
+            const int y3 = DIM == 2 ? 0 : (int)(rest % ny);
+            const int m0 = (int)(DIM == 2 ? rest : rest / ny) * run;
+            const int m1 = m0 + run < mlen ? m0 + run : mlen;
+            const int x = seg * kSeg + lane * V;
+            const bool ok = x < nx;
+            // window w[0..P+1] = rows m-1 .. m+P along the march; w[0], w[1]
+            // carry over from the previous batch
+            Row w[P + 2], fq[P], nq[P], sq[P];
             if (DIM == 2) {
-                s = add_rn(add_rn(add_rn(at(u, k, i - 1, j), at(u, k, i + 1, j)), at(u, k, i, j - 1)),
-                           at(u, k, i, j + 1));
+                row(u, m0 - 1, 0, x, ok, w[0]);
+                row(u, m0, 0, x, ok, w[1]);
             } else {
-                s = add_rn(add_rn(add_rn(add_rn(add_rn(at(u, k, i, j - 1), at(u, k, i, j + 1)),
-                                                at(u, k, i - 1, j)), at(u, k, i + 1, j)),
-                                  at(u, k - 1, i, j)), at(u, k + 1, i, j));
+                row(u, y3, m0 - 1, x, ok, w[0]);
+                row(u, y3, m0, x, ok, w[1]);
             }
-            const C t = mul_rn(h2, Store<T>::ldf(f + c));
-            const T nv = Store<T>::st(div_rn(add_rn(t, s), d));
-            v[c] = nv;
-            if (REDUCE) max_bits(mx, sub_rn(Store<T>::back(nv), uc));
+            for (int m = m0; m < m1; m += P) {
+                // every load of the batch first, so their latencies overlap
+#pragma unroll
+                for (int j = 0; j < P; ++j) {
+                    w[j + 2].ghost = fq[j].ghost = nq[j].ghost = sq[j].ghost = true;
+                    if (m + 1 + j <= m1) {
+                        if (DIM == 2) row(u, m + 1 + j, 0, x, ok, w[j + 2]);
+                        else row(u, y3, m + 1 + j, x, ok, w[j + 2]);
+                    }
+                    if (m + j < m1 && ok) {
+                        fq[j].load(f + off(DIM == 2 ? m + j : y3, DIM == 2 ? 0 : m + j, x), true);
+                        if (DIM == 3) {
+                            row(u, y3 - 1, m + j, x, ok, nq[j]);
+                            row(u, y3 + 1, m + j, x, ok, sq[j]);
+                        }
+                    }
+                }
+#pragma unroll
+                for (int j = 0; j < P; ++j) {
+                    if (m + j < m1) {
+                        if (DIM == 2) update<REDUCE>(u, v, m + j, 0, x, ok, lane, w[j], w[j + 1], w[j + 2], fq[j], nq[j], sq[j], mx);
+                        else update<REDUCE>(u, v, y3, m + j, x, ok, lane, w[j], w[j + 1], w[j + 2], fq[j], nq[j], sq[j], mx);
+                    }
+                }
+                w[0] = w[P];
+                w[1] = w[P + 1];
+            }
         }
         if (REDUCE) block_to_slot(slot, widen_bits(mx), 0ull, 0ull, mx != 0);
     }
 };
 
 template <class Op>
-__global__ void __launch_bounds__(kJThreads, 1) jacobi_persistent_kernel(Op op, LoopArgs la)
+__global__ void __launch_bounds__(kJThreads, 3) jacobi_persistent_kernel(const __grid_constant__ Op op, LoopArgs la)
 {
+    op.prologue();
     persistent_loop_body(op, la);
 }
 
 template <class Op>
-__global__ void __launch_bounds__(kJThreads, 1) jacobi_sweep_kernel(Op op, const void *src, void *dst)
+__global__ void __launch_bounds__(kJThreads, 3) jacobi_sweep_kernel(const __grid_constant__ Op op, const void *src,
+                                                                     void *dst)
 {
+    op.prologue();
     op.template sweep<false>(src, dst, nullptr);
-}
-
-template <class T, int DIM>
-JacobiOp<T, DIM> make_op(const Problem &p, const void *f)
-{
-    JacobiOp<T, DIM> op;
-    op.nx = p.nx; op.ny = p.ny; op.nz = p.nz; op.wrap = p.wrap;
-    if (sizeof(typename Store<T>::C) == 8) {
-        op.ghost = (typename Store<T>::C)p.ghost; op.h2 = (typename Store<T>::C)p.h2; op.d = (typename Store<T>::C)p.d;
-    } else {
-        op.ghost = (typename Store<T>::C)p.ghostf; op.h2 = (typename Store<T>::C)p.h2f; op.d = (typename Store<T>::C)p.df;
-    }
-    op.f = (const T *)f;
-    return op;
 }
 
 int sm_count()
@@ -184,18 +345,65 @@ int sm_count()
     return sms > 0 ? sms : 1;
 }
 
+template <class T, int DIM, int V>
+JacobiStream<T, DIM, V> make_op(const Problem &p, const void *f)
+{
+    JacobiStream<T, DIM, V> op;
+    op.nx = (int)p.nx; op.ny = (int)p.ny; op.nz = (int)p.nz; op.wrap = p.wrap;
+    op.nseg = (int)((p.nx + JacobiStream<T, DIM, V>::kSeg - 1) / JacobiStream<T, DIM, V>::kSeg);
+    // run length: up to 32, short enough that every warp of a full grid gets
+    // about four units
+    const long long across = (long long)op.nseg * (DIM == 2 ? 1 : p.ny);
+    const long long mlen = DIM == 2 ? p.ny : p.nz;
+    const long long warps = (long long)sm_count() * 3 * (kJThreads / 32);
+    long long run = mlen * across / (4 * warps);
+    op.run = (int)(run < 1 ? 1 : (run > 32 ? 32 : run));
+    if (sizeof(typename Store<T>::C) == 8) {
+        op.ghost = (typename Store<T>::C)p.ghost; op.h2 = (typename Store<T>::C)p.h2; op.d = (typename Store<T>::C)p.d;
+    } else {
+        op.ghost = (typename Store<T>::C)p.ghostf; op.h2 = (typename Store<T>::C)p.h2f; op.d = (typename Store<T>::C)p.df;
+    }
+    op.dconst = div_const_ok(op.d);
+    op.yd = host_rcp_rn(op.d);
+    op.f = (const T *)f;
+    return op;
+}
+
+// 16-byte accesses need rows of whole 16-byte groups and 16-byte aligned arrays
+// (grids too small to give every lane of a full grid V cells run one cell per
+// lane instead, which spreads their arithmetic over more SMs)
+template <class T>
+bool vector_ok(const Problem &p, const void *a, const void *b, const void *f)
+{
+    constexpr int V = 16 / sizeof(T);
+    const long long lanes = (long long)sm_count() * 3 * kJThreads;
+    if (p.nx * p.ny * p.nz / V < 2 * lanes) return false;
+    return p.nx % V == 0 && ((uintptr_t)a % 16) == 0 && ((uintptr_t)b % 16) == 0 && ((uintptr_t)f % 16) == 0;
+}
+
 template <class T, int DIM>
 cudaError_t run_persistent(const Problem &p, LoopArgs la, cudaStream_t st)
 {
-    auto op = make_op<T, DIM>(p, la.aux);
-    return launch_cooperative(jacobi_persistent_kernel<JacobiOp<T, DIM>>, kJThreads, 0, 1, la, &op, st);
+    constexpr int V = 16 / sizeof(T);
+    if (vector_ok<T>(p, la.a, la.b, la.aux)) {
+        auto op = make_op<T, DIM, V>(p, la.aux);
+        return launch_cooperative(jacobi_persistent_kernel<JacobiStream<T, DIM, V>>, kJThreads, 0, 3, la, &op, st);
+    }
+    auto op = make_op<T, DIM, 1>(p, la.aux);
+    return launch_cooperative(jacobi_persistent_kernel<JacobiStream<T, DIM, 1>>, kJThreads, 0, 3, la, &op, st);
 }
 
 template <class T, int DIM>
 cudaError_t run_sweep(const Problem &p, const void *src, void *dst, const void *f, cudaStream_t st)
 {
-    auto op = make_op<T, DIM>(p, f);
-    jacobi_sweep_kernel<JacobiOp<T, DIM>><<<sm_count(), kJThreads, 0, st>>>(op, src, dst);
+    constexpr int V = 16 / sizeof(T);
+    if (vector_ok<T>(p, src, dst, f)) {
+        auto op = make_op<T, DIM, V>(p, f);
+        jacobi_sweep_kernel<JacobiStream<T, DIM, V>><<<sm_count() * 3, kJThreads, 0, st>>>(op, src, dst);
+    } else {
+        auto op = make_op<T, DIM, 1>(p, f);
+        jacobi_sweep_kernel<JacobiStream<T, DIM, 1>><<<sm_count() * 3, kJThreads, 0, st>>>(op, src, dst);
+    }
     return cudaGetLastError();
 }
 

@@ -24,6 +24,7 @@
 // host-driven loop.
 #include <string.h>
 
+#include "crmath.cuh"
 #include "slr_internal.cuh"
 #include "tma.cuh"
 
@@ -72,7 +73,7 @@ struct RestoreOp {
                         den += w;
                     } else {
                         const float t = __fsub_rn(uc, uj);
-                        const float w = __frcp_rn(__fsqrt_rn(__fadd_rn(alpha, __fmul_rn(t, t))));
+                        const float w = inv_sqrt_rn2(__fadd_rn(alpha, __fmul_rn(t, t)));
                         num = __fadd_rn(num, __fmul_rn(w, uj));
                         den = __fadd_rn(den, w);
                     }
@@ -103,17 +104,6 @@ constexpr uint32_t kTxBytes = kUBoxW * kBoxH * 4 + kMBoxW * kBoxH; // bytes the 
 constexpr int kTThreads = 256;                    // 8 warps x 4 tile rows
 constexpr size_t kTSmem = 128 + 2 * (size_t)kStage + 32;   // stages, 2 mbarriers, tile counter
 static_assert(kStage % 128 == 0 && kUBytes % 128 == 0, "TMA destinations must be 128-byte aligned");
-
-__device__ __forceinline__ float weight(float uc, float uj, float alpha, bool fast)
-{
-    if (fast) {
-        const float t = uc - uj;
-        return rsqrtf(fmaf(t, t, alpha));
-    }
-    // 1/s rounded once: the IEEE reciprocal equals the IEEE division 1.0f / s
-    const float t = __fsub_rn(uc, uj);
-    return __frcp_rn(__fsqrt_rn(__fadd_rn(alpha, __fmul_rn(t, t))));
-}
 
 template <bool FAST>
 struct RestoreTma {
@@ -148,6 +138,21 @@ struct RestoreTma {
         __syncthreads();
     }
 
+    // one neighbour's term of the weighted mean
+    __device__ __forceinline__ void accumulate(float uc, float uj, float &num, float &den) const
+    {
+        if (FAST) {
+            const float w = rsqrtf(fmaf(uc - uj, uc - uj, alpha));
+            num = fmaf(w, uj, num);
+            den += w;
+        } else {
+            const float tt = __fsub_rn(uc, uj);
+            const float w = inv_sqrt_rn2(__fadd_rn(alpha, __fmul_rn(tt, tt)));
+            num = __fadd_rn(num, __fmul_rn(w, uj));
+            den = __fadd_rn(den, w);
+        }
+    }
+
     __device__ __forceinline__ void issue(int tile, int mi, int sb) const
     {
         const int tx = tile % tiles_x, ty = tile / tiles_x;
@@ -161,104 +166,94 @@ struct RestoreTma {
     template <bool REDUCE>
     __device__ __forceinline__ void sweep(const void *src_v, void *dst_v, Slot *slot) const
     {
-        __shared__ int s_ok;
-        __shared__ unsigned s_masks[64];
-        __shared__ int s_pref[65];
+        // noisy pixels of a tile, listed as (row << 6 | column); two lists
+        // alternate between tiles, three counters rotate so that a counter is
+        // reset one barrier before its next use
+        __shared__ unsigned short s_list[2][kTH * kTW];
+        __shared__ int s_count[3];
+        __shared__ int s_fail;
         float *dst = (float *)dst_v;
         const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+        const unsigned lt_mask = (1u << lane) - 1u;
         const int mi = src_v == base[0] ? 0 : 1;
         const int ntiles = tiles_x * tiles_y;
         const int mine = (int)blockIdx.x < ntiles ? (ntiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
         const unsigned q0 = *counter();
-        __syncthreads();                                        // everyone has read the counter
-        if (tid == 0) {
+        if (tid < 3) s_count[tid] = 0;
+        if (tid == 0) s_fail = 0;
+        __syncthreads();                                        // counter read, counters zeroed
+        if (tid == 0 && mine > 0) {
             tma::fence_proxy_async_global();   // the previous sweep's stores, published by the grid barrier
-            for (int i = 0; i < 2 && i < mine; ++i)
-                issue((int)blockIdx.x + i * (int)gridDim.x, mi, (int)((q0 + (unsigned)i) & 1u));
+            issue((int)blockIdx.x, mi, (int)(q0 & 1u));
         }
+        const int nxi = (int)nx, nyi = (int)ny;                 // extents are below 2^31 on this path
         unsigned long long sum = 0ull, cnt = 0ull;
         for (int i = 0; i < mine; ++i) {
             const unsigned qn = q0 + (unsigned)i;
-            const int sb = (int)(qn & 1u);
-            if (tid == 0) s_ok = tma::bounded_wait(&bars()[sb], (qn >> 1) & 1u, 2000000000ll, err);
-            __syncthreads();
-            if (!s_ok) break;
+            const int sb = (int)(qn & 1u), lb = i & 1;
             const int tile = (int)blockIdx.x + i * (int)gridDim.x;
-            // coordinates in 32 bits (extents are below 2^31 on this path)
             const int x0 = (tile % tiles_x) * kTW, y0 = (tile / tiles_x) * kTH;
-            const int nxi = (int)nx, nyi = (int)ny;
             const float *U = (const float *)(stages() + sb * kStage);   // [34][72]: row y0-1+r, column x0-4+c
             const unsigned char *M = stages() + sb * kStage + kUBytes;  // [34][96]: row y0-1+r, column x0-16+c
-            // clean pixels are copied; the noisy ones of the whole tile are
-            // listed as 64 ballots (8 warps x 8 row halves) with a prefix sum,
-            // then split evenly over the 8 warps, 32 at a time, so every warp
-            // does the same share of the weight arithmetic
+            // phase 1: every thread waits for the tile itself; clean pixels
+            // are copied, noisy ones appended to this tile's list
+            if (tma::bounded_wait(&bars()[sb], (qn >> 1) & 1u, 2000000000ll, err)) {
+                int *count = &s_count[i % 3];
+                unsigned short *list = s_list[lb];
 #pragma unroll
-            for (int h = 0; h < 8; ++h) {
-                const int rr = warp * 4 + (h >> 1), cc = (h & 1) * 32 + lane;
-                const int y = y0 + rr, x = x0 + cc;
-                const bool valid = y < nyi && x < nxi;
-                const bool noisy = valid && M[(rr + 1) * kMBoxW + cc + 16] != 0;
-                if (valid && !noisy) dst[(size_t)y * (size_t)nxi + x] = U[(rr + 1) * kUBoxW + cc + 4];
-                const unsigned m = __ballot_sync(0xffffffffu, noisy);
-                if (lane == 0) s_masks[warp * 8 + h] = m;
-            }
-            __syncthreads();
-            if (warp == 0) {
-                // exclusive prefix of the 64 ballot counts (two per lane)
-                const int c0 = __popc(s_masks[2 * lane]), c1 = __popc(s_masks[2 * lane + 1]);
-                int incl = c0 + c1;
-#pragma unroll
-                for (int o = 1; o < 32; o <<= 1) {
-                    const int t2 = __shfl_up_sync(0xffffffffu, incl, o);
-                    if (lane >= o) incl += t2;
+                for (int h = 0; h < 8; ++h) {
+                    const int rr = warp * 4 + (h >> 1), cc = (h & 1) * 32 + lane;
+                    const int y = y0 + rr, x = x0 + cc;
+                    const bool valid = y < nyi && x < nxi;
+                    const bool noisy = valid && M[(rr + 1) * kMBoxW + cc + 16] != 0;
+                    if (valid && !noisy) dst[(size_t)y * (size_t)nxi + x] = U[(rr + 1) * kUBoxW + cc + 4];
+                    const unsigned m = __ballot_sync(0xffffffffu, noisy);
+                    int at = 0;
+                    if (lane == 0 && m) at = atomicAdd(count, __popc(m));
+                    at = __shfl_sync(0xffffffffu, at, 0);
+                    if (noisy) list[at + __popc(m & lt_mask)] = (unsigned short)(rr << 6 | cc);
                 }
-                const int excl = incl - c0 - c1;
-                s_pref[2 * lane] = excl;
-                s_pref[2 * lane + 1] = excl + c0;
-                if (lane == 31) s_pref[64] = incl;
+            } else {
+                s_fail = 1;
             }
-            __syncthreads();
-            const int total = s_pref[64];
-            const int share = (total + 8 * 32 - 1) / (8 * 32) * 32;   // multiple of 32 per warp
+            __syncthreads();                                    // list complete; tile i-1 fully consumed
+            if (s_fail) break;
+            if (tid == 0) {
+                s_count[(i + 2) % 3] = 0;                       // next used by tile i + 2, after the next barrier
+                if (i + 1 < mine) issue(tile + (int)gridDim.x, mi, sb ^ 1);   // into the stage tile i-1 used
+            }
+            // phase 2: the list split evenly over the 8 warps, 32 at a time
+            const int total = s_count[i % 3];
+            const int share = (total + 8 * 32 - 1) / (8 * 32) * 32;
             const int lo = warp * share, hi = lo + share < total ? lo + share : total;
-            for (int first = lo; first < hi; first += 32) {
-                const int t = first + lane;
-                if (t >= hi) continue;
-                int a = 0, b = 64;                                 // s_pref[a] <= t < s_pref[b]
-                while (b - a > 1) {
-                    const int mid = (a + b) >> 1;
-                    if (s_pref[mid] <= t) a = mid; else b = mid;
-                }
-                const unsigned fb = __fns(s_masks[a], 0u, t - s_pref[a] + 1);   // bit of that noisy pixel
-                if (fb > 31u) continue;                                          // cannot happen: t < total
-                const int rr = (a >> 3) * 4 + ((a & 7) >> 1), cc = (a & 1) * 32 + (int)fb;
+            const unsigned short *list = s_list[lb];
+            for (int t = lo + lane; t < hi; t += 32) {
+                const int e = list[t];
+                const int rr = e >> 6, cc = e & 63;
                 const int y = y0 + rr, x = x0 + cc;
-                const float uc = U[(rr + 1) * kUBoxW + cc + 4];
+                const float *C = U + (rr + 1) * kUBoxW + cc + 4;
+                const float uc = *C;
                 float num = 0.0f, den = 0.0f;
-                const bool inner = y > 0 && y + 1 < nyi && x > 0 && x + 1 < nxi;   // all 8 neighbours exist
+                if (y > 0 && y + 1 < nyi && x > 0 && x + 1 < nxi) {
+                    // all 8 neighbours exist (every pixel off the grid's border)
 #pragma unroll
-                for (int di = -1; di <= 1; ++di) {
+                    for (int n = 0; n < 9; ++n)
+                        if (n != 4) accumulate(uc, C[(n / 3 - 1) * kUBoxW + n % 3 - 1], num, den);
+                } else {
 #pragma unroll
-                    for (int dj = -1; dj <= 1; ++dj) {
-                        if (di == 0 && dj == 0) continue;
-                        if (!inner && (y + di < 0 || y + di >= nyi || x + dj < 0 || x + dj >= nxi)) continue;
-                        const float uj = U[(rr + 1 + di) * kUBoxW + cc + 4 + dj];
-                        const float w = weight(uc, uj, alpha, FAST);
-                        if (FAST) { num = fmaf(w, uj, num); den += w; }
-                        else { num = __fadd_rn(num, __fmul_rn(w, uj)); den = __fadd_rn(den, w); }
+                    for (int n = 0; n < 9; ++n) {
+                        const int di = n / 3 - 1, dj = n % 3 - 1;
+                        if (n == 4 || y + di < 0 || y + di >= nyi || x + dj < 0 || x + dj >= nxi) continue;
+                        accumulate(uc, C[di * kUBoxW + dj], num, den);
                     }
                 }
-                const float nv = den > 0.0f ? __fdiv_rn(num, den) : uc;
+                const float nv = den > 0.0f ? (FAST ? __fdividef(num, den) : __fdiv_rn(num, den)) : uc;
                 dst[(size_t)y * (size_t)nxi + x] = nv;
-                if (REDUCE) {
-                    sum += fixed_2m24(__fsub_rn(nv, uc));
-                    cnt += 1ull;
-                }
+                if (REDUCE) sum += fixed_2m24(__fsub_rn(nv, uc));
             }
-            __syncthreads();                                   // stage sb is free again
-            if (tid == 0 && i + 2 < mine) issue((int)blockIdx.x + (i + 2) * (int)gridDim.x, mi, sb);
+            if (REDUCE && tid == 0) cnt += (unsigned long long)total;
         }
+        __syncthreads();                                       // the last tile is consumed before the counter moves
         if (tid == 0) *counter() = q0 + (unsigned)mine;
         tma::fence_proxy_async_global();                       // this sweep's stores before the next TMA reads
         if (REDUCE) block_to_slot(slot, 0ull, sum, cnt, sum != 0ull);

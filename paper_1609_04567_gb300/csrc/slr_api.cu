@@ -62,7 +62,8 @@ std::string check_desc(const slr_desc *d, bool *unsupported)
     if (!d) return "descriptor is NULL";
     if (d->stencil < SLR_J2D5 || d->stencil > SLR_RESTORE8) return "unknown stencil";
     if (d->nx < 1 || d->ny < 1 || d->nz < 1) return "extents must be >= 1";
-    if (d->nx > (1ll << 31) || d->ny > (1ll << 31) || d->nz > (1ll << 31)) return "extent too large";
+    if (d->nx > (1ll << 31) - 4096 || d->ny > (1ll << 31) - 4096 || d->nz > (1ll << 31) - 4096)
+        return "extent too large (each must be below 2^31 - 4096)";
     if (d->stencil != SLR_J3D7 && d->nz != 1) return "2D stencil needs nz == 1";
     if (d->boundary != SLR_DIRICHLET && d->boundary != SLR_WRAP) return "unknown boundary";
     if (d->reduce != reduce_of(d->stencil)) return "reduce operator does not match the stencil";

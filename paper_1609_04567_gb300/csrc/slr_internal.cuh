@@ -163,13 +163,24 @@ __device__ __forceinline__ void block_to_slot(Slot *slot, unsigned long long max
 
 // |delta| truncated to a multiple of 2^-24, as an integer: trunc(|d| * 2^24).
 // Scaling by 2^24 is exact in binary32, so for |d| < 256 (the product below
-// 2^32) a binary32 multiply and an unsigned 32-bit truncation give the same
-// integer as the binary64 route, without binary64 arithmetic.
+// 2^32) a binary32 multiply and an unsigned 32-bit truncation give the
+// integer.  From 256 up the product is an integer already: the significand
+// shifted by the exponent (integer operations only, so no binary64 work is
+// compiled into the sweeps).  Products of 2^64 and more (|d| >= 2^40, or NaN)
+// saturate.
+static __device__ __noinline__ unsigned long long fixed_2m24_large(float a)
+{
+    if (!(a < 1099511627776.0f)) return ~0ull;
+    const uint32_t b = __float_as_uint(a);
+    // a = m * 2^(E - 150) with m the 24-bit significand; a * 2^24 = m << (E - 126)
+    const unsigned long long m = (b & 0x7FFFFFu) | 0x800000u;
+    return m << ((int)(b >> 23) - 126);
+}
 __device__ __forceinline__ unsigned long long fixed_2m24(float d)
 {
     const float a = fabsf(d);
     if (a < 256.0f) return (unsigned long long)__float2uint_rz(a * 16777216.0f);
-    return (unsigned long long)__double2ull_rz((double)a * 16777216.0);
+    return fixed_2m24_large(a);
 }
 
 // What every stencil's loop needs to decide after a sweep.

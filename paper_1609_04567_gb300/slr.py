@@ -61,7 +61,7 @@ EXPORTS = ["slr_desc_init", "slr_workspace_size", "slr_create", "slr_run_until",
            "slr_batch_workspace_size", "slr_batch_scratch_size", "slr_batch_create", "slr_batch_add",
            "slr_batch_run", "slr_batch_poll", "slr_batch_result", "slr_batch_remove", "slr_batch_destroy",
            "slr_batch_last_error", "slr_tune_scratch_size", "slr_tune", "slr_tune_lookup", "slr_tune_clear",
-           "slr_tune_last_error"]
+           "slr_tune_last_error", "slr_check_exact_math", "slr_check_exact_division"]
 SLR_STATIC_STATE_BYTES = 4 << 20
 
 _lib = None
@@ -139,6 +139,11 @@ def load(path: str = LIB_PATH):
     lib.slr_tune_clear.restype = None
     lib.slr_tune_last_error.argtypes = []
     lib.slr_tune_last_error.restype = ctypes.c_char_p
+    lib.slr_check_exact_math.argtypes = [ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64), P]
+    lib.slr_check_exact_math.restype = i32
+    lib.slr_check_exact_division.argtypes = [ctypes.c_double, ctypes.POINTER(ctypes.c_uint64),
+                                             ctypes.POINTER(ctypes.c_uint64), P]
+    lib.slr_check_exact_division.restype = i32
     _lib = lib
     return lib
 
@@ -293,6 +298,25 @@ def slr_tune_clear() -> None:
 
 def slr_tune_last_error() -> str:
     return load().slr_tune_last_error().decode()
+
+
+def slr_check_exact_math(stream: int = 0):
+    """Returns (mismatches of the three checks, inputs checked)."""
+    mm = (ctypes.c_uint64 * 3)()
+    n = ctypes.c_uint64()
+    st = load().slr_check_exact_math(mm, ctypes.byref(n), stream or None)
+    if st != SLR_OK:
+        raise SlrError(st, "exact-math self-check failed to run")
+    return list(mm), n.value
+
+
+def slr_check_exact_division(d: float, stream: int = 0):
+    """Returns ([mismatches binary32, binary64], [numerators checked binary32, binary64])."""
+    mm, n = (ctypes.c_uint64 * 2)(), (ctypes.c_uint64 * 2)()
+    st = load().slr_check_exact_division(d, mm, n, stream or None)
+    if st != SLR_OK:
+        raise SlrError(st, "division self-check refused or failed")
+    return list(mm), list(n)
 
 
 def tune(stencil: int, u, aux=None, *, stream=None, trial_iters: int = 0, **fields) -> dict:

@@ -128,3 +128,13 @@ def test_wait_limit_reports_timeout_and_context_survives(gpu, orc):
     s.close()
     assert st == gpu.SLR_ERR_TIMEOUT
     jacobi_case(gpu, orc, (64, 64))
+
+
+@pytest.mark.parametrize("d", [4.0 + (1.0 / 257) ** 2, 4.0 + (1.0 / 8193) ** 2, 4.0 + (1.0 / 65) ** 2,
+                               6.0 + (1.0 / 513) ** 2, 4.0, 6.0, 3.0, 7.0, 0.1, 3.14159265, 1e-5, 12345.678])
+def test_constant_division_matches_ieee(gpu, d):
+    # the sweeps' a / d (reciprocal + two corrections) against the IEEE division:
+    # every binary32 numerator, 2^26 binary64 numerators
+    mismatches, checked = gpu.slr_check_exact_division(d)
+    assert checked == [1 << 32, 1 << 26]
+    assert mismatches == [0, 0]

@@ -55,3 +55,11 @@ def test_full_size_4096_sample(gpu, orc):
     assert r.iters == rr.iters == 3
     assert np.array_equal(out.view(np.uint32), ref.view(np.uint32))
     assert r.value == rr.value
+
+
+def test_exact_weight_arithmetic_matches_ieee_for_every_input(gpu):
+    # the EXACT sweeps' 1/sqrt with two roundings against __frcp_rn(__fsqrt_rn(x)),
+    # all 2^31 non-negative binary32 inputs, on the device
+    mismatches, checked = gpu.slr_check_exact_math()
+    assert checked == 1 << 31
+    assert mismatches == [0, 0, 0]
