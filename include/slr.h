@@ -128,16 +128,24 @@ typedef struct {
     int32_t grid_ctas;     /* CTAs of the persistent launch, capped at the number that can
                               be co-resident; 0 = library choice (all co-resident CTAs).
                               Results do not depend on it. */
-    int32_t tiling;        /* slr_tiling of the RESTORE8 sweep; other stencils ignore it */
+    int32_t tiling;        /* slr_tiling of the RESTORE8 and Jacobi persistent sweeps; Life
+                              ignores it */
     int32_t reserved;      /* 0 */
 } slr_desc;
 
-/* How the RESTORE8 sweep stages its input.  Results do not depend on it. */
+/* How a persistent sweep stages its input.  Results do not depend on it.
+ * RESTORE8: TMA = 32x64 tiles with halo in shared memory (nx a multiple of 16).
+ * J2D5/J3D7: TMA = a CTA marches a 256-cell-wide column along y (2D, blocks of
+ * rows) or z (3D, plane tiles with their y-halo), every step staged by TMA
+ * in a 4-stage ring; needs a Dirichlet ghost of +0, rows of whole 16-byte
+ * groups and 16-byte aligned u, f and workspace.  NONE = warps march row
+ * segments with the rows in registers (any boundary).  Where TMA does not
+ * apply the sweep falls back to NONE. */
 typedef enum {
-    SLR_TILING_AUTO = 0,   /* library choice (TMA when nx is a multiple of 16) */
-    SLR_TILING_NONE = 1,   /* each thread reads its 3x3 neighbourhood from global memory */
-    SLR_TILING_TMA = 2     /* 32x64 tiles with halo staged in shared memory by TMA
-                              (needs nx a multiple of 16; falls back to NONE otherwise) */
+    SLR_TILING_AUTO = 0,   /* library choice: TMA where it applies (Jacobi: grids of at least
+                              about 2 x (SMs x 768) 16-byte groups) */
+    SLR_TILING_NONE = 1,
+    SLR_TILING_TMA = 2
 } slr_tiling;
 
 /* Fault injection for tests of the device-side wait limit: the last CTA of a
@@ -271,7 +279,8 @@ const char *slr_static_last_error(void);
  *   loop        (SLR_LOOP_AUTO: persistent device loop or the host-driven loop;
  *                defect correction keeps the persistent loop),
  *   temporal_k  (0, Life only: generations per HBM pass, 1 = none),
- *   tiling      (SLR_TILING_AUTO, RESTORE8 only: TMA tiles or none),
+ *   tiling      (SLR_TILING_AUTO, RESTORE8 and Jacobi without defect correction:
+ *                TMA tiles or none),
  *   grid_ctas   (0: CTAs of the persistent launch),
  * first loop x temporal_k x tiling with all co-resident CTAs, then grid_ctas
  * for the winner.  Fields set explicitly are held fixed.  Each candidate runs

@@ -14,10 +14,12 @@
 // sequential evaluation of the same formula.
 #include <string.h>
 
+#include <cmath>
 #include <type_traits>
 
 #include "crmath.cuh"
 #include "slr_internal.cuh"
+#include "tma.cuh"
 
 namespace slr {
 namespace {
@@ -189,7 +191,7 @@ struct JacobiStream {
     __device__ __forceinline__ size_t state_bytes() const { return (size_t)nx * ny * nz * sizeof(T); }
     __device__ __forceinline__ void prologue() const {}
 
-    __device__ __forceinline__ C divide(C a) const { return dconst ? div_const_rn(a, d, yd) : div_rn(a, d); }
+    __device__ __forceinline__ C divide(C a) const { return dconst ? div_const_rn(a, d, yd) : div_ieee(a, d); }
 
     __device__ __forceinline__ size_t off(int y, int z, int x) const { return ((size_t)z * ny + y) * nx + x; }
 
@@ -322,6 +324,264 @@ struct JacobiStream {
     }
 };
 
+// ---- TMA tiles (Dirichlet boundary with ghost 0, large grids) -----------------
+// A CTA owns a column of the grid 256 cells wide (3D: and kTY rows high) and
+// marches along the slowest axis: in 3D one z-plane of its tile per step
+// (the tile's kTY rows plus the rows above and below), in 2D a block of kTY
+// rows per step.  Every step arrives in a ring of kNS shared-memory stages as
+// TMA boxes: the tile, a 16-byte column on each side of it (the x-neighbours
+// of the tile's edge cells) and the tile of f; the tensor maps fill
+// everything outside the grid with zeros, which is the ghost.  The CTA
+// computes step j from the stages of steps j - 1, j and j + 1 while the next
+// step's boxes are in flight; one CTA barrier per step frees the oldest
+// stage, which thread 0 refills.  (column, step) pairs are dealt out to the
+// CTAs in contiguous ranges of equal length, so every CTA does the same work
+// in a sweep.
+template <class T, int DIM>
+struct JacobiTma {
+    using C = typename Store<T>::C;
+    using Row = Packed<T, 16 / sizeof(T)>;
+    static constexpr int V = 16 / (int)sizeof(T);
+    static constexpr int kTX = 256;                                  // tile width (cells)
+    static constexpr int kG = kTX / V;                               // 16-byte groups per tile row
+    static constexpr int kTY = 32 / (int)sizeof(T);                  // tile rows (a tile row is kTX cells)
+    static constexpr int kHalo = DIM == 3 ? 1 : 0;                   // y-halo rows above and below (3D)
+    static constexpr int kRowBytes = kTX * (int)sizeof(T);
+    static constexpr int kMainBytes = (kTY + 2 * kHalo) * kRowBytes;
+    static constexpr int kSideBytes = (kTY * 16 + 127) / 128 * 128;
+    static constexpr int kFBytes = kTY * kRowBytes;
+    static constexpr int kStage = kMainBytes + 2 * kSideBytes + kFBytes;
+    static constexpr int kNS = 4;                                    // stages (a power of 2)
+    static constexpr int kPer = kTY * kG / kJThreads;                // 16-byte groups per thread per step
+    static constexpr size_t kSmem = 128 + (size_t)kNS * kStage + kNS * 8 + 16;
+    static_assert(kStage % 128 == 0 && kMainBytes % 128 == 0 && kFBytes % 128 == 0, "TMA destinations");
+    static_assert(kPer * kJThreads == kTY * kG, "threads tile the step");
+
+    CUtensorMap umap[2], smap[2], fmap;      // tile and side-column maps over A and B, f map
+    const void *base[2];
+    int *err;
+    long long limit_ns;
+    int nx, ny, nz;
+    int tiles_x, tiles_y;                    // tiles across the plane (2D: tiles_y = 1)
+    C h2, d, yd;
+    int dconst;
+
+    __device__ __forceinline__ size_t state_bytes() const { return (size_t)nx * ny * nz * sizeof(T); }
+    __device__ __forceinline__ C divide(C a) const { return dconst ? div_const_rn(a, d, yd) : div_ieee(a, d); }
+
+    __device__ __forceinline__ unsigned char *stages() const
+    {
+        extern __shared__ unsigned char smem_dyn[];
+        return (unsigned char *)(((uintptr_t)smem_dyn + 127) & ~(uintptr_t)127);
+    }
+    __device__ __forceinline__ const T *main_of(int s) const { return (const T *)(stages() + s * kStage); }
+    __device__ __forceinline__ const T *side_of(int s, int i) const
+    {
+        return (const T *)(stages() + s * kStage + kMainBytes + i * kSideBytes);   // 0: left, 1: right
+    }
+    __device__ __forceinline__ const T *f_of(int s) const
+    {
+        return (const T *)(stages() + s * kStage + kMainBytes + 2 * kSideBytes);
+    }
+    __device__ __forceinline__ uint64_t *bar(int s) const { return (uint64_t *)(stages() + kNS * kStage) + s; }
+    __device__ __forceinline__ unsigned *counter() const { return (unsigned *)(bar(kNS)); }
+
+    __device__ __forceinline__ void prologue() const
+    {
+        if (threadIdx.x == 0) {
+            for (int s = 0; s < kNS; ++s) tma::mbar_init(bar(s), 1);
+            *counter() = 0u;
+            tma::mbar_init_fence();
+        }
+        __syncthreads();
+    }
+
+    // thread 0: boxes of step j of column col into stage sl; f only for the
+    // steps the CTA computes.  A box entirely outside the grid is not issued
+    // (its cells are ghosts, and the compute side knows which ones).
+    __device__ __forceinline__ void issue(int mi, int sl, int col, int j, bool with_f) const
+    {
+        unsigned char *st = stages() + sl * kStage;
+        const int tx = col % tiles_x, ty = col / tiles_x;
+        const int x0 = tx * kTX;
+        const bool step_in = DIM == 3 ? (j >= 0 && j < nz) : (j >= 0 && j * kTY < ny);
+        const bool left_in = step_in && x0 > 0, right_in = step_in && x0 + kTX < nx;
+        const uint32_t bytes = (step_in ? (uint32_t)kMainBytes : 0u) + (left_in ? kTY * 16u : 0u) +
+                               (right_in ? kTY * 16u : 0u) + (with_f ? (uint32_t)kFBytes : 0u);
+        tma::mbar_expect_tx(bar(sl), bytes);
+        const int y0 = DIM == 3 ? ty * kTY : j * kTY;
+        if (DIM == 3) {
+            if (step_in) tma::load_3d(st, &umap[mi], x0, y0 - 1, j, bar(sl));
+            if (left_in) tma::load_3d(st + kMainBytes, &smap[mi], x0 - V, y0, j, bar(sl));
+            if (right_in) tma::load_3d(st + kMainBytes + kSideBytes, &smap[mi], x0 + kTX, y0, j, bar(sl));
+            if (with_f) tma::load_3d(st + kMainBytes + 2 * kSideBytes, &fmap, x0, y0, j, bar(sl));
+        } else {
+            if (step_in) tma::load_2d(st, &umap[mi], x0, y0, bar(sl));
+            if (left_in) tma::load_2d(st + kMainBytes, &smap[mi], x0 - V, y0, bar(sl));
+            if (right_in) tma::load_2d(st + kMainBytes + kSideBytes, &smap[mi], x0 + kTX, y0, bar(sl));
+            if (with_f) tma::load_2d(st + kMainBytes + 2 * kSideBytes, &fmap, x0, y0, bar(sl));
+        }
+    }
+
+    __device__ __forceinline__ Row lds(const T *p) const
+    {
+        const uint4 q = *(const uint4 *)p;
+        Row r;
+        r.w[0] = q.x; r.w[1] = q.y; r.w[2] = q.z; r.w[3] = q.w;
+        r.ghost = false;
+        return r;
+    }
+
+    // all threads: rows [r0, r0 + n) of stage s's tile set to +0
+    __device__ __forceinline__ void zero_rows(int s, int r0, int n) const
+    {
+        uint4 *p = (uint4 *)(stages() + s * kStage + r0 * kRowBytes);
+        for (int i = threadIdx.x; i < n * kRowBytes / 16; i += kJThreads) p[i] = make_uint4(0u, 0u, 0u, 0u);
+    }
+
+    template <bool REDUCE>
+    __device__ __forceinline__ void sweep(const void *src_v, void *dst_v, Slot *slot) const
+    {
+        __shared__ int s_stop;
+        T *v = (T *)dst_v;
+        const int tid = threadIdx.x;
+        const int mi = src_v == base[0] ? 0 : 1;
+        const int ncols = tiles_x * tiles_y;
+        const int mlen = DIM == 3 ? nz : (ny + kTY - 1) / kTY;       // steps per column
+        typename MaxBits<C>::type mx = 0;
+        unsigned q = *counter();
+        if (tid == 0) {
+            s_stop = ld_relaxed_u32((const unsigned *)err) != 0u;   // a wait ran out earlier
+            tma::fence_proxy_async_global();   // the previous sweep's stores before this sweep's copies
+        }
+        __syncthreads();
+        const long long total = (long long)ncols * mlen;
+        long long L = s_stop ? 0 : (long long)blockIdx.x * total / gridDim.x;
+        const long long Lend = s_stop ? 0 : ((long long)blockIdx.x + 1) * total / gridDim.x;
+        bool alive = true;
+        while (L < Lend && alive) {
+            const int col = (int)(L / mlen);
+            const int ja = (int)(L - (long long)col * mlen);
+            const int jb = (long long)mlen - ja < Lend - L ? mlen : ja + (int)(Lend - L);
+            const int R = jb - ja + 2;                               // steps ja - 1 .. jb
+            const int tx = col % tiles_x, ty = col / tiles_x;
+            const int x0 = tx * kTX, y0 = ty * kTY;
+            if (tid == 0)
+                for (int i = 0; i < R && i < kNS; ++i)
+                    issue(mi, (int)((q + (unsigned)i) & (kNS - 1)), col, ja - 1 + i, i >= 1 && i <= jb - ja);
+            int waited = -1;
+            for (int j = ja; j < jb; ++j) {
+                const int ic = j - ja + 1;
+                bool got = true;
+                while (waited < ic + 1) {
+                    ++waited;
+                    const unsigned qi = q + (unsigned)waited;
+                    got = got && tma::bounded_wait(bar((int)(qi & (kNS - 1))), (qi / kNS) & 1u, limit_ns, err);
+                }
+                const int sa = (int)((q + (unsigned)(ic - 1)) & (kNS - 1)), sc = (int)((q + (unsigned)ic) & (kNS - 1)),
+                          sb = (int)((q + (unsigned)(ic + 1)) & (kNS - 1));
+                // steps -1 and mlen lie outside the grid and were not loaded:
+                // the rows of them this step reads are set to the ghost 0
+                if (j == 0 || j + 1 == mlen) {
+                    if (j == 0) zero_rows(sa, DIM == 3 ? 1 : kTY - 1, DIM == 3 ? kTY : 1);
+                    if (j + 1 == mlen) zero_rows(sb, DIM == 3 ? 1 : 0, DIM == 3 ? kTY : 1);
+                    __syncthreads();
+                }
+                const T *Mc = main_of(sc), *Ma = main_of(sa), *Mb = main_of(sb), *F = f_of(sc);
+                const T *SL = side_of(sc, 0), *SR = side_of(sc, 1);
+#pragma unroll
+                for (int p = 0; p < kPer; ++p) {
+                    const int g = tid + p * kJThreads;
+                    const int r = g / kG, c = g % kG;
+                    const int x = x0 + c * V;
+                    const int y = DIM == 3 ? y0 + r : j * kTY + r;
+                    if (!got || x >= nx || y >= ny) continue;
+                    const T *ctr = Mc + (r + kHalo) * kTX + c * V;
+                    const Row cv = lds(ctr), fr = lds(F + r * kTX + c * V);
+                    Row nr, sr, ar, br;                              // y-1, y+1, march-1, march+1
+                    if (DIM == 3) {
+                        nr = lds(ctr - kTX);
+                        sr = lds(ctr + kTX);
+                        ar = lds(Ma + (r + 1) * kTX + c * V);
+                        br = lds(Mb + (r + 1) * kTX + c * V);
+                    } else {
+                        ar = lds(r > 0 ? ctr - kTX : Ma + (kTY - 1) * kTX + c * V);
+                        br = lds(r < kTY - 1 ? ctr + kTX : Mb + c * V);
+                        nr.ghost = sr.ghost = true;
+                    }
+                    const C zero = C(0);
+                    const C left = c > 0 ? Store<T>::back(ctr[-1]) : (x0 > 0 ? Store<T>::back(SL[r * V + V - 1]) : zero);
+                    const C right = c < kG - 1 ? Store<T>::back(ctr[V])
+                                               : (x0 + kTX < nx ? Store<T>::back(SR[r * V]) : zero);
+                    uint32_t ow[Row::kWords];
+                    if constexpr (std::is_same<C, float>::value) {
+                        // two cells per paired binary32 operation (same rounding per cell)
+#pragma unroll
+                        for (int k = 0; k < V; k += 2) {
+                            const float2 w = make_float2(k > 0 ? cv.raw(k - 1) : left, cv.raw(k));
+                            const float2 e = make_float2(cv.raw(k + 1), k + 2 < V ? cv.raw(k + 2) : right);
+                            const float2 a2 = make_float2(ar.raw(k), ar.raw(k + 1));
+                            const float2 b2 = make_float2(br.raw(k), br.raw(k + 1));
+                            float2 sum;
+                            if (DIM == 2) {
+                                sum = __fadd2_rn(__fadd2_rn(__fadd2_rn(a2, b2), w), e);
+                            } else {
+                                const float2 n2 = make_float2(nr.raw(k), nr.raw(k + 1));
+                                const float2 s2 = make_float2(sr.raw(k), sr.raw(k + 1));
+                                sum = __fadd2_rn(__fadd2_rn(__fadd2_rn(__fadd2_rn(__fadd2_rn(w, e), n2), s2), a2), b2);
+                            }
+                            // h^2 f with the scalar operation: a paired product feeding a paired
+                            // sum may be contracted into one fused operation
+                            const float2 t = make_float2(__fmul_rn(h2, fr.raw(k)), __fmul_rn(h2, fr.raw(k + 1)));
+                            const float2 q = dconst ? div_const_rn2(__fadd2_rn(t, sum), d, yd)
+                                                    : make_float2(div_ieee(__fadd_rn(t.x, sum.x), d),
+                                                                  div_ieee(__fadd_rn(t.y, sum.y), d));
+                            const T o0 = Store<T>::st(q.x), o1 = Store<T>::st(q.y);
+                            if (REDUCE) {
+                                const float2 dl = __fadd2_rn(make_float2(Store<T>::back(o0), Store<T>::back(o1)),
+                                                             make_float2(-cv.raw(k), -cv.raw(k + 1)));
+                                max_bits(mx, dl.x);
+                                max_bits(mx, dl.y);
+                            }
+                            if constexpr (sizeof(T) == 4) {
+                                ow[k] = __float_as_uint((float)o0);
+                                ow[k + 1] = __float_as_uint((float)o1);
+                            } else {
+                                ow[k >> 1] = bits16(o0) | bits16(o1) << 16;
+                            }
+                        }
+                    } else {
+#pragma unroll
+                        for (int k = 0; k < V; ++k) {
+                            const C w = k > 0 ? cv.raw(k - 1) : left, e = k < V - 1 ? cv.raw(k + 1) : right;
+                            C sum;
+                            if (DIM == 2) sum = add_rn(add_rn(add_rn(ar.raw(k), br.raw(k)), w), e);
+                            else sum = add_rn(add_rn(add_rn(add_rn(add_rn(w, e), nr.raw(k)), sr.raw(k)), ar.raw(k)),
+                                              br.raw(k));
+                            const T o = Store<T>::st(divide(add_rn(mul_rn(h2, fr.raw(k)), sum)));
+                            if (REDUCE) max_bits(mx, sub_rn(Store<T>::back(o), cv.raw(k)));
+                            ow[2 * k] = (uint32_t)__double2loint((double)o);
+                            ow[2 * k + 1] = (uint32_t)__double2hiint((double)o);
+                        }
+                    }
+                    const size_t off = DIM == 3 ? ((size_t)j * ny + y) * nx + x : (size_t)y * nx + x;
+                    *(uint4 *)(v + off) = make_uint4(ow[0], ow[1], ow[2], ow[3]);
+                }
+                // the stage of step j - 1 is free once every thread is past this step
+                if (__syncthreads_or(!got)) { alive = false; break; }
+                if (tid == 0 && ic - 1 + kNS < R)
+                    issue(mi, sa, col, j - 1 + kNS, ic - 1 + kNS <= jb - ja);
+            }
+            q += (unsigned)R;
+            L += jb - ja;
+        }
+        __syncthreads();
+        if (tid == 0) *counter() = q;
+        tma::fence_proxy_async_global();                             // this sweep's stores before later copies
+        if (REDUCE) block_to_slot(slot, widen_bits(mx), 0ull, 0ull, mx != 0);
+    }
+};
+
 template <class Op>
 __global__ void __launch_bounds__(kJThreads, 3) jacobi_persistent_kernel(const __grid_constant__ Op op, LoopArgs la)
 {
@@ -373,18 +633,72 @@ JacobiStream<T, DIM, V> make_op(const Problem &p, const void *f)
 // (grids too small to give every lane of a full grid V cells run one cell per
 // lane instead, which spreads their arithmetic over more SMs)
 template <class T>
-bool vector_ok(const Problem &p, const void *a, const void *b, const void *f)
+bool vector_ok(const Problem &p, const void *a, const void *b, const void *f, bool any_size = false)
 {
     constexpr int V = 16 / sizeof(T);
     const long long lanes = (long long)sm_count() * 3 * kJThreads;
-    if (p.nx * p.ny * p.nz / V < 2 * lanes) return false;
+    if (!any_size && p.nx * p.ny * p.nz / V < 2 * lanes) return false;
     return p.nx % V == 0 && ((uintptr_t)a % 16) == 0 && ((uintptr_t)b % 16) == 0 && ((uintptr_t)f % 16) == 0;
+}
+
+template <class T> CUtensorMapDataType tma_type();
+template <> CUtensorMapDataType tma_type<double>() { return CU_TENSOR_MAP_DATA_TYPE_FLOAT64; }
+template <> CUtensorMapDataType tma_type<float>() { return CU_TENSOR_MAP_DATA_TYPE_FLOAT32; }
+template <> CUtensorMapDataType tma_type<__nv_bfloat16>() { return CU_TENSOR_MAP_DATA_TYPE_BFLOAT16; }
+template <> CUtensorMapDataType tma_type<__half>() { return CU_TENSOR_MAP_DATA_TYPE_FLOAT16; }
+
+// The TMA path: Dirichlet boundary with ghost +0 (the tensor maps' fill),
+// rows of whole 16-byte groups, large grids.  Returns cudaErrorNotSupported
+// when the problem does not qualify.
+template <class T, int DIM>
+cudaError_t run_tma(const Problem &p, LoopArgs la, cudaStream_t st)
+{
+    using Op = JacobiTma<T, DIM>;
+    // SLR_TILING_TMA asks for the TMA path whatever the grid's size
+    if (p.wrap || p.ghost != 0.0 || std::signbit(p.ghost) ||
+        !vector_ok<T>(p, la.a, la.b, la.aux, p.tiling == SLR_TILING_TMA) || !tma::encode_fn())
+        return cudaErrorNotSupported;
+    Op op;
+    memset(&op, 0, sizeof(op));
+    const CUtensorMapDataType dt = tma_type<T>();
+    const size_t es = sizeof(T);
+    bool ok = true;
+    for (int i = 0; i < 2; ++i) {
+        const void *b = i == 0 ? la.a : la.b;
+        if (DIM == 3) {
+            ok = ok && tma::make_map_3d(&op.umap[i], b, dt, es, p.nx, p.ny, p.nz, Op::kTX, Op::kTY + 2, 1) &&
+                 tma::make_map_3d(&op.smap[i], b, dt, es, p.nx, p.ny, p.nz, Op::V, Op::kTY, 1);
+        } else {
+            ok = ok && tma::make_map_2d(&op.umap[i], b, dt, es, p.nx, p.ny, Op::kTX, Op::kTY) &&
+                 tma::make_map_2d(&op.smap[i], b, dt, es, p.nx, p.ny, Op::V, Op::kTY);
+        }
+    }
+    ok = ok && (DIM == 3 ? tma::make_map_3d(&op.fmap, la.aux, dt, es, p.nx, p.ny, p.nz, Op::kTX, Op::kTY, 1)
+                         : tma::make_map_2d(&op.fmap, la.aux, dt, es, p.nx, p.ny, Op::kTX, Op::kTY));
+    if (!ok) return cudaErrorNotSupported;
+    const auto sop = make_op<T, DIM, Op::V>(p, la.aux);
+    op.base[0] = la.a;
+    op.base[1] = la.b;
+    op.err = &la.ctl->err;
+    op.limit_ns = la.limit_ns;
+    op.nx = (int)p.nx; op.ny = (int)p.ny; op.nz = (int)p.nz;
+    op.tiles_x = (int)((p.nx + Op::kTX - 1) / Op::kTX);
+    op.tiles_y = DIM == 3 ? (int)((p.ny + Op::kTY - 1) / Op::kTY) : 1;
+    op.h2 = sop.h2; op.d = sop.d; op.yd = sop.yd; op.dconst = sop.dconst;
+    auto kern = jacobi_persistent_kernel<Op>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Op::kSmem);
+    if (e != cudaSuccess) return e;
+    return launch_cooperative(kern, kJThreads, Op::kSmem, 3, la, &op, st);
 }
 
 template <class T, int DIM>
 cudaError_t run_persistent(const Problem &p, LoopArgs la, cudaStream_t st)
 {
     constexpr int V = 16 / sizeof(T);
+    if (p.tiling != SLR_TILING_NONE) {
+        const cudaError_t e = run_tma<T, DIM>(p, la, st);
+        if (e != cudaErrorNotSupported) return e;
+    }
     if (vector_ok<T>(p, la.a, la.b, la.aux)) {
         auto op = make_op<T, DIM, V>(p, la.aux);
         return launch_cooperative(jacobi_persistent_kernel<JacobiStream<T, DIM, V>>, kJThreads, 0, 3, la, &op, st);
@@ -432,6 +746,18 @@ cudaError_t dispatch_sweep(const Problem &p, const void *src, void *dst, const v
 }
 
 }  // namespace
+
+bool jacobi_tma_ok(const Problem &p, const void *a, const void *b, const void *f, bool forced)
+{
+    if (p.wrap || p.ghost != 0.0 || std::signbit(p.ghost) || !tma::encode_fn()) return false;
+    switch (p.storage) {
+    case SLR_F64: return vector_ok<double>(p, a, b, f, forced);
+    case SLR_F32: return vector_ok<float>(p, a, b, f, forced);
+    case SLR_BF16: return vector_ok<__nv_bfloat16>(p, a, b, f, forced);
+    case SLR_F16: return vector_ok<__half>(p, a, b, f, forced);
+    default: return false;
+    }
+}
 
 cudaError_t jacobi_persistent(const Problem &p, LoopArgs la, cudaStream_t st)
 {

@@ -350,6 +350,9 @@ int life_tb_resolve_k(const Problem &p, int grid_request);
 size_t life_tb_bits_bytes(long long nx, long long ny);
 cudaError_t life_tb_persistent(const Problem &p, LoopArgs la, void *bits0, void *bits1, cudaStream_t st);
 cudaError_t jacobi_persistent(const Problem &p, LoopArgs la, cudaStream_t st);
+// Whether a persistent Jacobi sweep over state buffers a, b with right-hand
+// side f takes the TMA path (forced: as for SLR_TILING_TMA, any grid size).
+bool jacobi_tma_ok(const Problem &p, const void *a, const void *b, const void *f, bool forced);
 cudaError_t jacobi_sweep(const Problem &p, const void *src, void *dst, const void *f, cudaStream_t st);
 cudaError_t restore_persistent(const Problem &p, LoopArgs la, cudaStream_t st);
 // Whether the TMA-tiled restoration sweep accepts p (nx % 16 == 0).

@@ -70,6 +70,17 @@ __device__ __forceinline__ void load_2d(void *dst, const CUtensorMap *map, int x
         : "memory");
 }
 
+// One 3D box of `map` at element coordinates (x, y, z); x * element size a
+// multiple of 16.
+__device__ __forceinline__ void load_3d(void *dst, const CUtensorMap *map, int x, int y, int z, uint64_t *bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+        "[%5];"
+        ::"r"(smem_u32(dst)), "l"((unsigned long long)map), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
+        : "memory");
+}
+
 // Order this thread's generic-proxy global accesses with later async-proxy
 // (TMA) accesses, across a grid barrier.
 __device__ __forceinline__ void fence_proxy_async_global() { asm volatile("fence.proxy.async.global;" ::: "memory"); }
@@ -103,6 +114,22 @@ inline bool make_map_2d(CUtensorMap *m, const void *base, CUtensorMapDataType dt
     cuuint32_t estr[2] = {1, 1};
     return fn(m, dt, 2, const_cast<void *>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, swz,
               CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// Row-major 3D map of nx x ny x nz elements (x fastest), box box_x x box_y x
+// box_z, no swizzle, zero fill out of range.
+inline bool make_map_3d(CUtensorMap *m, const void *base, CUtensorMapDataType dt, size_t esize, long long nx,
+                        long long ny, long long nz, uint32_t box_x, uint32_t box_y, uint32_t box_z)
+{
+    auto fn = encode_fn();
+    if (!fn) return false;
+    cuuint64_t dims[3] = {(cuuint64_t)nx, (cuuint64_t)ny, (cuuint64_t)nz};
+    cuuint64_t strides[2] = {(cuuint64_t)(nx * (long long)esize), (cuuint64_t)(nx * ny * (long long)esize)};
+    cuuint32_t box[3] = {box_x, box_y, box_z};
+    cuuint32_t estr[3] = {1, 1, 1};
+    return fn(m, dt, 3, const_cast<void *>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+              CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
 }  // namespace tma

@@ -153,10 +153,10 @@ void tune_fill(slr_desc *d)
     if (!lookup_locked(d, &r)) return;
     if (d->loop == SLR_LOOP_AUTO) d->loop = r.loop;
     if (d->temporal_k == 0 && d->stencil == SLR_LIFE) d->temporal_k = r.temporal_k;
-    if (d->tiling == SLR_TILING_AUTO && d->stencil == SLR_RESTORE8) d->tiling = r.tiling;
+    if (d->tiling == SLR_TILING_AUTO && d->stencil != SLR_LIFE) d->tiling = r.tiling;
     // the grid size was timed with the kernel of the cached choice only
     const bool same_kernel = d->loop == r.loop && (d->stencil != SLR_LIFE || d->temporal_k == r.temporal_k) &&
-                             (d->stencil != SLR_RESTORE8 || d->tiling == r.tiling);
+                             (d->stencil == SLR_LIFE || d->tiling == r.tiling);
     if (d->grid_ctas == 0 && same_kernel) d->grid_ctas = r.grid_ctas;
 }
 }  // namespace slr
@@ -211,7 +211,11 @@ slr_status slr_tune(const slr_desc *d, const void *u, const void *aux, void *scr
     if (base.loop == SLR_LOOP_AUTO) base.loop = SLR_LOOP_PERSISTENT;
     const bool persistent = base.loop == SLR_LOOP_PERSISTENT;
     const bool life_tb = d->stencil == SLR_LIFE && slr::life_tb_supported(p);
-    const bool tma = d->stencil == SLR_RESTORE8 && slr::restore_tma_ok(p);
+    const bool jacobi = (d->stencil == SLR_J2D5 || d->stencil == SLR_J3D7) && !d->defect_correction;
+    // the trial buffers stand in for the caller's (same alignment: 256 bytes)
+    const void *ta = b.state, *tb = b.ws + slr::kCtlBytes;
+    const bool tma = (d->stencil == SLR_RESTORE8 && slr::restore_tma_ok(p)) ||
+                     (jacobi && slr::jacobi_tma_ok(p, ta, tb, aux, true));
 
     // What the default resolves to, so that equal configurations are timed once.
     auto resolved_k = [&](const slr_desc &c) {
@@ -219,8 +223,11 @@ slr_status slr_tune(const slr_desc *d, const void *u, const void *aux, void *scr
         return slr::life_tb_resolve_k(slr::problem_of(&c), c.grid_ctas);
     };
     auto resolved_tiling = [&](const slr_desc &c) {
-        return c.loop == SLR_LOOP_PERSISTENT && tma && c.tiling != SLR_TILING_NONE ? SLR_TILING_TMA
-                                                                                   : SLR_TILING_NONE;
+        if (c.loop != SLR_LOOP_PERSISTENT || !tma || c.tiling == SLR_TILING_NONE) return (int)SLR_TILING_NONE;
+        if (jacobi && c.tiling == SLR_TILING_AUTO)   // the size rule of the library default
+            return slr::jacobi_tma_ok(slr::problem_of(&c), ta, tb, aux, false) ? (int)SLR_TILING_TMA
+                                                                                 : (int)SLR_TILING_NONE;
+        return (int)SLR_TILING_TMA;
     };
 
     std::vector<slr_desc> stage1;
@@ -235,9 +242,10 @@ slr_status slr_tune(const slr_desc *d, const void *u, const void *aux, void *scr
             stage1.push_back(c);
         }
     }
-    if (persistent && d->stencil == SLR_RESTORE8 && d->tiling == SLR_TILING_AUTO && tma) {
+    if (persistent && (d->stencil == SLR_RESTORE8 || jacobi) && d->tiling == SLR_TILING_AUTO && tma) {
+        // the other staging than the default's
         slr_desc c = base;
-        c.tiling = SLR_TILING_NONE;
+        c.tiling = resolved_tiling(base) == SLR_TILING_TMA ? SLR_TILING_NONE : SLR_TILING_TMA;
         stage1.push_back(c);
     }
     if (d->loop == SLR_LOOP_AUTO && !d->defect_correction) {
@@ -283,7 +291,7 @@ slr_status slr_tune(const slr_desc *d, const void *u, const void *aux, void *scr
     memset(&r, 0, sizeof(r));
     r.loop = best.loop;
     r.temporal_k = d->stencil == SLR_LIFE ? resolved_k(best) : 0;
-    r.tiling = d->stencil == SLR_RESTORE8 ? resolved_tiling(best) : SLR_TILING_AUTO;
+    r.tiling = d->stencil == SLR_RESTORE8 || jacobi ? resolved_tiling(best) : SLR_TILING_AUTO;
     r.grid_ctas = best.loop == SLR_LOOP_PERSISTENT ? best.grid_ctas : 0;
     r.trials = b.trials;
     r.ms_per_iter = best_ms;

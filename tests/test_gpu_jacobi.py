@@ -138,3 +138,34 @@ def test_constant_division_matches_ieee(gpu, d):
     mismatches, checked = gpu.slr_check_exact_division(d)
     assert checked == [1 << 32, 1 << 26]
     assert mismatches == [0, 0]
+
+
+# ---- TMA-staged sweeps (Dirichlet ghost +0, rows of whole 16-byte groups) ----
+# forced with SLR_TILING_TMA on grids with ragged tiles in x (nx not a multiple
+# of 256) and in y (ny not a multiple of the tile's rows), a fixed number of
+# sweeps (tol 0), bit-exact against the oracle
+@pytest.mark.parametrize("shape,storage", [((300, 520), "f32"), ((96, 1024), "f64"), ((70, 1040), "bf16"),
+                                           ((33, 264), "f16"), ((9, 37, 264), "bf16"), ((17, 20, 256), "f32"),
+                                           ((5, 9, 128), "f64"), ((4, 3, 520), "f16"), ((1, 1, 8), "bf16")])
+def test_tma_path_bit_exact(gpu, orc, shape, storage):
+    r = jacobi_case(gpu, orc, shape, storage=storage, tol=0.0, max_iters=23, tiling=gpu.SLR_TILING_TMA)
+    assert r.iters == 23 and not r.converged
+
+
+@pytest.mark.parametrize("kw", [dict(wrap=True), dict(ghost=0.25), dict(ghost=-0.0)])
+def test_tma_request_falls_back_where_it_does_not_apply(gpu, orc, kw):
+    jacobi_case(gpu, orc, (40, 512), storage="f32", tol=0.0, max_iters=9, tiling=gpu.SLR_TILING_TMA, **kw)
+
+
+@pytest.mark.parametrize("tiling", [1, 2])
+def test_tma_and_register_paths_agree_to_convergence(gpu, orc, tiling):
+    # the FP32 form of the 256 x 256 Helmholtz problem, both staging choices
+    r = jacobi_case(gpu, orc, (256, 256), storage="f32", tol=1e-6, tiling=tiling)
+    assert r.converged
+
+
+@pytest.mark.slow
+def test_full_size_2d_f32_and_3d_bf16_default_path(gpu, orc):
+    # the large single grids of the Jacobi bench, a few sweeps, library-chosen staging
+    jacobi_case(gpu, orc, (8192, 8192), storage="f32", tol=0.0, max_iters=3)
+    jacobi_case(gpu, orc, (512, 512, 512), storage="bf16", tol=0.0, max_iters=2)
