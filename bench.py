@@ -587,6 +587,80 @@ def run_jacobi(args):
     return 0
 
 
+def run_precision(args):
+    """Mixed precision at the same accuracy: 2D Helmholtz (sigma 1, h = 1/(n+1),
+    f ~ U[-1, 1], zero Dirichlet) solved until the change of the next FP64
+    sweep, max |h^2 r / (4 + sigma h^2)|, is below 1e-10, three ways: the plain
+    loop (one FP64 sweep launch, one reduce launch and a host test per
+    iteration), the fused FP64 device loop, and FP32 inner Jacobi solves under
+    FP64 defect correction.  Storage precisions (FP32, BF16, FP16 state with
+    FP32 arithmetic) run the fused loop to tol 1e-6 next to FP64 at the same
+    tol, and the plain FP32 loop to tol 1e-6.  Every result's error is
+    max |u - u*| / max |u*| against the discrete solution u* (the FP64 oracle
+    iterated to 1e-14); the oracle's own 1e-10 solve is the CPU leg of this
+    workload and is timed.  Storage with fewer bits can stop at the cap: its
+    +-1-ulp updates may never meet the tolerance."""
+    import numpy as np
+    import torch
+    import oracle
+    from paper_1609_04567_gb300 import inputs, slr
+    slr.load()
+    stream = torch.cuda.Stream()
+    out = {}
+    for n in args.precision_sides:
+        f64 = inputs.helmholtz_rhs((n, n))
+        f = torch.from_numpy(f64).cuda()
+        t0 = time.perf_counter()
+        ref10, rr10 = oracle.j2d5(np.zeros((n, n)), f64, tol=1e-10, max_iters=10 ** 6)
+        cpu10 = time.perf_counter() - t0
+        # the discrete solution, to well below either stopping rule's error
+        ref, _ = oracle.j2d5(ref10, f64, tol=1e-14, max_iters=10 ** 6)
+        scale = float(np.max(np.abs(ref)))
+
+        def solve(name, dtype, reps, **fields):
+            fs = f.to(torch.float32).to(dtype) if dtype != torch.float64 else f
+            u = torch.zeros((n, n), dtype=dtype, device="cuda")
+            with torch.cuda.stream(stream):
+                s = slr.Solver(slr.SLR_J2D5, u, fs, stream=stream, **fields)
+
+                def step():
+                    u.zero_()
+                    slr.slr_destroy(s.handle)
+                    s.handle = slr.slr_create(s.desc, u.data_ptr(), fs.data_ptr(),
+                                              s.ws.data_ptr() + ((-s.ws.data_ptr()) % 256),
+                                              slr.slr_workspace_size(s.desc), stream.cuda_stream)
+                    s.run(args.precision_cap)
+                step()                                          # warm-up
+                torch.cuda.synchronize()
+                t1 = time.perf_counter()
+                for _ in range(reps):
+                    step()
+                torch.cuda.synchronize()
+                ms = (time.perf_counter() - t1) / reps * 1e3
+                r = s.result(check=False)
+                s.close()
+            return u.double().cpu().numpy(), r, ms
+
+        row = {"oracle_fp64_1e-10": {"sweeps": rr10.iters, "cpu_ms": cpu10 * 1e3}}
+        for name, dtype, reps, fields in (
+                ("plain_fp64_1e-10", torch.float64, 1, dict(tol=1e-10, loop=slr.SLR_LOOP_HOST)),
+                ("fused_fp64_1e-10", torch.float64, 3, dict(tol=1e-10)),
+                ("fused_dc_fp32_inner_1e-10", torch.float64, 3, dict(tol=1e-10, defect_correction=1)),
+                ("plain_fp32_1e-6", torch.float32, 1, dict(tol=1e-6, loop=slr.SLR_LOOP_HOST)),
+                ("fused_fp64_1e-6", torch.float64, 3, dict(tol=1e-6)),
+                ("fused_fp32_1e-6", torch.float32, 3, dict(tol=1e-6)),
+                ("fused_bf16_1e-6", torch.bfloat16, 3, dict(tol=1e-6)),
+                ("fused_fp16_1e-6", torch.float16, 3, dict(tol=1e-6))):
+            u, r, ms = solve(name, dtype, reps, **fields)
+            row[name] = {"ms": ms, "iters": r.iters, "converged": r.converged, "value": r.value,
+                         "rel_err_vs_fp64_oracle": float(np.max(np.abs(u - ref)) / scale)}
+        out[f"{n}x{n}"] = row
+    line = {"workload": "precision_helmholtz_2d", "metric": "time to the same stopping rule", "unit": "ms",
+            "note": "defect correction iterations are corrections of 50 FP32 sweeps each", "cases": out}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_batch(args):
     """512 2D Helmholtz grids (side log-uniform in [64, 1024]) + one 512^3 3D
     grid, bfloat16 storage, tol 1e-6, in one batch; against the same grids
@@ -679,7 +753,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="life",
-                    choices=["life", "helmholtz", "restore", "jacobi", "batch", "serve"])
+                    choices=["life", "helmholtz", "restore", "jacobi", "precision", "batch", "serve"])
     ap.add_argument("--batch3d", type=int, default=512, help="side of the 3D grid of the batch workload (0: none)")
     ap.add_argument("--rate", type=float, default=2000.0)
     ap.add_argument("--serve-seconds", type=float, default=10.0)
@@ -688,6 +762,9 @@ def main():
     ap.add_argument("--gens", type=int, default=2000,
                     help="generations per solve (the workload has 2000; shorter runs are for profiler captures "
                          "and are named as such in config.workload)")
+    ap.add_argument("--precision-sides", type=int, nargs="+", default=[64, 128],
+                    help="grid sides of the precision workload")
+    ap.add_argument("--precision-cap", type=int, default=200000, help="iteration cap of the precision workload")
     ap.add_argument("--no-tune", action="store_true", help="skip the autotuner (built-in launch defaults)")
     ap.add_argument("--grid-ctas", type=int, default=0, help="CTAs of the persistent launch (0 = library choice)")
     ap.add_argument("--tune-iters", type=int, default=240, help="iterations per autotuner trial")
@@ -698,8 +775,8 @@ def main():
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     if args.workload != "life":
-        fn = {"helmholtz": run_helmholtz, "restore": run_restore, "jacobi": run_jacobi, "batch": run_batch,
-              "serve": run_serve}
+        fn = {"helmholtz": run_helmholtz, "restore": run_restore, "jacobi": run_jacobi, "precision": run_precision,
+              "batch": run_batch, "serve": run_serve}
         return fn[args.workload](args)
     wl = WORKLOADS[args.workload]
     world, rank, local = dist_setup()
