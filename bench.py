@@ -734,14 +734,17 @@ def run_serve(args):
     from paper_1609_04567_gb300 import serve, slr
     slr.load()
     reqs = serve.make_requests(args.serve_seconds + 1.0, args.rate)
-    srv = serve.Server(max_slots=1024, step_sweeps=args.step_sweeps)
+    srv = serve.Server(max_slots=1024, step_sweeps=args.step_sweeps, solo_cells=args.solo_cells or None)
     st = srv.serve(reqs, warmup_s=1.0, time_limit_s=args.serve_seconds * 6 + 30)
     srv.close()
     line = {"workload": f"serve_poisson{args.rate:g}rps_denoise256-4096_solve64-2048",
             "metric": "p50/p99 latency and throughput", "unit": "ms", "p50_ms": st.p50_ms, "p99_ms": st.p99_ms,
             "mean_ms": st.mean_ms, "throughput_rps": st.throughput_rps, "gcell_per_s": st.gcell_per_s,
             "requests": st.requests, "completed": st.completed, "wall_s": st.wall_s, "steps": st.steps,
-            "max_in_flight": st.max_in_flight, "max_queue": st.max_queue}
+            "max_in_flight": st.max_in_flight, "max_queue": st.max_queue,
+            "solo_lane": {"min_cells": args.solo_cells, "requests": sum(srv.is_solo(r) for r in reqs),
+                          "what": "denoise jobs of at least min_cells pixels run on their own TMA-tiled solver, "
+                                  "resumed step_sweeps sweeps per iteration after the batch launch"}}
     print(json.dumps(line), flush=True)
     return 0
 
@@ -758,6 +761,8 @@ def main():
     ap.add_argument("--rate", type=float, default=2000.0)
     ap.add_argument("--serve-seconds", type=float, default=10.0)
     ap.add_argument("--step-sweeps", type=int, default=32)
+    ap.add_argument("--solo-cells", type=int, default=1024 * 1024,
+                    help="serving: denoise jobs of at least this many pixels take the solo lane (0: none)")
     ap.add_argument("--k", type=int, default=0, help="generations per HBM pass (0 = library choice)")
     ap.add_argument("--gens", type=int, default=2000,
                     help="generations per solve (the workload has 2000; shorter runs are for profiler captures "

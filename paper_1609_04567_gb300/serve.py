@@ -14,6 +14,13 @@ Admission is by device memory: a request needs its state, its auxiliary input
 (f or mask) and one scratch buffer; it is admitted only while the sum of the
 footprints of admitted requests stays inside the budget (by default a fraction
 of the free memory reported by the driver at start-up).
+
+Large denoise jobs (at least ``solo_cells`` pixels) take a second lane: each
+gets its own resident solver (the TMA-tiled restoration loop, which streams a
+large frame several times faster than the batch's warp units) and is resumed
+for the same number of sweeps per iteration, on the same stream, right after
+the batch launch.  Both lanes therefore advance every admitted request by the
+same number of sweeps per iteration; results do not depend on the lane.
 """
 from __future__ import annotations
 
@@ -42,6 +49,8 @@ class Request:
     value: float = 0.0
     slot: int = -1
     tensors: tuple = field(default=(), repr=False)
+    solver: object = field(default=None, repr=False)   # the solo lane's solver
+    target: int = 0                                     # the solo lane's iteration cap so far
 
 
 def bucket_sides(lo: int, hi: int, n: int) -> list[int]:
@@ -120,7 +129,8 @@ class Server:
     """One resident batch served with continuous batching."""
 
     def __init__(self, *, max_slots: int = 1024, budget_bytes: int | None = None, step_sweeps: int = 32,
-                 denoise_tol: float = 1e-3, solve_tol: float = 1e-6, cap: int = 5000, device=None):
+                 denoise_tol: float = 1e-3, solve_tol: float = 1e-6, cap: int = 5000, device=None,
+                 solo_cells: int | None = 1024 * 1024):
         import torch
         self.torch = torch
         self.device = torch.device(device or "cuda")
@@ -136,11 +146,16 @@ class Server:
         self.tol = {KIND_DENOISE: denoise_tol, KIND_SOLVE: solve_tol}
         self.cap = cap
         self.pool = InputPool()
-        self.active = {}
+        self.active = {}          # batch slot -> request
+        self.solo = {}            # request id -> request with its own solver
+        self.solo_cells = solo_cells
+
+    def is_solo(self, r: Request) -> bool:
+        return self.solo_cells is not None and r.kind == KIND_DENOISE and r.side * r.side >= self.solo_cells
 
     def admit(self, r: Request, now: float) -> bool:
         need = footprint(r.kind, r.side)
-        if len(self.active) >= self.max_slots or self.in_use + need > self.budget:
+        if len(self.active) + len(self.solo) >= self.max_slots or self.in_use + need > self.budget:
             return False
         torch = self.torch
         host_u, host_aux = self.pool.get(r.kind, r.side)
@@ -150,22 +165,59 @@ class Server:
             u.copy_(host_u, non_blocking=True)
             aux.copy_(host_aux, non_blocking=True)
             stencil = slr.SLR_RESTORE8 if r.kind == KIND_DENOISE else slr.SLR_J2D5
-            r.slot = self.batch.add(stencil, u, aux, self.cap, tol=self.tol[r.kind])
+            if self.is_solo(r):
+                r.solver = slr.Solver(stencil, u, aux, stream=self.stream, tol=self.tol[r.kind])
+                r.target = 0
+                self.solo[r.rid] = r
+            else:
+                r.slot = self.batch.add(stencil, u, aux, self.cap, tol=self.tol[r.kind])
+                self.active[r.slot] = r
         r.tensors = (u, aux)
         r.admitted = now
         self.in_use += need
-        self.active[r.slot] = r
         return True
 
-    def retire(self, slot: int, now: float, keep: bool) -> Request:
-        r = self.active.pop(slot)
-        res = self.batch.result(slot)
+    def _finish(self, r: Request, now: float, res, keep: bool) -> Request:
         r.finished, r.iters, r.converged, r.value = now, res.iters, res.converged, res.value
-        self.batch.remove(slot)
         self.in_use -= footprint(r.kind, r.side)
         if not keep:
             r.tensors = ()
         return r
+
+    def retire(self, slot: int, now: float, keep: bool) -> Request:
+        r = self.active.pop(slot)
+        res = self.batch.result(slot)
+        self.batch.remove(slot)
+        return self._finish(r, now, res, keep)
+
+    def step(self) -> list[int]:
+        """Enqueue step_sweeps more sweeps of every admitted request (the
+        batch launch, then each solo solver), wait, and return the finished
+        batch slots."""
+        if self.active:
+            self.batch.run(self.step_sweeps)
+        for r in self.solo.values():
+            r.target = min(self.cap, r.target + self.step_sweeps)
+            r.solver.run(r.target)
+        if self.active:
+            finished, _ = self.batch.poll()
+            return finished
+        self.stream.synchronize()
+        return []
+
+    def retire_solo(self, now: float, keep: bool) -> list[Request]:
+        out = []
+        for rid in list(self.solo):
+            r = self.solo[rid]
+            res = r.solver.result(check=False)
+            if res.status < 0:
+                raise slr.SlrError(res.status, "solo solve failed")
+            if res.converged or res.iters >= self.cap:
+                del self.solo[rid]
+                r.solver.close()
+                r.solver = None
+                out.append(self._finish(r, now, res, keep))
+        return out
 
     def serve(self, requests: list[Request], *, warmup_s: float = 0.0, keep_results: bool = False,
               time_limit_s: float | None = None) -> ServeStats:
@@ -179,7 +231,7 @@ class Server:
         queue: list[Request] = []
         steps = max_in_flight = max_queue = 0
         t0 = time.perf_counter()
-        while qi < len(pending) or queue or self.active:
+        while qi < len(pending) or queue or self.active or self.solo:
             now = time.perf_counter() - t0
             if time_limit_s is not None and now > time_limit_s:
                 break
@@ -189,17 +241,17 @@ class Server:
             while queue and self.admit(queue[0], now):
                 queue.pop(0)
             max_queue = max(max_queue, len(queue))
-            max_in_flight = max(max_in_flight, len(self.active))
-            if not self.active:
+            max_in_flight = max(max_in_flight, len(self.active) + len(self.solo))
+            if not self.active and not self.solo:
                 if qi < len(pending):
                     time.sleep(max(0.0, min(pending[qi].arrival - now, 0.001)))
                 continue
-            self.batch.run(self.step_sweeps)
-            finished, _ = self.batch.poll()
+            finished = self.step()
             steps += 1
             now = time.perf_counter() - t0
             for s in finished:
                 done.append(self.retire(s, now, keep_results))
+            done.extend(self.retire_solo(now, keep_results))
         wall = time.perf_counter() - t0
         self.done = done
         measured = [r for r in done if r.arrival >= warmup_s]
@@ -213,4 +265,7 @@ class Server:
             steps=steps, max_in_flight=max_in_flight, max_queue=max_queue, budget_bytes=self.budget)
 
     def close(self):
+        for r in self.solo.values():
+            r.solver.close()
+        self.solo = {}
         self.batch.close()

@@ -20,16 +20,21 @@ def solve_alone(slr, r, server):
     return u, res
 
 
-def test_results_alone_equal_results_in_the_mix(gpu):
+@pytest.mark.parametrize("solo_cells", [None, 128 * 128])
+def test_results_alone_equal_results_in_the_mix(gpu, solo_cells):
+    # solo_cells = 128^2: the denoise jobs of 128^2 pixels and more take the solo lane
     from paper_1609_04567_gb300 import serve
     reqs = serve.make_requests(0.4, 300.0, seed=3, denoise_sides=(32, 256), solve_sides=(16, 128), buckets=5)
     assert len(reqs) > 60
-    srv = serve.Server(max_slots=64, step_sweeps=8)
+    srv = serve.Server(max_slots=64, step_sweeps=8, solo_cells=solo_cells)
+    n_solo = sum(srv.is_solo(r) for r in reqs)
+    assert (n_solo > 5) == (solo_cells is not None)
     stats = srv.serve(reqs, keep_results=True)
     assert stats.completed == len(reqs)
     assert stats.max_in_flight > 1                     # work really overlapped in the batch
     done = {r.rid: r for r in srv.done}
-    for r in list(done.values())[::7]:
+    picks = list(done.values())[::7] + [r for r in done.values() if srv.is_solo(r)][:6]
+    for r in picks:
         u_alone, res = solve_alone(gpu, r, srv)
         assert (r.iters, r.converged) == (res.iters, res.converged)
         assert torch.equal(r.tensors[0], u_alone)
