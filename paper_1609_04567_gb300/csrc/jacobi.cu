@@ -492,12 +492,23 @@ struct JacobiTma {
 #pragma unroll
                 for (int p = 0; p < kPer; ++p) {
                     const int g = tid + p * kJThreads;
-                    const int r = g / kG, c = g % kG;
+                    const int r = g / kG, c = g % kG;          // a warp covers 32 consecutive groups of one row
                     const int x = x0 + c * V;
                     const int y = DIM == 3 ? y0 + r : j * kTY + r;
-                    if (!got || x >= nx || y >= ny) continue;
                     const T *ctr = Mc + (r + kHalo) * kTX + c * V;
-                    const Row cv = lds(ctr), fr = lds(F + r * kTX + c * V);
+                    const Row cv = lds(ctr);
+                    // x-neighbours of the lane's first and last cell from the adjacent lanes;
+                    // the warp's two end lanes read them from the tile or the side columns
+                    const int lane = tid & 31;
+                    C left = __shfl_up_sync(0xffffffffu, cv.raw(V - 1), 1);
+                    C right = __shfl_down_sync(0xffffffffu, cv.raw(0), 1);
+                    if (!got || x >= nx || y >= ny) continue;
+                    const C zero = C(0);
+                    if (lane == 0)
+                        left = c > 0 ? Store<T>::back(ctr[-1]) : (x0 > 0 ? Store<T>::back(SL[r * V + V - 1]) : zero);
+                    if (lane == 31)
+                        right = c < kG - 1 ? Store<T>::back(ctr[V]) : (x0 + kTX < nx ? Store<T>::back(SR[r * V]) : zero);
+                    const Row fr = lds(F + r * kTX + c * V);
                     Row nr, sr, ar, br;                              // y-1, y+1, march-1, march+1
                     if (DIM == 3) {
                         nr = lds(ctr - kTX);
@@ -509,10 +520,6 @@ struct JacobiTma {
                         br = lds(r < kTY - 1 ? ctr + kTX : Mb + c * V);
                         nr.ghost = sr.ghost = true;
                     }
-                    const C zero = C(0);
-                    const C left = c > 0 ? Store<T>::back(ctr[-1]) : (x0 > 0 ? Store<T>::back(SL[r * V + V - 1]) : zero);
-                    const C right = c < kG - 1 ? Store<T>::back(ctr[V])
-                                               : (x0 + kTX < nx ? Store<T>::back(SR[r * V]) : zero);
                     uint32_t ow[Row::kWords];
                     if constexpr (std::is_same<C, float>::value) {
                         // two cells per paired binary32 operation (same rounding per cell)
