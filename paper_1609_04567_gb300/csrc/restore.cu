@@ -102,9 +102,16 @@ constexpr int kMBytes = (kMBoxW * kBoxH + 127) / 128 * 128;       // 3264 -> 332
 constexpr int kStage = kUBytes + kMBytes;                         // 13184
 constexpr uint32_t kTxBytes = kUBoxW * kBoxH * 4 + kMBoxW * kBoxH; // bytes the two boxes deliver
 constexpr int kTThreads = 256;                    // 8 warps x 4 tile rows
-constexpr size_t kTSmem = 128 + 2 * (size_t)kStage + 32;   // stages, 2 mbarriers, tile counter
+constexpr int kNS = 3;                            // stages in the ring
+constexpr size_t kTSmem = 128 + (size_t)kNS * kStage + kNS * 8 + kNS * 4 + 16;   // stages, mbarriers, counts, counter
 static_assert(kStage % 128 == 0 && kUBytes % 128 == 0, "TMA destinations must be 128-byte aligned");
 
+// Each warp owns four rows of every tile: it copies their clean pixels,
+// lists their noisy ones in its own shared-memory list and computes them, so
+// warps never wait for one another inside a sweep.  Tiles stream through a
+// ring of kNS stages; the last warp to finish with a stage refills it with the
+// tile kNS further on, so a fast warp can run up to kNS - 1 tiles ahead and the
+// tile-to-tile differences in noisy pixels per warp even out.
 template <bool FAST>
 struct RestoreTma {
     CUtensorMap umap[2];      // state maps over buffer A and buffer B
@@ -117,21 +124,24 @@ struct RestoreTma {
 
     __device__ __forceinline__ size_t state_bytes() const { return (size_t)nx * ny * sizeof(float); }
 
-    // dynamic shared memory: [stage 0][stage 1][mbarrier 0, 1][tile counter]
+    // dynamic shared memory: [stages][mbarriers][warps done per stage][tile counter]
     __device__ __forceinline__ unsigned char *stages() const
     {
         extern __shared__ unsigned char smem_dyn[];
         return (unsigned char *)(((uintptr_t)smem_dyn + 127) & ~(uintptr_t)127);
     }
-    __device__ __forceinline__ uint64_t *bars() const { return (uint64_t *)(stages() + 2 * kStage); }
-    // tiles consumed by this CTA so far: tile q uses stage q & 1, phase (q >> 1) & 1
-    __device__ __forceinline__ unsigned *counter() const { return (unsigned *)(bars() + 2); }
+    __device__ __forceinline__ uint64_t *bars() const { return (uint64_t *)(stages() + kNS * kStage); }
+    __device__ __forceinline__ unsigned *done() const { return (unsigned *)(bars() + kNS); }
+    // tiles consumed by this CTA so far: tile q uses stage q % kNS, phase (q / kNS) & 1
+    __device__ __forceinline__ unsigned *counter() const { return done() + kNS; }
 
     __device__ __forceinline__ void prologue() const
     {
         if (threadIdx.x == 0) {
-            tma::mbar_init(&bars()[0], 1);
-            tma::mbar_init(&bars()[1], 1);
+            for (int i = 0; i < kNS; ++i) {
+                tma::mbar_init(&bars()[i], 1);
+                done()[i] = 0u;
+            }
             tma::mbar_init_fence();
             *counter() = 0u;
         }
@@ -166,12 +176,8 @@ struct RestoreTma {
     template <bool REDUCE>
     __device__ __forceinline__ void sweep(const void *src_v, void *dst_v, Slot *slot) const
     {
-        // noisy pixels of a tile, listed as (row << 6 | column); two lists
-        // alternate between tiles, three counters rotate so that a counter is
-        // reset one barrier before its next use
-        __shared__ unsigned short s_list[2][kTH * kTW];
-        __shared__ int s_count[3];
-        __shared__ int s_fail;
+        __shared__ unsigned short s_list[kTThreads / 32][4 * kTW];   // each warp's noisy pixels of a tile
+        __shared__ int s_stop;
         float *dst = (float *)dst_v;
         const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
         const unsigned lt_mask = (1u << lane) - 1u;
@@ -179,55 +185,42 @@ struct RestoreTma {
         const int ntiles = tiles_x * tiles_y;
         const int mine = (int)blockIdx.x < ntiles ? (ntiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
         const unsigned q0 = *counter();
-        if (tid < 3) s_count[tid] = 0;
-        if (tid == 0) s_fail = 0;
-        __syncthreads();                                        // counter read, counters zeroed
-        if (tid == 0 && mine > 0) {
-            tma::fence_proxy_async_global();   // the previous sweep's stores, published by the grid barrier
-            issue((int)blockIdx.x, mi, (int)(q0 & 1u));
+        if (tid == 0) {
+            s_stop = ld_relaxed_u32((const unsigned *)err) != 0u;   // a wait ran out earlier
+            if (!s_stop) {
+                tma::fence_proxy_async_global();   // the previous sweep's stores, published by the grid barrier
+                for (int i = 0; i < kNS && i < mine; ++i)
+                    issue((int)blockIdx.x + i * (int)gridDim.x, mi, (int)((q0 + (unsigned)i) % kNS));
+            }
         }
+        __syncthreads();                                        // counter read, first tiles issued
         const int nxi = (int)nx, nyi = (int)ny;                 // extents are below 2^31 on this path
+        unsigned short *list = s_list[warp];
         unsigned long long sum = 0ull, cnt = 0ull;
-        for (int i = 0; i < mine; ++i) {
+        for (int i = 0; i < mine && !s_stop; ++i) {
             const unsigned qn = q0 + (unsigned)i;
-            const int sb = (int)(qn & 1u), lb = i & 1;
+            const int sb = (int)(qn % kNS);
             const int tile = (int)blockIdx.x + i * (int)gridDim.x;
             const int x0 = (tile % tiles_x) * kTW, y0 = (tile / tiles_x) * kTH;
             const float *U = (const float *)(stages() + sb * kStage);   // [34][72]: row y0-1+r, column x0-4+c
             const unsigned char *M = stages() + sb * kStage + kUBytes;  // [34][96]: row y0-1+r, column x0-16+c
-            // phase 1: every thread waits for the tile itself; clean pixels
-            // are copied, noisy ones appended to this tile's list
-            if (tma::bounded_wait(&bars()[sb], (qn >> 1) & 1u, 2000000000ll, err)) {
-                int *count = &s_count[i % 3];
-                unsigned short *list = s_list[lb];
+            const bool got = tma::bounded_wait(&bars()[sb], (qn / kNS) & 1u, 2000000000ll, err);
+            if (!__all_sync(0xffffffffu, got)) break;
+            // the warp's four rows: clean pixels copied, noisy ones listed
+            int n = 0;
 #pragma unroll
-                for (int h = 0; h < 8; ++h) {
-                    const int rr = warp * 4 + (h >> 1), cc = (h & 1) * 32 + lane;
-                    const int y = y0 + rr, x = x0 + cc;
-                    const bool valid = y < nyi && x < nxi;
-                    const bool noisy = valid && M[(rr + 1) * kMBoxW + cc + 16] != 0;
-                    if (valid && !noisy) dst[(size_t)y * (size_t)nxi + x] = U[(rr + 1) * kUBoxW + cc + 4];
-                    const unsigned m = __ballot_sync(0xffffffffu, noisy);
-                    int at = 0;
-                    if (lane == 0 && m) at = atomicAdd(count, __popc(m));
-                    at = __shfl_sync(0xffffffffu, at, 0);
-                    if (noisy) list[at + __popc(m & lt_mask)] = (unsigned short)(rr << 6 | cc);
-                }
-            } else {
-                s_fail = 1;
+            for (int h = 0; h < 8; ++h) {
+                const int rr = warp * 4 + (h >> 1), cc = (h & 1) * 32 + lane;
+                const int y = y0 + rr, x = x0 + cc;
+                const bool valid = y < nyi && x < nxi;
+                const bool noisy = valid && M[(rr + 1) * kMBoxW + cc + 16] != 0;
+                if (valid && !noisy) dst[(size_t)y * (size_t)nxi + x] = U[(rr + 1) * kUBoxW + cc + 4];
+                const unsigned m = __ballot_sync(0xffffffffu, noisy);
+                if (noisy) list[n + __popc(m & lt_mask)] = (unsigned short)(rr << 6 | cc);
+                n += __popc(m);
             }
-            __syncthreads();                                    // list complete; tile i-1 fully consumed
-            if (s_fail) break;
-            if (tid == 0) {
-                s_count[(i + 2) % 3] = 0;                       // next used by tile i + 2, after the next barrier
-                if (i + 1 < mine) issue(tile + (int)gridDim.x, mi, sb ^ 1);   // into the stage tile i-1 used
-            }
-            // phase 2: the list split evenly over the 8 warps, 32 at a time
-            const int total = s_count[i % 3];
-            const int share = (total + 8 * 32 - 1) / (8 * 32) * 32;
-            const int lo = warp * share, hi = lo + share < total ? lo + share : total;
-            const unsigned short *list = s_list[lb];
-            for (int t = lo + lane; t < hi; t += 32) {
+            __syncwarp();
+            for (int t = lane; t < n; t += 32) {
                 const int e = list[t];
                 const int rr = e >> 6, cc = e & 63;
                 const int y = y0 + rr, x = x0 + cc;
@@ -237,13 +230,13 @@ struct RestoreTma {
                 if (y > 0 && y + 1 < nyi && x > 0 && x + 1 < nxi) {
                     // all 8 neighbours exist (every pixel off the grid's border)
 #pragma unroll
-                    for (int n = 0; n < 9; ++n)
-                        if (n != 4) accumulate(uc, C[(n / 3 - 1) * kUBoxW + n % 3 - 1], num, den);
+                    for (int k = 0; k < 9; ++k)
+                        if (k != 4) accumulate(uc, C[(k / 3 - 1) * kUBoxW + k % 3 - 1], num, den);
                 } else {
 #pragma unroll
-                    for (int n = 0; n < 9; ++n) {
-                        const int di = n / 3 - 1, dj = n % 3 - 1;
-                        if (n == 4 || y + di < 0 || y + di >= nyi || x + dj < 0 || x + dj >= nxi) continue;
+                    for (int k = 0; k < 9; ++k) {
+                        const int di = k / 3 - 1, dj = k % 3 - 1;
+                        if (k == 4 || y + di < 0 || y + di >= nyi || x + dj < 0 || x + dj >= nxi) continue;
                         accumulate(uc, C[di * kUBoxW + dj], num, den);
                     }
                 }
@@ -251,9 +244,20 @@ struct RestoreTma {
                 dst[(size_t)y * (size_t)nxi + x] = nv;
                 if (REDUCE) sum += fixed_2m24(__fsub_rn(nv, uc));
             }
-            if (REDUCE && tid == 0) cnt += (unsigned long long)total;
+            if (REDUCE && lane == 0) cnt += (unsigned long long)n;
+            // done with the stage (and with the list): the last warp out refills it
+            __syncwarp();
+            if (lane == 0) {
+                __threadfence_block();
+                const unsigned before = atomicAdd(&done()[sb], 1u);
+                if (before == kTThreads / 32 - 1) {
+                    __threadfence_block();
+                    done()[sb] = 0u;
+                    if (i + kNS < mine) issue(tile + kNS * (int)gridDim.x, mi, sb);
+                }
+            }
         }
-        __syncthreads();                                       // the last tile is consumed before the counter moves
+        __syncthreads();                                       // every tile consumed, no copy in flight
         if (tid == 0) *counter() = q0 + (unsigned)mine;
         tma::fence_proxy_async_global();                       // this sweep's stores before the next TMA reads
         if (REDUCE) block_to_slot(slot, 0ull, sum, cnt, sum != 0ull);
