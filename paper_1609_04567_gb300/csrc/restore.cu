@@ -229,9 +229,25 @@ struct RestoreTma {
                 float num = 0.0f, den = 0.0f;
                 if (y > 0 && y + 1 < nyi && x > 0 && x + 1 < nxi) {
                     // all 8 neighbours exist (every pixel off the grid's border)
+                    if (FAST) {
 #pragma unroll
-                    for (int k = 0; k < 9; ++k)
-                        if (k != 4) accumulate(uc, C[(k / 3 - 1) * kUBoxW + k % 3 - 1], num, den);
+                        for (int k = 0; k < 9; ++k)
+                            if (k != 4) accumulate(uc, C[(k / 3 - 1) * kUBoxW + k % 3 - 1], num, den);
+                    } else {
+                        // neighbours in pairs (row-major order kept for the sums)
+                        float2 nd = make_float2(0.0f, 0.0f);
+#pragma unroll
+                        for (int k = 0; k < 8; k += 2) {
+                            const int k0 = k < 4 ? k : k + 1, k1 = k + 1 < 4 ? k + 1 : k + 2;
+                            const float u0 = C[(k0 / 3 - 1) * kUBoxW + k0 % 3 - 1];
+                            const float u1 = C[(k1 / 3 - 1) * kUBoxW + k1 % 3 - 1];
+                            const float2 w = weights_rn2(uc, u0, u1, alpha);
+                            nd = __fadd2_rn(nd, make_float2(__fmul_rn(w.x, u0), w.x));
+                            nd = __fadd2_rn(nd, make_float2(__fmul_rn(w.y, u1), w.y));
+                        }
+                        num = nd.x;
+                        den = nd.y;
+                    }
                 } else {
 #pragma unroll
                     for (int k = 0; k < 9; ++k) {
