@@ -221,6 +221,39 @@ __device__ __forceinline__ uint32_t load_word(const TbParams &tp, const unsigned
     return __ldcg(row + xw);
 }
 
+// One generation of a thread's row (34 words in registers, updated in place):
+// horizontal 2-bit sums by funnel shifts and logic, the rows above and below
+// by shuffle, the B3/S23 rule.  `changed` collects owned cells that changed;
+// in the pass's last generation (LAST) `cnt` counts the owned live cells.
+template <bool WRAP, bool FULL, bool LAST>
+__device__ __forceinline__ void generation(uint32_t (&cur)[kWords], bool own, int own_words, bool row_in, int wlo,
+                                           int whi, uint32_t &changed, uint32_t &cnt)
+{
+    uint32_t prevC = 0u, C = cur[0];
+#pragma unroll
+    for (int w = 0; w < kWords; ++w) {
+        const uint32_t nextC = w + 1 < kWords ? cur[w + 1] : 0u;
+        const uint32_t L = __funnelshift_l(prevC, C, 1);   // left neighbours (bit b-1)
+        const uint32_t R = __funnelshift_r(C, nextC, 1);   // right neighbours (bit b+1)
+        const uint32_t s0 = L ^ C ^ R, s1 = (L & C) | (L & R) | (C & R);   // L + C + R
+        const uint32_t m0 = L ^ R, m1 = L & R;                              // L + R
+        const uint32_t u0 = __shfl_up_sync(0xffffffffu, s0, 1), u1 = __shfl_up_sync(0xffffffffu, s1, 1);
+        const uint32_t d0 = __shfl_down_sync(0xffffffffu, s0, 1), d1 = __shfl_down_sync(0xffffffffu, s1, 1);
+        // n = (u0 + m0 + d0) + 2 (u1 + m1 + d1) = bit0 + 2 (c0 + u1 + m1 + d1)
+        const uint32_t bit0 = u0 ^ m0 ^ d0, c0 = (u0 & m0) | (u0 & d0) | (m0 & d0);
+        const uint32_t x = u1 ^ m1 ^ d1, yy = (u1 & m1) | (u1 & d1) | (m1 & d1);
+        uint32_t nw = ((x ^ c0) & ~yy) & (C | bit0);       // n == 3, or n == 2 and alive
+        if (!WRAP && !(row_in && w >= wlo && w <= whi)) nw = 0u;
+        if (w >= 1 && w <= kOwnWords && own && (FULL || w <= own_words)) {
+            changed |= nw ^ C;
+            if (LAST) cnt += (uint32_t)__popc(nw);
+        }
+        prevC = C;
+        cur[w] = nw;
+        C = nextC;
+    }
+}
+
 template <bool WRAP>
 __device__ __forceinline__ void run_tile(const TbParams &tp, int tile, int kp, const unsigned int *src,
                                          unsigned int *dst, uint32_t *xch, unsigned long long *s_cnt,
@@ -270,28 +303,14 @@ __device__ __forceinline__ void run_tile(const TbParams &tp, int tile, int kp, c
 
     for (int j = 0; j < kp; ++j) {
         uint32_t changed = 0u, cnt = 0u;
-        uint32_t prevC = 0u, C = cur[0];
-#pragma unroll
-        for (int w = 0; w < kWords; ++w) {
-            const uint32_t nextC = w + 1 < kWords ? cur[w + 1] : 0u;
-            const uint32_t L = __funnelshift_l(prevC, C, 1);   // left neighbours (bit b-1)
-            const uint32_t R = __funnelshift_r(C, nextC, 1);   // right neighbours (bit b+1)
-            const uint32_t s0 = L ^ C ^ R, s1 = (L & C) | (L & R) | (C & R);   // L + C + R
-            const uint32_t m0 = L ^ R, m1 = L & R;                              // L + R
-            const uint32_t u0 = __shfl_up_sync(0xffffffffu, s0, 1), u1 = __shfl_up_sync(0xffffffffu, s1, 1);
-            const uint32_t d0 = __shfl_down_sync(0xffffffffu, s0, 1), d1 = __shfl_down_sync(0xffffffffu, s1, 1);
-            // n = (u0 + m0 + d0) + 2 (u1 + m1 + d1) = bit0 + 2 (c0 + u1 + m1 + d1)
-            const uint32_t bit0 = u0 ^ m0 ^ d0, c0 = (u0 & m0) | (u0 & d0) | (m0 & d0);
-            const uint32_t x = u1 ^ m1 ^ d1, yy = (u1 & m1) | (u1 & d1) | (m1 & d1);
-            uint32_t nw = ((x ^ c0) & ~yy) & (C | bit0);       // n == 3, or n == 2 and alive
-            if (!WRAP && !(row_in && w >= wlo && w <= whi)) nw = 0u;
-            if (w >= 1 && w <= own_words && own) {
-                changed |= nw ^ C;
-                if (j == kp - 1) cnt += (uint32_t)__popc(nw);   // the count is taken on the pass's last state
-            }
-            prevC = C;
-            cur[w] = nw;
-            C = nextC;
+        // full tiles (every owned word inside the grid) drop the per-word
+        // bound; the live count is taken in the pass's last generation only
+        if (own_words == kOwnWords) {
+            if (j == kp - 1) generation<WRAP, true, true>(cur, own, own_words, row_in, wlo, whi, changed, cnt);
+            else generation<WRAP, true, false>(cur, own, own_words, row_in, wlo, whi, changed, cnt);
+        } else {
+            if (j == kp - 1) generation<WRAP, false, true>(cur, own, own_words, row_in, wlo, whi, changed, cnt);
+            else generation<WRAP, false, false>(cur, own, own_words, row_in, wlo, whi, changed, cnt);
         }
         // refresh the two copied rows from the neighbour warps (exchange rows
         // double buffered by generation parity: one barrier per generation;
