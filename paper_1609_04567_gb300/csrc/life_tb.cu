@@ -323,14 +323,12 @@ __device__ __forceinline__ void run_tile(const TbParams &tp, int tile, int kp, c
                 ((uint4 *)row)[i] = make_uint4(cur[4 * i], cur[4 * i + 1], cur[4 * i + 2], cur[4 * i + 3]);
             ((uint2 *)row)[16] = make_uint2(cur[32], cur[33]);
         }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
-            changed |= __shfl_xor_sync(0xffffffffu, changed, o);
-        }
+        // warp reduces: one vote for "changed", the count (last generation only) by one reduction
+        const bool any_changed = __any_sync(0xffffffffu, changed != 0u);
+        if (j == kp - 1) cnt = __reduce_add_sync(0xffffffffu, cnt);
         if (lane == 0) {
             if (cnt) atomicAdd(&s_cnt[kp - 1], (unsigned long long)cnt);
-            if (changed) atomicOr(&s_ch[j], 1u);
+            if (any_changed) atomicOr(&s_ch[j], 1u);
         }
         __syncthreads();
         if ((lane == 0 && warp > 0) || (lane == 31 && warp < kWarps - 1)) {
