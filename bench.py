@@ -282,12 +282,12 @@ def run_ours(args, wl, world, rank, local):
     value = world * cell_updates / (ms_step / 1e3) / 1e9
     kern_ms = statistics.mean(a.elapsed_time(b) for a, b in ev)
     # generations per pass: the tuner's choice, else the built-in default for
-    # 8192 x 8192 on 152 SMs, 12 (the largest k up to 16 whose 1024 x (242 - 2k)
-    # tiles fit 304 CTAs)
+    # 8192 x 8192 on 152 SMs, 25 (the largest k up to 32 whose 1024 x (482 - 2k)
+    # tiles fit the 152 co-resident CTAs)
     if tuned is not None:
         k_eff = tuned["temporal_k"]
     else:
-        k_eff = 1 if args.k == 1 else (args.k if args.k > 0 else 12)
+        k_eff = 1 if args.k == 1 else (args.k if args.k > 0 else 25)
     passes = -(-gens // k_eff)
     # k = 1 moves every cell as uint8 per pass; the temporal-blocked path reads
     # and writes the uint8 grid once per launch and the bit-packed grid once

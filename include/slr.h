@@ -113,7 +113,7 @@ typedef struct {
     int32_t loop;          /* slr_loop */
     int32_t math;          /* slr_math */
     int32_t temporal_k;    /* sweeps per HBM pass for Life (1, 2, 4, ..., 32); 0 = library
-                              choice (the autotuner's, else the largest k in [4, 16] whose
+                              choice (the autotuner's, else the largest k in [4, 32] whose
                               tiles fit the co-resident CTAs) */
     int64_t wait_limit_ns; /* device-side barrier wait limit; <= 0 selects 2 s */
     int32_t debug_flags;   /* SLR_DEBUG_* bits; 0 in normal use */

@@ -14,8 +14,8 @@
 //  G. Passes: each pass reads the packed grid, runs up to K generations on
 //     chip, and writes the packed grid to the other workspace buffer.  A tile
 //     is 1024 owned columns (plus one 32-cell word of halo on each side) by
-//     242 - 2K owned rows (plus K halo rows above and below); K generations
-//     stay exact inside it.  Thread (w, l) of the 8 warps holds tile row
+//     482 - 2K owned rows (plus K halo rows above and below); K generations
+//     stay exact inside it.  Thread (w, l) of the 16 warps holds tile row
 //     30w + l as 34 words in registers, so warps overlap by two rows: lanes
 //     1..30 are the warp's own rows, lanes 0 and 31 are copies of the
 //     neighbour warps' edge rows, refreshed through shared memory after every
@@ -42,10 +42,10 @@
 namespace slr {
 namespace {
 
-constexpr int kThreads = 256;
+constexpr int kThreads = 512;
 constexpr int kWarps = kThreads / 32;
 constexpr int kRowsPerWarp = 30;                      // own rows of a warp (lanes 1..30)
-constexpr int kTileRows = kWarps * kRowsPerWarp + 2;  // 242 distinct tile rows
+constexpr int kTileRows = kWarps * kRowsPerWarp + 2;  // 482 distinct tile rows
 constexpr int kWords = 34;                            // 1 halo + 32 owned + 1 halo
 constexpr int kOwnWords = 32;
 constexpr int kOwnCols = 32 * kOwnWords;              // 1024
@@ -362,7 +362,7 @@ __device__ __forceinline__ void run_tile(const TbParams &tp, int tile, int kp, c
 }
 
 template <bool WRAP>
-__global__ void __launch_bounds__(kThreads, 2) life_tb_kernel(const __grid_constant__ TbParams tp, LoopArgs la)
+__global__ void __launch_bounds__(kThreads, 1) life_tb_kernel(const __grid_constant__ TbParams tp, LoopArgs la)
 {
     extern __shared__ unsigned char smem_raw[];
     unsigned char *base = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -496,11 +496,12 @@ bool life_tb_supported(const Problem &p)
 size_t life_tb_bits_bytes(long long nx, long long ny) { return (size_t)(pitch_words(nx) * ny * 4); }
 
 // Generations per pass when the caller leaves it to the library: the largest K
-// (up to 16) whose tiling needs no more tiles than the CTAs resident at once.
+// (up to kMaxK) whose tiling needs no more tiles than the CTAs resident at
+// once, so every pass is one wave of tiles.
 int life_tb_default_k(const Problem &p, int nblocks)
 {
     const long long tx = (p.nx + kOwnCols - 1) / kOwnCols;
-    for (int k = 16; k >= 4; --k) {
+    for (int k = kMaxK; k >= 4; --k) {
         const long long own = kTileRows - 2 * k;
         if (tx * ((p.ny + own - 1) / own) <= nblocks) return k;
     }

@@ -118,12 +118,13 @@ def test_full_size_2000_generations_properties(gpu):
 
 # ---- temporal-blocked path (K generations per pass over a bit-packed grid) ----
 # It serves widths that are multiples of 32; tiles own 1024 columns and
-# 242 - 2K rows.
+# 482 - 2K rows (several tiles in y from ny = 1000).
 
 @pytest.mark.parametrize("ny,nx,wrap", [
     (256, 1024, True), (96, 2176, True), (32, 128, True), (480, 3072, True), (64, 1152, True),
     (257, 1024, True), (1, 32, True), (7, 96, True), (450, 2048, True),
     (257, 512, False), (70, 2080, False), (500, 1056, False), (33, 32, False), (1, 64, False),
+    (1000, 1024, True), (1000, 1056, False),
 ])
 @pytest.mark.parametrize("k", [2, 7, 16, 32])
 def test_temporal_blocked_matches_oracle(gpu, orc, ny, nx, wrap, k):
