@@ -221,6 +221,12 @@ __device__ __forceinline__ uint32_t load_word(const TbParams &tp, const unsigned
     return __ldcg(row + xw);
 }
 
+// Named barrier `id` (1..kWarps-1) for the two warps id - 1 and id.
+__device__ __forceinline__ void pair_sync(int id)
+{
+    asm volatile("bar.sync %0, 64;" ::"r"(id) : "memory");
+}
+
 // One generation of a thread's row (34 words in registers, updated in place):
 // horizontal 2-bit sums by funnel shifts and logic, the rows above and below
 // by shuffle, the B3/S23 rule.  `changed` collects owned cells that changed;
@@ -313,8 +319,10 @@ __device__ __forceinline__ void run_tile(const TbParams &tp, int tile, int kp, c
             else generation<WRAP, false, false>(cur, own, own_words, row_in, wlo, whi, changed, cnt);
         }
         // refresh the two copied rows from the neighbour warps (exchange rows
-        // double buffered by generation parity: one barrier per generation;
-        // 16-byte shared-memory accesses)
+        // double buffered by generation parity; 16-byte shared-memory
+        // accesses).  Each warp synchronises with its two neighbours only:
+        // named barrier w + 1 joins warps w and w + 1; even warps take the one
+        // below first, odd warps the one above, so pairs never wait in a chain
         uint32_t *xb = xch + (j & 1) * kWarps * 2 * kXchStride;
         if (lane == 1 || lane == kRowsPerWarp) {
             uint32_t *row = xb + (warp * 2 + (lane == 1 ? 0 : 1)) * kXchStride;
@@ -330,7 +338,13 @@ __device__ __forceinline__ void run_tile(const TbParams &tp, int tile, int kp, c
             if (cnt) atomicAdd(&s_cnt[kp - 1], (unsigned long long)cnt);
             if (any_changed) atomicOr(&s_ch[j], 1u);
         }
-        __syncthreads();
+        if (warp & 1) {
+            pair_sync(warp);                                   // with warp - 1
+            if (warp < kWarps - 1) pair_sync(warp + 1);        // with warp + 1
+        } else {
+            if (warp < kWarps - 1) pair_sync(warp + 1);
+            if (warp > 0) pair_sync(warp);
+        }
         if ((lane == 0 && warp > 0) || (lane == 31 && warp < kWarps - 1)) {
             // lane 0 takes lane 30 of the warp above, lane 31 lane 1 of the warp below
             const uint32_t *row = xb + (lane == 0 ? (warp - 1) * 2 + 1 : (warp + 1) * 2) * kXchStride;
