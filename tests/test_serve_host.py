@@ -1,0 +1,53 @@
+"""Host logic of the serving loop, no GPU: the Poisson request stream, the
+size buckets, device-memory footprints and which requests take the solo lane."""
+import math
+
+import numpy as np
+import pytest
+
+
+def test_bucket_sides_are_log_spaced_multiples_of_8():
+    from paper_1609_04567_gb300 import serve
+    sides = serve.bucket_sides(256, 4096, 8)
+    assert sides[0] == 256 and sides[-1] == 4096 and len(sides) == 8
+    assert all(s % 8 == 0 for s in sides)
+    ratios = [b / a for a, b in zip(sides, sides[1:])]
+    assert max(ratios) / min(ratios) < 1.05           # equal steps in log size
+
+
+def test_request_stream_is_poisson_and_reproducible():
+    from paper_1609_04567_gb300 import serve
+    a = serve.make_requests(20.0, 500.0, seed=7)
+    b = serve.make_requests(20.0, 500.0, seed=7)
+    assert [(r.kind, r.side, r.arrival) for r in a] == [(r.kind, r.side, r.arrival) for r in b]
+    n = len(a)
+    assert abs(n - 10000) < 4 * math.sqrt(10000)       # Poisson count within 4 sigma
+    gaps = np.diff([r.arrival for r in a])
+    assert np.all(gaps >= 0) and abs(gaps.mean() - 1 / 500.0) < 0.05 / 500.0
+    # exponential gaps: coefficient of variation 1
+    assert abs(gaps.std() / gaps.mean() - 1.0) < 0.05
+    share = sum(r.kind == serve.KIND_DENOISE for r in a) / n
+    assert abs(share - 0.5) < 0.02
+    dsides = set(serve.bucket_sides(256, 4096, 8))
+    ssides = set(serve.bucket_sides(64, 2048, 8))
+    assert {r.side for r in a if r.kind == serve.KIND_DENOISE} == dsides
+    assert {r.side for r in a if r.kind == serve.KIND_SOLVE} == ssides
+
+
+def test_footprints_count_state_aux_and_scratch():
+    from paper_1609_04567_gb300 import serve
+    assert serve.footprint(serve.KIND_DENOISE, 100) == 100 * 100 * 9       # f32 state, u8 mask, f32 scratch
+    assert serve.footprint(serve.KIND_SOLVE, 100) == 100 * 100 * 24        # f64 state, f, scratch
+
+
+@pytest.mark.parametrize("solo_cells", [None, 1024 * 1024, 1])
+def test_solo_lane_rule(solo_cells):
+    from paper_1609_04567_gb300 import serve
+    srv = object.__new__(serve.Server)                  # the rule needs no GPU state
+    srv.solo_cells = solo_cells
+    big = serve.Request(0, serve.KIND_DENOISE, 2048, 0.0)
+    small = serve.Request(1, serve.KIND_DENOISE, 512, 0.0)
+    solve = serve.Request(2, serve.KIND_SOLVE, 2048, 0.0)
+    assert srv.is_solo(big) == (solo_cells is not None)
+    assert srv.is_solo(small) == (solo_cells == 1)
+    assert not srv.is_solo(solve)                       # solves stay in the batch
