@@ -31,6 +31,10 @@ namespace {
 constexpr int kBThreads = 256;
 constexpr int kTileW = 64, kTileH = 16;
 constexpr int kMaxBatch = 1024;
+// Jacobi instances whose grid (two states and f in the compute type) fits the
+// CTA's staging area are run by one CTA, in shared memory, for all the sweeps
+// of a launch, with CTA barriers instead of the grid barrier.
+constexpr long long kLocalBytes = 8 * (long long)(64 + 2) * (16 + 2) * 8;   // the 8 warps' staging areas
 
 // One instance as the kernel sees it.  Host-written fields first; the kernel
 // writes the results at the end of a run (and value/count/converged when the
@@ -49,7 +53,7 @@ struct BInst {
     int parity;       // 0: current state in a, 1: in b
     int done;         // stopped (converged or capped)
     int converged;
-    int pad;
+    int local;        // small Jacobi instance run whole by one CTA (see cta_local_run)
     double value;
     unsigned long long count;
 };
@@ -376,6 +380,132 @@ __device__ __forceinline__ int find_running(const int *s_upref, int nrun, int u)
     return lo;
 }
 
+// A small Jacobi instance run whole by one CTA: the grid (both states and f,
+// in the compute type) is held in shared memory for all the sweeps of a
+// launch; each sweep updates every cell (the same operations in the same
+// order as jacobi_unit), takes a block max of |delta| and the instance's test,
+// so the instance stops at exactly the sweep it would stop at in the
+// batch-wide loop, with CTA barriers instead of grid barriers.  The final
+// state goes back to a (parity 0).  `smem` holds 3 * cells compute values.
+template <class T, int DIM>
+__device__ void cta_local_run(BInst &Ig, long long iters0, int par0, long long sweeps, unsigned char *smem)
+{
+    using C = typename St<T>::C;
+    __shared__ unsigned long long s_wmax[kBThreads / 32];
+    __shared__ unsigned long long s_max;
+    const BInst I = Ig;                 // a private copy: the stores below cannot alias it
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const C ghost = sizeof(C) == 8 ? (C)I.ghost : (C)I.ghostf;
+    const C h2 = sizeof(C) == 8 ? (C)I.h2 : (C)I.h2f;
+    const C d = sizeof(C) == 8 ? (C)I.d : (C)I.df;
+    const int nx = (int)I.nx, ny = (int)I.ny, nz = (int)I.nz, cells = nx * ny * nz;
+    C *buf0 = (C *)smem, *buf1 = buf0 + cells, *fs = buf1 + cells;
+    const void *cur0 = par0 ? I.b : I.a;
+    for (int c = tid; c < cells; c += kBThreads) {
+        buf0[c] = St<T>::ld(cur0, c);
+        fs[c] = St<T>::ldf(I.aux, c);
+    }
+    __syncthreads();
+    auto get = [&](const C *u, int k, int i, int j) -> C {
+        if (i < 0 || i >= ny || j < 0 || j >= nx || k < 0 || k >= nz) {
+            if (!I.wrap) return ghost;
+            i = i < 0 ? i + ny : (i >= ny ? i - ny : i);
+            j = j < 0 ? j + nx : (j >= nx ? j - nx : j);
+            k = k < 0 ? k + nz : (k >= nz ? k - nz : k);
+        }
+        return u[(k * ny + i) * nx + j];
+    };
+    long long it = iters0;
+    int cur = 0;
+    bool stop = false;
+    Decision dcs;
+    dcs.value = 0.0; dcs.count = 0ull; dcs.changed = 0; dcs.converged = 0;
+    const int rows = ny * nz;
+    for (long long s = 0; s < sweeps && !stop; ++s) {
+        const C *u = cur ? buf1 : buf0;
+        C *v = cur ? buf0 : buf1;
+        typename MaxBits<C>::type mx = 0;
+        for (int row = warp; row < rows; row += kBThreads / 32) {
+            const int k = row / ny, i = row - k * ny;
+            for (int j = lane; j < nx; j += 32) {
+                const int idx = (k * ny + i) * nx + j;
+                const C uc = u[idx];
+                C sum;
+                if (DIM == 2) {
+                    sum = add_rn(add_rn(add_rn(get(u, k, i - 1, j), get(u, k, i + 1, j)), get(u, k, i, j - 1)),
+                                 get(u, k, i, j + 1));
+                } else {
+                    sum = add_rn(add_rn(add_rn(add_rn(add_rn(get(u, k, i, j - 1), get(u, k, i, j + 1)),
+                                                      get(u, k, i - 1, j)), get(u, k, i + 1, j)),
+                                        get(u, k - 1, i, j)), get(u, k + 1, i, j));
+                }
+                const C tt = mul_rn(h2, fs[idx]);
+                // the value rounded to the storage type, widened back (exact)
+                T stv;
+                const C stored = St<T>::put(&stv, 0, div_rn(add_rn(tt, sum), d));
+                v[idx] = stored;
+                max_bits(mx, sub_rn(stored, uc));
+            }
+        }
+        unsigned long long m = widen_bits(mx);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const unsigned long long t = __shfl_xor_sync(0xffffffffu, m, o);
+            m = t > m ? t : m;
+        }
+        if (lane == 0) s_wmax[warp] = m;
+        __syncthreads();                             // the sweep's values are visible to the CTA
+        if (tid == 0) {
+            unsigned long long b = 0ull;
+            for (int w = 0; w < kBThreads / 32; ++w) b = s_wmax[w] > b ? s_wmax[w] : b;
+            s_max = b;
+        }
+        __syncthreads();
+        Slot sl;
+        memset(&sl, 0, sizeof(sl));
+        sl.maxbits = s_max;
+        sl.changed = s_max != 0ull;
+        dcs = decide(I.reduce, sl, I.tol);
+        it += 1;
+        cur ^= 1;
+        stop = dcs.converged || it >= I.max_iters;
+        __syncthreads();                             // s_max is read before the next sweep writes it
+    }
+    const C *fin = cur ? buf1 : buf0;
+    for (int c = tid; c < cells; c += kBThreads) St<T>::put(I.a, c, fin[c]);
+    if (tid == 0) {
+        Ig.iters = it;
+        Ig.parity = 0;
+        Ig.done = stop;
+        if (stop) {
+            Ig.value = dcs.value;
+            Ig.count = dcs.count;
+            Ig.converged = dcs.converged;
+        }
+    }
+    __syncthreads();                                 // the shared grid is free for the next instance
+}
+
+__device__ void cta_local_dispatch(BInst &I, long long iters0, int par0, long long sweeps, unsigned char *smem)
+{
+    const bool d3 = I.stencil == SLR_J3D7;
+    switch (I.storage) {
+    case SLR_F64:
+        d3 ? cta_local_run<double, 3>(I, iters0, par0, sweeps, smem) : cta_local_run<double, 2>(I, iters0, par0, sweeps, smem);
+        break;
+    case SLR_F32:
+        d3 ? cta_local_run<float, 3>(I, iters0, par0, sweeps, smem) : cta_local_run<float, 2>(I, iters0, par0, sweeps, smem);
+        break;
+    case SLR_BF16:
+        d3 ? cta_local_run<__nv_bfloat16, 3>(I, iters0, par0, sweeps, smem)
+           : cta_local_run<__nv_bfloat16, 2>(I, iters0, par0, sweeps, smem);
+        break;
+    default:
+        d3 ? cta_local_run<__half, 3>(I, iters0, par0, sweeps, smem) : cta_local_run<__half, 2>(I, iters0, par0, sweeps, smem);
+        break;
+    }
+}
+
 __global__ void __launch_bounds__(kBThreads, 2) batch_kernel(BatchArgs ba)
 {
     extern __shared__ unsigned char smem_raw[];
@@ -395,14 +525,29 @@ __global__ void __launch_bounds__(kBThreads, 2) batch_kernel(BatchArgs ba)
         const BInst &I = ba.inst[ba.act[i]];
         s_iters0[i] = I.iters;
         s_par0[i] = (unsigned char)I.parity;
-        s_stop[i] = I.done ? -2 : -1;
+        s_stop[i] = I.done ? -2 : (I.local ? -3 : -1);   // -3: run by one CTA below
         s_units[i] = (int)I.units;
     }
     __syncthreads();
     int nrun = compact_running(n, s_stop, s_units, s_aidx, s_upref);
+    // the small instances get CTAs of their own (the highest indices), which
+    // run them concurrently with the batch-wide loop of the other CTAs; every
+    // CTA counts them alike
+    int nlocal = 0;
+    for (int i = 0; i < n; ++i) nlocal += s_stop[i] == -3;
+    const int nloc = nlocal == 0 ? 0 : (nrun == 0 ? (int)gridDim.x : min(nlocal, (int)gridDim.x / 2));
+    const int G = (int)gridDim.x - nloc;               // CTAs of the batch-wide loop
+    if ((int)blockIdx.x >= G) {
+        for (int i = 0, q = 0; i < n; ++i) {
+            if (s_stop[i] != -3) continue;
+            if (q++ % nloc != (int)blockIdx.x - G) continue;
+            cta_local_dispatch(ba.inst[ba.act[i]], s_iters0[i], s_par0[i], ba.sweeps, smem_raw);
+        }
+        return;
+    }
     // warps interleave across CTAs so that consecutive units land on different SMs
-    const int warps = (int)gridDim.x * (kBThreads / 32);
-    const int gw = (tid >> 5) * (int)gridDim.x + (int)blockIdx.x;
+    const int warps = G * (kBThreads / 32);
+    const int gw = (tid >> 5) * G + (int)blockIdx.x;
     long long s = 0;
     for (; s < ba.sweeps; ++s) {
         const int U = s_upref[nrun];
@@ -450,7 +595,7 @@ __global__ void __launch_bounds__(kBThreads, 2) batch_kernel(BatchArgs ba)
                 }
             }
         }
-        if (!grid_barrier(ba.ctl, (unsigned long long)(s + 1) * (unsigned long long)ba.nblocks, ba.limit_ns))
+        if (!grid_barrier(ba.ctl, (unsigned long long)(s + 1) * (unsigned long long)G, ba.limit_ns))
             return;
         // every CTA takes the same per-instance decision
         if (tid == 0) s_alive = 0;
@@ -484,7 +629,7 @@ __global__ void __launch_bounds__(kBThreads, 2) batch_kernel(BatchArgs ba)
     // results (CTA 0) and the write-back of stopped instances whose state is in b
     if (blockIdx.x == 0) {
         for (int i = tid; i < n; i += kBThreads) {
-            if (s_stop[i] == -2) continue;
+            if (s_stop[i] == -2 || s_stop[i] == -3) continue;
             BInst &I = ba.inst[ba.act[i]];
             const long long done_sweeps = s_stop[i] >= 0 ? s_stop[i] + 1 : ran;
             I.iters = s_iters0[i] + done_sweeps;
@@ -632,6 +777,8 @@ slr_status slr_batch_add(slr_batch b, const slr_desc *d, void *u, const void *au
     I.tiles_x = (p.nx + slr::kTileW - 1) / slr::kTileW;
     I.tiles_y = (p.ny + slr::kTileH - 1) / slr::kTileH;
     I.units = I.tiles_x * I.tiles_y * p.nz;
+    I.local = p.stencil != SLR_RESTORE8 &&
+              3 * p.nx * p.ny * p.nz * (p.storage == SLR_F64 ? 8 : 4) <= slr::kLocalBytes;
     b->inst[(size_t)s] = I;
     b->used[(size_t)s] = 1;
     b->reported[(size_t)s] = 0;
