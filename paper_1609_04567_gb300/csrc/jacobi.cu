@@ -449,6 +449,7 @@ struct JacobiTma {
         const int ncols = tiles_x * tiles_y;
         const int mlen = DIM == 3 ? nz : (ny + kTY - 1) / kTY;       // steps per column
         typename MaxBits<C>::type mx = 0;
+        float mxf = 0.0f;                                          // binary32 compute: max |delta|
         unsigned q = *counter();
         if (tid == 0) {
             s_stop = ld_relaxed_u32((const unsigned *)err) != 0u;   // a wait ran out earlier
@@ -547,8 +548,9 @@ struct JacobiTma {
                             if (REDUCE) {
                                 const float2 dl = __fadd2_rn(make_float2(Store<T>::back(o0), Store<T>::back(o1)),
                                                              make_float2(-cv.raw(k), -cv.raw(k + 1)));
-                                max_bits(mx, dl.x);
-                                max_bits(mx, dl.y);
+                                // |delta| max as binary32 (one op; a NaN is skipped, as by the
+                                // sequential test d > max)
+                                mxf = fmaxf(mxf, fmaxf(fabsf(dl.x), fabsf(dl.y)));
                             }
                             if constexpr (sizeof(T) == 4) {
                                 ow[k] = __float_as_uint((float)o0);
@@ -585,6 +587,7 @@ struct JacobiTma {
         __syncthreads();
         if (tid == 0) *counter() = q;
         tma::fence_proxy_async_global();                             // this sweep's stores before later copies
+        if constexpr (std::is_same<C, float>::value) mx = __float_as_uint(mxf);   // non-negative: bits order as values
         if (REDUCE) block_to_slot(slot, widen_bits(mx), 0ull, 0ull, mx != 0);
     }
 };
