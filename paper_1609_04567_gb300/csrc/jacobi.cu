@@ -9,9 +9,17 @@
 // Storage: binary64 (binary64 arithmetic), binary32, bfloat16 or binary16
 // (binary32 arithmetic; the new value is rounded to nearest even into the
 // storage type and the change is taken between stored values).  Every
-// operation is an explicitly rounded IEEE operation (no contraction into
-// fused multiply-adds), in the order above, so results are bit-identical to a
-// sequential evaluation of the same formula.
+// operation rounds as the IEEE operation in the order above (no contraction
+// of a product into a sum), so results are bit-identical to a sequential
+// evaluation of the same formula; the division by the constant d is formed
+// from its correctly rounded reciprocal with two FMA corrections
+// (crmath.cuh), which gives the IEEE quotient.
+//
+// Two sweep implementations, both one cooperative persistent launch per run:
+// JacobiTma (Dirichlet ghost +0, rows of whole 16-byte groups, large grids)
+// marches 256-cell columns with every step staged by TMA in a ring of
+// shared-memory stages; JacobiStream (any boundary and width) marches row
+// segments with the rows held in registers.
 #include <string.h>
 
 #include <cmath>

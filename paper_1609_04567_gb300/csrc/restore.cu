@@ -17,11 +17,13 @@
 // reciprocal square root and products fuse into FMAs.
 //
 // Two sweep implementations: RestoreTma (rows a multiple of 16 bytes) streams
-// 32 x 64 tiles through shared memory, each tile arriving as two TMA boxes
-// (state with a 1-pixel halo, mask) double buffered per CTA, and compacts the
-// noisy pixels of each warp with ballots so the weight arithmetic runs on full
-// warps; RestoreOp is the plain per-pixel form for other widths and for the
-// host-driven loop.
+// 32 x 64 tiles through a ring of shared-memory stages, each tile arriving as
+// two TMA boxes (state with a 1-pixel halo, mask); every warp lists the noisy
+// pixels of its four rows with ballots, so the weight arithmetic runs on full
+// warps, and the last warp done with a stage refills it.  RestoreOp is the
+// plain per-pixel form for other widths and for the host-driven loop.  EXACT
+// weights come from crmath.cuh (Markstein-corrected estimates, equal to the
+// IEEE square root and reciprocal).
 #include <string.h>
 
 #include "crmath.cuh"
