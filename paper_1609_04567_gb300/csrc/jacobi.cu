@@ -529,7 +529,13 @@ struct JacobiTma {
                     }
                     uint32_t ow[Row::kWords];
                     if constexpr (std::is_same<C, float>::value) {
-                        // two cells per paired binary32 operation (same rounding per cell)
+                        // two cells per paired binary32 operation (same rounding per cell).
+                        // The numerators of the group come first; one range test over all of
+                        // them (|a| in [2^-40, 2^40)) then picks Markstein's corrected quotient
+                        // for the whole group, or the per-cell path when any falls outside.
+                        float q[V];
+                        uint32_t amin = 0xFFFFFFFFu, amax = 0u;   // |numerator| bits over the group
+                        const float2 y2 = make_float2(yd, yd), d2 = make_float2(d, d);
 #pragma unroll
                         for (int k = 0; k < V; k += 2) {
                             const float2 w = make_float2(k > 0 ? cv.raw(k - 1) : left, cv.raw(k));
@@ -547,10 +553,32 @@ struct JacobiTma {
                             // h^2 f with the scalar operation: a paired product feeding a paired
                             // sum may be contracted into one fused operation
                             const float2 t = make_float2(__fmul_rn(h2, fr.raw(k)), __fmul_rn(h2, fr.raw(k + 1)));
-                            const float2 q = dconst ? div_const_rn2(__fadd2_rn(t, sum), d, yd)
-                                                    : make_float2(div_ieee(__fadd_rn(t.x, sum.x), d),
-                                                                  div_ieee(__fadd_rn(t.y, sum.y), d));
-                            const T o0 = Store<T>::st(q.x), o1 = Store<T>::st(q.y);
+                            const float2 num = __fadd2_rn(t, sum);
+                            const uint32_t b0 = __float_as_uint(num.x) & 0x7FFFFFFFu;
+                            const uint32_t b1 = __float_as_uint(num.y) & 0x7FFFFFFFu;
+                            amin = min(amin, min(b0, b1));
+                            amax = max(amax, max(b0, b1));
+                            q[k] = num.x;
+                            q[k + 1] = num.y;
+                        }
+                        if (dconst && amin >= kDivLoBits && amax < kDivHiBits) {
+#pragma unroll
+                            for (int k = 0; k < V; k += 2) {
+                                const float2 num = make_float2(q[k], q[k + 1]);
+                                const float2 q0 = __fmul2_rn(num, y2);
+                                const float2 q1 = __ffma2_rn(__ffma2_rn(make_float2(-q0.x, -q0.y), d2, num), y2, q0);
+                                const float2 qq = __ffma2_rn(__ffma2_rn(make_float2(-q1.x, -q1.y), d2, num), y2, q1);
+                                q[k] = qq.x;
+                                q[k + 1] = qq.y;
+                            }
+                        } else {
+                            // rare: a numerator outside the range of the corrected quotient
+#pragma unroll
+                            for (int k = 0; k < V; ++k) q[k] = divide(q[k]);
+                        }
+#pragma unroll
+                        for (int k = 0; k < V; k += 2) {
+                            const T o0 = Store<T>::st(q[k]), o1 = Store<T>::st(q[k + 1]);
                             if (REDUCE) {
                                 const float2 dl = __fadd2_rn(make_float2(Store<T>::back(o0), Store<T>::back(o1)),
                                                              make_float2(-cv.raw(k), -cv.raw(k + 1)));
