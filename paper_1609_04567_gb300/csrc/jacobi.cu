@@ -169,6 +169,32 @@ struct Packed {
 __device__ __forceinline__ uint32_t bits16(__nv_bfloat16 h) { return (uint32_t)__bfloat16_as_ushort(h); }
 __device__ __forceinline__ uint32_t bits16(__half h) { return (uint32_t)__half_as_ushort(h); }
 
+// two computed values rounded to the storage type by one paired conversion, in
+// one 32-bit word (the first in the low half), and the stored values widened back
+template <class T> struct Pair2;
+template <> struct Pair2<__nv_bfloat16> {
+    __device__ __forceinline__ static uint32_t pack(float a, float b)
+    {
+        const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+        return *(const uint32_t *)&h;
+    }
+    __device__ __forceinline__ static float2 widen(uint32_t w)
+    {
+        return make_float2(__uint_as_float(w << 16), __uint_as_float(w & 0xFFFF0000u));
+    }
+};
+template <> struct Pair2<__half> {
+    __device__ __forceinline__ static uint32_t pack(float a, float b)
+    {
+        const __half2 h = __floats2half2_rn(a, b);
+        return *(const uint32_t *)&h;
+    }
+    __device__ __forceinline__ static float2 widen(uint32_t w)
+    {
+        return __half22float2(*(const __half2 *)&w);
+    }
+};
+
 // ---- streaming sweep ----------------------------------------------------------
 // A warp owns a segment of 32*V consecutive cells of a row (V cells per lane,
 // one 16-byte access when the row allows it) and marches along the slowest
@@ -449,6 +475,7 @@ struct JacobiTma {
     __device__ __forceinline__ void sweep(const void *src_v, void *dst_v, Slot *slot) const
     {
         __shared__ int s_stop;
+        __shared__ T s_ghost;                                      // the ghost value 0, for the end lanes
         T *v = (T *)dst_v;
         const int tid = threadIdx.x;
         const int mi = src_v == base[0] ? 0 : 1;
@@ -459,6 +486,7 @@ struct JacobiTma {
         unsigned q = *counter();
         if (tid == 0) {
             s_stop = ld_relaxed_u32((const unsigned *)err) != 0u;   // a wait ran out earlier
+            s_ghost = Store<T>::st(C(0));
             tma::fence_proxy_async_global();   // the previous sweep's stores before this sweep's copies
         }
         __syncthreads();
@@ -495,7 +523,10 @@ struct JacobiTma {
                     __syncthreads();
                 }
                 const T *Mc = main_of(sc), *Ma = main_of(sa), *Mb = main_of(sb), *F = f_of(sc);
-                const T *SL = side_of(sc, 0), *SR = side_of(sc, 1);
+                // the side columns, or the ghost where the tile touches the grid's edge
+                const T *SL = x0 > 0 ? side_of(sc, 0) + V - 1 : &s_ghost;
+                const T *SR = x0 + kTX < nx ? side_of(sc, 1) : &s_ghost;
+                const int sstep_l = x0 > 0 ? V : 0, sstep_r = x0 + kTX < nx ? V : 0;
 #pragma unroll
                 for (int p = 0; p < kPer; ++p) {
                     const int g = tid + p * kJThreads;
@@ -510,11 +541,10 @@ struct JacobiTma {
                     C left = __shfl_up_sync(0xffffffffu, cv.raw(V - 1), 1);
                     C right = __shfl_down_sync(0xffffffffu, cv.raw(0), 1);
                     if (!got || x >= nx || y >= ny) continue;
-                    const C zero = C(0);
-                    if (lane == 0)
-                        left = c > 0 ? Store<T>::back(ctr[-1]) : (x0 > 0 ? Store<T>::back(SL[r * V + V - 1]) : zero);
-                    if (lane == 31)
-                        right = c < kG - 1 ? Store<T>::back(ctr[V]) : (x0 + kTX < nx ? Store<T>::back(SR[r * V]) : zero);
+                    const T *lp = c > 0 ? ctr - 1 : SL + r * sstep_l;
+                    const T *rp = c < kG - 1 ? ctr + V : SR + r * sstep_r;
+                    if (lane == 0) left = Store<T>::back(*lp);
+                    if (lane == 31) right = Store<T>::back(*rp);
                     const Row fr = lds(F + r * kTX + c * V);
                     Row nr, sr, ar, br;                              // y-1, y+1, march-1, march+1
                     if (DIM == 3) {
@@ -534,8 +564,8 @@ struct JacobiTma {
                         // them (|a| in [2^-40, 2^40)) then picks Markstein's corrected quotient
                         // for the whole group, or the per-cell path when any falls outside.
                         float q[V];
-                        uint32_t amin = 0xFFFFFFFFu, amax = 0u;   // |numerator| bits over the group
-                        const float2 y2 = make_float2(yd, yd), d2 = make_float2(d, d);
+                        float amin = INFINITY, amax = 0.0f;       // |numerator| over the group
+                        const float2 y2 = make_float2(yd, yd), nd2 = make_float2(-d, -d);
 #pragma unroll
                         for (int k = 0; k < V; k += 2) {
                             const float2 w = make_float2(k > 0 ? cv.raw(k - 1) : left, cv.raw(k));
@@ -554,20 +584,20 @@ struct JacobiTma {
                             // sum may be contracted into one fused operation
                             const float2 t = make_float2(__fmul_rn(h2, fr.raw(k)), __fmul_rn(h2, fr.raw(k + 1)));
                             const float2 num = __fadd2_rn(t, sum);
-                            const uint32_t b0 = __float_as_uint(num.x) & 0x7FFFFFFFu;
-                            const uint32_t b1 = __float_as_uint(num.y) & 0x7FFFFFFFu;
-                            amin = min(amin, min(b0, b1));
-                            amax = max(amax, max(b0, b1));
+                            // a NaN numerator passes the test and gives NaN either way
+                            amin = fminf(amin, fminf(fabsf(num.x), fabsf(num.y)));
+                            amax = fmaxf(amax, fmaxf(fabsf(num.x), fabsf(num.y)));
                             q[k] = num.x;
                             q[k + 1] = num.y;
                         }
-                        if (dconst && amin >= kDivLoBits && amax < kDivHiBits) {
+                        if (dconst && amin >= 0x1p-40f && amax < 0x1p40f) {
 #pragma unroll
                             for (int k = 0; k < V; k += 2) {
+                                // Markstein's corrected quotient; fma(q, -d, a) is the residual a - q d
                                 const float2 num = make_float2(q[k], q[k + 1]);
                                 const float2 q0 = __fmul2_rn(num, y2);
-                                const float2 q1 = __ffma2_rn(__ffma2_rn(make_float2(-q0.x, -q0.y), d2, num), y2, q0);
-                                const float2 qq = __ffma2_rn(__ffma2_rn(make_float2(-q1.x, -q1.y), d2, num), y2, q1);
+                                const float2 q1 = __ffma2_rn(__ffma2_rn(q0, nd2, num), y2, q0);
+                                const float2 qq = __ffma2_rn(__ffma2_rn(q1, nd2, num), y2, q1);
                                 q[k] = qq.x;
                                 q[k + 1] = qq.y;
                             }
@@ -576,21 +606,24 @@ struct JacobiTma {
 #pragma unroll
                             for (int k = 0; k < V; ++k) q[k] = divide(q[k]);
                         }
+                        const float2 m1 = make_float2(-1.0f, -1.0f);
 #pragma unroll
                         for (int k = 0; k < V; k += 2) {
-                            const T o0 = Store<T>::st(q[k]), o1 = Store<T>::st(q[k + 1]);
-                            if (REDUCE) {
-                                const float2 dl = __fadd2_rn(make_float2(Store<T>::back(o0), Store<T>::back(o1)),
-                                                             make_float2(-cv.raw(k), -cv.raw(k + 1)));
-                                // |delta| max as binary32 (one op; a NaN is skipped, as by the
-                                // sequential test d > max)
-                                mxf = fmaxf(mxf, fmaxf(fabsf(dl.x), fabsf(dl.y)));
-                            }
+                            float2 o;                                // the stored values, widened
                             if constexpr (sizeof(T) == 4) {
-                                ow[k] = __float_as_uint((float)o0);
-                                ow[k + 1] = __float_as_uint((float)o1);
+                                ow[k] = __float_as_uint(q[k]);
+                                ow[k + 1] = __float_as_uint(q[k + 1]);
+                                o = make_float2(q[k], q[k + 1]);
                             } else {
-                                ow[k >> 1] = bits16(o0) | bits16(o1) << 16;
+                                ow[k >> 1] = Pair2<T>::pack(q[k], q[k + 1]);
+                                o = Pair2<T>::widen(ow[k >> 1]);
+                            }
+                            if (REDUCE) {
+                                // |old - new| (fma(new, -1, old) is the rounded difference);
+                                // max as binary32 in one op, a NaN skipped as by the
+                                // sequential test d > max
+                                const float2 dl = __ffma2_rn(o, m1, make_float2(cv.raw(k), cv.raw(k + 1)));
+                                mxf = fmaxf(mxf, fmaxf(fabsf(dl.x), fabsf(dl.y)));
                             }
                         }
                     } else {
