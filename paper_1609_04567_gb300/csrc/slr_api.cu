@@ -7,6 +7,7 @@
 #include <new>
 #include <string>
 
+#include "jacobi_tb.h"
 #include "slr_internal.cuh"
 
 using slr::Ctl;
@@ -182,7 +183,9 @@ slr_status run_persistent(slr_handle h, int64_t max_iters)
         e = h->desc.defect_correction
                 ? slr::dc_persistent(h->prob, la, h->desc.inner_sweeps,
                                      h->ws + slr::kCtlBytes + round_up(h->prob.state_bytes, 256), h->stream)
-                : slr::jacobi_persistent(h->prob, la, h->stream);
+                : slr::jacobi_tb_resolve_k(h->prob, la.a, la.b, la.aux) > 1
+                      ? slr::jacobi_tb_persistent(h->prob, la, h->stream)
+                      : slr::jacobi_persistent(h->prob, la, h->stream);
         break;
     case SLR_RESTORE8: e = slr::restore_persistent(h->prob, la, h->stream); break;
     default: e = cudaErrorInvalidValue;
