@@ -112,9 +112,14 @@ typedef struct {
     float alpha;           /* restoration constant (100) */
     int32_t loop;          /* slr_loop */
     int32_t math;          /* slr_math */
-    int32_t temporal_k;    /* sweeps per HBM pass for Life (1, 2, 4, ..., 32); 0 = library
-                              choice (the autotuner's, else the largest k in [4, 32] whose
-                              tiles fit the co-resident CTAs) */
+    int32_t temporal_k;    /* sweeps per HBM pass, 1 = one.  Life: 1 .. 32.  SLR_J2D5 with
+                              binary32 arithmetic (storage F32, BF16 or F16), Dirichlet
+                              ghost +0, rows of whole 16-byte groups: 1 .. 8 (larger values
+                              run 8; a solve that stops inside a pass recomputes that pass
+                              up to the stopping sweep, so results equal those of k = 1).
+                              0 = library choice: the autotuner's, else for Life the
+                              largest k in [4, 32] whose tiles fit the co-resident CTAs,
+                              for SLR_J2D5 8 when tiling is SLR_TILING_AUTO (1 otherwise) */
     int64_t wait_limit_ns; /* device-side barrier wait limit; <= 0 selects 2 s */
     int32_t debug_flags;   /* SLR_DEBUG_* bits; 0 in normal use */
     int32_t defect_correction; /* 1: FP64 defect correction around FP32 Jacobi inner solves
@@ -278,7 +283,7 @@ const char *slr_static_last_error(void);
  * slr_tune searches the fields of *d left at their library-choice value:
  *   loop        (SLR_LOOP_AUTO: persistent device loop or the host-driven loop;
  *                defect correction keeps the persistent loop),
- *   temporal_k  (0, Life only: generations per HBM pass, 1 = none),
+ *   temporal_k  (0, Life and SLR_J2D5: sweeps per HBM pass, 1 = none),
  *   tiling      (SLR_TILING_AUTO, RESTORE8 and Jacobi without defect correction:
  *                TMA tiles or none),
  *   grid_ctas   (0: CTAs of the persistent launch),
@@ -293,7 +298,7 @@ const char *slr_static_last_error(void);
  *   scratch     device buffer of slr_tune_scratch_size(d) bytes, 256-byte
  *               aligned, owned by the caller; free to reuse after return.
  *   out         receives the choice with every searched field explicit (loop
- *               HOST or PERSISTENT, temporal_k >= 1 for Life, tiling NONE or TMA
+ *               HOST or PERSISTENT, temporal_k >= 1 for Life and SLR_J2D5, tiling NONE or TMA
  *               for RESTORE8, grid_ctas >= 0 where 0 kept the default), the
  *               number of candidates timed and the two scores; may be NULL.
  * The call waits for `stream`.  It stores the choice under (device, SM count,
@@ -302,7 +307,7 @@ const char *slr_static_last_error(void);
  * (floor(log2)).  slr_create then fills the library-choice fields of a
  * descriptor from the exact entry, else from the bucket entry, else from the
  * built-in defaults; grid_ctas only when the descriptor then names the
- * choice's loop, temporal_k (Life) and tiling (RESTORE8), the kernel that
+ * choice's loop, temporal_k (Life, SLR_J2D5) and tiling, the kernel that
  * grid size was timed with.  Returns SLR_OK, SLR_ERR_INVALID_ARG / UNSUPPORTED for a
  * descriptor slr_create would refuse or a NULL/misaligned pointer,
  * SLR_ERR_WORKSPACE for a short scratch, or the error of a failed trial

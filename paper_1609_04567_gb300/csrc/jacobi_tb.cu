@@ -517,7 +517,9 @@ bool jacobi_tb_supported(const Problem &p, const void *a, const void *b, const v
 int jacobi_tb_resolve_k(const Problem &p, const void *a, const void *b, const void *f)
 {
     if (p.k == 1 || !jacobi_tb_supported(p, a, b, f)) return 1;
-    if (p.k == 0) return 1;
+    // the library's choice: 8 sweeps per pass unless a staging of the
+    // one-sweep kernel was asked for
+    if (p.k == 0) return p.tiling == SLR_TILING_AUTO ? kJacobiTbMaxK : 1;
     return p.k > kJacobiTbMaxK ? kJacobiTbMaxK : p.k;
 }
 

@@ -13,8 +13,9 @@ constexpr int kJacobiTbMaxK = 8;
 // Dirichlet ghost +0, rows of whole 16-byte groups, 16-byte aligned arrays.
 bool jacobi_tb_supported(const Problem &p, const void *a, const void *b, const void *f);
 
-// Sweeps per pass for p: temporal_k 1 (or unsupported) gives 1, a value above
-// kJacobiTbMaxK gives kJacobiTbMaxK, 0 the library's default.
+// Sweeps per pass for p: 1 (the one-sweep kernels) for temporal_k 1 or a
+// problem the loop does not accept; temporal_k clamped to kJacobiTbMaxK; for
+// temporal_k 0, kJacobiTbMaxK when tiling is SLR_TILING_AUTO, else 1.
 int jacobi_tb_resolve_k(const Problem &p, const void *a, const void *b, const void *f);
 
 // The whole repeat-until loop with k = jacobi_tb_resolve_k(...) > 1 sweeps per

@@ -18,6 +18,7 @@
 
 #include <mutex>
 
+#include "jacobi_tb.h"
 #include "slr_internal.cuh"
 
 namespace {
@@ -102,7 +103,8 @@ slr_status slr_run_static(const slr_desc *d, void *u, const void *f, int64_t max
     la.reduce = p.reduce;
     la.nblocks = 0;
     la.debug_flags = 0;
-    e = slr::jacobi_persistent(p, la, st);
+    e = slr::jacobi_tb_resolve_k(p, la.a, la.b, la.aux) > 1 ? slr::jacobi_tb_persistent(p, la, st)
+                                                             : slr::jacobi_persistent(p, la, st);
     if (e != cudaSuccess) return static_fail(SLR_ERR_CUDA, std::string("persistent loop launch: ") + cudaGetErrorString(e));
     slr::Ctl h;
     e = cudaMemcpyAsync(&h, ctl, sizeof(slr::Ctl), cudaMemcpyDeviceToHost, st);
