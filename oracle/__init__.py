@@ -74,6 +74,8 @@ def _load():
     lib.orc_life.argtypes = [P, i64, i64, i32, i64, R]
     lib.orc_restore8.argtypes = [P, P, i64, i64, ctypes.c_float, f64, i64, R]
     lib.orc_j2d5_dc.argtypes = [P, P, i64, i64, f64, f64, f64, i64, i64, R]
+    lib.orc_amf_detect.argtypes = [P, P, i64, i64, i32]
+    lib.orc_amf_detect.restype = i32
     lib.orc_j2d5_scaled_defect.argtypes = [P, P, i64, i64, f64, f64]
     lib.orc_j2d5_scaled_defect.restype = f64
     for name in ("orc_j2d5_f64", "orc_j2d5_f32", "orc_j3d7_f64", "orc_j3d7_f32",
@@ -173,6 +175,18 @@ def restore8(u0, mask, *, alpha=100.0, tol=1e-3, max_iters=5000):
     _check(lib.orc_restore8(_ptr(u), _ptr(m), nx, ny, alpha, tol, max_iters,
                             ctypes.byref(r)), "restore8")
     return u, _res(r)
+
+
+def amf_detect(img, *, wmax=7) -> np.ndarray:
+    """Adaptive median noise detector (the detection phase of the Sec. 4.3
+    denoiser) on a uint8 image: a uint8 mask, 1 where the filter with windows
+    3 x 3 .. wmax x wmax replaces the pixel."""
+    lib = _load()
+    a = np.ascontiguousarray(img, dtype=np.uint8)
+    ny, nx = a.shape
+    m = np.zeros((ny, nx), dtype=np.uint8)
+    _check(lib.orc_amf_detect(_ptr(a), _ptr(m), nx, ny, int(wmax)), "amf_detect")
+    return m
 
 
 def j2d5_dc(u0, f, *, sigma=1.0, h=0.0, tol=1e-10, k_in=50, max_outer=100000):

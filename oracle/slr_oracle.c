@@ -575,3 +575,52 @@ void orc_round_storage_array(const float *x, float *out, int64_t n, int storage)
 {
     for (int64_t i = 0; i < n; ++i) out[i] = to_storage(x[i], storage);
 }
+
+/* ------------------------------------------------------------------------- */
+/* Adaptive median noise detector: the detection phase of the two-phase      */
+/* restoration of Sec. 4.3 ("a traditional adaptive median filter"; the      */
+/* paper does not define it, this is the textbook filter).  For the pixel z  */
+/* at (i, j), square windows of side w = 3, 5, ..., wmax centred on it and   */
+/* clipped to the image give zmin, zmax and zmed, the lower median (element  */
+/* floor((n - 1) / 2) of the window's n values in ascending order).  The     */
+/* first window with zmin < zmed < zmax decides: the filter outputs z when   */
+/* zmin < z < zmax, else zmed.  When no window qualifies the output is zmed  */
+/* of the largest window.  mask = 1 where the output differs from z (a noisy */
+/* pixel), else 0.  The window values are counted in a 256-bin histogram.    */
+/* ------------------------------------------------------------------------- */
+
+int orc_amf_detect(const uint8_t *img, uint8_t *mask, int64_t nx, int64_t ny, int wmax)
+{
+    if (nx < 1 || ny < 1 || wmax < 3 || wmax % 2 == 0) return -1;
+    int64_t cnt[256];
+    for (int64_t i = 0; i < ny; ++i)
+        for (int64_t j = 0; j < nx; ++j) {
+            int z = img[i * nx + j];
+            int out = -1, zmed = z;
+            for (int64_t r = 1; 2 * r + 1 <= wmax; ++r) {
+                memset(cnt, 0, sizeof cnt);
+                int64_t n = 0;
+                for (int64_t a = i - r; a <= i + r; ++a)
+                    for (int64_t b = j - r; b <= j + r; ++b)
+                        if (a >= 0 && a < ny && b >= 0 && b < nx) {
+                            cnt[img[a * nx + b]] += 1;
+                            n += 1;
+                        }
+                int zmin = 0, zmax = 255;
+                while (cnt[zmin] == 0) ++zmin;
+                while (cnt[zmax] == 0) --zmax;
+                /* the value whose cumulative count first exceeds (n - 1) / 2 */
+                int64_t m = (n - 1) / 2, seen = 0;
+                int v = 0;
+                while (seen + cnt[v] <= m) { seen += cnt[v]; ++v; }
+                zmed = v;
+                if (zmin < zmed && zmed < zmax) {
+                    out = (zmin < z && z < zmax) ? z : zmed;
+                    break;
+                }
+            }
+            if (out < 0) out = zmed;
+            mask[i * nx + j] = (uint8_t)(out != z);
+        }
+    return 0;
+}

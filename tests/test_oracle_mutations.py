@@ -68,6 +68,18 @@ MUTATIONS = [
     ("bfloat16 rounds half up instead of to even",
      "    if (rest > 0x8000u || (rest == 0x8000u && (keep & 1u)))\n        keep += 1u;",
      "    if (rest >= 0x8000u)\n        keep += 1u;"),
+    ("detector takes the upper median",
+     "                int64_t m = (n - 1) / 2, seen = 0;",
+     "                int64_t m = n / 2, seen = 0;"),
+    ("detector keeps pixels equal to a window extreme",
+     "                    out = (zmin < z && z < zmax) ? z : zmed;",
+     "                    out = (zmin <= z && z <= zmax) ? z : zmed;"),
+    ("detector decides on a window whose median is an extreme",
+     "                if (zmin < zmed && zmed < zmax) {",
+     "                if (zmin <= zmed && zmed < zmax) {"),
+    ("detector keeps the pixel when no window decides",
+     "            if (out < 0) out = zmed;",
+     "            if (out < 0) out = z;"),
     ("binary16 subnormal shift off by one",
      "    int32_t shift = -(e + 1);                        /* >= 14 */",
      "    int32_t shift = -(e + 2);                        /* >= 14 */"),
