@@ -757,6 +757,48 @@ def run_serve(args):
     return 0
 
 
+def run_video(args):
+    """The video restoration stream of Sec. 4.3, pipe(read, detect,
+    ofarm(restore), write): 100-frame streams at VGA, 720p and 1080p (each a
+    seeded permutation of 4 distinct 50% salt-and-pepper frames of the
+    restoration generator), pinned host frames in and out, adaptive median
+    detection (windows up to 7 x 7), EXACT restoration to mean |delta| < 1e-3,
+    rounding back to uint8, with 1, 2 and 4 frames in flight.  The oracle's
+    detection and restoration of one VGA frame is the CPU leg."""
+    import numpy as np
+    import torch
+    import oracle
+    from paper_1609_04567_gb300 import slr, video
+    slr.load()
+    out = {}
+    for name, (ny, nx) in [("vga_640x480", (480, 640)), ("720p_1280x720", (720, 1280)),
+                           ("1080p_1920x1080", (1080, 1920))]:
+        frames, _ = video.make_video(ny, nx, args.video_frames, distinct=4)
+        host_in = [torch.from_numpy(f).pin_memory() for f in frames]
+        host_out = [torch.empty((ny, nx), dtype=torch.uint8).pin_memory() for _ in frames]
+        row = {}
+        for lanes in (1, 2, 4):
+            p = video.VideoPipeline(ny, nx, lanes=lanes)
+            p.run(host_in[:lanes * 2], host_out[:lanes * 2])           # warm-up
+            st = p.run(host_in, host_out)
+            p.close()
+            row[f"lanes{lanes}"] = {"fps": st.fps, "wall_s": st.wall_s, "p50_ms": st.p50_ms, "p99_ms": st.p99_ms,
+                                    "mean_sweeps": st.mean_iters, "gcell_per_s": st.gcell_per_s}
+        out[name] = row
+    # CPU leg: the oracle's detection and restoration of one VGA frame
+    frames, _ = video.make_video(480, 640, 1, distinct=1)
+    t0 = time.perf_counter()
+    m = oracle.amf_detect(frames[0], wmax=7)
+    ref, rr = oracle.restore8(frames[0].astype(np.float32), m, tol=1e-3, max_iters=5000)
+    cpu_s = time.perf_counter() - t0
+    line = {"workload": f"video_restore_{args.video_frames}frames_vga_720p_1080p", "metric": "frames/s",
+            "unit": "frames/s", "cases": out,
+            "cpu_baseline": {"value": 1.0 / cpu_s, "unit": "frames/s", "cores": 1, "kind": "oracle",
+                             "sample": f"one 640x480 frame, detection and {rr.iters} restoration sweeps"}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -764,7 +806,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="life",
-                    choices=["life", "helmholtz", "restore", "jacobi", "precision", "batch", "serve"])
+                    choices=["life", "helmholtz", "restore", "jacobi", "precision", "batch", "serve", "video"])
+    ap.add_argument("--video-frames", type=int, default=100, help="frames per stream of the video workload")
     ap.add_argument("--batch3d", type=int, default=512, help="side of the 3D grid of the batch workload (0: none)")
     ap.add_argument("--rate", type=float, default=2000.0)
     ap.add_argument("--serve-seconds", type=float, default=10.0)
@@ -789,7 +832,7 @@ def main():
         ap.error("--warmup must be >= 3")
     if args.workload != "life":
         fn = {"helmholtz": run_helmholtz, "restore": run_restore, "jacobi": run_jacobi, "precision": run_precision,
-              "batch": run_batch, "serve": run_serve}
+              "batch": run_batch, "serve": run_serve, "video": run_video}
         return fn[args.workload](args)
     wl = WORKLOADS[args.workload]
     world, rank, local = dist_setup()

@@ -202,6 +202,30 @@ slr_status slr_destroy(slr_handle h);
  * NULL).  Never NULL. */
 const char *slr_last_error(slr_handle h);
 
+/* ---- Noise detection (the detection phase of the Sec. 4.3 denoiser) ----------
+ * The paper's two-phase restoration marks noisy pixels with a traditional
+ * adaptive median filter before RESTORE8 restores them (its mask input).  For
+ * every pixel z of the uint8 image img (nx x ny, row-major): square windows of
+ * side 3, 5, ..., wmax centred on z and clipped to the image give zmin, zmax
+ * and zmed, the lower median (element floor((n-1)/2) of the n window values in
+ * ascending order); the first window with zmin < zmed < zmax decides: the
+ * filter keeps z when zmin < z < zmax and outputs zmed otherwise; when no
+ * window qualifies it outputs zmed of the largest window.  mask (uint8, same
+ * layout) receives 1 where the output differs from z, else 0.  state, when
+ * not NULL, receives the image as binary32 values (float, same layout, 4-byte
+ * aligned): the restoration's initial state, written in the same pass.  img,
+ * mask and state are device pointers that must not overlap; wmax odd in
+ * [3, 15].  Enqueued on `stream` (nothing waits); returns SLR_OK, or
+ * SLR_ERR_INVALID_ARG / SLR_ERR_CUDA with the message in slr_last_error(NULL). */
+slr_status slr_detect_noise(const void *img, void *mask, void *state, int64_t nx, int64_t ny, int32_t wmax,
+                            void *stream);
+
+/* A restored binary32 state (n values, device, 4-byte aligned) written back as
+ * a uint8 frame: img[i] = u[i] rounded to the nearest integer (ties to even)
+ * and clamped to [0, 255] (NaN gives 0).  Enqueued on `stream`; SLR_OK or SLR_ERR_INVALID_ARG
+ * / SLR_ERR_CUDA (message in slr_last_error(NULL)). */
+slr_status slr_state_to_frame(const void *state, void *img, int64_t n, void *stream);
+
 /* Library build string (architecture, version). */
 const char *slr_version(void);
 

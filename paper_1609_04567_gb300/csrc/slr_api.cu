@@ -253,6 +253,8 @@ slr_status run_host(slr_handle h, int64_t max_iters)
 namespace slr {
 // Validation and problem set-up shared with entry points in other files.
 std::string describe_invalid(const slr_desc *d, bool *unsupported) { return check_desc(d, unsupported); }
+// Entry points without a handle report through slr_last_error(NULL).
+void set_handleless_error(const std::string &msg) { g_create_error = msg; }
 Problem problem_of(const slr_desc *d) { return make_problem(d); }
 
 // slr_create without the autotuner's cache: the descriptor's library-choice

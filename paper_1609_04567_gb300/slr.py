@@ -61,7 +61,8 @@ EXPORTS = ["slr_desc_init", "slr_workspace_size", "slr_create", "slr_run_until",
            "slr_batch_workspace_size", "slr_batch_scratch_size", "slr_batch_create", "slr_batch_add",
            "slr_batch_run", "slr_batch_poll", "slr_batch_result", "slr_batch_remove", "slr_batch_destroy",
            "slr_batch_last_error", "slr_tune_scratch_size", "slr_tune", "slr_tune_lookup", "slr_tune_clear",
-           "slr_tune_last_error", "slr_check_exact_math", "slr_check_exact_division"]
+           "slr_tune_last_error", "slr_check_exact_math", "slr_check_exact_division", "slr_detect_noise",
+           "slr_state_to_frame"]
 SLR_STATIC_STATE_BYTES = 4 << 20
 
 _lib = None
@@ -144,6 +145,10 @@ def load(path: str = LIB_PATH):
     lib.slr_check_exact_division.argtypes = [ctypes.c_double, ctypes.POINTER(ctypes.c_uint64),
                                              ctypes.POINTER(ctypes.c_uint64), P]
     lib.slr_check_exact_division.restype = i32
+    lib.slr_detect_noise.argtypes = [P, P, P, i64, i64, i32, P]
+    lib.slr_detect_noise.restype = i32
+    lib.slr_state_to_frame.argtypes = [P, P, i64, P]
+    lib.slr_state_to_frame.restype = i32
     _lib = lib
     return lib
 
@@ -317,6 +322,57 @@ def slr_check_exact_division(d: float, stream: int = 0):
     if st != SLR_OK:
         raise SlrError(st, "division self-check refused or failed")
     return list(mm), list(n)
+
+
+def slr_detect_noise(img_ptr: int, mask_ptr: int, state_ptr: int, nx: int, ny: int, wmax: int = 7,
+                     stream: int = 0) -> int:
+    """Adaptive median noise detection of a device uint8 image into a device
+    uint8 mask, and the image as binary32 into `state_ptr` unless 0 (enqueued
+    on `stream`)."""
+    st = load().slr_detect_noise(img_ptr or None, mask_ptr or None, state_ptr or None, nx, ny, wmax,
+                                 stream or None)
+    if st != SLR_OK:
+        raise SlrError(st, slr_last_error(None))
+    return st
+
+
+def slr_state_to_frame(state_ptr: int, img_ptr: int, n: int, stream: int = 0) -> int:
+    st = load().slr_state_to_frame(state_ptr or None, img_ptr or None, n, stream or None)
+    if st != SLR_OK:
+        raise SlrError(st, slr_last_error(None))
+    return st
+
+
+def detect_noise(img, mask=None, state=None, *, wmax: int = 7, stream=None):
+    """The noisy-pixel mask of a uint8 CUDA image tensor (the detection phase
+    of the two-phase restoration); `mask` (uint8, same shape) is filled and
+    returned, allocated when None; `state` (float32, same shape), when given,
+    receives the image as the restoration's initial state."""
+    import torch
+    if not img.is_cuda or img.dtype != torch.uint8 or img.dim() != 2 or not img.is_contiguous():
+        raise ValueError("img must be a contiguous 2D uint8 CUDA tensor")
+    if mask is None:
+        mask = torch.empty_like(img)
+    if state is not None and (state.dtype != torch.float32 or state.shape != img.shape or not state.is_contiguous()):
+        raise ValueError("state must be a contiguous float32 tensor shaped like img")
+    st = stream if stream is not None else torch.cuda.current_stream(img.device)
+    ny, nx = img.shape
+    slr_detect_noise(img.data_ptr(), mask.data_ptr(), state.data_ptr() if state is not None else 0, nx, ny, wmax,
+                     st.cuda_stream)
+    return mask
+
+
+def state_to_frame(state, img=None, *, stream=None):
+    """A restored float32 CUDA state as a uint8 frame (nearest, ties to even,
+    clamped to [0, 255])."""
+    import torch
+    if not state.is_cuda or state.dtype != torch.float32 or not state.is_contiguous():
+        raise ValueError("state must be a contiguous float32 CUDA tensor")
+    if img is None:
+        img = torch.empty(state.shape, dtype=torch.uint8, device=state.device)
+    st = stream if stream is not None else torch.cuda.current_stream(state.device)
+    slr_state_to_frame(state.data_ptr(), img.data_ptr(), state.numel(), st.cuda_stream)
+    return img
 
 
 def tune(stencil: int, u, aux=None, *, stream=None, trial_iters: int = 0, **fields) -> dict:
