@@ -76,6 +76,8 @@ def _load():
     lib.orc_j2d5_dc.argtypes = [P, P, i64, i64, f64, f64, f64, i64, i64, R]
     lib.orc_amf_detect.argtypes = [P, P, i64, i64, i32]
     lib.orc_amf_detect.restype = i32
+    lib.orc_sobel.argtypes = [P, P, i64, i64]
+    lib.orc_sobel.restype = i32
     lib.orc_j2d5_scaled_defect.argtypes = [P, P, i64, i64, f64, f64]
     lib.orc_j2d5_scaled_defect.restype = f64
     for name in ("orc_j2d5_f64", "orc_j2d5_f32", "orc_j3d7_f64", "orc_j3d7_f32",
@@ -187,6 +189,17 @@ def amf_detect(img, *, wmax=7) -> np.ndarray:
     m = np.zeros((ny, nx), dtype=np.uint8)
     _check(lib.orc_amf_detect(_ptr(a), _ptr(m), nx, ny, int(wmax)), "amf_detect")
     return m
+
+
+def sobel(img) -> np.ndarray:
+    """Sobel edge magnitude (Sec. 4.2) of a uint8 image: min(255,
+    floor(sqrt(Gx^2 + Gy^2))) inside, 0 on the border."""
+    lib = _load()
+    a = np.ascontiguousarray(img, dtype=np.uint8)
+    ny, nx = a.shape
+    out = np.zeros((ny, nx), dtype=np.uint8)
+    _check(lib.orc_sobel(_ptr(a), _ptr(out), nx, ny), "sobel")
+    return out
 
 
 def j2d5_dc(u0, f, *, sigma=1.0, h=0.0, tol=1e-10, k_in=50, max_outer=100000):

@@ -624,3 +624,43 @@ int orc_amf_detect(const uint8_t *img, uint8_t *mask, int64_t nx, int64_t ny, in
         }
     return 0;
 }
+
+/* ------------------------------------------------------------------------- */
+/* Sobel edge detector (Sec. 4.2): one 3x3 stencil sweep, no reduce.  The    */
+/* paper applies the filter "from its definition" without fixing the         */
+/* magnitude, the output type or the border; here: the two 3x3 gradients     */
+/*   Gx = (z[i-1][j+1] - z[i-1][j-1]) + 2 (z[i][j+1] - z[i][j-1])            */
+/*        + (z[i+1][j+1] - z[i+1][j-1])                                       */
+/*   Gy = (z[i+1][j-1] - z[i-1][j-1]) + 2 (z[i+1][j] - z[i-1][j])            */
+/*        + (z[i+1][j+1] - z[i-1][j+1])                                       */
+/* in integers, out = min(255, floor(sqrt(Gx^2 + Gy^2))) for pixels with a   */
+/* full 3x3 neighbourhood, 0 on the image's border.                          */
+/* ------------------------------------------------------------------------- */
+
+static int64_t isqrt_floor(int64_t n)
+{
+    int64_t r = (int64_t)sqrt((double)n);
+    while (r * r > n) --r;
+    while ((r + 1) * (r + 1) <= n) ++r;
+    return r;
+}
+
+int orc_sobel(const uint8_t *img, uint8_t *out, int64_t nx, int64_t ny)
+{
+    if (nx < 1 || ny < 1) return -1;
+    for (int64_t i = 0; i < ny; ++i)
+        for (int64_t j = 0; j < nx; ++j) {
+            if (i == 0 || j == 0 || i == ny - 1 || j == nx - 1) {
+                out[i * nx + j] = 0;
+                continue;
+            }
+            const uint8_t *up = img + (i - 1) * nx, *mid = img + i * nx, *dn = img + (i + 1) * nx;
+            int64_t gx = ((int64_t)up[j + 1] - up[j - 1]) + 2 * ((int64_t)mid[j + 1] - mid[j - 1]) +
+                         ((int64_t)dn[j + 1] - dn[j - 1]);
+            int64_t gy = ((int64_t)dn[j - 1] - up[j - 1]) + 2 * ((int64_t)dn[j] - up[j]) +
+                         ((int64_t)dn[j + 1] - up[j + 1]);
+            int64_t m = isqrt_floor(gx * gx + gy * gy);
+            out[i * nx + j] = (uint8_t)(m > 255 ? 255 : m);
+        }
+    return 0;
+}

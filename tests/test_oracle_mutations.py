@@ -80,6 +80,18 @@ MUTATIONS = [
     ("detector keeps the pixel when no window decides",
      "            if (out < 0) out = zmed;",
      "            if (out < 0) out = z;"),
+    ("Sobel drops the centre row's weight 2",
+     "            int64_t gx = ((int64_t)up[j + 1] - up[j - 1]) + 2 * ((int64_t)mid[j + 1] - mid[j - 1]) +",
+     "            int64_t gx = ((int64_t)up[j + 1] - up[j - 1]) + ((int64_t)mid[j + 1] - mid[j - 1]) +"),
+    ("Sobel magnitude rounded up",
+     "    while ((r + 1) * (r + 1) <= n) ++r;",
+     "    while (r * r < n) ++r;"),
+    ("Sobel clamps at 254",
+     "            out[i * nx + j] = (uint8_t)(m > 255 ? 255 : m);",
+     "            out[i * nx + j] = (uint8_t)(m > 254 ? 254 : m);"),
+    ("Sobel copies the border",
+     "                out[i * nx + j] = 0;\n                continue;",
+     "                out[i * nx + j] = img[i * nx + j];\n                continue;"),
     ("binary16 subnormal shift off by one",
      "    int32_t shift = -(e + 1);                        /* >= 14 */",
      "    int32_t shift = -(e + 2);                        /* >= 14 */"),
