@@ -799,6 +799,69 @@ def run_video(args):
     return 0
 
 
+def run_sobel(args):
+    """The Sobel edge detector of Sec. 4.2 (one stencil sweep, no reduce) on
+    uint8 images of the paper's sides 512, 4096 and 16384 (smooth synthetic
+    images of the restoration generator): the kernel alone with the image
+    resident (HBM bytes: 1 read + 1 written per pixel; the 16384 image is
+    larger than L2), end to end with the pinned host copies in and out, and
+    image streams pipe(read, sobel, write) with 3 images in flight.  The
+    oracle filtering one 4096 x 4096 image is the CPU leg."""
+    import numpy as np
+    import torch
+    import oracle
+    from paper_1609_04567_gb300 import inputs, slr, video
+    slr.load()
+    peak, peak_src = measured_peaks()
+    out = {}
+    base = inputs.smooth_image(4096, 4096, seed=2)
+    for side, stream_n in ((512, 100), (4096, 100), (16384, 12)):
+        img_np = base[:side, :side] if side <= 4096 else np.tile(base, (side // 4096, side // 4096))
+        img_np = np.ascontiguousarray(img_np)
+        img = torch.from_numpy(img_np).cuda()
+        dst = torch.empty_like(img)
+        st = torch.cuda.Stream()
+        with torch.cuda.stream(st):
+            for _ in range(args.warmup):
+                slr.sobel(img, dst, stream=st)
+            reps = 200 if side <= 4096 else 20
+            ms = _stream_time(st, lambda: slr.sobel(img, dst, stream=st), reps)
+        host_in = torch.from_numpy(img_np).pin_memory()
+        host_out = torch.empty_like(host_in).pin_memory()
+        with torch.cuda.stream(st):
+            def e2e():
+                img.copy_(host_in, non_blocking=True)
+                slr.sobel(img, dst, stream=st)
+                host_out.copy_(dst, non_blocking=True)
+            for _ in range(args.warmup):
+                e2e()
+            e2e_ms = _stream_time(st, e2e, 20)
+        px = side * side
+        row = {"kernel_ms": ms, "gpixel_per_s": px / ms / 1e6, "hbm_gbs": 2 * px / ms / 1e6,
+               "frac": 2 * px / ms / 1e6 / peak, "e2e_ms": e2e_ms, "e2e_gpixel_per_s": px / e2e_ms / 1e6,
+               "h2d_bytes": px, "d2h_bytes": px,
+               "l2_resident": 2 * px < 126 * 2 ** 20}   # in and out fit L2: the kernel rate is not an HBM rate
+        imgs = [host_in] * stream_n
+        outs = [torch.empty_like(host_in).pin_memory() for _ in range(min(stream_n, 8))]
+        outs = [outs[k % len(outs)] for k in range(stream_n)]
+        video.sobel_stream(imgs[:6], outs[:6], lanes=3)
+        s = video.sobel_stream(imgs, outs, lanes=3)
+        row["stream"] = {"images": s.images, "images_per_s": s.images_per_s, "gbytes_per_s": s.gbytes_per_s,
+                         "in_flight": s.lanes}
+        out[f"{side}x{side}"] = row
+        del img, dst, host_in, host_out, imgs, outs
+        torch.cuda.empty_cache()
+    t0 = time.perf_counter()
+    oracle.sobel(base)
+    cpu_s = time.perf_counter() - t0
+    line = {"workload": "sobel_512_4096_16384", "metric": "Gpixel/s", "unit": "Gpixel/s", "peak_gbs": peak,
+            "peak_source": peak_src, "cases": out,
+            "cpu_baseline": {"value": 4096 * 4096 / cpu_s / 1e9, "unit": "Gpixel/s", "cores": 1, "kind": "oracle",
+                             "sample": "one 4096 x 4096 image"}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -806,7 +869,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="life",
-                    choices=["life", "helmholtz", "restore", "jacobi", "precision", "batch", "serve", "video"])
+                    choices=["life", "helmholtz", "restore", "jacobi", "precision", "batch", "serve", "video", "sobel"])
     ap.add_argument("--video-frames", type=int, default=100, help="frames per stream of the video workload")
     ap.add_argument("--batch3d", type=int, default=512, help="side of the 3D grid of the batch workload (0: none)")
     ap.add_argument("--rate", type=float, default=2000.0)
@@ -832,7 +895,7 @@ def main():
         ap.error("--warmup must be >= 3")
     if args.workload != "life":
         fn = {"helmholtz": run_helmholtz, "restore": run_restore, "jacobi": run_jacobi, "precision": run_precision,
-              "batch": run_batch, "serve": run_serve, "video": run_video}
+              "batch": run_batch, "serve": run_serve, "video": run_video, "sobel": run_sobel}
         return fn[args.workload](args)
     wl = WORKLOADS[args.workload]
     world, rank, local = dist_setup()

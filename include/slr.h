@@ -226,6 +226,17 @@ slr_status slr_detect_noise(const void *img, void *mask, void *state, int64_t nx
  * / SLR_ERR_CUDA (message in slr_last_error(NULL)). */
 slr_status slr_state_to_frame(const void *state, void *img, int64_t n, void *stream);
 
+/* ---- Sobel edge detector (Sec. 4.2): one stencil sweep, no reduce ----------
+ * out (uint8, nx x ny, row-major) = the edge magnitude of the uint8 image img:
+ * with the 3x3 gradients Gx = (z[i-1][j+1] - z[i-1][j-1]) + 2 (z[i][j+1] -
+ * z[i][j-1]) + (z[i+1][j+1] - z[i+1][j-1]) and Gy = (z[i+1][j-1] - z[i-1][j-1])
+ * + 2 (z[i+1][j] - z[i-1][j]) + (z[i+1][j+1] - z[i-1][j+1]) in integers,
+ * out = min(255, floor(sqrt(Gx^2 + Gy^2))) where the 3x3 neighbourhood lies in
+ * the image and 0 on its border.  img and out are device pointers that must not
+ * overlap.  Enqueued on `stream`; SLR_OK or SLR_ERR_INVALID_ARG / SLR_ERR_CUDA
+ * (message in slr_last_error(NULL)). */
+slr_status slr_sobel(const void *img, void *out, int64_t nx, int64_t ny, void *stream);
+
 /* Library build string (architecture, version). */
 const char *slr_version(void);
 

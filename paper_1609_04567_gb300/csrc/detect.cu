@@ -160,3 +160,180 @@ slr_status slr_state_to_frame(const void *state, void *img, int64_t n, void *str
 }
 
 }  // extern "C"
+
+// ---- Sobel edge detector (Sec. 4.2) --------------------------------------------
+// One 3x3 stencil sweep with no reduce: the gradients
+//   Gx = V1[j+1] - V1[j-1],  V1 = z[i-1] + 2 z[i] + z[i+1]   (per column)
+//   Gy = V2[j-1] + 2 V2[j] + V2[j+1],  V2 = z[i+1] - z[i-1]
+// in integers, out = min(255, floor(sqrt(Gx^2 + Gy^2))) inside, 0 on the
+// image's border.  A warp owns a strip of 512 columns (16 consecutive pixels
+// per lane, one 16-byte access per row) and marches down a segment of rows,
+// keeping rows i-1, i, i+1 unpacked in registers (three rows per turn, no
+// copies): each pixel is read from memory once and written once.  The
+// neighbours across lanes come by shuffles of the column sums; the strip's two
+// outer columns by single loads.  The square root is the hardware estimate,
+// corrected to the exact integer floor.
+namespace slr {
+namespace {
+
+constexpr int kSobelPx = 16;                      // pixels per lane
+constexpr int kSobelStrip = 32 * kSobelPx;        // columns per warp
+constexpr int kSobelWarps = 8;
+
+__device__ __forceinline__ void sobel_load(const unsigned char *img, int nx, int y, int x0, bool vec, int (&v)[16])
+{
+    const unsigned char *row = img + (size_t)y * nx;
+    if (vec) {
+        const uint4 w = *(const uint4 *)(row + x0);
+        const uint32_t ws[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+        for (int k = 0; k < 16; ++k) v[k] = (ws[k >> 2] >> (8 * (k & 3))) & 0xFFu;
+    } else {
+#pragma unroll
+        for (int k = 0; k < 16; ++k) v[k] = x0 + k < nx ? row[x0 + k] : 0;
+    }
+}
+
+__device__ __forceinline__ int isqrt_floor_u21(int n)
+{
+    // n < 2^22: the estimate is within one of the square root; two integer steps make it exact
+    float s;
+    asm("sqrt.approx.f32 %0, %1;" : "=f"(s) : "f"((float)n));
+    int r = (int)s;
+    r -= r * r > n;
+    r += (r + 1) * (r + 1) <= n;
+    return r;
+}
+
+// output row y of the lane's 16 pixels from rows y-1 (a), y (c), y+1 (b)
+__device__ __forceinline__ void sobel_row(const unsigned char *img, unsigned char *out, int nx, int ny, int y,
+                                          int x0, bool vec, const int (&a)[16], const int (&c)[16],
+                                          const int (&b)[16])
+{
+    const int lane = threadIdx.x & 31;
+    int v1[16], v2[16];
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+        v1[k] = a[k] + 2 * c[k] + b[k];
+        v2[k] = b[k] - a[k];
+    }
+    // the column sums left of pixel 0 and right of pixel 15
+    int l1 = __shfl_up_sync(0xffffffffu, v1[15], 1), l2 = __shfl_up_sync(0xffffffffu, v2[15], 1);
+    int r1 = __shfl_down_sync(0xffffffffu, v1[0], 1), r2 = __shfl_down_sync(0xffffffffu, v2[0], 1);
+    if (y == 0 || y == ny - 1 || x0 >= nx) {
+        if (x0 < nx) {
+            unsigned char *o = out + (size_t)y * nx;
+            if (vec) *(uint4 *)(o + x0) = make_uint4(0u, 0u, 0u, 0u);
+            else
+                for (int k = 0; k < 16 && x0 + k < nx; ++k) o[x0 + k] = 0;
+        }
+        return;
+    }
+    if (lane == 0 && x0 > 0) {
+        const size_t i = (size_t)y * nx + x0 - 1;
+        const int za = img[i - nx], zc = img[i], zb = img[i + nx];
+        l1 = za + 2 * zc + zb;
+        l2 = zb - za;
+    }
+    if ((lane == 31 || x0 + 16 >= nx) && x0 + 16 < nx) {
+        const size_t i = (size_t)y * nx + x0 + 16;
+        const int za = img[i - nx], zc = img[i], zb = img[i + nx];
+        r1 = za + 2 * zc + zb;
+        r2 = zb - za;
+    }
+    uint32_t w[4] = {0u, 0u, 0u, 0u};
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+        const int p1 = k > 0 ? v1[k - 1] : l1, n1 = k < 15 ? v1[k + 1] : r1;
+        const int p2 = k > 0 ? v2[k - 1] : l2, n2 = k < 15 ? v2[k + 1] : r2;
+        const int gx = n1 - p1, gy = p2 + 2 * v2[k] + n2;
+        const int m2 = gx * gx + gy * gy;
+        int m = m2 >= 65536 ? 255 : isqrt_floor_u21(m2);
+        const int x = x0 + k;
+        if (x == 0 || x == nx - 1) m = 0;
+        w[k >> 2] |= (uint32_t)m << (8 * (k & 3));
+    }
+    unsigned char *o = out + (size_t)y * nx;
+    if (vec) {
+        *(uint4 *)(o + x0) = make_uint4(w[0], w[1], w[2], w[3]);
+    } else {
+#pragma unroll
+        for (int k = 0; k < 16; ++k)
+            if (x0 + k < nx) o[x0 + k] = (unsigned char)(w[k >> 2] >> (8 * (k & 3)));
+    }
+}
+
+__global__ void __launch_bounds__(32 * kSobelWarps) sobel_kernel(const unsigned char *img, unsigned char *out,
+                                                                 int nx, int ny, int seg_rows, int aligned)
+{
+    const int lane = threadIdx.x & 31;
+    const long long unit = (long long)blockIdx.x * kSobelWarps + (threadIdx.x >> 5);
+    const int strips = (nx + kSobelStrip - 1) / kSobelStrip;
+    const long long units = (long long)strips * ((ny + seg_rows - 1) / seg_rows);
+    if (unit >= units) return;
+    const int strip = (int)(unit % strips), seg = (int)(unit / strips);
+    const int x0 = strip * kSobelStrip + lane * kSobelPx;
+    const int y0 = seg * seg_rows, y1 = min(ny, y0 + seg_rows);
+    // whole 16-byte groups inside the row, and 16-byte aligned rows
+    const bool vec = aligned && x0 + 16 <= nx;
+    int R0[16], R1[16], R2[16];
+    if (y0 > 0) sobel_load(img, nx, y0 - 1, x0, vec, R0);
+    else
+#pragma unroll
+        for (int k = 0; k < 16; ++k) R0[k] = 0;
+    sobel_load(img, nx, y0, x0, vec, R1);
+    for (int y = y0; y < y1; y += 3) {
+        if (y + 1 < ny) sobel_load(img, nx, y + 1, x0, vec, R2);
+        sobel_row(img, out, nx, ny, y, x0, vec, R0, R1, R2);
+        if (y + 1 >= y1) break;
+        if (y + 2 < ny) sobel_load(img, nx, y + 2, x0, vec, R0);
+        sobel_row(img, out, nx, ny, y + 1, x0, vec, R1, R2, R0);
+        if (y + 2 >= y1) break;
+        if (y + 3 < ny) sobel_load(img, nx, y + 3, x0, vec, R1);
+        sobel_row(img, out, nx, ny, y + 2, x0, vec, R2, R0, R1);
+    }
+}
+
+}  // namespace
+}  // namespace slr
+
+extern "C" {
+
+slr_status slr_sobel(const void *img, void *out, int64_t nx, int64_t ny, void *stream)
+{
+    if (!img || !out) {
+        slr::set_handleless_error("slr_sobel: img and out must be device pointers");
+        return SLR_ERR_INVALID_ARG;
+    }
+    if (nx < 1 || ny < 1 || nx >= (1ll << 31) - 4096 || ny >= (1ll << 31)) {
+        slr::set_handleless_error("slr_sobel: nx and ny must lie in [1, 2^31 - 4096)");
+        return SLR_ERR_INVALID_ARG;
+    }
+    const size_t bytes = (size_t)nx * (size_t)ny;
+    const uintptr_t pi = (uintptr_t)img, po = (uintptr_t)out;
+    if (pi < po + bytes && po < pi + bytes) {
+        slr::set_handleless_error("slr_sobel: img and out overlap");
+        return SLR_ERR_INVALID_ARG;
+    }
+    // segments of rows: about four warps' worth of work per SM slot, at least 16 rows
+    const long long strips = (nx + slr::kSobelStrip - 1) / slr::kSobelStrip;
+    long long seg = ny * strips / (152 * 64 * 4);
+    seg = seg < 16 ? 16 : (seg > 1024 ? 1024 : seg);
+    const long long units = strips * ((ny + seg - 1) / seg);
+    const long long blocks = (units + slr::kSobelWarps - 1) / slr::kSobelWarps;
+    if (blocks > 0x7FFFFFFFll) {
+        slr::set_handleless_error("slr_sobel: image too large");
+        return SLR_ERR_INVALID_ARG;
+    }
+    const int aligned = nx % 16 == 0 && pi % 16 == 0 && po % 16 == 0;
+    slr::sobel_kernel<<<(unsigned)blocks, 32 * slr::kSobelWarps, 0, (cudaStream_t)stream>>>(
+        (const unsigned char *)img, (unsigned char *)out, (int)nx, (int)ny, (int)seg, aligned);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        slr::set_handleless_error(std::string("slr_sobel: launch: ") + cudaGetErrorString(e));
+        return SLR_ERR_CUDA;
+    }
+    return SLR_OK;
+}
+
+}  // extern "C"

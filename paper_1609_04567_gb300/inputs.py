@@ -36,6 +36,7 @@ STREAM_IMAGE_PARAMS = 3
 STREAM_NOISE = 4
 STREAM_BATCH_SIDES = 5
 STREAM_ARRIVALS = 6
+STREAM_PIXELS = 7               # uniformly random uint8 images
 STREAM_BATCH_F0 = 1000          # per-instance right-hand sides start here
 
 
@@ -134,6 +135,12 @@ def noisy_frame(ny: int, nx: int, seed: int = DEFAULT_SEED, p_noise: float = 0.5
     frame[noisy & salt] = 255
     frame[noisy & ~salt] = 0
     return frame, clean
+
+
+def random_image(ny: int, nx: int, seed: int = DEFAULT_SEED) -> np.ndarray:
+    """uint8 image with every pixel uniform in [0, 255] (the low byte of its
+    random word)."""
+    return (raw_u64(seed, STREAM_PIXELS, 0, ny * nx) & np.uint64(0xFF)).astype(np.uint8).reshape(ny, nx)
 
 
 def noise_mask(frame: np.ndarray) -> np.ndarray:

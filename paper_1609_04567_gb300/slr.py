@@ -62,7 +62,7 @@ EXPORTS = ["slr_desc_init", "slr_workspace_size", "slr_create", "slr_run_until",
            "slr_batch_run", "slr_batch_poll", "slr_batch_result", "slr_batch_remove", "slr_batch_destroy",
            "slr_batch_last_error", "slr_tune_scratch_size", "slr_tune", "slr_tune_lookup", "slr_tune_clear",
            "slr_tune_last_error", "slr_check_exact_math", "slr_check_exact_division", "slr_detect_noise",
-           "slr_state_to_frame"]
+           "slr_state_to_frame", "slr_sobel"]
 SLR_STATIC_STATE_BYTES = 4 << 20
 
 _lib = None
@@ -149,6 +149,8 @@ def load(path: str = LIB_PATH):
     lib.slr_detect_noise.restype = i32
     lib.slr_state_to_frame.argtypes = [P, P, i64, P]
     lib.slr_state_to_frame.restype = i32
+    lib.slr_sobel.argtypes = [P, P, i64, i64, P]
+    lib.slr_sobel.restype = i32
     _lib = lib
     return lib
 
@@ -341,6 +343,26 @@ def slr_state_to_frame(state_ptr: int, img_ptr: int, n: int, stream: int = 0) ->
     if st != SLR_OK:
         raise SlrError(st, slr_last_error(None))
     return st
+
+
+def slr_sobel(img_ptr: int, out_ptr: int, nx: int, ny: int, stream: int = 0) -> int:
+    st = load().slr_sobel(img_ptr or None, out_ptr or None, nx, ny, stream or None)
+    if st != SLR_OK:
+        raise SlrError(st, slr_last_error(None))
+    return st
+
+
+def sobel(img, out=None, *, stream=None):
+    """Sobel edge magnitude (Sec. 4.2) of a uint8 CUDA image tensor."""
+    import torch
+    if not img.is_cuda or img.dtype != torch.uint8 or img.dim() != 2 or not img.is_contiguous():
+        raise ValueError("img must be a contiguous 2D uint8 CUDA tensor")
+    if out is None:
+        out = torch.empty_like(img)
+    st = stream if stream is not None else torch.cuda.current_stream(img.device)
+    ny, nx = img.shape
+    slr_sobel(img.data_ptr(), out.data_ptr(), nx, ny, st.cuda_stream)
+    return out
 
 
 def detect_noise(img, mask=None, state=None, *, wmax: int = 7, stream=None):

@@ -1,5 +1,6 @@
-"""Video restoration over a stream of frames: the pipe(read, detect,
-ofarm(restore), write) of Sec. 4.3 on one GPU.
+"""Image streams of Sec. 4: the video restoration pipe(read, detect,
+ofarm(restore), write) of Sec. 4.3 and the Sobel pipe(read, sobel, write) of
+Sec. 4.2, on one GPU.
 
 * read: the frames of a noisy video (uint8) sit in pinned host memory and are
   copied to the device on the frame's stream;
@@ -83,6 +84,49 @@ class _Lane:
         self.desc = desc
         self.handle = None
         self.pending = None       # (FrameResult, event) of the frame in flight
+
+
+@dataclass
+class ImageStats:
+    images: int
+    lanes: int
+    wall_s: float
+    images_per_s: float
+    gbytes_per_s: float          # image bytes in and out per second, end to end
+
+
+def sobel_stream(images_host, out_host, *, lanes: int = 3, device=None) -> ImageStats:
+    """pipe(read, sobel, write) of Sec. 4.2 over pinned uint8 host images of
+    one shape: each image is copied in, filtered and copied out on the stream
+    of its lane, `lanes` images in flight so copies overlap the filter;
+    written in input order."""
+    import torch
+    dev = torch.device(device or "cuda")
+    shape = tuple(images_host[0].shape)
+    streams = [torch.cuda.Stream(dev) for _ in range(lanes)]
+    bufs = [(torch.empty(shape, dtype=torch.uint8, device=dev), torch.empty(shape, dtype=torch.uint8, device=dev))
+            for _ in range(lanes)]
+    events = [None] * lanes
+    n = len(images_host)
+    t0 = time.perf_counter()
+    for f in range(n):
+        k = f % lanes
+        if events[k] is not None:
+            events[k].synchronize()            # image f - lanes written
+        s, (din, dout) = streams[k], bufs[k]
+        with torch.cuda.stream(s):
+            din.copy_(images_host[f], non_blocking=True)
+        slr.slr_sobel(din.data_ptr(), dout.data_ptr(), shape[1], shape[0], s.cuda_stream)
+        with torch.cuda.stream(s):
+            out_host[f].copy_(dout, non_blocking=True)
+        events[k] = torch.cuda.Event()
+        events[k].record(s)
+    for f in range(n, n + lanes):
+        if events[f % lanes] is not None:
+            events[f % lanes].synchronize()
+    wall = time.perf_counter() - t0
+    return ImageStats(images=n, lanes=lanes, wall_s=wall, images_per_s=n / wall,
+                      gbytes_per_s=2.0 * n * shape[0] * shape[1] / wall / 1e9)
 
 
 class VideoPipeline:
