@@ -393,6 +393,13 @@ slr_status slr_check_exact_math(uint64_t *mismatches, uint64_t *checked, void *s
  * the range above.  Waits for `stream`; static device counters. */
 slr_status slr_check_exact_division(double d, uint64_t *mismatches, uint64_t *checked, void *stream);
 
+/* Self-check of the Sobel magnitude's clamped integer square root (the
+ * hardware estimate of sqrt(n + 1/2), truncated): compares it with
+ * min(255, floor(sqrt(n))) for every integer 0 <= n < 2^22; *mismatches
+ * counts differences (0 on a correct build), *checked the values tried.
+ * Waits for `stream`; static device counters. */
+slr_status slr_check_exact_isqrt(uint64_t *mismatches, uint64_t *checked, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -20,6 +20,7 @@
 // restored state back into a uint8 frame (round to nearest even, clamped).
 #include <string>
 
+#include "crmath.cuh"
 #include "slr_internal.cuh"
 
 namespace slr {
@@ -166,66 +167,57 @@ slr_status slr_state_to_frame(const void *state, void *img, int64_t n, void *str
 //   Gx = V1[j+1] - V1[j-1],  V1 = z[i-1] + 2 z[i] + z[i+1]   (per column)
 //   Gy = V2[j-1] + 2 V2[j] + V2[j+1],  V2 = z[i+1] - z[i-1]
 // in integers, out = min(255, floor(sqrt(Gx^2 + Gy^2))) inside, 0 on the
-// image's border.  A warp owns a strip of 512 columns (16 consecutive pixels
-// per lane, one 16-byte access per row) and marches down a segment of rows,
+// image's border.  A warp owns a strip of 256 columns (8 consecutive pixels
+// per lane, one 8-byte access per row) and marches down a segment of rows,
 // keeping rows i-1, i, i+1 unpacked in registers (three rows per turn, no
 // copies): each pixel is read from memory once and written once.  The
 // neighbours across lanes come by shuffles of the column sums; the strip's two
-// outer columns by single loads.  The square root is the hardware estimate,
-// corrected to the exact integer floor.
+// outer columns by single loads.  The clamped integer square root is the
+// hardware estimate of sqrt(n + 1/2), truncated (exact: isqrt_clamp255).
 namespace slr {
 namespace {
 
-constexpr int kSobelPx = 16;                      // pixels per lane
-constexpr int kSobelStrip = 32 * kSobelPx;        // columns per warp
+constexpr int kPx = 8;                            // pixels per lane (one 8-byte access per row)
+constexpr int kPW = kPx / 4;                      // 32-bit words per lane and row
+constexpr int kSobelStrip = 32 * kPx;             // columns per warp
 constexpr int kSobelWarps = 8;
 
-__device__ __forceinline__ void sobel_load(const unsigned char *img, int nx, int y, int x0, bool vec, int (&v)[16])
+__device__ __forceinline__ void sobel_load(const unsigned char *img, int nx, int y, int x0, bool vec, int (&v)[kPx])
 {
     const unsigned char *row = img + (size_t)y * nx;
     if (vec) {
-        const uint4 w = *(const uint4 *)(row + x0);
-        const uint32_t ws[4] = {w.x, w.y, w.z, w.w};
+        const uint2 w = *(const uint2 *)(row + x0);
+        const uint32_t ws[2] = {w.x, w.y};
 #pragma unroll
-        for (int k = 0; k < 16; ++k) v[k] = (ws[k >> 2] >> (8 * (k & 3))) & 0xFFu;
+        for (int k = 0; k < kPx; ++k) v[k] = (ws[k >> 2] >> (8 * (k & 3))) & 0xFFu;
     } else {
 #pragma unroll
-        for (int k = 0; k < 16; ++k) v[k] = x0 + k < nx ? row[x0 + k] : 0;
+        for (int k = 0; k < kPx; ++k) v[k] = x0 + k < nx ? row[x0 + k] : 0;
     }
 }
 
-__device__ __forceinline__ int isqrt_floor_u21(int n)
-{
-    // n < 2^22: the estimate is within one of the square root; two integer steps make it exact
-    float s;
-    asm("sqrt.approx.f32 %0, %1;" : "=f"(s) : "f"((float)n));
-    int r = (int)s;
-    r -= r * r > n;
-    r += (r + 1) * (r + 1) <= n;
-    return r;
-}
-
-// output row y of the lane's 16 pixels from rows y-1 (a), y (c), y+1 (b)
+// output row y of the lane's pixels from rows y-1 (a), y (c), y+1 (b);
+// keep[] clears the bytes of the image's first and last columns
 __device__ __forceinline__ void sobel_row(const unsigned char *img, unsigned char *out, int nx, int ny, int y,
-                                          int x0, bool vec, const int (&a)[16], const int (&c)[16],
-                                          const int (&b)[16])
+                                          int x0, bool vec, const uint32_t (&keep)[kPW], const int (&a)[kPx],
+                                          const int (&c)[kPx], const int (&b)[kPx])
 {
     const int lane = threadIdx.x & 31;
-    int v1[16], v2[16];
+    int v1[kPx], v2[kPx];
 #pragma unroll
-    for (int k = 0; k < 16; ++k) {
+    for (int k = 0; k < kPx; ++k) {
         v1[k] = a[k] + 2 * c[k] + b[k];
         v2[k] = b[k] - a[k];
     }
-    // the column sums left of pixel 0 and right of pixel 15
-    int l1 = __shfl_up_sync(0xffffffffu, v1[15], 1), l2 = __shfl_up_sync(0xffffffffu, v2[15], 1);
+    // the column sums left of the lane's first pixel and right of its last
+    int l1 = __shfl_up_sync(0xffffffffu, v1[kPx - 1], 1), l2 = __shfl_up_sync(0xffffffffu, v2[kPx - 1], 1);
     int r1 = __shfl_down_sync(0xffffffffu, v1[0], 1), r2 = __shfl_down_sync(0xffffffffu, v2[0], 1);
     if (y == 0 || y == ny - 1 || x0 >= nx) {
         if (x0 < nx) {
             unsigned char *o = out + (size_t)y * nx;
-            if (vec) *(uint4 *)(o + x0) = make_uint4(0u, 0u, 0u, 0u);
+            if (vec) *(uint2 *)(o + x0) = make_uint2(0u, 0u);
             else
-                for (int k = 0; k < 16 && x0 + k < nx; ++k) o[x0 + k] = 0;
+                for (int k = 0; k < kPx && x0 + k < nx; ++k) o[x0 + k] = 0;
         }
         return;
     }
@@ -235,30 +227,30 @@ __device__ __forceinline__ void sobel_row(const unsigned char *img, unsigned cha
         l1 = za + 2 * zc + zb;
         l2 = zb - za;
     }
-    if ((lane == 31 || x0 + 16 >= nx) && x0 + 16 < nx) {
-        const size_t i = (size_t)y * nx + x0 + 16;
+    if (lane == 31 && x0 + kPx < nx) {
+        const size_t i = (size_t)y * nx + x0 + kPx;
         const int za = img[i - nx], zc = img[i], zb = img[i + nx];
         r1 = za + 2 * zc + zb;
         r2 = zb - za;
     }
-    uint32_t w[4] = {0u, 0u, 0u, 0u};
+    uint32_t w[kPW];
 #pragma unroll
-    for (int k = 0; k < 16; ++k) {
-        const int p1 = k > 0 ? v1[k - 1] : l1, n1 = k < 15 ? v1[k + 1] : r1;
-        const int p2 = k > 0 ? v2[k - 1] : l2, n2 = k < 15 ? v2[k + 1] : r2;
+    for (int q = 0; q < kPW; ++q) w[q] = 0u;
+#pragma unroll
+    for (int k = 0; k < kPx; ++k) {
+        const int p1 = k > 0 ? v1[k - 1] : l1, n1 = k < kPx - 1 ? v1[k + 1] : r1;
+        const int p2 = k > 0 ? v2[k - 1] : l2, n2 = k < kPx - 1 ? v2[k + 1] : r2;
         const int gx = n1 - p1, gy = p2 + 2 * v2[k] + n2;
-        const int m2 = gx * gx + gy * gy;
-        int m = m2 >= 65536 ? 255 : isqrt_floor_u21(m2);
-        const int x = x0 + k;
-        if (x == 0 || x == nx - 1) m = 0;
-        w[k >> 2] |= (uint32_t)m << (8 * (k & 3));
+        w[k >> 2] |= (uint32_t)isqrt_clamp255(gx * gx + gy * gy) << (8 * (k & 3));
     }
+#pragma unroll
+    for (int q = 0; q < kPW; ++q) w[q] &= keep[q];
     unsigned char *o = out + (size_t)y * nx;
     if (vec) {
-        *(uint4 *)(o + x0) = make_uint4(w[0], w[1], w[2], w[3]);
+        *(uint2 *)(o + x0) = make_uint2(w[0], w[1]);
     } else {
 #pragma unroll
-        for (int k = 0; k < 16; ++k)
+        for (int k = 0; k < kPx; ++k)
             if (x0 + k < nx) o[x0 + k] = (unsigned char)(w[k >> 2] >> (8 * (k & 3)));
     }
 }
@@ -272,25 +264,31 @@ __global__ void __launch_bounds__(32 * kSobelWarps) sobel_kernel(const unsigned 
     const long long units = (long long)strips * ((ny + seg_rows - 1) / seg_rows);
     if (unit >= units) return;
     const int strip = (int)(unit % strips), seg = (int)(unit / strips);
-    const int x0 = strip * kSobelStrip + lane * kSobelPx;
+    const int x0 = strip * kSobelStrip + lane * kPx;
     const int y0 = seg * seg_rows, y1 = min(ny, y0 + seg_rows);
-    // whole 16-byte groups inside the row, and 16-byte aligned rows
-    const bool vec = aligned && x0 + 16 <= nx;
-    int R0[16], R1[16], R2[16];
+    // whole 8-byte groups inside the row, and 8-byte aligned rows
+    const bool vec = aligned && x0 + kPx <= nx;
+    uint32_t keep[kPW];
+#pragma unroll
+    for (int q = 0; q < kPW; ++q) keep[q] = ~0u;
+#pragma unroll
+    for (int k = 0; k < kPx; ++k)
+        if (x0 + k == 0 || x0 + k == nx - 1) keep[k >> 2] &= ~(0xFFu << (8 * (k & 3)));
+    int R0[kPx], R1[kPx], R2[kPx];
     if (y0 > 0) sobel_load(img, nx, y0 - 1, x0, vec, R0);
     else
 #pragma unroll
-        for (int k = 0; k < 16; ++k) R0[k] = 0;
+        for (int k = 0; k < kPx; ++k) R0[k] = 0;
     sobel_load(img, nx, y0, x0, vec, R1);
     for (int y = y0; y < y1; y += 3) {
         if (y + 1 < ny) sobel_load(img, nx, y + 1, x0, vec, R2);
-        sobel_row(img, out, nx, ny, y, x0, vec, R0, R1, R2);
+        sobel_row(img, out, nx, ny, y, x0, vec, keep, R0, R1, R2);
         if (y + 1 >= y1) break;
         if (y + 2 < ny) sobel_load(img, nx, y + 2, x0, vec, R0);
-        sobel_row(img, out, nx, ny, y + 1, x0, vec, R1, R2, R0);
+        sobel_row(img, out, nx, ny, y + 1, x0, vec, keep, R1, R2, R0);
         if (y + 2 >= y1) break;
         if (y + 3 < ny) sobel_load(img, nx, y + 3, x0, vec, R1);
-        sobel_row(img, out, nx, ny, y + 2, x0, vec, R2, R0, R1);
+        sobel_row(img, out, nx, ny, y + 2, x0, vec, keep, R2, R0, R1);
     }
 }
 
@@ -325,7 +323,7 @@ slr_status slr_sobel(const void *img, void *out, int64_t nx, int64_t ny, void *s
         slr::set_handleless_error("slr_sobel: image too large");
         return SLR_ERR_INVALID_ARG;
     }
-    const int aligned = nx % 16 == 0 && pi % 16 == 0 && po % 16 == 0;
+    const int aligned = nx % 8 == 0 && pi % 8 == 0 && po % 8 == 0;
     slr::sobel_kernel<<<(unsigned)blocks, 32 * slr::kSobelWarps, 0, (cudaStream_t)stream>>>(
         (const unsigned char *)img, (unsigned char *)out, (int)nx, (int)ny, (int)seg, aligned);
     const cudaError_t e = cudaGetLastError();

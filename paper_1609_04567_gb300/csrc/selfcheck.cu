@@ -139,3 +139,43 @@ extern "C" slr_status slr_check_exact_math(uint64_t *mismatches, uint64_t *check
     if (checked) *checked = h[3];
     return SLR_OK;
 }
+
+// The Sobel magnitude's clamped integer square root: isqrt_clamp255(n) must
+// equal min(255, floor(sqrt(n))) (from the IEEE binary64 square root and two
+// integer steps) for every 0 <= n < 2^22, the range of Gx^2 + Gy^2.
+namespace {
+static __device__ unsigned long long g_isqrt_counts[2];
+
+__global__ void __launch_bounds__(256) isqrt_check_kernel(int n)
+{
+    unsigned long long bad = 0ull, seen = 0ull;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        long long r = (long long)__dsqrt_rn((double)i);
+        while (r * r > i) --r;
+        while ((r + 1) * (r + 1) <= i) ++r;
+        bad += slr::isqrt_clamp255(i) != (int)(r < 255 ? r : 255);
+        seen += 1ull;
+    }
+    atomicAdd(&g_isqrt_counts[0], bad);
+    atomicAdd(&g_isqrt_counts[1], seen);
+}
+}  // namespace
+
+extern "C" slr_status slr_check_exact_isqrt(uint64_t *mismatches, uint64_t *checked, void *stream)
+{
+    cudaStream_t st = (cudaStream_t)stream;
+    void *counts = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&counts, g_isqrt_counts);
+    if (e == cudaSuccess) e = cudaMemsetAsync(counts, 0, sizeof(unsigned long long) * 2, st);
+    if (e == cudaSuccess) {
+        isqrt_check_kernel<<<1024, 256, 0, st>>>(1 << 22);
+        e = cudaGetLastError();
+    }
+    unsigned long long h[2] = {0ull, 0ull};
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h, counts, sizeof h, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return SLR_ERR_CUDA;
+    if (mismatches) *mismatches = h[0];
+    if (checked) *checked = h[1];
+    return SLR_OK;
+}

@@ -62,7 +62,7 @@ EXPORTS = ["slr_desc_init", "slr_workspace_size", "slr_create", "slr_run_until",
            "slr_batch_run", "slr_batch_poll", "slr_batch_result", "slr_batch_remove", "slr_batch_destroy",
            "slr_batch_last_error", "slr_tune_scratch_size", "slr_tune", "slr_tune_lookup", "slr_tune_clear",
            "slr_tune_last_error", "slr_check_exact_math", "slr_check_exact_division", "slr_detect_noise",
-           "slr_state_to_frame", "slr_sobel"]
+           "slr_state_to_frame", "slr_sobel", "slr_check_exact_isqrt"]
 SLR_STATIC_STATE_BYTES = 4 << 20
 
 _lib = None
@@ -151,6 +151,8 @@ def load(path: str = LIB_PATH):
     lib.slr_state_to_frame.restype = i32
     lib.slr_sobel.argtypes = [P, P, i64, i64, P]
     lib.slr_sobel.restype = i32
+    lib.slr_check_exact_isqrt.argtypes = [ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64), P]
+    lib.slr_check_exact_isqrt.restype = i32
     _lib = lib
     return lib
 
@@ -395,6 +397,15 @@ def state_to_frame(state, img=None, *, stream=None):
     st = stream if stream is not None else torch.cuda.current_stream(state.device)
     slr_state_to_frame(state.data_ptr(), img.data_ptr(), state.numel(), st.cuda_stream)
     return img
+
+
+def slr_check_exact_isqrt(stream: int = 0):
+    """Returns (mismatches, values checked) of the Sobel magnitude's integer square root."""
+    mm, n = ctypes.c_uint64(), ctypes.c_uint64()
+    st = load().slr_check_exact_isqrt(ctypes.byref(mm), ctypes.byref(n), stream or None)
+    if st != SLR_OK:
+        raise SlrError(st, "integer square root self-check failed")
+    return mm.value, n.value
 
 
 def tune(stencil: int, u, aux=None, *, stream=None, trial_iters: int = 0, **fields) -> dict:

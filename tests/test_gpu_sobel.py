@@ -57,6 +57,19 @@ def test_image_stream_in_order(gpu):
         assert np.array_equal(o.numpy(), sobel(gpu, a))
 
 
+def test_integer_square_root_is_exact(gpu):
+    # every value Gx^2 + Gy^2 can take
+    mismatches, checked = gpu.slr_check_exact_isqrt()
+    assert (mismatches, checked) == (0, 1 << 22)
+
+
+def test_large_random_image(gpu, orc):
+    # millions of gradient pairs across the whole magnitude range
+    from paper_1609_04567_gb300 import inputs
+    img = inputs.random_image(2048, 2048, seed=21)
+    assert np.array_equal(sobel(gpu, img), orc.sobel(img))
+
+
 def test_rejects_bad_arguments(gpu):
     img = torch.zeros((16, 16), dtype=torch.uint8, device="cuda")
     with pytest.raises(gpu.SlrError, match="overlap"):
