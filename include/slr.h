@@ -237,6 +237,60 @@ slr_status slr_state_to_frame(const void *state, void *img, int64_t n, void *str
  * (message in slr_last_error(NULL)). */
 slr_status slr_sobel(const void *img, void *out, int64_t nx, int64_t ny, void *stream);
 
+/* ---- User-defined elemental functions (Sec. 3.2, Fig. 1) --------------------
+ * The paper's pattern takes the elemental stencil and reduce functions from the
+ * user as source code compiled for the device at run time.  slr_user_create
+ * compiles (NVRTC, sm_103a, no floating-point contraction: every operation
+ * rounds as written) CUDA C++ source that defines
+ *
+ *   __device__ slr_t  slr_update(const slr_nbr &u, slr_t aux, long long i, long long j,
+ *                                const double *p);
+ *   __device__ double slr_delta(slr_t new_value, slr_t old_value);
+ *
+ * where slr_t is float (dtype SLR_F32) or double (SLR_F64); u(di, dj) returns
+ * the state at row i + di, column j + dj under the boundary rule (the ghost
+ * value outside the grid, or wrapped); aux is the item of the aux array (0
+ * when aux is NULL); p[0..7] are desc.params.  One iteration sets every item
+ * to slr_update(...) of the previous state (ping-pong buffers), reduces
+ * slr_delta(new, old) over all items by max (identity -inf, NaN skipped) or
+ * sum (identity 0; per-CTA partials then a fold, in a fixed order: the same
+ * inputs give the same value on every run), and stops when the value is below
+ * tol or at the cap; the host reads the value after every iteration (the
+ * schema of Fig. 2).  Programs are cached per (source, dtype).  Compile errors
+ * return SLR_ERR_INVALID_ARG with the compiler's log in
+ * slr_user_last_error(NULL). */
+typedef enum { SLR_USER_MAX = 0, SLR_USER_SUM = 1 } slr_user_reduce;
+
+typedef struct {
+    int32_t dtype;         /* SLR_F32 or SLR_F64: state and aux elements */
+    int32_t boundary;      /* SLR_DIRICHLET (ghost) or SLR_WRAP */
+    int64_t nx, ny;        /* extents, row-major, nx contiguous; nx * ny < 2^40 */
+    double ghost;          /* value outside the grid for SLR_DIRICHLET */
+    double tol;            /* stop when the reduced value < tol */
+    int32_t reduce;        /* slr_user_reduce */
+    int32_t reserved;      /* 0 */
+    double params[8];      /* constants handed to slr_update as p */
+} slr_user_desc;
+
+typedef struct slr_user_handle_s *slr_user_handle;
+
+/* Device workspace bytes for d (0 for an invalid descriptor). */
+size_t slr_user_workspace_size(const slr_user_desc *d);
+/* Compile (or reuse) the program and bind the caller's u (in/out), aux (may be
+ * NULL) and workspace (256-byte aligned, slr_user_workspace_size bytes), all
+ * device memory owned by the caller; work is enqueued on `stream`. */
+slr_status slr_user_create(const slr_user_desc *d, const char *source, void *u, const void *aux, void *workspace,
+                           size_t workspace_bytes, void *stream, slr_user_handle *out);
+/* Iterate until the test passes or the handle has run max_iters iterations in
+ * all (waits for the stream; u holds the state on return).  SLR_OK when
+ * converged, SLR_NOT_CONVERGED at the cap. */
+slr_status slr_user_run_until(slr_user_handle h, int64_t max_iters);
+/* The last iteration's reduced value, the iterations run, the convergence flag. */
+slr_status slr_user_reduce_value(slr_user_handle h, double *value, int64_t *iters, int32_t *converged);
+slr_status slr_user_destroy(slr_user_handle h);
+/* Message of the last error on h (of the last failed create when h is NULL). */
+const char *slr_user_last_error(slr_user_handle h);
+
 /* Library build string (architecture, version). */
 const char *slr_version(void);
 

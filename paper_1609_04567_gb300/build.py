@@ -17,7 +17,7 @@ CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libslr.so")
 INCLUDE = os.path.join(ROOT, "include")
-SOURCES = ["slr_api.cu", "life.cu", "life_tb.cu", "jacobi.cu", "jacobi_tb.cu", "restore.cu", "reduce.cu", "static_scratch.cu", "batch.cu", "dc.cu", "tune.cu", "selfcheck.cu", "detect.cu"]
+SOURCES = ["slr_api.cu", "life.cu", "life_tb.cu", "jacobi.cu", "jacobi_tb.cu", "restore.cu", "reduce.cu", "static_scratch.cu", "batch.cu", "dc.cu", "tune.cu", "selfcheck.cu", "detect.cu", "user.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -70,7 +70,7 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
     if force or jobs or _stale(LIB, objs):
         tmp = LIB + ".%d.tmp" % os.getpid()
         cmd = [nvcc()] + ARCH + ["-shared", "-cudart", "shared", "-o", tmp] + objs + [
-            "-Xlinker", "-rpath=" + cuda_lib_dir()]
+            "-lnvrtc", "-Xlinker", "-rpath=" + cuda_lib_dir()]
         run(cmd)
         os.replace(tmp, LIB)
     return LIB

@@ -56,13 +56,25 @@ class slr_tune_result(ctypes.Structure):
         return {name: getattr(self, name) for name, _ in self._fields_ if name != "reserved"}
 
 
+class slr_user_desc(ctypes.Structure):
+    _fields_ = [
+        ("dtype", ctypes.c_int32), ("boundary", ctypes.c_int32), ("nx", ctypes.c_int64), ("ny", ctypes.c_int64),
+        ("ghost", ctypes.c_double), ("tol", ctypes.c_double), ("reduce", ctypes.c_int32),
+        ("reserved", ctypes.c_int32), ("params", ctypes.c_double * 8),
+    ]
+
+
+SLR_USER_MAX, SLR_USER_SUM = 0, 1
+
 EXPORTS = ["slr_desc_init", "slr_workspace_size", "slr_create", "slr_run_until", "slr_reduce_value",
            "slr_destroy", "slr_last_error", "slr_version", "slr_run_static", "slr_static_last_error",
            "slr_batch_workspace_size", "slr_batch_scratch_size", "slr_batch_create", "slr_batch_add",
            "slr_batch_run", "slr_batch_poll", "slr_batch_result", "slr_batch_remove", "slr_batch_destroy",
            "slr_batch_last_error", "slr_tune_scratch_size", "slr_tune", "slr_tune_lookup", "slr_tune_clear",
            "slr_tune_last_error", "slr_check_exact_math", "slr_check_exact_division", "slr_detect_noise",
-           "slr_state_to_frame", "slr_sobel", "slr_check_exact_isqrt"]
+           "slr_state_to_frame", "slr_sobel", "slr_check_exact_isqrt", "slr_user_workspace_size",
+           "slr_user_create", "slr_user_run_until", "slr_user_reduce_value", "slr_user_destroy",
+           "slr_user_last_error"]
 SLR_STATIC_STATE_BYTES = 4 << 20
 
 _lib = None
@@ -153,6 +165,20 @@ def load(path: str = LIB_PATH):
     lib.slr_sobel.restype = i32
     lib.slr_check_exact_isqrt.argtypes = [ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64), P]
     lib.slr_check_exact_isqrt.restype = i32
+    UD = ctypes.POINTER(slr_user_desc)
+    lib.slr_user_workspace_size.argtypes = [UD]
+    lib.slr_user_workspace_size.restype = ctypes.c_size_t
+    lib.slr_user_create.argtypes = [UD, ctypes.c_char_p, P, P, P, ctypes.c_size_t, P, ctypes.POINTER(P)]
+    lib.slr_user_create.restype = i32
+    lib.slr_user_run_until.argtypes = [P, i64]
+    lib.slr_user_run_until.restype = i32
+    lib.slr_user_reduce_value.argtypes = [P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i64),
+                                          ctypes.POINTER(i32)]
+    lib.slr_user_reduce_value.restype = i32
+    lib.slr_user_destroy.argtypes = [P]
+    lib.slr_user_destroy.restype = i32
+    lib.slr_user_last_error.argtypes = [P]
+    lib.slr_user_last_error.restype = ctypes.c_char_p
     _lib = lib
     return lib
 
@@ -406,6 +432,73 @@ def slr_check_exact_isqrt(stream: int = 0):
     if st != SLR_OK:
         raise SlrError(st, "integer square root self-check failed")
     return mm.value, n.value
+
+
+class UserSolver:
+    """A loop-of-stencil-reduce over elemental functions given as CUDA C++
+    source (compiled at run time; see slr_user_create in slr.h):
+    ``slr_update(u, aux, i, j, p)`` gives an item's new value from its
+    neighbours ``u(di, dj)``, ``slr_delta(new, old)`` its contribution to the
+    reduce (``reduce`` "max" or "sum"), the loop stops when the reduced value
+    is below ``tol``.  ``u`` (float32 or float64, 2D, contiguous CUDA) is
+    updated in place; ``aux`` (same dtype and shape) or None."""
+
+    def __init__(self, source: str, u, aux=None, *, params=(), boundary: int = 0, ghost: float = 0.0,
+                 reduce: str = "max", tol: float = 1e-6, stream=None):
+        import torch
+        if not u.is_cuda or u.dim() != 2 or not u.is_contiguous() or u.dtype not in (torch.float32, torch.float64):
+            raise ValueError("u must be a contiguous 2D float32 or float64 CUDA tensor")
+        if aux is not None and (aux.dtype != u.dtype or aux.shape != u.shape or not aux.is_contiguous()):
+            raise ValueError("aux must match u's dtype and shape")
+        if len(params) > 8:
+            raise ValueError("at most 8 params")
+        d = slr_user_desc()
+        d.dtype = SLR_F32 if u.dtype == torch.float32 else SLR_F64
+        d.boundary, d.ny, d.nx = boundary, u.shape[0], u.shape[1]
+        d.ghost, d.tol = ghost, tol
+        d.reduce = {"max": SLR_USER_MAX, "sum": SLR_USER_SUM}[reduce]
+        for k, v in enumerate(params):
+            d.params[k] = v
+        self.desc = d
+        self.stream = stream if stream is not None else torch.cuda.current_stream(u.device)
+        lib = load()
+        ws = lib.slr_user_workspace_size(ctypes.byref(d))
+        if ws == 0:
+            raise SlrError(SLR_ERR_INVALID_ARG, "invalid user descriptor")
+        self.ws = torch.empty(ws + 256, dtype=torch.uint8, device=u.device)
+        off = (-self.ws.data_ptr()) % 256
+        self.u, self.aux = u, aux
+        h = ctypes.c_void_p()
+        st = lib.slr_user_create(ctypes.byref(d), source.encode(), u.data_ptr(),
+                                 aux.data_ptr() if aux is not None else None, self.ws.data_ptr() + off, ws,
+                                 self.stream.cuda_stream, ctypes.byref(h))
+        if st != SLR_OK:
+            raise SlrError(st, lib.slr_user_last_error(None).decode())
+        self.handle = h.value
+
+    def run(self, max_iters: int) -> int:
+        lib = load()
+        st = lib.slr_user_run_until(self.handle, max_iters)
+        if st < 0:
+            raise SlrError(st, lib.slr_user_last_error(self.handle).decode())
+        return st
+
+    def result(self):
+        """(value, iters, converged) of the last iteration."""
+        v, it, c = ctypes.c_double(), ctypes.c_int64(), ctypes.c_int32()
+        load().slr_user_reduce_value(self.handle, ctypes.byref(v), ctypes.byref(it), ctypes.byref(c))
+        return v.value, it.value, bool(c.value)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            load().slr_user_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def tune(stencil: int, u, aux=None, *, stream=None, trial_iters: int = 0, **fields) -> dict:
