@@ -585,8 +585,8 @@ struct JacobiTma {
                             const float2 t = make_float2(__fmul_rn(h2, fr.raw(k)), __fmul_rn(h2, fr.raw(k + 1)));
                             const float2 num = __fadd2_rn(t, sum);
                             // a NaN numerator passes the test and gives NaN either way
-                            amin = fminf(amin, fminf(fabsf(num.x), fabsf(num.y)));
-                            amax = fmaxf(amax, fmaxf(fabsf(num.x), fabsf(num.y)));
+                            amin = min3f(amin, fabsf(num.x), fabsf(num.y));
+                            amax = max3f(amax, fabsf(num.x), fabsf(num.y));
                             q[k] = num.x;
                             q[k + 1] = num.y;
                         }
@@ -623,7 +623,7 @@ struct JacobiTma {
                                 // max as binary32 in one op, a NaN skipped as by the
                                 // sequential test d > max
                                 const float2 dl = __ffma2_rn(o, m1, make_float2(cv.raw(k), cv.raw(k + 1)));
-                                mxf = fmaxf(mxf, fmaxf(fabsf(dl.x), fabsf(dl.y)));
+                                mxf = max3f(mxf, fabsf(dl.x), fabsf(dl.y));
                             }
                         }
                     } else {

@@ -165,20 +165,6 @@ __device__ __forceinline__ void load8(const T *row, int lane, float (&v)[8])
     Lane8<T>::widen(w, v);
 }
 
-// three-input minimum / maximum (a NaN input is ignored, as by fminf / fmaxf)
-__device__ __forceinline__ float min3f(float a, float b, float c)
-{
-    float r;
-    asm("min.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
-    return r;
-}
-__device__ __forceinline__ float max3f(float a, float b, float c)
-{
-    float r;
-    asm("max.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
-    return r;
-}
-
 // One row of a sweep: the new values of row y of the lane's cells from the old
 // rows above (a), at (c) and below (b) and f of row y; stored in place for the
 // groups inside the grid; max |delta| over the reduced groups into mx.
