@@ -23,16 +23,18 @@
 //     2-bit sums (left + self + right, and left + right) with two funnel shifts
 //     and four logic operations, takes the rows above and below by shuffle,
 //     and finishes the B3/S23 rule with six more logic operations: twelve per
-//     32 cells.  "Any cell changed" is reduced per generation over the owned
-//     cells, the live count once per pass (see the decision below).
+//     32 cells.  "Any cell changed" is reduced over the owned cells in the
+//     pass's last generation, the live count too (see the decision below).
 //  U. Unpack: the final packed grid is expanded back into the caller's uint8
 //     grid.
 //
-// After each pass a bounded grid barrier publishes the per-generation
-// reduces and every CTA takes the same decision: stop at the first generation
-// that changed nothing (a still state is a fixed point, so the packed state at
-// the end of the pass equals it), or at the iteration cap (the last pass runs
-// only the generations left).  The dead border stays dead: cells of a tile
+// After each pass a bounded grid barrier publishes the reduces and every CTA
+// takes the same decision: stop at the first generation that changed nothing
+// (a still state is a fixed point, so the packed state at the end of the pass
+// equals it), or at the iteration cap (the last pass runs only the generations
+// left).  A pass whose last generation changed nothing reached its still state
+// at some generation of the pass; it runs again from its input with a
+// "changed" flag per generation to find the first.  The dead border stays dead: cells of a tile
 // outside the grid are cleared after every generation.
 #include <cuda.h>
 #include <cudaTypedefs.h>
@@ -229,9 +231,10 @@ __device__ __forceinline__ void pair_sync(int id)
 
 // One generation of a thread's row (34 words in registers, updated in place):
 // horizontal 2-bit sums by funnel shifts and logic, the rows above and below
-// by shuffle, the B3/S23 rule.  `changed` collects owned cells that changed;
-// in the pass's last generation (LAST) `cnt` counts the owned live cells.
-template <bool WRAP, bool FULL, bool LAST>
+// by shuffle, the B3/S23 rule.  With TRACK `changed` collects owned cells that
+// changed; in the pass's last generation (LAST) `cnt` counts the owned live
+// cells.
+template <bool WRAP, bool FULL, bool LAST, bool TRACK>
 __device__ __forceinline__ void generation(uint32_t (&cur)[kWords], bool own, int own_words, bool row_in, int wlo,
                                            int whi, uint32_t &changed, uint32_t &cnt)
 {
@@ -251,7 +254,7 @@ __device__ __forceinline__ void generation(uint32_t (&cur)[kWords], bool own, in
         uint32_t nw = ((x ^ c0) & ~yy) & (C | bit0);       // n == 3, or n == 2 and alive
         if (!WRAP && !(row_in && w >= wlo && w <= whi)) nw = 0u;
         if (w >= 1 && w <= kOwnWords && own && (FULL || w <= own_words)) {
-            changed |= nw ^ C;
+            if (TRACK) changed |= nw ^ C;
             if (LAST) cnt += (uint32_t)__popc(nw);
         }
         prevC = C;
@@ -260,8 +263,9 @@ __device__ __forceinline__ void generation(uint32_t (&cur)[kWords], bool own, in
     }
 }
 
+// `exact`: track "changed" in every generation, else in the last one only
 template <bool WRAP>
-__device__ __forceinline__ void run_tile(const TbParams &tp, int tile, int kp, const unsigned int *src,
+__device__ __forceinline__ void run_tile(const TbParams &tp, int tile, int kp, int exact, const unsigned int *src,
                                          unsigned int *dst, uint32_t *xch, unsigned long long *s_cnt,
                                          unsigned int *s_ch)
 {
@@ -312,11 +316,13 @@ __device__ __forceinline__ void run_tile(const TbParams &tp, int tile, int kp, c
         // full tiles (every owned word inside the grid) drop the per-word
         // bound; the live count is taken in the pass's last generation only
         if (own_words == kOwnWords) {
-            if (j == kp - 1) generation<WRAP, true, true>(cur, own, own_words, row_in, wlo, whi, changed, cnt);
-            else generation<WRAP, true, false>(cur, own, own_words, row_in, wlo, whi, changed, cnt);
+            if (j == kp - 1) generation<WRAP, true, true, true>(cur, own, own_words, row_in, wlo, whi, changed, cnt);
+            else if (exact) generation<WRAP, true, false, true>(cur, own, own_words, row_in, wlo, whi, changed, cnt);
+            else generation<WRAP, true, false, false>(cur, own, own_words, row_in, wlo, whi, changed, cnt);
         } else {
-            if (j == kp - 1) generation<WRAP, false, true>(cur, own, own_words, row_in, wlo, whi, changed, cnt);
-            else generation<WRAP, false, false>(cur, own, own_words, row_in, wlo, whi, changed, cnt);
+            if (j == kp - 1) generation<WRAP, false, true, true>(cur, own, own_words, row_in, wlo, whi, changed, cnt);
+            else if (exact) generation<WRAP, false, false, true>(cur, own, own_words, row_in, wlo, whi, changed, cnt);
+            else generation<WRAP, false, false, false>(cur, own, own_words, row_in, wlo, whi, changed, cnt);
         }
         // refresh the two copied rows from the neighbour warps (exchange rows
         // double buffered by generation parity; 16-byte shared-memory
@@ -385,7 +391,7 @@ __global__ void __launch_bounds__(kThreads, 1) life_tb_kernel(const __grid_const
     uint64_t *mbar = (uint64_t *)(xch + kXchWords);                // [2]
     unsigned long long *s_cnt = (unsigned long long *)(mbar + 2);  // [kMaxK]
     unsigned int *s_ch = (unsigned int *)(s_cnt + kMaxK);          // [kMaxK]
-    __shared__ int s_ok, s_stop;
+    __shared__ int s_ok, s_stop, s_rerun;
     __shared__ long long s_it;
 
     const int tid = threadIdx.x;
@@ -415,43 +421,58 @@ __global__ void __launch_bounds__(kThreads, 1) life_tb_kernel(const __grid_const
     for (long long p = 0;; ++p) {
         const long long left = la.max_iters - it;
         const int kp = (int)((long long)tp.K < left ? (long long)tp.K : left);
-        for (int t = (int)blockIdx.x; t < ntiles; t += (int)gridDim.x)
-            run_tile<WRAP>(tp, t, kp, tp.bits[cur], tp.bits[cur ^ 1], xch, s_cnt, s_ch);
-        __syncthreads();
-        if (tid < kp) {
-            Slot *s = &ctl->sub[p % kSlots][tid];
-            if (s_cnt[tid]) atomicAdd(&s->cnt, s_cnt[tid]);
-            if (s_ch[tid]) atomicOr(&s->changed, 1u);
-            s_cnt[tid] = 0ull;
-            s_ch[tid] = 0u;
-        }
-        bar_target += (unsigned long long)la.nblocks;
-        if (!grid_barrier(ctl, bar_target, la.limit_ns)) return;
-        cur ^= 1;
-        if (tid < 32) {
-            if (blockIdx.x == 0) zero_slot(&ctl->sub[(p + 2) % kSlots][tid]);
-            // a generation that changed nothing is a still state, a fixed
-            // point: the state (and live count) at the end of the pass equal it.
-            // Lane j reads generation j's flag; the first unchanged one wins.
-            const bool unchanged = tid < kp && ld_relaxed_u32(&ctl->sub[p % kSlots][tid].changed) == 0u;
-            const unsigned still = __ballot_sync(0xffffffffu, unchanged);
-            const int jstop = still ? __ffs(still) - 1 : -1;
-            const unsigned long long cnt = ld_relaxed_u64(&ctl->sub[p % kSlots][kp - 1].cnt);
-            const long long itn = jstop >= 0 ? it + jstop + 1 : it + kp;
-            const int conv = jstop >= 0;
-            if (tid == 0) {
-                s_stop = conv || itn >= la.max_iters;
-                s_it = itn;
-                if ((conv || itn >= la.max_iters) && blockIdx.x == 0) {
-                    ctl->iters = itn;
-                    ctl->value = (double)cnt;
-                    ctl->count = cnt;
-                    ctl->changed = !conv;
-                    ctl->converged = conv;
+        // A pass tracks "changed" in its last generation only.  A still state
+        // stays still, so the last generation changed nothing exactly when some
+        // generation of the pass did; the pass then runs again from its input
+        // (untouched: the buffers alternate) with a flag per generation, into
+        // the next pass's slots, to find the first.
+        int exact = 0;
+        int slot = (int)(p % kSlots);
+        for (;;) {
+            for (int t = (int)blockIdx.x; t < ntiles; t += (int)gridDim.x)
+                run_tile<WRAP>(tp, t, kp, exact, tp.bits[cur], tp.bits[cur ^ 1], xch, s_cnt, s_ch);
+            __syncthreads();
+            if (tid < kp) {
+                Slot *s = &ctl->sub[slot][tid];
+                if (s_cnt[tid]) atomicAdd(&s->cnt, s_cnt[tid]);
+                if (s_ch[tid]) atomicOr(&s->changed, 1u);
+                s_cnt[tid] = 0ull;
+                s_ch[tid] = 0u;
+            }
+            bar_target += (unsigned long long)la.nblocks;
+            if (!grid_barrier(ctl, bar_target, la.limit_ns)) return;
+            if (tid < 32) {
+                if (blockIdx.x == 0 && !exact) zero_slot(&ctl->sub[(p + 2) % kSlots][tid]);
+                // a generation that changed nothing is a still state, a fixed
+                // point: the state (and live count) at the end of the pass equal
+                // it.  Lane j reads generation j's flag; the first unchanged one wins.
+                const bool unchanged = tid < kp && (exact || tid == kp - 1) &&
+                                       ld_relaxed_u32(&ctl->sub[slot][tid].changed) == 0u;
+                const unsigned still = __ballot_sync(0xffffffffu, unchanged);
+                const int jstop = still ? __ffs(still) - 1 : -1;
+                const int rerun = !exact && jstop >= 0;
+                const unsigned long long cnt = ld_relaxed_u64(&ctl->sub[slot][kp - 1].cnt);
+                const long long itn = jstop >= 0 ? it + jstop + 1 : it + kp;
+                const int conv = jstop >= 0;
+                if (tid == 0) {
+                    s_rerun = rerun;
+                    s_stop = !rerun && (conv || itn >= la.max_iters);
+                    s_it = itn;
+                    if (!rerun && (conv || itn >= la.max_iters) && blockIdx.x == 0) {
+                        ctl->iters = itn;
+                        ctl->value = (double)cnt;
+                        ctl->count = cnt;
+                        ctl->changed = !conv;
+                        ctl->converged = conv;
+                    }
                 }
             }
+            __syncthreads();
+            if (!s_rerun) break;
+            exact = 1;
+            slot = (int)((p + 1) % kSlots);
         }
-        __syncthreads();
+        cur ^= 1;
         it = s_it;
         if (s_stop) break;
     }
