@@ -170,7 +170,8 @@ slr_status slr_state_to_frame(const void *state, void *img, int64_t n, void *str
 // image's border.  A warp owns a strip of 256 columns (8 consecutive pixels
 // per lane, one 8-byte access per row) and marches down a segment of rows,
 // keeping rows i-1, i, i+1 unpacked in registers (three rows per turn, no
-// copies): each pixel is read from memory once and written once.  The
+// copies), each row's bytes loaded one row ahead of their use: each pixel is
+// read from memory once and written once.  The
 // neighbours across lanes come by shuffles of the column sums; the strip's two
 // outer columns by single loads.  The clamped integer square root is the
 // hardware estimate of sqrt(n + 1/2), truncated (exact: isqrt_clamp255).
@@ -182,18 +183,21 @@ constexpr int kPW = kPx / 4;                      // 32-bit words per lane and r
 constexpr int kSobelStrip = 32 * kPx;             // columns per warp
 constexpr int kSobelWarps = 8;
 
-__device__ __forceinline__ void sobel_load(const unsigned char *img, int nx, int y, int x0, bool vec, int (&v)[kPx])
+// the lane's 8 bytes of row y (0 outside the image)
+__device__ __forceinline__ uint2 sobel_raw(const unsigned char *img, int nx, int ny, int y, int x0, bool vec)
 {
+    if (y < 0 || y >= ny || x0 >= nx) return make_uint2(0u, 0u);
     const unsigned char *row = img + (size_t)y * nx;
-    if (vec) {
-        const uint2 w = *(const uint2 *)(row + x0);
-        const uint32_t ws[2] = {w.x, w.y};
+    if (vec) return *(const uint2 *)(row + x0);
+    uint32_t w[2] = {0u, 0u};
+    for (int k = 0; k < kPx && x0 + k < nx; ++k) w[k >> 2] |= (uint32_t)row[x0 + k] << (8 * (k & 3));
+    return make_uint2(w[0], w[1]);
+}
+
+__device__ __forceinline__ void unpack8(uint2 r, int (&v)[kPx])
+{
 #pragma unroll
-        for (int k = 0; k < kPx; ++k) v[k] = (ws[k >> 2] >> (8 * (k & 3))) & 0xFFu;
-    } else {
-#pragma unroll
-        for (int k = 0; k < kPx; ++k) v[k] = x0 + k < nx ? row[x0 + k] : 0;
-    }
+    for (int k = 0; k < kPx; ++k) v[k] = ((k < 4 ? r.x : r.y) >> (8 * (k & 3))) & 0xFFu;
 }
 
 // output row y of the lane's pixels from rows y-1 (a), y (c), y+1 (b);
@@ -275,19 +279,21 @@ __global__ void __launch_bounds__(32 * kSobelWarps) sobel_kernel(const unsigned 
     for (int k = 0; k < kPx; ++k)
         if (x0 + k == 0 || x0 + k == nx - 1) keep[k >> 2] &= ~(0xFFu << (8 * (k & 3)));
     int R0[kPx], R1[kPx], R2[kPx];
-    if (y0 > 0) sobel_load(img, nx, y0 - 1, x0, vec, R0);
-    else
-#pragma unroll
-        for (int k = 0; k < kPx; ++k) R0[k] = 0;
-    sobel_load(img, nx, y0, x0, vec, R1);
+    unpack8(sobel_raw(img, nx, ny, y0 - 1, x0, vec), R0);
+    unpack8(sobel_raw(img, nx, ny, y0, x0, vec), R1);
+    // the next row's bytes are loaded one row ahead of their use
+    uint2 nxt = sobel_raw(img, nx, ny, y0 + 1, x0, vec);
     for (int y = y0; y < y1; y += 3) {
-        if (y + 1 < ny) sobel_load(img, nx, y + 1, x0, vec, R2);
+        unpack8(nxt, R2);
+        nxt = sobel_raw(img, nx, ny, y + 2, x0, vec);
         sobel_row(img, out, nx, ny, y, x0, vec, keep, R0, R1, R2);
         if (y + 1 >= y1) break;
-        if (y + 2 < ny) sobel_load(img, nx, y + 2, x0, vec, R0);
+        unpack8(nxt, R0);
+        nxt = sobel_raw(img, nx, ny, y + 3, x0, vec);
         sobel_row(img, out, nx, ny, y + 1, x0, vec, keep, R1, R2, R0);
         if (y + 2 >= y1) break;
-        if (y + 3 < ny) sobel_load(img, nx, y + 3, x0, vec, R1);
+        unpack8(nxt, R1);
+        nxt = sobel_raw(img, nx, ny, y + 4, x0, vec);
         sobel_row(img, out, nx, ny, y + 2, x0, vec, keep, R2, R0, R1);
     }
 }
