@@ -489,7 +489,8 @@ __device__ double slr_delta(slr_t a, slr_t b) { return fabs(a - b); }
             us.close()
     user_ms = (time.perf_counter() - t0) / max(args.steps, 3) * 1e3
     res["user_functions"] = {"ms_per_solve": user_ms, "iters": uit, "gcell_per_s": n * n * uit / user_ms / 1e6,
-                             "what": "slr_update / slr_delta compiled at run time, host test per sweep"}
+                             "what": "slr_update / slr_delta compiled at run time, the loop in one cooperative "
+                                     "launch; wall time per solve including the handle's set-up and result read"}
     t0 = time.perf_counter()
     _, rr = oracle.j2d5(np.zeros((n, n)), f.cpu().numpy(), tol=1e-6, max_iters=5000)
     cpu_ms = (time.perf_counter() - t0) * 1e3

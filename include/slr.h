@@ -255,8 +255,9 @@ slr_status slr_sobel(const void *img, void *out, int64_t nx, int64_t ny, void *s
  * slr_delta(new, old) over all items by max (identity -inf, NaN skipped) or
  * sum (identity 0; per-CTA partials then a fold, in a fixed order: the same
  * inputs give the same value on every run), and stops when the value is below
- * tol or at the cap; the host reads the value after every iteration (the
- * schema of Fig. 2).  Programs are cached per (source, dtype).  Compile errors
+ * tol or at the cap, in one cooperative launch by default or with the host
+ * reading the value after every iteration (the schema of Fig. 2; desc.loop).
+ * Programs are cached per (source, dtype).  Compile errors
  * return SLR_ERR_INVALID_ARG with the compiler's log in
  * slr_user_last_error(NULL). */
 typedef enum { SLR_USER_MAX = 0, SLR_USER_SUM = 1 } slr_user_reduce;
@@ -268,7 +269,10 @@ typedef struct {
     double ghost;          /* value outside the grid for SLR_DIRICHLET */
     double tol;            /* stop when the reduced value < tol */
     int32_t reduce;        /* slr_user_reduce */
-    int32_t reserved;      /* 0 */
+    int32_t loop;          /* slr_loop: AUTO or PERSISTENT = the whole loop in one cooperative
+                              launch (bounded grid barrier, the test on the device); HOST =
+                              a sweep and a fold launch and a host test per iteration.  Both
+                              give the same values. */
     double params[8];      /* constants handed to slr_update as p */
 } slr_user_desc;
 

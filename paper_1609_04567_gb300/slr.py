@@ -60,7 +60,7 @@ class slr_user_desc(ctypes.Structure):
     _fields_ = [
         ("dtype", ctypes.c_int32), ("boundary", ctypes.c_int32), ("nx", ctypes.c_int64), ("ny", ctypes.c_int64),
         ("ghost", ctypes.c_double), ("tol", ctypes.c_double), ("reduce", ctypes.c_int32),
-        ("reserved", ctypes.c_int32), ("params", ctypes.c_double * 8),
+        ("loop", ctypes.c_int32), ("params", ctypes.c_double * 8),
     ]
 
 
@@ -444,7 +444,7 @@ class UserSolver:
     updated in place; ``aux`` (same dtype and shape) or None."""
 
     def __init__(self, source: str, u, aux=None, *, params=(), boundary: int = 0, ghost: float = 0.0,
-                 reduce: str = "max", tol: float = 1e-6, stream=None):
+                 reduce: str = "max", tol: float = 1e-6, loop: int = 0, stream=None):
         import torch
         if not u.is_cuda or u.dim() != 2 or not u.is_contiguous() or u.dtype not in (torch.float32, torch.float64):
             raise ValueError("u must be a contiguous 2D float32 or float64 CUDA tensor")
@@ -457,6 +457,7 @@ class UserSolver:
         d.boundary, d.ny, d.nx = boundary, u.shape[0], u.shape[1]
         d.ghost, d.tol = ghost, tol
         d.reduce = {"max": SLR_USER_MAX, "sum": SLR_USER_SUM}[reduce]
+        d.loop = loop
         for k, v in enumerate(params):
             d.params[k] = v
         self.desc = d

@@ -90,3 +90,32 @@ def test_compile_errors_report_the_log(gpu):
     with pytest.raises(gpu.SlrError, match="does not compile") as e:
         gpu.UserSolver("__device__ slr_t slr_update(const slr_nbr &u) { return undefined_name; }", u)
     assert "undefined_name" in str(e.value)
+
+
+@pytest.mark.parametrize("dtype", ["f32", "f64"])
+def test_device_and_host_loops_agree(gpu, orc, dtype):
+    # the cooperative loop and the host-driven loop give the same state, value
+    # and count (max reduce: Jacobi; sum reduce: Life)
+    from paper_1609_04567_gb300 import inputs
+    f64 = inputs.helmholtz_rhs((70, 90), seed=9)
+    h2, d = jacobi_constants(90)
+    tdt = torch.float32 if dtype == "f32" else torch.float64
+    f = torch.from_numpy(f64).to(tdt).cuda()
+    params = (float(np.float32(h2)), float(np.float32(d))) if dtype == "f32" else (h2, d)
+    out = []
+    for loop in (gpu.SLR_LOOP_PERSISTENT, gpu.SLR_LOOP_HOST):
+        u = torch.zeros((70, 90), dtype=tdt, device="cuda")
+        s = gpu.UserSolver(JACOBI, u, f, params=params, tol=1e-6, loop=loop)
+        s.run(5000)
+        out.append((s.result(), u.cpu().numpy()))
+        s.close()
+    assert out[0][0] == out[1][0] and np.array_equal(out[0][1], out[1][1])
+    cells = inputs.life_cells(33, 47, seed=4).astype(np.float32)
+    res = []
+    for loop in (gpu.SLR_LOOP_PERSISTENT, gpu.SLR_LOOP_HOST):
+        u = torch.from_numpy(cells).cuda()
+        s = gpu.UserSolver(LIFE, u, boundary=1, reduce="sum", tol=0.5, loop=loop)
+        s.run(300)
+        res.append((s.result(), u.cpu().numpy()))
+        s.close()
+    assert res[0][0] == res[1][0] and np.array_equal(res[0][1], res[1][1])
