@@ -23,7 +23,7 @@ def test_matches_oracle(gpu, orc, ny, nx, wmax):
 
 
 @pytest.mark.parametrize("p", [0.1, 0.3, 0.8, 0.95])
-@pytest.mark.parametrize("wmax", [5, 9])
+@pytest.mark.parametrize("wmax", [5, 9, 11, 13])
 def test_noise_levels(gpu, orc, p, wmax):
     from paper_1609_04567_gb300 import inputs
     frame, _ = inputs.noisy_frame(120, 200, seed=5, p_noise=p)

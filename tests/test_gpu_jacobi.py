@@ -16,7 +16,9 @@ TORCH = {"f64": torch.float64, "f32": torch.float32, "bf16": torch.bfloat16, "f1
 
 
 def rel_err(a, b):
-    return float(np.max(np.abs(a.astype(np.float64) - b.astype(np.float64))) / max(np.max(np.abs(b)), 1e-300))
+    # in binary64 throughout: an all-zero reference must not divide 0 by a 1e-300 rounded to 0
+    return float(np.max(np.abs(a.astype(np.float64) - b.astype(np.float64)))) / max(
+        float(np.max(np.abs(b.astype(np.float64)))), 1e-300)
 
 
 def prepare(f64, storage):

@@ -89,8 +89,17 @@ def test_requests_it_does_not_apply_to_fall_back(gpu, orc, storage, kw):
     jacobi_case(gpu, orc, shape, storage=storage, tol=0.0, max_iters=11, temporal_k=8, **kw)
 
 
+@pytest.mark.parametrize("storage,kw", [("f32", dict(sigma=0.0)), ("bf16", dict(h=0.01, sigma=3.0)),
+                                        ("f32", dict(sigma=1e20)), ("f16", dict(sigma=1e20))])
+def test_other_constants(gpu, orc, storage, kw):
+    # Poisson (sigma 0), another mesh width, and a divisor outside the range of
+    # the corrected quotient (every division through the IEEE operation)
+    jacobi_case(gpu, orc, (150, 264), storage=storage, tol=0.0, max_iters=19, temporal_k=8, **kw)
+
+
 @pytest.mark.slow
 def test_full_size_2d(gpu, orc):
     # the large single grids of the Jacobi bench: one whole pass and one sweep
     jacobi_case(gpu, orc, (8192, 8192), storage="f32", tol=0.0, max_iters=9, temporal_k=8)
     jacobi_case(gpu, orc, (8192, 8192), storage="bf16", tol=0.0, max_iters=9, temporal_k=8)
+    jacobi_case(gpu, orc, (8192, 8192), storage="f16", tol=0.0, max_iters=9, temporal_k=8)
