@@ -51,3 +51,25 @@ def test_solo_lane_rule(solo_cells):
     assert srv.is_solo(big) == (solo_cells is not None)
     assert srv.is_solo(small) == (solo_cells == 1)
     assert not srv.is_solo(solve)                       # solves stay in the batch
+
+
+def test_video_streams_are_seeded_permutations():
+    # every round of a stream deals each distinct frame once; the same seed
+    # gives the same stream
+    from paper_1609_04567_gb300 import video
+    frames, order = video.make_video(24, 40, 10, distinct=4)
+    frames2, order2 = video.make_video(24, 40, 10, distinct=4)
+    assert order == order2 and all((a == b).all() for a, b in zip(frames, frames2))
+    assert sorted(order[:4]) == [0, 1, 2, 3] and sorted(order[4:8]) == [0, 1, 2, 3]
+    assert len(frames) == 10 and frames[0].dtype.name == "uint8"
+    for k, i in enumerate(order):
+        assert (frames[k] == frames[order.index(i)]).all()
+
+
+def test_random_images_are_seeded_and_uniform():
+    import numpy as np
+    from paper_1609_04567_gb300 import inputs
+    a = inputs.random_image(64, 96, seed=3)
+    assert (a == inputs.random_image(64, 96, seed=3)).all() and not (a == inputs.random_image(64, 96, seed=4)).all()
+    counts = np.bincount(a.reshape(-1), minlength=256)
+    assert counts.min() > 0 and abs(a.mean() - 127.5) < 3
