@@ -113,8 +113,9 @@ typedef struct {
     int32_t loop;          /* slr_loop */
     int32_t math;          /* slr_math */
     int32_t temporal_k;    /* sweeps per HBM pass, 1 = one.  Life: 1 .. 32.  SLR_J2D5 with
-                              binary32 arithmetic (storage F32, BF16 or F16), Dirichlet
-                              ghost +0, rows of whole 16-byte groups: 1 .. 8 (larger values
+                              binary32 arithmetic (storage F32, BF16 or F16), a Dirichlet
+                              ghost exact in the storage type, rows of whole 16-byte
+                              groups: 1 .. 8 (larger values
                               run 8; a solve that stops inside a pass recomputes that pass
                               up to the stopping sweep, so results equal those of k = 1).
                               0 = library choice: the autotuner's, else for Life the

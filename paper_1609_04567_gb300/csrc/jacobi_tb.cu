@@ -5,18 +5,19 @@
 // Sec. 4.1, u' = (h^2 f + ((u_N + u_S) + u_W) + u_E) / (4 + sigma h^2), in
 // binary32 arithmetic with the state stored as binary32, bfloat16 or binary16
 // (every new value rounded to the storage type, the change taken between
-// stored values), Dirichlet ghost 0, reduce max |u' - u|, stop at the first
+// stored values), a Dirichlet ghost value, reduce max |u' - u|, stop at the first
 // sweep whose reduced value is below tol or at the iteration cap.
 //
 // Tiles.  A pass cuts the grid into tiles of 240 owned columns by H - 16 owned
 // rows (H = 112 rows for 4-byte storage, 224 for 2-byte storage).  A CTA
 // loads a tile's state and f with a halo of 8 cells on every side, 256 x H
-// cells each, by two TMA boxes (the hardware's zero fill outside the grid is
-// the ghost 0), runs k <= 8 sweeps on them in shared memory, and stores the
-// owned cells to the other state buffer.  Sweep s updates the tile rows
-// s .. H-1-s; cells within s of the tile's edge are out of date after s
-// sweeps, the owned cells never are.  Cells outside the grid are never
-// written and stay 0.
+// cells each, by two TMA boxes (the hardware fills the cells outside the
+// grid with 0; for another Dirichlet ghost value, which must be exact in the
+// storage type, the border tiles then set them to it), runs k <= 8 sweeps on
+// them in shared memory, and stores the owned cells to the other state
+// buffer.  Sweep s updates the tile rows s .. H-1-s; cells within s of the
+// tile's edge are out of date after s sweeps, the owned cells never are.
+// Cells outside the grid are never written and keep the ghost value.
 //
 // Threads.  16 warps; warp w owns tile rows [w R, (w+1) R) (R = H / 16) and
 // updates them in place, top to bottom, keeping the old rows y-1, y, y+1 of
@@ -87,6 +88,8 @@ struct JTb {
     int K;                      // sweeps per pass
     float h2, d, yd;            // h^2, 4 + sigma h^2, RN(1 / d)
     int dconst;                 // d in the range of the corrected quotient
+    T ghost;                    // the Dirichlet ghost value in storage form
+    int ghost_fill;             // the ghost is not +0: cells outside the grid are set to it
 };
 
 // ---- the eight cells of a lane in a row ------------------------------------
@@ -321,6 +324,14 @@ __device__ bool tb_pass(const JTb<T> &tp, unsigned char *smem, uint64_t *bar, un
         const bool ok = tma::bounded_wait(bar, phase & 1u, la.limit_ns, &la.ctl->err);
         ++phase;
         if (!__syncthreads_and(ok)) return false;
+        if (tp.ghost_fill && (x0 < 0 || x0 + kTW > tp.nx || y0 < 0 || y0 + Sh::kH > tp.ny)) {
+            // the copy filled the cells outside the grid with +0: they hold the ghost
+            for (int i = tid; i < kTW * Sh::kH; i += kTThreads) {
+                const int gy = y0 + i / kTW, gx = x0 + i % kTW;
+                if (gy < 0 || gy >= tp.ny || gx < 0 || gx >= tp.nx) S[i] = tp.ghost;
+            }
+            __syncthreads();
+        }
         const int yin_lo = y0 < 0 ? -y0 : 0;
         const int yin_hi = tp.ny - y0 < Sh::kH ? tp.ny - y0 : Sh::kH;
         bool gin[2] = {false, false}, red[2] = {false, false};
@@ -473,6 +484,8 @@ cudaError_t run_tb(const Problem &p, LoopArgs la, int K, cudaStream_t st)
     tp.d = p.df;
     tp.yd = host_rcp_rn(p.df);
     tp.dconst = div_const_ok(p.df);
+    tp.ghost = (T)p.ghostf;
+    tp.ghost_fill = p.ghostf != 0.0f || std::signbit(p.ghostf);
     auto kern = jacobi_tb_kernel<T>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Sh::kSmem);
     if (e != cudaSuccess) return e;
@@ -489,12 +502,31 @@ size_t elem_bytes(int storage)
     }
 }
 
+// The ghost value as the tile holds it (storage form) must be the value the
+// update reads: exactly representable in the storage type.
+bool ghost_exact(const Problem &p)
+{
+    const float g = p.ghostf;
+    if (g != g) return false;
+    switch (p.storage) {
+    case SLR_F32: return true;
+    case SLR_BF16: {
+        uint32_t b;
+        memcpy(&b, &g, 4);
+        return (b & 0xFFFFu) == 0u;
+    }
+    case SLR_F16: return __half2float(__float2half_rn(g)) == g && (g != 0.0f || !std::signbit(g) ||
+                                                                    std::signbit(__half2float(__float2half_rn(g))));
+    default: return false;
+    }
+}
+
 }  // namespace
 
 bool jacobi_tb_supported(const Problem &p, const void *a, const void *b, const void *f)
 {
     const size_t es = elem_bytes(p.storage);
-    if (p.stencil != SLR_J2D5 || es == 0 || p.wrap || p.ghost != 0.0 || std::signbit(p.ghost)) return false;
+    if (p.stencil != SLR_J2D5 || es == 0 || p.wrap || !ghost_exact(p)) return false;
     if ((p.nx * (long long)es) % 16 != 0 || p.nx >= (1ll << 31) - 4096 || p.ny >= (1ll << 31) - 4096) return false;
     if (((uintptr_t)a | (uintptr_t)b | (uintptr_t)f) % 16 != 0) return false;
     return tma::encode_fn() != nullptr;

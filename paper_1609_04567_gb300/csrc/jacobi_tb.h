@@ -10,7 +10,8 @@ constexpr int kJacobiTbMaxK = 8;
 
 // Whether the temporal-blocked loop accepts p with state buffers a, b and
 // right-hand side f: SLR_J2D5, binary32 arithmetic (storage F32, BF16 or F16),
-// Dirichlet ghost +0, rows of whole 16-byte groups, 16-byte aligned arrays.
+// a Dirichlet ghost value exact in the storage type, rows of whole 16-byte
+// groups, 16-byte aligned arrays.
 bool jacobi_tb_supported(const Problem &p, const void *a, const void *b, const void *f);
 
 // Sweeps per pass for p: 1 (the one-sweep kernels) for temporal_k 1 or a

@@ -79,14 +79,22 @@ def test_cap_and_resume(gpu, orc):
     assert np.array_equal(u.cpu().numpy().view(np.uint32), ref.view(np.uint32))
 
 
-@pytest.mark.parametrize("storage,kw", [("f32", dict(wrap=True)), ("f32", dict(ghost=0.25)),
-                                        ("f64", dict()), ("bf16", dict()), ("f32", dict(ghost=-0.0))])
+@pytest.mark.parametrize("storage,kw", [("f32", dict(wrap=True)), ("f64", dict()), ("bf16", dict()),
+                                        ("bf16", dict(ghost=0.1))])
 def test_requests_it_does_not_apply_to_fall_back(gpu, orc, storage, kw):
-    # periodic boundary, a non-zero (or negative-zero) ghost, binary64 state, and
-    # 2-byte rows that are not whole 16-byte groups (nx = 36) run the
+    # periodic boundary, binary64 state, 2-byte rows that are not whole 16-byte
+    # groups (nx = 36), and a ghost value bfloat16 cannot hold run the
     # one-sweep-per-pass loop
     shape = (40, 36) if storage == "bf16" and not kw else (40, 64)
     jacobi_case(gpu, orc, shape, storage=storage, tol=0.0, max_iters=11, temporal_k=8, **kw)
+
+
+@pytest.mark.parametrize("storage,ghost", [("f32", 0.25), ("f32", -0.0), ("f32", 1.0 / 3.0), ("bf16", 0.75),
+                                           ("f16", -1.5), ("bf16", -0.0)])
+@pytest.mark.parametrize("shape", [(130, 500), (33, 40)])
+def test_dirichlet_ghost_values(gpu, orc, storage, ghost, shape):
+    # the tiles' cells outside the grid hold the ghost value, to convergence
+    jacobi_case(gpu, orc, shape, storage=storage, tol=1e-5, max_iters=3000, temporal_k=8, ghost=ghost)
 
 
 @pytest.mark.parametrize("storage,kw", [("f32", dict(sigma=0.0)), ("bf16", dict(h=0.01, sigma=3.0)),
