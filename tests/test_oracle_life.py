@@ -144,3 +144,64 @@ def test_life_is_equivariant_under_torus_symmetries(orc):
     assert np.array_equal(sh, np.roll(out, (5, -7), axis=(0, 1)))
     tr, _ = orc.life(g.T, wrap=True, max_gens=12)
     assert np.array_equal(tr, out.T)
+
+
+def _next_by_definition(g, wrap):
+    """Conway's rule applied from its statement, independently of the oracle:
+    a dead cell with exactly three live neighbours is born, a live cell with two
+    or three survives, every other cell is dead next.  Neighbours are the eight
+    cells at offsets (dy, dx) != (0, 0), |dy|, |dx| <= 1, taken modulo the
+    extents on the torus and dead outside the grid otherwise."""
+    ny, nx = g.shape
+    out = np.zeros_like(g)
+    for y in range(ny):
+        for x in range(nx):
+            n = 0
+            for dy in (-1, 0, 1):
+                for dx in (-1, 0, 1):
+                    if dy == 0 and dx == 0:
+                        continue
+                    yy, xx = y + dy, x + dx
+                    if wrap:
+                        n += int(g[yy % ny, xx % nx] != 0)
+                    elif 0 <= yy < ny and 0 <= xx < nx:
+                        n += int(g[yy, xx] != 0)
+            alive = g[y, x] != 0
+            out[y, x] = 1 if (n in (2, 3) if alive else n == 3) else 0
+    return out
+
+
+def test_rule_table_over_all_512_neighbourhoods(orc):
+    # Each of the 2^9 states of a 3 x 3 block (bit 4 = the centre) placed side
+    # by side: a block's centre sees only its own block, so one generation of
+    # the whole grid evaluates the rule on every neighbourhood at once.
+    rows, cols = 16, 32
+    g = np.zeros((3 * rows, 3 * cols), dtype=np.uint8)
+    for cfg in range(512):
+        by, bx = divmod(cfg, cols)
+        for b in range(9):
+            g[3 * by + b // 3, 3 * bx + b % 3] = (cfg >> b) & 1
+    for wrap in (True, False):
+        out, _ = orc.life(g, wrap=wrap, max_gens=1)
+        for cfg in range(512):
+            by, bx = divmod(cfg, cols)
+            alive = (cfg >> 4) & 1
+            n = bin(cfg & ~(1 << 4)).count("1")
+            born_or_survives = n == 3 or (alive == 1 and n == 2)
+            assert out[3 * by + 1, 3 * bx + 1] == int(born_or_survives), (cfg, wrap)
+
+
+@pytest.mark.parametrize("shape,wrap", [((8, 8), True), ((8, 8), False), ((7, 13), True), ((5, 9), False)])
+def test_brute_force_generations_on_small_grids(orc, shape, wrap):
+    # Generation by generation against the rule evaluated from its statement,
+    # with the loop's reduces: the live count and whether any cell changed.
+    from paper_1609_04567_gb300 import inputs
+    g = inputs.life_cells(shape[0], shape[1], seed=5 + shape[1])
+    for _ in range(12):
+        expect = _next_by_definition(g, wrap)
+        out, r = orc.life(g, wrap=wrap, max_gens=1)
+        assert np.array_equal(out, expect)
+        assert r.iters == 1 and r.count == int(expect.sum())
+        assert bool(r.changed) == bool((expect != g).any())
+        assert bool(r.converged) == (not (expect != g).any())
+        g = out

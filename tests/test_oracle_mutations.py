@@ -48,6 +48,20 @@ MUTATIONS = [
     ("Life wrap-around off by one to the west",
      "                        if (wrap) { y = wrap_index(y, ny); x = wrap_index(x, nx); }",
      "                        if (wrap) { y = wrap_index(y, ny); x = wrap_index(x + (x < 0), nx); }"),
+    ("Life counts the cell itself as a neighbour",
+     "                        if (di == 0 && dj == 0) continue;\n                        int64_t y = i + di, x = j + dj;\n"
+     "                        if (wrap) {",
+     "                        int64_t y = i + di, x = j + dj;\n"
+     "                        if (wrap) {"),
+    ("Life also births on six neighbours (HighLife)",
+     "                int next = (alive_nbrs == 3) || (self && alive_nbrs == 2);",
+     "                int next = (alive_nbrs == 3) || (!self && alive_nbrs == 6) || (self && alive_nbrs == 2);"),
+    ("Life dead border wraps its columns",
+     "                        else if (y < 0 || y >= ny || x < 0 || x >= nx) continue;\n"
+     "                        alive_nbrs",
+     "                        else if (y < 0 || y >= ny) continue;\n"
+     "                        else if (x < 0 || x >= nx) x = wrap_index(x, nx);\n"
+     "                        alive_nbrs"),
     ("restoration skips a neighbour",
      "                        if (di == 0 && dj == 0) continue;\n                        int64_t y = i + di, x = j + dj;\n"
      "                        if (y < 0 || y >= ny || x < 0 || x >= nx) continue;\n                        float uj",
