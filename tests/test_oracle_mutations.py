@@ -126,7 +126,8 @@ def run_pins(tmp_path, source: str) -> subprocess.CompletedProcess:
     shutil.copytree(os.path.join(ROOT, "tests", "golden"), work / "tests" / "golden")
     shutil.copy(os.path.join(ROOT, "pytest.ini"), work / "pytest.ini")
     env = dict(os.environ, PYTHONPATH=ROOT)     # the input generators come from the package
-    return subprocess.run([sys.executable, "-m", "pytest", "-q", "-x", "-m", "not gpu", "tests"],
+    # the exhaustive (slow) pins run once in the main suite, not for every mutant
+    return subprocess.run([sys.executable, "-m", "pytest", "-q", "-x", "-m", "not gpu and not slow", "tests"],
                           cwd=work, env=env, capture_output=True, text=True, timeout=300)
 
 

@@ -1,8 +1,9 @@
 """Pins for the oracle's storage rounding (bfloat16 and binary16, round to
 nearest even): compared with torch's and numpy's own conversions on every
-exponent, around every rounding boundary and on a random sample of bit
-patterns.  NaNs are compared by class only."""
+exponent, around every rounding boundary, on a random sample of bit patterns
+and (marked slow) on all 2^32 of them.  NaNs are compared by class only."""
 import numpy as np
+import pytest
 import torch
 
 
@@ -54,3 +55,24 @@ def test_round_storage_roundtrip(orc):
     h = orc.round_storage(x, "f16")
     assert np.array_equal(h, x.astype(np.float16).astype(np.float32))
     assert np.array_equal(orc.round_storage(x, "f32"), x)
+
+
+@pytest.mark.slow
+def test_bf16_and_f16_over_every_binary32_pattern(orc):
+    # All 2^32 bit patterns, in chunks: the oracle's bit-level rounding to
+    # nearest even against torch's bfloat16 and binary16 conversions (their
+    # own implementations of the same rule); NaNs by class.
+    chunk = 1 << 25
+    base = np.arange(chunk, dtype=np.uint32)
+    for c in range((1 << 32) // chunk):
+        x = (base + np.uint32(c * chunk)).view(np.float32)
+        ob = orc.f32_to_bf16_array(x)
+        tb = torch.from_numpy(x).to(torch.bfloat16).view(torch.int16).numpy().view(np.uint16)
+        oh = orc.f32_to_f16_array(x)
+        nh = torch.from_numpy(x).to(torch.float16).view(torch.int16).numpy().view(np.uint16)
+        for ours, ref, exp_mask, man_mask in ((ob, tb, 0x7F80, 0x7F), (oh, nh, 0x7C00, 0x3FF)):
+            diff = ours != ref
+            if diff.any():
+                assert np.all(np.isnan(x[diff])), f"chunk {c}: non-NaN input rounded differently"
+                bad = ours[diff]
+                assert np.all((bad & exp_mask) == exp_mask) and np.all(bad & man_mask)
