@@ -1,0 +1,147 @@
+"""Argument checks of the C ABI that run before any CUDA call.
+
+Every call below is refused by the library's own validation, so nothing is
+launched and no pointer is dereferenced (the pointers are made-up integers);
+the tests need no GPU.  They pin the documented error behaviour of
+include/slr.h: the status, and a message that names the problem."""
+import ctypes
+
+import pytest
+
+FAKE_U, FAKE_AUX, FAKE_WS = 0x100000, 0x900000, 0x2000000
+
+
+@pytest.fixture(scope="module")
+def slr():
+    from paper_1609_04567_gb300 import build, slr as binding
+    build.build()
+    binding.load()
+    return binding
+
+
+def test_detection_refuses_bad_arguments(slr):
+    cases = [
+        (dict(img=0), "device pointers"),
+        (dict(nx=0), "[1, 2^31)"),
+        (dict(wmax=4), "odd"),
+        (dict(wmax=1), "odd"),
+        (dict(wmax=17), "odd"),
+        (dict(mask=FAKE_U + 100), "overlap"),                  # mask inside the image
+        (dict(state=FAKE_AUX - 8), "overlap"),                 # state runs into the mask
+        (dict(state=FAKE_WS + 2), "4-byte aligned"),
+        (dict(ny=65536 * 8 + 1), "rows"),                      # more row blocks than a grid holds
+    ]
+    for change, words in cases:
+        a = dict(img=FAKE_U, mask=FAKE_AUX, state=FAKE_WS, nx=64, ny=64, wmax=7)
+        a.update(change)
+        if "ny" in change:
+            a.update(nx=1, mask=FAKE_U + (1 << 24), state=FAKE_U + (1 << 26))
+        with pytest.raises(slr.SlrError) as e:
+            slr.slr_detect_noise(a["img"], a["mask"], a["state"], a["nx"], a["ny"], a["wmax"])
+        assert e.value.status == slr.SLR_ERR_INVALID_ARG, change
+        assert words in slr.slr_last_error(None), (change, slr.slr_last_error(None))
+
+
+def test_sobel_refuses_bad_arguments(slr):
+    for img, out, nx, ny, words in [(0, FAKE_AUX, 64, 64, "device pointers"),
+                                    (FAKE_U, 0, 64, 64, "device pointers"),
+                                    (FAKE_U, FAKE_AUX, 0, 64, "[1, 2^31 - 4096)"),
+                                    (FAKE_U, FAKE_AUX, 64, -1, "[1, 2^31 - 4096)"),
+                                    (FAKE_U, FAKE_U + 63, 64, 64, "overlap")]:
+        with pytest.raises(slr.SlrError) as e:
+            slr.slr_sobel(img, out, nx, ny)
+        assert e.value.status == slr.SLR_ERR_INVALID_ARG
+        assert words in slr.slr_last_error(None)
+
+
+def test_state_to_frame_refuses_bad_arguments(slr):
+    for state, img, n in [(0, FAKE_AUX, 16), (FAKE_U, 0, 16), (FAKE_U + 2, FAKE_AUX, 16), (FAKE_U, FAKE_AUX, -1)]:
+        with pytest.raises(slr.SlrError) as e:
+            slr.slr_state_to_frame(state, img, n)
+        assert e.value.status == slr.SLR_ERR_INVALID_ARG
+    # an empty state is a no-op: nothing is enqueued
+    assert slr.slr_state_to_frame(FAKE_U, FAKE_AUX, 0) == slr.SLR_OK
+
+
+def test_static_solve_refuses_what_its_array_cannot_hold(slr):
+    # 1024 x 1024 binary64 is 8 MiB of state; the static array holds 4 MiB
+    d = slr.slr_desc_init(slr.SLR_J2D5, 1024, 1024, 1)
+    st, *_ = slr.slr_run_static(d, FAKE_U, FAKE_AUX, 10, 0, check=False)
+    assert st == slr.SLR_ERR_INVALID_ARG
+    msg = slr.slr_static_last_error()
+    assert "SLR_STATIC_STATE_BYTES" in msg and str(slr.SLR_STATIC_STATE_BYTES) in msg
+    # 724 x 724 binary64 = 4,193,408 bytes fits; 725 x 724 does not
+    assert 724 * 724 * 8 <= slr.SLR_STATIC_STATE_BYTES < 725 * 724 * 8
+    d = slr.slr_desc_init(slr.SLR_J2D5, 724, 725, 1)
+    st, *_ = slr.slr_run_static(d, FAKE_U, FAKE_AUX, 10, 0, check=False)
+    assert st == slr.SLR_ERR_INVALID_ARG
+    # other stencils, defect correction, a misaligned u, no f, a negative cap
+    for stencil, change in [(slr.SLR_LIFE, {}), (slr.SLR_RESTORE8, {}),
+                            (slr.SLR_J2D5, dict(defect_correction=1))]:
+        d = slr.slr_desc_init(stencil, 64, 64, 1, **change)
+        st, *_ = slr.slr_run_static(d, FAKE_U, FAKE_AUX, 10, 0, check=False)
+        assert st == slr.SLR_ERR_UNSUPPORTED, (stencil, change)
+    d = slr.slr_desc_init(slr.SLR_J2D5, 64, 64, 1)
+    for u, f, cap in [(FAKE_U + 8, FAKE_AUX, 10), (FAKE_U, 0, 10), (FAKE_U, FAKE_AUX, -1)]:
+        st, *_ = slr.slr_run_static(d, u, f, cap, 0, check=False)
+        assert st == slr.SLR_ERR_INVALID_ARG, (u, f, cap)
+
+
+def test_batch_sizes_and_create_checks(slr):
+    assert slr.slr_batch_workspace_size(0) == 0
+    assert slr.slr_batch_workspace_size(1025) == 0
+    assert slr.slr_batch_workspace_size(1) > 0
+    assert slr.slr_batch_workspace_size(1024) >= slr.slr_batch_workspace_size(512) >= slr.slr_batch_workspace_size(1)
+    assert slr.slr_batch_workspace_size(7) % 256 == 0
+    # the scratch of an instance is its second state buffer, rounded to 256 bytes
+    d = slr.slr_desc_init(slr.SLR_J2D5, 100, 30, 1)
+    assert slr.slr_batch_scratch_size(d) == -(-100 * 30 * 8 // 256) * 256
+    assert slr.slr_batch_scratch_size(slr.slr_desc_init(slr.SLR_LIFE, 64, 64, 1)) == 0
+    assert slr.slr_batch_scratch_size(slr.slr_desc_init(slr.SLR_J2D5, 0, 64, 1)) == 0
+    need = slr.slr_batch_workspace_size(8)
+    for n, ws, nbytes, status in [(0, FAKE_WS, need, slr.SLR_ERR_INVALID_ARG),
+                                  (1025, FAKE_WS, 1 << 30, slr.SLR_ERR_INVALID_ARG),
+                                  (8, FAKE_WS + 16, need, slr.SLR_ERR_INVALID_ARG),
+                                  (8, 0, need, slr.SLR_ERR_INVALID_ARG),
+                                  (8, FAKE_WS, need - 1, slr.SLR_ERR_WORKSPACE)]:
+        with pytest.raises(slr.SlrError) as e:
+            slr.slr_batch_create(n, ws, nbytes, 0)
+        assert e.value.status == status, (n, ws, nbytes)
+
+
+def _user_desc(slr, **change):
+    d = slr.slr_user_desc()
+    d.dtype, d.boundary, d.nx, d.ny, d.tol = slr.SLR_F32, slr.SLR_DIRICHLET, 64, 32, 1e-6
+    d.reduce, d.loop = slr.SLR_USER_MAX, slr.SLR_LOOP_AUTO
+    for k, v in change.items():
+        setattr(d, k, v)
+    return d
+
+
+def test_user_descriptor_checks(slr):
+    lib = slr.load()
+    size = lambda d: int(lib.slr_user_workspace_size(ctypes.byref(d)))
+    base = size(_user_desc(slr))
+    assert base > 0 and base % 256 == 0
+    assert size(_user_desc(slr, dtype=slr.SLR_F64)) > base        # twice the state bytes
+    for change in [dict(dtype=slr.SLR_BF16), dict(dtype=slr.SLR_U8), dict(nx=0), dict(ny=-3),
+                   dict(nx=1 << 21, ny=1 << 20), dict(boundary=2), dict(reduce=2), dict(loop=3)]:
+        assert size(_user_desc(slr, **change)) == 0, change
+    src = b"__device__ slr_t slr_update(const slr_nbr &u, slr_t f, long long i, long long j, const double *p)" \
+          b"{ return u(0, 0); }\n__device__ double slr_delta(slr_t a, slr_t b) { return 0.0; }\n"
+    h = ctypes.c_void_p()
+    d = _user_desc(slr)
+    cases = [(src, FAKE_U, FAKE_WS, base, slr.SLR_ERR_INVALID_ARG, "source"),           # NULL source below
+             (src, FAKE_U + 2, FAKE_WS, base, slr.SLR_ERR_INVALID_ARG, "aligned"),
+             (src, FAKE_U, FAKE_WS + 64, base, slr.SLR_ERR_INVALID_ARG, "256-byte"),
+             (src, FAKE_U, FAKE_WS, base - 1, slr.SLR_ERR_WORKSPACE, "workspace")]
+    for i, (s, u, ws, nbytes, status, words) in enumerate(cases):
+        st = lib.slr_user_create(ctypes.byref(d), None if i == 0 else s, u, None, ws, nbytes, None,
+                                 ctypes.byref(h))
+        assert st == status, words
+        assert words in lib.slr_user_last_error(None).decode(), words
+        assert not h.value
+    bad = _user_desc(slr, dtype=slr.SLR_U8)
+    assert lib.slr_user_create(ctypes.byref(bad), src, FAKE_U, None, FAKE_WS, 1 << 20, None,
+                               ctypes.byref(h)) == slr.SLR_ERR_INVALID_ARG
+    assert "dtype" in lib.slr_user_last_error(None).decode()
