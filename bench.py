@@ -799,6 +799,19 @@ def run_serve(args):
     srv = serve.Server(max_slots=1024, step_sweeps=args.step_sweeps, solo_cells=args.solo_cells or None)
     st = srv.serve(reqs, warmup_s=1.0, time_limit_s=args.serve_seconds * 6 + 30)
     srv.close()
+    # the same arrivals served by a queue alone, one request at a time: with the
+    # plain host-driven loop (one sweep launch, one reduce launch and a host
+    # test per sweep) and with the fused device loop; requests not started by
+    # the end of the arrival window are left unserved
+    fifo = {}
+    for name, loop in (("queue_plain_host_loop", slr.SLR_LOOP_HOST), ("queue_fused_device_loop", slr.SLR_LOOP_PERSISTENT)):
+        q = serve.make_requests(args.serve_seconds + 1.0, args.rate)
+        fs = serve.serve_fifo(q, loop=loop, warmup_s=1.0, time_limit_s=args.serve_seconds + 1.0, pool=srv.pool)
+        num = (lambda x: None if x != x else x)            # NaN (no latency sample) -> null
+        fifo[name] = {"p50_ms": num(fs.p50_ms), "p99_ms": num(fs.p99_ms), "mean_ms": num(fs.mean_ms),
+                      "latency_sample": fs.measured, "throughput_rps": fs.throughput_rps,
+                      "gcell_per_s": fs.gcell_per_s, "requests": fs.requests, "completed": fs.completed,
+                      "unserved": fs.requests - fs.completed, "max_queue": fs.max_queue, "wall_s": fs.wall_s}
     line = {"workload": f"serve_poisson{args.rate:g}rps_denoise256-4096_solve64-2048",
             "metric": "p50/p99 latency and throughput", "unit": "ms", "p50_ms": st.p50_ms, "p99_ms": st.p99_ms,
             "mean_ms": st.mean_ms, "throughput_rps": st.throughput_rps, "gcell_per_s": st.gcell_per_s,
@@ -806,7 +819,11 @@ def run_serve(args):
             "max_in_flight": st.max_in_flight, "max_queue": st.max_queue,
             "solo_lane": {"min_cells": args.solo_cells, "requests": sum(srv.is_solo(r) for r in reqs),
                           "what": "denoise jobs of at least min_cells pixels run on their own TMA-tiled solver, "
-                                  "resumed step_sweeps sweeps per iteration after the batch launch"}}
+                                  "resumed step_sweeps sweeps per iteration after the batch launch"},
+            "latency_sample": st.measured,
+            "queue_alone": dict(fifo, what="the same arrivals, one request at a time in arrival order, each "
+                                           "solved alone; p50/p99 over the served requests that arrived after "
+                                           "the 1 s warm-up (latency_sample of them; null when none)")}
     print(json.dumps(line), flush=True)
     return 0
 

@@ -123,6 +123,7 @@ class ServeStats:
     max_in_flight: int
     max_queue: int
     budget_bytes: int
+    measured: int = 0              # completed requests that arrived after the warm-up (the latency sample)
 
 
 class Server:
@@ -262,10 +263,73 @@ class Server:
             requests=len(requests), completed=len(done), wall_s=wall,
             p50_ms=float(np.percentile(lat, 50)), p99_ms=float(np.percentile(lat, 99)), mean_ms=float(lat.mean()),
             throughput_rps=len(measured) / span, cell_updates=cells, gcell_per_s=cells / wall / 1e9,
-            steps=steps, max_in_flight=max_in_flight, max_queue=max_queue, budget_bytes=self.budget)
+            steps=steps, max_in_flight=max_in_flight, max_queue=max_queue, budget_bytes=self.budget,
+            measured=len(measured))
 
     def close(self):
         for r in self.solo.values():
             r.solver.close()
         self.solo = {}
         self.batch.close()
+
+
+def serve_fifo(requests: list[Request], *, loop: int, warmup_s: float = 0.0, time_limit_s: float | None = None,
+               denoise_tol: float = 1e-3, solve_tol: float = 1e-6, cap: int = 5000, device=None,
+               pool: InputPool | None = None) -> ServeStats:
+    """The same request stream served by a queue alone, the comparator of the
+    continuous-batching Server: one request at a time in arrival order, each
+    copied in and solved on its own from start to finish, with no batching and
+    no overlap.  loop=SLR_LOOP_HOST solves every request by the plain schema of
+    Fig. 2 (per sweep one sweep launch, one reduce launch and the test on the
+    host); SLR_LOOP_PERSISTENT by one device-looped launch.  Latency is arrival
+    -> the read of the request's result.  Requests not started by time_limit_s
+    are left unserved (completed counts the served ones)."""
+    import torch
+    dev = torch.device(device or "cuda")
+    stream = torch.cuda.Stream(dev)
+    pool = pool if pool is not None else InputPool()
+    for r in requests:
+        pool.get(r.kind, r.side)                  # inputs ready before the clock starts
+    tol = {KIND_DENOISE: denoise_tol, KIND_SOLVE: solve_tol}
+    pending = sorted(requests, key=lambda r: r.arrival)
+    arrivals = np.array([r.arrival for r in pending])
+    done: list[Request] = []
+    max_queue = 0
+    t0 = time.perf_counter()
+    for i, r in enumerate(pending):
+        now = time.perf_counter() - t0
+        if time_limit_s is not None and now > time_limit_s:
+            break
+        if r.arrival > now:
+            time.sleep(r.arrival - now)
+            now = time.perf_counter() - t0
+        max_queue = max(max_queue, int(np.searchsorted(arrivals, now, side="right")) - i)
+        host_u, host_aux = pool.get(r.kind, r.side)
+        with torch.cuda.stream(stream):
+            u = torch.empty(host_u.shape, dtype=host_u.dtype, device=dev)
+            aux = torch.empty(host_aux.shape, dtype=host_aux.dtype, device=dev)
+            u.copy_(host_u, non_blocking=True)
+            aux.copy_(host_aux, non_blocking=True)
+            stencil = slr.SLR_RESTORE8 if r.kind == KIND_DENOISE else slr.SLR_J2D5
+            solver = slr.Solver(stencil, u, aux, stream=stream, tol=tol[r.kind], loop=loop)
+            solver.run(cap)
+            res = solver.result(check=False)           # waits for the stream
+            solver.close()
+        if res.status < 0:
+            raise slr.SlrError(res.status, "solve failed")
+        r.admitted, r.finished = now, time.perf_counter() - t0
+        r.iters, r.converged, r.value = res.iters, res.converged, res.value
+        done.append(r)
+    wall = time.perf_counter() - t0
+    measured = [r for r in done if r.arrival >= warmup_s]
+    # a queue that fell behind may serve nothing that arrived after the
+    # warm-up: its latencies are then NaN (no sample), not 0
+    lat = np.array([(r.finished - r.arrival) * 1e3 for r in measured]) if measured else np.full(1, np.nan)
+    cells = float(sum(r.side * r.side * r.iters for r in done))
+    span = max(wall - warmup_s, 1e-9)
+    return ServeStats(
+        requests=len(requests), completed=len(done), wall_s=wall,
+        p50_ms=float(np.percentile(lat, 50)), p99_ms=float(np.percentile(lat, 99)), mean_ms=float(lat.mean()),
+        throughput_rps=len(measured) / span, cell_updates=cells, gcell_per_s=cells / wall / 1e9,
+        steps=len(done), max_in_flight=1 if done else 0, max_queue=max_queue, budget_bytes=0,
+        measured=len(measured))

@@ -61,3 +61,20 @@ def test_admission_respects_the_memory_budget(gpu):
     assert 0 < peak <= budget
     assert stats.p99_ms >= stats.p50_ms > 0
     srv.close()
+
+
+@pytest.mark.parametrize("loop", ["host", "persistent"])
+def test_queue_alone_gives_each_request_its_solo_result(gpu, loop):
+    # the plain comparator of the serving loop: one request at a time
+    from types import SimpleNamespace
+    from paper_1609_04567_gb300 import serve
+    reqs = serve.make_requests(0.1, 300.0, seed=5, denoise_sides=(32, 256), solve_sides=(16, 128), buckets=5)
+    assert len(reqs) > 10
+    lp = gpu.SLR_LOOP_HOST if loop == "host" else gpu.SLR_LOOP_PERSISTENT
+    st = serve.serve_fifo(reqs, loop=lp)
+    assert st.completed == len(reqs) and st.max_in_flight == 1
+    ref = SimpleNamespace(pool=serve.InputPool(), tol={"denoise": 1e-3, "solve": 1e-6}, cap=5000)
+    for r in reqs:
+        assert r.finished >= r.admitted >= r.arrival
+        _, res = solve_alone(gpu, r, ref)
+        assert (r.iters, r.converged, r.value) == (res.iters, res.converged, res.value), (r.kind, r.side)

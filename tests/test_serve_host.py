@@ -73,3 +73,59 @@ def test_random_images_are_seeded_and_uniform():
     assert (a == inputs.random_image(64, 96, seed=3)).all() and not (a == inputs.random_image(64, 96, seed=4)).all()
     counts = np.bincount(a.reshape(-1), minlength=256)
     assert counts.min() > 0 and abs(a.mean() - 127.5) < 3
+
+
+class _FakeResult:
+    status, iters, converged, value = 0, 7, True, 0.5
+
+
+def _fake_device(monkeypatch, service_s):
+    """Stand-ins for the CUDA stream, device tensors and the solver, so that
+    the queue's host logic runs on the CPU; every solve takes service_s."""
+    import contextlib
+    import time as _time
+    import torch
+    from paper_1609_04567_gb300 import serve
+
+    class FakeSolver:
+        def __init__(self, stencil, u, aux, stream=None, **fields):
+            assert {"tol", "loop"} <= set(fields)
+
+        def run(self, n):
+            _time.sleep(service_s)
+
+        def result(self, check=True):
+            return _FakeResult()
+
+        def close(self):
+            pass
+
+    real_empty = torch.empty
+    monkeypatch.setattr(torch.cuda, "Stream", lambda *a, **k: type("S", (), {"cuda_stream": 0})())
+    monkeypatch.setattr(torch.cuda, "stream", lambda s: contextlib.nullcontext())
+    monkeypatch.setattr(torch, "empty", lambda shape, dtype=None, device=None: real_empty(shape, dtype=dtype))
+    monkeypatch.setattr(torch.Tensor, "pin_memory", lambda self: self)
+    monkeypatch.setattr(serve.slr, "Solver", FakeSolver)
+
+
+def test_queue_alone_serves_in_arrival_order_and_keeps_up_when_it_can(monkeypatch):
+    from paper_1609_04567_gb300 import serve
+    _fake_device(monkeypatch, 0.001)
+    reqs = serve.make_requests(0.3, 100.0, seed=5, denoise_sides=(32, 64), solve_sides=(16, 32), buckets=3)
+    st = serve.serve_fifo(reqs, loop=serve.slr.SLR_LOOP_HOST, warmup_s=0.05, device="cpu")
+    assert st.completed == len(reqs) and st.max_in_flight == 1 and st.measured > 0
+    order = sorted(reqs, key=lambda r: r.arrival)
+    for a, b in zip(order, order[1:]):
+        assert a.finished <= b.admitted                   # one at a time, in arrival order
+    assert all(r.admitted >= r.arrival and r.iters == 7 for r in reqs)
+    assert 1.0 <= st.p50_ms < 50.0                       # about one service time
+
+
+def test_queue_alone_that_falls_behind_reports_no_latency_sample(monkeypatch):
+    import math
+    from paper_1609_04567_gb300 import serve
+    _fake_device(monkeypatch, 0.02)                     # 50 requests/s against 400/s offered
+    reqs = serve.make_requests(0.5, 400.0, seed=6, denoise_sides=(32, 64), solve_sides=(16, 32), buckets=3)
+    st = serve.serve_fifo(reqs, loop=serve.slr.SLR_LOOP_HOST, warmup_s=0.2, time_limit_s=0.1, device="cpu")
+    assert 0 < st.completed < len(reqs) and st.max_queue > 1
+    assert st.measured == 0 and math.isnan(st.p50_ms) and math.isnan(st.p99_ms)
