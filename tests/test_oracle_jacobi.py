@@ -135,26 +135,39 @@ def test_j3d7_sine_mode_closed_form(orc):
     assert r.converged and r.iters == expect_n
 
 
-def test_j3d7_brute_force_dense_solve(orc):
+@pytest.mark.parametrize("nz,ny,nx,h,wrap,ghost,sigma", [
+    (3, 4, 5, 0.0, False, 0.0, 1.0),
+    (4, 3, 5, 0.25, True, 0.0, 3.0),
+    (3, 5, 4, 0.0, False, -0.5, 1.0),
+    (5, 3, 3, 0.2, False, 1.25, 0.0),
+])
+def test_j3d7_brute_force_dense_solve(orc, nz, ny, nx, h, wrap, ghost, sigma):
     from paper_1609_04567_gb300 import inputs
-    nz, ny, nx, sigma = 3, 4, 5, 1.0
     f = inputs.helmholtz_rhs((nz, ny, nx), seed=11)
-    h = 1.0 / (nx + 1)
+    hh = h if h > 0 else 1.0 / (nx + 1)
     n = nx * ny * nz
     A = np.zeros((n, n))
+    b = f.reshape(-1).copy()
     for k in range(nz):
         for i in range(ny):
             for j in range(nx):
                 r = (k * ny + i) * nx + j
-                A[r, r] = (6 + sigma * h * h) / (h * h)
+                A[r, r] += (6 + sigma * hh * hh) / (hh * hh)
                 for dk, di, dj in ((-1, 0, 0), (1, 0, 0), (0, -1, 0), (0, 1, 0), (0, 0, -1), (0, 0, 1)):
                     z, y, x = k + dk, i + di, j + dj
-                    if 0 <= z < nz and 0 <= y < ny and 0 <= x < nx:
-                        A[r, (z * ny + y) * nx + x] = -1.0 / (h * h)
-    exact = np.linalg.solve(A, f.reshape(-1)).reshape(nz, ny, nx)
-    u, r = orc.j3d7(np.zeros_like(f), f, sigma=sigma, tol=1e-15, max_iters=100000)
+                    if wrap:
+                        A[r, ((z % nz) * ny + (y % ny)) * nx + (x % nx)] -= 1.0 / (hh * hh)
+                    elif 0 <= z < nz and 0 <= y < ny and 0 <= x < nx:
+                        A[r, (z * ny + y) * nx + x] -= 1.0 / (hh * hh)
+                    else:
+                        b[r] += ghost / (hh * hh)
+    exact = np.linalg.solve(A, b).reshape(nz, ny, nx)
+    u, r = orc.j3d7(np.zeros_like(f), f, sigma=sigma, h=h, wrap=wrap, ghost=ghost, tol=1e-15, max_iters=200000)
     assert r.converged
-    assert np.max(np.abs(u - exact)) <= 1e-12 * np.max(np.abs(exact))
+    jac = np.eye(n) - A / np.diag(A)[:, None]
+    rho = np.max(np.abs(np.linalg.eigvals(jac)))
+    bound = 2e-15 / (1 - rho) + 1e-13 * np.max(np.abs(exact))
+    assert np.max(np.abs(u - exact)) <= bound
 
 
 def test_j2d5_f32_closed_form(orc):

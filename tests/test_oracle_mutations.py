@@ -35,6 +35,16 @@ MUTATIONS = [
      "                    size_t c = (size_t)((k * ny + i) * nx + j);\n                    double nv",
      "                               0.0;\n"
      "                    size_t c = (size_t)((k * ny + i) * nx + j);\n                    double nv"),
+    ("J3D7 wraps z by the row count",
+     "                      int64_t k, int64_t i, int64_t j, int wrap, double ghost)\n{\n"
+     "    if (wrap) return a[(wrap_index(k, nz) * ny",
+     "                      int64_t k, int64_t i, int64_t j, int wrap, double ghost)\n{\n"
+     "    if (wrap) return a[(wrap_index(k, ny) * ny"),
+    ("J3D7 ignores the Dirichlet ghost value",
+     "    if (k < 0 || k >= nz || i < 0 || i >= ny || j < 0 || j >= nx) return ghost;\n"
+     "    return a[(k * ny + i) * nx + j];\n}\n\nstatic float at3_f32",
+     "    if (k < 0 || k >= nz || i < 0 || i >= ny || j < 0 || j >= nx) return 0.0;\n"
+     "    return a[(k * ny + i) * nx + j];\n}\n\nstatic float at3_f32"),
     ("J2D5 counts one sweep too few",
      "        memcpy(u, v, n * sizeof(double));   /* a = fst(b) */\n        it += 1;\n"
      "        conv = val < tol;\n    } while (!conv && it < max_iters);\n    free(v);\n"
