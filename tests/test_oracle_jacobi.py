@@ -233,3 +233,93 @@ def test_scaled_defect_of_zero_state(orc):
     v, h = sine_mode_2d(9, 1, 1)
     d = 4 + h * h
     assert orc.j2d5_scaled_defect(np.zeros_like(v), v) == pytest.approx(h * h * np.max(np.abs(v)) / d, rel=1e-14)
+
+
+def sine_mode_3d(n, modes):
+    h = 1.0 / (n + 1)
+    x = np.arange(1, n + 1) * h
+    v = (np.sin(modes[2] * math.pi * x)[:, None, None] * np.sin(modes[1] * math.pi * x)[None, :, None]
+         * np.sin(modes[0] * math.pi * x)[None, None, :])
+    return v, h
+
+
+def test_j3d7_f32_closed_form(orc):
+    n, modes, sigma = 13, (1, 1, 2), 1.0
+    v, h = sine_mode_3d(n, modes)
+    mu, cstar = jacobi_factor(h, sigma, modes)
+    v32 = v.astype(np.float32)
+    for sweeps in (1, 20, 60):
+        u, r = orc.j3d7(np.zeros_like(v32), v32, sigma=sigma, tol=0.0, max_iters=sweeps, storage="f32")
+        expect = cstar * (1 - mu ** sweeps) * v
+        assert np.max(np.abs(u - expect)) <= 1e-5 * abs(cstar)
+        dmax = abs(cstar) * mu ** (sweeps - 1) * (1 - mu) * np.max(np.abs(v))
+        assert r.value == pytest.approx(dmax, rel=1e-3, abs=1e-6 * abs(cstar))
+
+
+@pytest.mark.parametrize("storage", ["bf16", "f16"])
+def test_j3d7_storage_one_sweep_is_rounded_f32_sweep(orc, storage):
+    import torch
+    from paper_1609_04567_gb300 import inputs
+    f64 = inputs.helmholtz_rhs((6, 7, 9), seed=4)
+    tdt = torch.bfloat16 if storage == "bf16" else torch.float16
+    f_s = torch.from_numpy(f64.astype(np.float32)).to(tdt).float().numpy()
+    u0 = torch.from_numpy((0.01 * f64).astype(np.float32)).to(tdt).float().numpy()
+    for wrap in (False, True):
+        u32, _ = orc.j3d7(u0, f_s, wrap=wrap, tol=0.0, max_iters=1, storage="f32")
+        us, r = orc.j3d7(u0, f_s, wrap=wrap, tol=0.0, max_iters=1, storage=storage)
+        lib_rounded = torch.from_numpy(u32).to(tdt).float().numpy()
+        assert np.array_equal(us.view(np.uint32), lib_rounded.view(np.uint32))
+        # the change is taken between stored values
+        assert r.value == float(np.max(np.abs(us - u0)))
+
+
+@pytest.mark.parametrize("storage", ["bf16", "f16"])
+def test_j3d7_storage_state_representable_and_bounded(orc, storage):
+    import torch
+    n, modes = 11, (1, 1, 1)
+    v, h = sine_mode_3d(n, modes)
+    mu, cstar = jacobi_factor(h, 1.0, modes)
+    tdt = torch.bfloat16 if storage == "bf16" else torch.float16
+    f_s = torch.from_numpy(v.astype(np.float32)).to(tdt).float().numpy()
+    u, r = orc.j3d7(np.zeros_like(f_s), f_s, tol=1e-6, max_iters=20000, storage=storage)
+    assert np.array_equal(u, torch.from_numpy(u).to(tdt).float().numpy())
+    ulp = {"bf16": 2.0 ** -8, "f16": 2.0 ** -11}[storage] * np.max(np.abs(cstar * v))
+    assert r.converged
+    assert np.max(np.abs(u - cstar * v)) <= ulp / (1 - mu) + 1e-3 * abs(cstar)
+
+
+@pytest.mark.parametrize("dim,wrap,ghost", [(2, False, 0.5), (2, True, 0.0), (3, False, -0.25), (3, True, 0.0)])
+def test_f32_paths_reach_the_dense_solution(orc, dim, wrap, ghost):
+    # the binary32 loop, run to its stagnation level, against numpy's dense
+    # solve of the same discrete system (built here from the operator's
+    # definition): the error is bounded by a few binary32 roundings of the
+    # state amplified by 1 / (1 - rho)
+    from paper_1609_04567_gb300 import inputs
+    shape = (7, 6) if dim == 2 else (4, 5, 6)
+    sigma, h = 2.0, 0.2
+    f = inputs.helmholtz_rhs(shape, seed=9)
+    n = f.size
+    offs = [(-1, 0), (1, 0), (0, -1), (0, 1)] if dim == 2 else \
+        [(-1, 0, 0), (1, 0, 0), (0, -1, 0), (0, 1, 0), (0, 0, -1), (0, 0, 1)]
+    A = np.zeros((n, n))
+    b = f.reshape(-1).copy()
+    for idx in np.ndindex(shape):
+        r = np.ravel_multi_index(idx, shape)
+        A[r, r] += (2 * dim + sigma * h * h) / (h * h)
+        for o in offs:
+            nb = tuple(i + d for i, d in zip(idx, o))
+            if wrap:
+                A[r, np.ravel_multi_index(tuple(c % s for c, s in zip(nb, shape)), shape)] -= 1.0 / (h * h)
+            elif all(0 <= c < s for c, s in zip(nb, shape)):
+                A[r, np.ravel_multi_index(nb, shape)] -= 1.0 / (h * h)
+            else:
+                b[r] += ghost / (h * h)
+    exact = np.linalg.solve(A, b).reshape(shape)
+    run = orc.j2d5 if dim == 2 else orc.j3d7
+    f32 = f.astype(np.float32)
+    u, r = run(np.zeros_like(f32), f32, sigma=sigma, h=h, wrap=wrap, ghost=ghost, tol=1e-7, max_iters=100000,
+               storage="f32")
+    jac = np.eye(n) - A / np.diag(A)[:, None]
+    rho = np.max(np.abs(np.linalg.eigvals(jac)))
+    scale = np.max(np.abs(exact))
+    assert np.max(np.abs(u - exact)) <= (1e-7 + 8 * 2.0 ** -24 * scale) / (1 - rho) + 2e-7 * scale

@@ -45,6 +45,20 @@ MUTATIONS = [
      "    return a[(k * ny + i) * nx + j];\n}\n\nstatic float at3_f32",
      "    if (k < 0 || k >= nz || i < 0 || i >= ny || j < 0 || j >= nx) return 0.0;\n"
      "    return a[(k * ny + i) * nx + j];\n}\n\nstatic float at3_f32"),
+    ("J3D7 binary32 path divides by the 2D constant",
+     "    float h2 = (float)h2d, d = (float)(6.0 + sigma * h2d);   /* same constants as FP64, rounded */",
+     "    float h2 = (float)h2d, d = (float)(4.0 + sigma * h2d);   /* same constants as FP64, rounded */"),
+    ("J3D7 binary32 path skips the storage rounding",
+     "                    float nv = to_storage((t + s) / d, storage);\n                    float dl = fabsf(nv - u[c]);\n"
+     "                    if (dl > val) val = dl;\n                    v[c] = nv;\n                }\n"
+     "        memcpy(u, v, n * sizeof(float));\n        it += 1;\n        conv = (double)val < tol;\n"
+     "    } while (!conv && it < max_iters);\n    free(v);\n    res->iters = it; res->value = (double)val; res->converged = conv;\n"
+     "    res->changed = val > 0.0f; res->count = 0;\n    return 0;\n}\n\n/* ----",
+     "                    float nv = (t + s) / d;\n                    float dl = fabsf(nv - u[c]);\n"
+     "                    if (dl > val) val = dl;\n                    v[c] = nv;\n                }\n"
+     "        memcpy(u, v, n * sizeof(float));\n        it += 1;\n        conv = (double)val < tol;\n"
+     "    } while (!conv && it < max_iters);\n    free(v);\n    res->iters = it; res->value = (double)val; res->converged = conv;\n"
+     "    res->changed = val > 0.0f; res->count = 0;\n    return 0;\n}\n\n/* ----"),
     ("J2D5 counts one sweep too few",
      "        memcpy(u, v, n * sizeof(double));   /* a = fst(b) */\n        it += 1;\n"
      "        conv = val < tol;\n    } while (!conv && it < max_iters);\n    free(v);\n"
