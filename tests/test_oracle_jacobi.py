@@ -323,3 +323,31 @@ def test_f32_paths_reach_the_dense_solution(orc, dim, wrap, ghost):
     rho = np.max(np.abs(np.linalg.eigvals(jac)))
     scale = np.max(np.abs(exact))
     assert np.max(np.abs(u - exact)) <= (1e-7 + 8 * 2.0 ** -24 * scale) / (1 - rho) + 2e-7 * scale
+
+
+def test_defect_correction_steps(orc):
+    # The correction loop step by step against the oracle's binary32 Jacobi
+    # path (pinned above) and the operator built from its definition:
+    #   correction 1 from u = 0: r = f exactly, so u1 is K binary32 sweeps of
+    #   A e = f from e = 0, widened to binary64 -- bit for bit;
+    #   correction 2: u2 = u1 + K binary32 sweeps of A e = r1 from e = 0,
+    #   r1 = f - A u1 in binary64 (numpy's order here: equal up to rounding).
+    from paper_1609_04567_gb300 import inputs
+    ny, nx, K = 10, 12, 7
+    f = inputs.helmholtz_rhs((ny, nx), seed=8)
+    z64, z32 = np.zeros((ny, nx)), np.zeros((ny, nx), dtype=np.float32)
+    u1, r1 = orc.j2d5_dc(z64, f, tol=0.0, k_in=K, max_outer=1)
+    s1, _ = orc.j2d5(z32, f.astype(np.float32), tol=0.0, max_iters=K, storage="f32")
+    assert np.array_equal(u1, s1.astype(np.float64))
+    assert r1.iters == 1 and not r1.converged
+    assert r1.value == orc.j2d5_scaled_defect(u1, f)
+    h = 1.0 / (nx + 1)
+    A, b = dense_helmholtz(ny, nx, h, 1.0, False, 0.0, f)
+    res1 = (b - A @ u1.reshape(-1)).reshape(ny, nx)
+    e2, _ = orc.j2d5(z32, res1.astype(np.float32), tol=0.0, max_iters=K, storage="f32")
+    u2, r2 = orc.j2d5_dc(z64, f, tol=0.0, k_in=K, max_outer=2)
+    assert r2.iters == 2
+    assert np.max(np.abs(u2 - (u1 + e2.astype(np.float64)))) <= 1e-6 * np.max(np.abs(e2))
+    # the scaled defect it reports is the change the next FP64 Jacobi sweep makes
+    nxt, rj = orc.j2d5(u2, f, tol=0.0, max_iters=1)
+    assert r2.value == pytest.approx(rj.value, rel=1e-9)

@@ -103,6 +103,15 @@ MUTATIONS = [
     ("defect correction with the defect's sign flipped",
      "            double rv = f[i * nx + j] - au;",
      "            double rv = au - f[i * nx + j];"),
+    ("defect correction resumes the inner solve from the last correction",
+     "        for (size_t c = 0; c < n; ++c) { r32[c] = (float)r[c]; e[c] = 0.0f; }",
+     "        for (size_t c = 0; c < n; ++c) { r32[c] = (float)r[c]; }"),
+    ("defect correction inner solve on the binary64 defect's first sweep only",
+     "                    float t = h2f * r32[i * nx + j];\n                    e2[i * nx + j] = (t + sn) / df;",
+     "                    float t = s == 0 ? h2f * r32[i * nx + j] : 0.0f;\n                    e2[i * nx + j] = (t + sn) / df;"),
+    ("defect correction subtracts the correction",
+     "        for (size_t c = 0; c < n; ++c) u[c] = u[c] + (double)e[c];",
+     "        for (size_t c = 0; c < n; ++c) u[c] = u[c] - (double)e[c];"),
     ("bfloat16 rounds half up instead of to even",
      "    if (rest > 0x8000u || (rest == 0x8000u && (keep & 1u)))\n        keep += 1u;",
      "    if (rest >= 0x8000u)\n        keep += 1u;"),
