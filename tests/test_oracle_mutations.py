@@ -100,6 +100,16 @@ MUTATIONS = [
     ("restoration mean over every pixel",
      "        mean = nmask ? ((double)sum * 0x1p-24) / (double)nmask : 0.0;",
      "        mean = nmask ? ((double)sum * 0x1p-24) / (double)n : 0.0;"),
+    ("restoration reads this sweep's new values (Gauss-Seidel order)",
+     "                        float uj = u[y * nx + x];",
+     "                        float uj = (size_t)(y * nx + x) < c ? v[y * nx + x] : u[y * nx + x];"),
+    ("restoration replicates the edge instead of leaving out-of-range neighbours",
+     "                        if (y < 0 || y >= ny || x < 0 || x >= nx) continue;\n                        float uj",
+     "                        if (y < 0) y = 0;\n                        if (y >= ny) y = ny - 1;\n"
+     "                        if (x < 0) x = 0;\n                        if (x >= nx) x = nx - 1;\n                        float uj"),
+    ("restoration rounds each change to 2^-24 instead of truncating",
+     "static uint64_t fixed_2m24(float x) { return (uint64_t)((double)x * 16777216.0); }",
+     "static uint64_t fixed_2m24(float x) { return (uint64_t)((double)x * 16777216.0 + 0.5); }"),
     ("defect correction with the defect's sign flipped",
      "            double rv = f[i * nx + j] - au;",
      "            double rv = au - f[i * nx + j];"),

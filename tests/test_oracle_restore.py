@@ -102,13 +102,21 @@ def test_returned_state_is_stationary_point_of_functional(orc):
     assert worst < 1e-3
 
 
-def test_mean_abs_change_reduce_matches_brute_force(orc):
+@pytest.mark.parametrize("scale,before", [(1.0, 0), (1.0, 25), (1.0 / 512, 3)])
+def test_mean_abs_change_reduce_matches_brute_force(orc, scale, before):
+    # With pixel values of 20 .. 235 every binary32 change is a multiple of
+    # 2^-17; a state scaled below 1/2 has changes with bits under 2^-24,
+    # where truncating and rounding to 2^-24 differ.
     from paper_1609_04567_gb300 import inputs
     frame, _ = inputs.noisy_frame(64, 64, seed=21)
     mask = inputs.noise_mask(frame)
-    u0 = frame.astype(np.float32)
+    u0 = (frame.astype(np.float64) * scale).astype(np.float32)
+    if before:
+        u0, _ = orc.restore8(u0, mask, tol=0.0, max_iters=before)
     out, r = orc.restore8(u0, mask, tol=0.0, max_iters=1)
-    delta = np.abs(out.astype(np.float64) - u0.astype(np.float64))[mask == 1]
+    delta = np.abs(out.astype(np.float32) - u0.astype(np.float32)).astype(np.float64)[mask == 1]
+    if scale < 1.0:
+        assert np.mean(np.floor(delta * 2 ** 24) != delta * 2 ** 24) > 0.5
     # the reduce truncates each change to 2^-24 before the integer sum
     assert r.value == pytest.approx(delta.mean(), abs=2.0 ** -24)
     assert r.value == np.floor(delta * 2 ** 24).sum() / 2 ** 24 / delta.size
