@@ -59,6 +59,22 @@ MUTATIONS = [
      "        memcpy(u, v, n * sizeof(float));\n        it += 1;\n        conv = (double)val < tol;\n"
      "    } while (!conv && it < max_iters);\n    free(v);\n    res->iters = it; res->value = (double)val; res->converged = conv;\n"
      "    res->changed = val > 0.0f; res->count = 0;\n    return 0;\n}\n\n/* ----"),
+    ("J2D5 wraps rows by the column count",
+     "static double at2_f64(const double *a, int64_t nx, int64_t ny, int64_t i, int64_t j,\n"
+     "                      int wrap, double ghost)\n{\n    if (wrap) return a[wrap_index(i, ny) * nx",
+     "static double at2_f64(const double *a, int64_t nx, int64_t ny, int64_t i, int64_t j,\n"
+     "                      int wrap, double ghost)\n{\n    if (wrap) return a[wrap_index(i, nx) * nx"),
+    ("J2D5 binary32 path ignores the Dirichlet ghost value",
+     "    if (i < 0 || i >= ny || j < 0 || j >= nx) return ghost;\n    return a[i * nx + j];\n}\n\n"
+     "static double at3_f64",
+     "    if (i < 0 || i >= ny || j < 0 || j >= nx) return 0.0f;\n    return a[i * nx + j];\n}\n\n"
+     "static double at3_f64"),
+    ("default mesh width 1/nx instead of 1/(nx + 1)",
+     "static double mesh_h(double h, int64_t nx) { return h > 0.0 ? h : 1.0 / (double)(nx + 1); }",
+     "static double mesh_h(double h, int64_t nx) { return h > 0.0 ? h : 1.0 / (double)nx; }"),
+    ("J2D5 reduces the change against the new neighbour sum",
+     "            double dl = fabs(nv - u[i * nx + j]);\n            if (dl > dmax) dmax = dl;\n            v[i * nx + j] = nv;",
+     "            double dl = fabs(nv - s / 4.0);\n            if (dl > dmax) dmax = dl;\n            v[i * nx + j] = nv;"),
     ("J2D5 counts one sweep too few",
      "        memcpy(u, v, n * sizeof(double));   /* a = fst(b) */\n        it += 1;\n"
      "        conv = val < tol;\n    } while (!conv && it < max_iters);\n    free(v);\n"
