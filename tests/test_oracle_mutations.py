@@ -153,6 +153,21 @@ MUTATIONS = [
     ("detector keeps the pixel when no window decides",
      "            if (out < 0) out = zmed;",
      "            if (out < 0) out = z;"),
+    ("detector replicates the image edge into clipped windows",
+     "                        if (a >= 0 && a < ny && b >= 0 && b < nx) {\n                            cnt[img[a * nx + b]] += 1;",
+     "                        {\n                            int64_t aa = a < 0 ? 0 : (a >= ny ? ny - 1 : a), bb = b < 0 ? 0 : (b >= nx ? nx - 1 : b);\n"
+     "                            cnt[img[aa * nx + bb]] += 1;"),
+    ("detector starts at the 5 x 5 window",
+     "            for (int64_t r = 1; 2 * r + 1 <= wmax; ++r) {",
+     "            for (int64_t r = 2; 2 * r + 1 <= wmax; ++r) {"),
+    ("Sobel weights the wrong column of Gy",
+     "            int64_t gy = ((int64_t)dn[j - 1] - up[j - 1]) + 2 * ((int64_t)dn[j] - up[j]) +\n"
+     "                         ((int64_t)dn[j + 1] - up[j + 1]);",
+     "            int64_t gy = ((int64_t)dn[j - 1] - up[j - 1]) + ((int64_t)dn[j] - up[j]) +\n"
+     "                         2 * ((int64_t)dn[j + 1] - up[j + 1]);"),
+    ("Sobel takes Gx one column to the left",
+     "            int64_t gx = ((int64_t)up[j + 1] - up[j - 1]) + 2 * ((int64_t)mid[j + 1] - mid[j - 1]) +",
+     "            int64_t gx = ((int64_t)up[j] - up[j - 1]) + 2 * ((int64_t)mid[j] - mid[j - 1]) +"),
     ("Sobel drops the centre row's weight 2",
      "            int64_t gx = ((int64_t)up[j + 1] - up[j - 1]) + 2 * ((int64_t)mid[j + 1] - mid[j - 1]) +",
      "            int64_t gx = ((int64_t)up[j + 1] - up[j - 1]) + ((int64_t)mid[j + 1] - mid[j - 1]) +"),
