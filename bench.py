@@ -803,18 +803,18 @@ def run_serve(args):
     # plain host-driven loop (one sweep launch, one reduce launch and a host
     # test per sweep) and with the fused device loop; requests not started by
     # the end of the arrival window are left unserved
+    num = (lambda x: None if x != x else x)                # NaN (no latency sample) -> null
     fifo = {}
     for name, loop in (("queue_plain_host_loop", slr.SLR_LOOP_HOST), ("queue_fused_device_loop", slr.SLR_LOOP_PERSISTENT)):
         q = serve.make_requests(args.serve_seconds + 1.0, args.rate)
         fs = serve.serve_fifo(q, loop=loop, warmup_s=1.0, time_limit_s=args.serve_seconds + 1.0, pool=srv.pool)
-        num = (lambda x: None if x != x else x)            # NaN (no latency sample) -> null
         fifo[name] = {"p50_ms": num(fs.p50_ms), "p99_ms": num(fs.p99_ms), "mean_ms": num(fs.mean_ms),
                       "latency_sample": fs.measured, "throughput_rps": fs.throughput_rps,
                       "gcell_per_s": fs.gcell_per_s, "requests": fs.requests, "completed": fs.completed,
                       "unserved": fs.requests - fs.completed, "max_queue": fs.max_queue, "wall_s": fs.wall_s}
     line = {"workload": f"serve_poisson{args.rate:g}rps_denoise256-4096_solve64-2048",
-            "metric": "p50/p99 latency and throughput", "unit": "ms", "p50_ms": st.p50_ms, "p99_ms": st.p99_ms,
-            "mean_ms": st.mean_ms, "throughput_rps": st.throughput_rps, "gcell_per_s": st.gcell_per_s,
+            "metric": "p50/p99 latency and throughput", "unit": "ms", "p50_ms": num(st.p50_ms),
+            "p99_ms": num(st.p99_ms), "mean_ms": num(st.mean_ms), "throughput_rps": st.throughput_rps, "gcell_per_s": st.gcell_per_s,
             "requests": st.requests, "completed": st.completed, "wall_s": st.wall_s, "steps": st.steps,
             "max_in_flight": st.max_in_flight, "max_queue": st.max_queue,
             "solo_lane": {"min_cells": args.solo_cells, "requests": sum(srv.is_solo(r) for r in reqs),

@@ -256,7 +256,8 @@ class Server:
         wall = time.perf_counter() - t0
         self.done = done
         measured = [r for r in done if r.arrival >= warmup_s]
-        lat = np.array([(r.finished - r.arrival) * 1e3 for r in measured]) if measured else np.zeros(1)
+        # no request finished after the warm-up: no latency sample (NaN), not 0
+        lat = np.array([(r.finished - r.arrival) * 1e3 for r in measured]) if measured else np.full(1, np.nan)
         cells = float(sum(r.side * r.side * r.iters for r in done))
         span = max(wall - warmup_s, 1e-9)
         return ServeStats(
