@@ -145,3 +145,60 @@ def test_user_descriptor_checks(slr):
     assert lib.slr_user_create(ctypes.byref(bad), src, FAKE_U, None, FAKE_WS, 1 << 20, None,
                                ctypes.byref(h)) == slr.SLR_ERR_INVALID_ARG
     assert "dtype" in lib.slr_user_last_error(None).decode()
+
+
+NAN = float("nan")
+
+
+@pytest.mark.parametrize("stencil,ext,fields,unsupported,words", [
+    (9, (8, 8, 1), {}, False, "unknown stencil"),
+    ("J2D5", (0, 8, 1), {}, False, "extents must be >= 1"),
+    ("J2D5", (8, -1, 1), {}, False, "extents must be >= 1"),
+    ("J3D7", (8, 8, (1 << 31) - 4095), {}, False, "extent too large"),
+    ("J2D5", (8, 8, 2), {}, False, "nz == 1"),
+    ("LIFE", (8, 8, 3), {}, False, "nz == 1"),
+    ("J2D5", (8, 8, 1), dict(boundary=2), False, "unknown boundary"),
+    ("J2D5", (8, 8, 1), dict(reduce=2), False, "reduce operator"),
+    ("RESTORE8", (8, 8, 1), dict(reduce=0), False, "reduce operator"),
+    ("J2D5", (8, 8, 1), dict(loop=3), False, "loop mode"),
+    ("J2D5", (8, 8, 1), dict(math=2), False, "math mode"),
+    ("LIFE", (8, 8, 1), dict(temporal_k=33), False, "temporal_k"),
+    ("LIFE", (8, 8, 1), dict(temporal_k=-1), False, "temporal_k"),
+    ("J2D5", (8, 8, 1), dict(grid_ctas=-2), False, "grid_ctas"),
+    ("J2D5", (8, 8, 1), dict(tiling=-1), False, "tiling"),
+    ("J2D5", (8, 8, 1), dict(storage=0), False, "Jacobi storage"),
+    ("J3D7", (8, 8, 8), dict(sigma=NAN), False, "NaN"),
+    ("J2D5", (8, 8, 1), dict(h=NAN), False, "NaN"),
+    ("LIFE", (8, 8, 1), dict(storage=3), False, "Life storage"),
+    ("RESTORE8", (8, 8, 1), dict(storage=4), False, "restoration storage"),
+    ("RESTORE8", (8, 8, 1), dict(boundary=1), True, "DIRICHLET"),
+    ("RESTORE8", (8, 8, 1), dict(alpha=0.0), False, "alpha"),
+    ("RESTORE8", (8, 8, 1), dict(alpha=NAN), False, "alpha"),
+    ("J2D5", (8, 8, 1), dict(defect_correction=1, storage=3), True, "defect correction"),
+    ("J2D5", (8, 8, 1), dict(defect_correction=1, ghost=1.0), True, "defect correction"),
+    ("J2D5", (8, 8, 1), dict(defect_correction=1, boundary=1), True, "defect correction"),
+    ("J2D5", (8, 8, 1), dict(defect_correction=1, loop=1), True, "defect correction"),
+    ("J3D7", (8, 8, 8), dict(defect_correction=1), True, "defect correction"),
+    ("J2D5", (8, 8, 1), dict(defect_correction=1, inner_sweeps=-1), False, "inner_sweeps"),
+    ("J3D7", (8192, 8192, 1024), {}, False, "larger than device memory"),
+])
+def test_descriptor_rules(slr, stencil, ext, fields, unsupported, words):
+    # each rule of the descriptor check: slr_workspace_size returns 0 and
+    # slr_create refuses before it touches the device, with the status the
+    # header documents and a message that names the rule
+    s = getattr(slr, "SLR_" + stencil) if isinstance(stencil, str) else stencil
+    d = slr.slr_desc_init(s if isinstance(stencil, str) else slr.SLR_J2D5, *ext, **fields)
+    d.stencil = s
+    assert slr.slr_workspace_size(d) == 0
+    with pytest.raises(slr.SlrError) as e:
+        slr.slr_create(d, FAKE_U, FAKE_AUX, FAKE_WS, 1 << 40, 0)
+    assert e.value.status == (slr.SLR_ERR_UNSUPPORTED if unsupported else slr.SLR_ERR_INVALID_ARG)
+    assert words in slr.slr_last_error(None), slr.slr_last_error(None)
+
+
+def test_defaults_of_every_stencil_pass_the_rules(slr):
+    for s, ext in ((slr.SLR_J2D5, (8, 8, 1)), (slr.SLR_J3D7, (8, 8, 8)), (slr.SLR_LIFE, (8, 8, 1)),
+                   (slr.SLR_RESTORE8, (8, 8, 1))):
+        assert slr.slr_workspace_size(slr.slr_desc_init(s, *ext)) > 0
+    # and the defect correction's own defaults
+    assert slr.slr_workspace_size(slr.slr_desc_init(slr.SLR_J2D5, 8, 8, 1, defect_correction=1)) > 0
