@@ -143,3 +143,53 @@ def test_tune_scratch_size_and_argument_checks(lib):
         slr.slr_tune(j, 0x1000, 0, 0x3000, 1 << 20, 0)  # Jacobi needs f
     assert "aux" in slr.slr_tune_last_error()
     slr.slr_tune_clear()
+
+
+C_CALLER = r"""
+#include <stdio.h>
+#include <string.h>
+#include "slr.h"
+
+int main(void)
+{
+    slr_desc d;
+    slr_desc_init(&d, SLR_LIFE, 8192, 8192, 1);
+    size_t ws = slr_workspace_size(&d);
+    slr_desc j;
+    slr_desc_init(&j, SLR_J3D7, 64, 64, 64);
+    j.storage = SLR_BF16;
+    size_t wj = slr_workspace_size(&j);
+    slr_handle h = (slr_handle)0;
+    slr_status st = slr_create(&j, (void *)0x1001, (const void *)0x2000, (void *)0x3000, wj, NULL, &h);
+    printf("version %s\n", slr_version());
+    printf("life_ws %zu %d %d\n", ws, d.boundary == SLR_WRAP, d.storage == SLR_U8);
+    printf("j3d7_ws %zu\n", wj);
+    printf("create %d %d %s\n", (int)st, h == (slr_handle)0, slr_last_error(NULL));
+    printf("static_max %u\n", (unsigned)SLR_STATIC_STATE_BYTES);
+    return 0;
+}
+"""
+
+
+def test_plain_c_caller_links_and_uses_the_header(tmp_path):
+    # A C99 program built against include/slr.h and libslr.so alone: the
+    # boundary needs no Python, C++ or torch on the caller's side.  Only calls
+    # that need no GPU run here.
+    import subprocess
+    from paper_1609_04567_gb300 import build
+    lib = build.build()
+    src = tmp_path / "caller.c"
+    src.write_text(C_CALLER)
+    exe = tmp_path / "caller"
+    subprocess.run(["gcc", "-std=c99", "-Wall", "-Werror", "-I", os.path.join(ROOT, "include"), str(src),
+                    "-L", os.path.dirname(lib), "-l:" + os.path.basename(lib),
+                    "-Wl,-rpath," + os.path.dirname(lib), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.splitlines()
+    assert "sm_103a" in out[0]
+    life = out[1].split()
+    assert int(life[1]) >= 8192 * 8192 and life[2:] == ["1", "1"]
+    wj = int(out[2].split()[1])
+    assert wj >= 64 ** 3 * 2 and wj % 256 == 0
+    create = out[3].split(maxsplit=3)
+    assert int(create[1]) == -1 and create[2] == "1" and "16-byte aligned" in create[3]
+    assert int(out[4].split()[1]) == 4 << 20
