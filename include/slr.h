@@ -351,18 +351,24 @@ const char *slr_batch_last_error(slr_batch b);
  * Runs d's loop (SLR_J2D5 or SLR_J3D7, any storage, persistent device loop)
  * from the state in u with right-hand side f (both device pointers owned by
  * the caller, layout as for slr_create) until the test passes or max_iters
- * iterations, on `stream`, then waits for the stream and returns the reduced
- * value, the iterations run and the converged flag (NULL outputs are
- * skipped).  Returns SLR_OK / SLR_NOT_CONVERGED like slr_reduce_value,
- * SLR_ERR_INVALID_ARG for a grid whose state exceeds SLR_STATIC_STATE_BYTES
- * (message from slr_static_last_error()), SLR_ERR_UNSUPPORTED for other
- * stencils.
+ * iterations, on `stream`.  Every call then reads the control block back and
+ * waits for the stream before it returns the reduced value, the iterations
+ * run and the converged flag (NULL outputs are skipped).  Returns SLR_OK /
+ * SLR_NOT_CONVERGED like slr_reduce_value, SLR_ERR_INVALID_ARG for a grid
+ * whose state exceeds SLR_STATIC_STATE_BYTES (message from
+ * slr_static_last_error()), SLR_ERR_UNSUPPORTED for other stencils, for
+ * defect correction and for loop = SLR_LOOP_HOST.  Descriptor fields are
+ * read as slr_create reads them (grid_ctas, temporal_k and tiling
+ * included), except that library-choice fields take the built-in defaults,
+ * never the autotuner's cache, and debug_flags is ignored.
  *
  * The first call on each device looks up the array's device address (once per
  * device, with that device current); make that first call before any stream
- * capture begins.  Every call shares the one array: each call clears the
- * control block before it starts, and calls whose GPU work overlaps (several
- * streams or host threads on one device) race on it. */
+ * capture begins.  The address is kept for the life of the process, so the
+ * call must not be used on a device after a cudaDeviceReset of it.  Every
+ * call shares the one array: each call clears the control block before it
+ * starts, and calls whose GPU work overlaps (several streams or host threads
+ * on one device) race on it. */
 #define SLR_STATIC_STATE_BYTES (4u << 20)
 slr_status slr_run_static(const slr_desc *d, void *u, const void *f, int64_t max_iters, void *stream,
                           double *value, int64_t *iters, int32_t *converged);

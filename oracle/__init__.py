@@ -13,9 +13,17 @@ inputs.
 Parity status: every solver here is pinned by the ``-m "not gpu"`` tests in
 ``tests/test_oracle_*.py`` (closed forms, known patterns, brute force, library
 rounding); none is "parity unpinned".
+
+Threads: the same C file also builds with ``-fopenmp`` (``liboracle_omp.so``),
+which shares the rows of each sweep among host threads and leaves every value
+unchanged (the reduces are a maximum, an integer sum and an or).  Inside
+``with threads(n):`` the solvers run that build on n threads; outside it they
+run the single-threaded build.  ``tests/test_oracle_threads.py`` checks that
+both builds agree bit for bit.
 """
 from __future__ import annotations
 
+import contextlib
 import ctypes
 import os
 import subprocess
@@ -26,7 +34,9 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "slr_oracle.c")
 _LIB = os.path.join(_HERE, "liboracle.so")
-_lib = None
+_LIB_OMP = os.path.join(_HERE, "liboracle_omp.so")
+_libs = {}
+_omp_threads = 0          # > 0 inside `with threads(n)`: solvers use the OpenMP build
 
 STORAGE = {"f32": 0, "bf16": 1, "f16": 2}
 
@@ -48,22 +58,56 @@ class Result:
 
 def build(force: bool = False) -> str:
     """Compile ``slr_oracle.c`` into ``liboracle.so`` next to it (gcc, -O2,
-    -ffp-contract=off).  Returns the path of the shared object."""
-    if not force and os.path.exists(_LIB) and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC):
-        return _LIB
-    tmp = _LIB + ".%d.tmp" % os.getpid()
-    cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math",
-           "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"]
-    subprocess.check_call(cmd)
-    os.replace(tmp, _LIB)
+    -ffp-contract=off), and the threaded build ``liboracle_omp.so`` when gcc
+    accepts -fopenmp.  Returns the path of the single-threaded object."""
+    _compile(_LIB, [], force)
+    try:
+        _compile(_LIB_OMP, ["-fopenmp"], force)
+    except (subprocess.CalledProcessError, OSError):
+        pass                                  # no OpenMP here: threads() runs one thread
     return _LIB
 
 
-def _load():
-    global _lib
-    if _lib is not None:
-        return _lib
-    lib = ctypes.CDLL(build())
+def _compile(lib: str, extra, force: bool) -> str:
+    if not force and os.path.exists(lib) and os.path.getmtime(lib) >= os.path.getmtime(_SRC):
+        return lib
+    tmp = lib + ".%d.tmp" % os.getpid()
+    cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-Wno-unknown-pragmas",
+           "-fPIC", "-shared"] + list(extra) + ["-o", tmp, _SRC, "-lm"]
+    subprocess.check_call(cmd, stderr=subprocess.DEVNULL if extra else None)
+    os.replace(tmp, lib)
+    return lib
+
+
+def omp_available() -> bool:
+    """Whether the threaded build exists (gcc with -fopenmp)."""
+    build()
+    return os.path.exists(_LIB_OMP) and os.path.getmtime(_LIB_OMP) >= os.path.getmtime(_SRC)
+
+
+@contextlib.contextmanager
+def threads(n: int):
+    """Run the solvers on n host threads (the OpenMP build) inside the block;
+    yields the thread count actually used (1 without OpenMP)."""
+    global _omp_threads
+    saved = _omp_threads
+    used = 1
+    if n > 1 and omp_available():
+        used = int(_load(True).orc_set_threads(int(n)))
+        _omp_threads = used
+    try:
+        yield used
+    finally:
+        _omp_threads = saved
+
+
+def _load(omp=None):
+    if omp is None:
+        omp = _omp_threads > 0
+    if omp in _libs:
+        return _libs[omp]
+    build()
+    lib = ctypes.CDLL(_LIB_OMP if omp else _LIB)
     P = ctypes.c_void_p
     i64, f64, i32 = ctypes.c_int64, ctypes.c_double, ctypes.c_int
     R = ctypes.POINTER(_CResult)
@@ -94,7 +138,9 @@ def _load():
         getattr(lib, name).restype = None
     lib.orc_round_storage_array.argtypes = [P, P, i64, i32]
     lib.orc_round_storage_array.restype = None
-    _lib = lib
+    lib.orc_set_threads.argtypes = [i32]
+    lib.orc_set_threads.restype = i32
+    _libs[omp] = lib
     return lib
 
 

@@ -11,6 +11,14 @@
  * Build: gcc -O2 -std=c11 -ffp-contract=off -fno-fast-math -shared -fPIC.
  * No fused multiply-add, IEEE round-to-nearest-even, no flush-to-zero.
  *
+ * The same file also builds with -fopenmp, for timing the oracle on every host
+ * core.  The only change that build makes is that the rows (3D: planes and
+ * rows) of one sweep are shared among threads: every new item is still
+ * computed from the old array alone by the same expression, and the per-sweep
+ * reduces are a maximum, a 64-bit integer sum and an or, which give the same
+ * result in any order.  So the threaded build returns bit-for-bit what the
+ * single-threaded one does (a test checks this on every solver).
+ *
  * Every solver is the loop-of-stencil-reduce-d-s procedure of Sec. 3.1 written
  * out step by step:
  *
@@ -43,6 +51,9 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 /* Result of one solve: iterations run, reduced value of the last sweep,
  * whether the convergence test (rather than the cap) stopped the loop, and an
@@ -55,6 +66,19 @@ typedef struct {
     int32_t changed;
     uint64_t count;
 } orc_result;
+
+/* Threads a sweep may use: n >= 1 in the -fopenmp build; the single-threaded
+ * build ignores n.  Returns the number that will be used. */
+int orc_set_threads(int n)
+{
+#ifdef _OPENMP
+    if (n >= 1) omp_set_num_threads(n);
+    return omp_get_max_threads();
+#else
+    (void)n;
+    return 1;
+#endif
+}
 
 /* ------------------------------------------------------------------------- */
 /* Storage rounding (IEEE 754 round to nearest, ties to even).               */
@@ -187,6 +211,7 @@ static double j2d5_sweep_f64(const double *u, double *v, const double *f,
                              int wrap, double ghost)
 {
     double dmax = 0.0;
+#pragma omp parallel for reduction(max : dmax) schedule(static)
     for (int64_t i = 0; i < ny; ++i)
         for (int64_t j = 0; j < nx; ++j) {
             double uN = at2_f64(u, nx, ny, i - 1, j, wrap, ghost);
@@ -246,6 +271,7 @@ int orc_j2d5_f32(float *u, const float *f, int64_t nx, int64_t ny, double sigma,
     int conv = 0;
     do {
         val = 0.0f;
+#pragma omp parallel for reduction(max : val) schedule(static)
         for (int64_t i = 0; i < ny; ++i)
             for (int64_t j = 0; j < nx; ++j) {
                 float s = ((at2_f32(u, nx, ny, i - 1, j, wrap, ghost) +
@@ -290,6 +316,7 @@ int orc_j3d7_f64(double *u, const double *f, int64_t nx, int64_t ny, int64_t nz,
     int conv = 0;
     do {
         val = 0.0;
+#pragma omp parallel for collapse(2) reduction(max : val) schedule(static)
         for (int64_t k = 0; k < nz; ++k)
             for (int64_t i = 0; i < ny; ++i)
                 for (int64_t j = 0; j < nx; ++j) {
@@ -330,6 +357,7 @@ int orc_j3d7_f32(float *u, const float *f, int64_t nx, int64_t ny, int64_t nz,
     int conv = 0;
     do {
         val = 0.0f;
+#pragma omp parallel for collapse(2) reduction(max : val) schedule(static)
         for (int64_t k = 0; k < nz; ++k)
             for (int64_t i = 0; i < ny; ++i)
                 for (int64_t j = 0; j < nx; ++j) {
@@ -377,6 +405,7 @@ int orc_life(uint8_t *a, int64_t nx, int64_t ny, int wrap, int64_t max_gens,
     do {
         live = 0;
         changed = 0;
+#pragma omp parallel for reduction(+ : live) reduction(| : changed) schedule(static)
         for (int64_t i = 0; i < ny; ++i)
             for (int64_t j = 0; j < nx; ++j) {
                 int alive_nbrs = 0;
@@ -433,6 +462,7 @@ int orc_restore8(float *u, const uint8_t *mask, int64_t nx, int64_t ny, float al
     uint64_t sum = 0;
     do {
         sum = 0;
+#pragma omp parallel for reduction(+ : sum) schedule(static)
         for (int64_t i = 0; i < ny; ++i)
             for (int64_t j = 0; j < nx; ++j) {
                 size_t c = (size_t)(i * nx + j);
@@ -485,6 +515,7 @@ static double defect_f64(const double *u, const double *f, double *r, int64_t nx
                          int64_t ny, double h2, double d)
 {
     double rho = 0.0;
+#pragma omp parallel for reduction(max : rho) schedule(static)
     for (int64_t i = 0; i < ny; ++i)
         for (int64_t j = 0; j < nx; ++j) {
             double s = ((at2_f64(u, nx, ny, i - 1, j, 0, 0.0) +
@@ -520,6 +551,7 @@ int orc_j2d5_dc(double *u, const double *f, int64_t nx, int64_t ny, double sigma
     do {
         for (size_t c = 0; c < n; ++c) { r32[c] = (float)r[c]; e[c] = 0.0f; }
         for (int64_t s = 0; s < k_in; ++s) {
+#pragma omp parallel for schedule(static)
             for (int64_t i = 0; i < ny; ++i)
                 for (int64_t j = 0; j < nx; ++j) {
                     float sn = ((at2_f32(e, nx, ny, i - 1, j, 0, 0.0f) +

@@ -511,7 +511,7 @@ struct JacobiTma {
                 while (waited < ic + 1) {
                     ++waited;
                     const unsigned qi = q + (unsigned)waited;
-                    got = got && tma::bounded_wait(bar((int)(qi & (kNS - 1))), (qi / kNS) & 1u, limit_ns, err);
+                    got = got && tma::bounded_wait(bar((int)(qi & (kNS - 1))), (qi / kNS) & 1u, tma::kLoadWaitNs, err);
                 }
                 const int sa = (int)((q + (unsigned)(ic - 1)) & (kNS - 1)), sc = (int)((q + (unsigned)ic) & (kNS - 1)),
                           sb = (int)((q + (unsigned)(ic + 1)) & (kNS - 1));

@@ -321,7 +321,7 @@ __device__ bool tb_pass(const JTb<T> &tp, unsigned char *smem, uint64_t *bar, un
             tma::load_2d(S, &tp.umap[cur], x0, y0, bar);
             tma::load_2d(F, &tp.fmap, x0, y0, bar);
         }
-        const bool ok = tma::bounded_wait(bar, phase & 1u, la.limit_ns, &la.ctl->err);
+        const bool ok = tma::bounded_wait(bar, phase & 1u, tma::kLoadWaitNs, &la.ctl->err);
         ++phase;
         if (!__syncthreads_and(ok)) return false;
         if (tp.ghost_fill && (x0 < 0 || x0 + kTW > tp.nx || y0 < 0 || y0 + Sh::kH > tp.ny)) {

@@ -40,6 +40,7 @@
 #include <cudaTypedefs.h>
 
 #include "slr_internal.cuh"
+#include "tma.cuh"
 
 namespace slr {
 namespace {
@@ -70,41 +71,6 @@ struct TbParams {
     long long nxw, pitch;        // words per row, row pitch in words (multiple of 4)
     int wrap, K, own_rows, tiles_x, tiles_y;
 };
-
-// ---- PTX wrappers -----------------------------------------------------------
-__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
-{
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes)
-{
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
-                 : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
-{
-    uint32_t done;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(done)
-        : "r"(smem_u32(bar)), "r"(parity)
-        : "memory");
-    return done != 0;
-}
-
-__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, int x, int y, uint64_t *bar)
-{
-    asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
-        ::"r"(smem_u32(dst)), "l"((unsigned long long)map), "r"(x), "r"(y), "r"(smem_u32(bar))
-        : "memory");
-}
 
 // ---- cell packing -----------------------------------------------------------
 // Four 0/1 bytes -> 4 bits (byte i -> bit i): the partial products land on
@@ -142,20 +108,6 @@ __device__ __forceinline__ long long wrap_mod(long long v, long long n)
     return v < 0 ? v + n : v;
 }
 
-__device__ __forceinline__ bool bounded_wait(uint64_t *bar, uint32_t parity, long long limit_ns, int *err)
-{
-    long long t0 = 0;
-    unsigned spins = 0;
-    while (!mbar_try_wait(bar, parity)) {
-        if ((++spins & 255u) == 0u) {
-            const long long t = global_timer_ns();
-            if (t0 == 0) t0 = t;
-            else if (t - t0 > limit_ns) { atomicOr(err, DEV_ERR_TIMEOUT); return false; }
-        }
-    }
-    return true;
-}
-
 // ---- phase P: uint8 -> bits ---------------------------------------------------
 __device__ __forceinline__ void issue_pack_unit(const TbParams &tp, int unit, unsigned char *stage, uint64_t *bar)
 {
@@ -165,14 +117,13 @@ __device__ __forceinline__ void issue_pack_unit(const TbParams &tp, int unit, un
     uint32_t bytes = 0;
     for (int b = 0; b < kBoxes; ++b)
         if (x0 + (long long)b * kBoxW < tp.nx) bytes += kBoxBytes;
-    mbar_expect_tx(bar, bytes);
+    tma::mbar_expect_tx(bar, bytes);
     for (int b = 0; b < kBoxes; ++b)
         if (x0 + (long long)b * kBoxW < tp.nx)
-            tma_load_2d(stage + b * kBoxBytes, &tp.cells, (int)(x0 + (long long)b * kBoxW), (int)y, bar);
+            tma::load_2d(stage + b * kBoxBytes, &tp.cells, (int)(x0 + (long long)b * kBoxW), (int)y, bar);
 }
 
-__device__ bool pack_phase(const TbParams &tp, unsigned char *stage, uint64_t *mbar, int *s_ok, long long limit_ns,
-                           int *err)
+__device__ bool pack_phase(const TbParams &tp, unsigned char *stage, uint64_t *mbar, int *s_ok, int *err)
 {
     const int tid = threadIdx.x;
     const int cbs = (int)((tp.nx + kOwnCols - 1) / kOwnCols);
@@ -186,7 +137,7 @@ __device__ bool pack_phase(const TbParams &tp, unsigned char *stage, uint64_t *m
     for (int i = 0; i < mine; ++i) {
         const int unit = (int)blockIdx.x + i * (int)gridDim.x;
         const int sb = i & 1;
-        if (tid == 0) *s_ok = bounded_wait(&mbar[sb], (uint32_t)(i >> 1) & 1u, limit_ns, err);
+        if (tid == 0) *s_ok = tma::bounded_wait(&mbar[sb], (uint32_t)(i >> 1) & 1u, tma::kLoadWaitNs, err);
         __syncthreads();
         if (!*s_ok) return false;
         const long long y0 = (long long)(unit / cbs) * kPackRows;
@@ -401,16 +352,15 @@ __global__ void __launch_bounds__(kThreads, 1) life_tb_kernel(const __grid_const
     if ((la.debug_flags & SLR_DEBUG_SKIP_ARRIVAL) && blockIdx.x == gridDim.x - 1) return;
 
     if (tid == 0) {
-        mbar_init(&mbar[0], 1);
-        mbar_init(&mbar[1], 1);
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        tma::mbar_init(&mbar[0], 1);
+        tma::mbar_init(&mbar[1], 1);
+        tma::mbar_init_fence();
     }
     if (tid < kMaxK) { s_cnt[tid] = 0ull; s_ch[tid] = 0u; }
     __syncthreads();
 
     // ---- P: pack the caller's cells into bits[0]
-    if (!pack_phase(tp, stage, mbar, &s_ok, la.limit_ns, &ctl->err)) return;
+    if (!pack_phase(tp, stage, mbar, &s_ok, &ctl->err)) return;
     unsigned long long bar_target = (unsigned long long)la.nblocks;
     if (!grid_barrier(ctl, bar_target, la.limit_ns)) return;
 
@@ -490,23 +440,9 @@ __global__ void __launch_bounds__(kThreads, 1) life_tb_kernel(const __grid_const
     }
 }
 
-PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
-{
-    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-    if (!fn) {
-        void *p = nullptr;
-        cudaDriverEntryPointQueryResult qr;
-        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &qr) ==
-                cudaSuccess &&
-            qr == cudaDriverEntryPointSuccess)
-            fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
-    }
-    return fn;
-}
-
 bool make_cells_map(CUtensorMap *m, void *base, long long nx, long long ny)
 {
-    auto fn = encode_fn();
+    auto fn = tma::encode_fn();
     if (!fn) return false;
     cuuint64_t dims[2] = {(cuuint64_t)nx, (cuuint64_t)ny};
     cuuint64_t strides[1] = {(cuuint64_t)nx};
@@ -525,7 +461,7 @@ bool life_tb_supported(const Problem &p)
 {
     if (p.nx % 32 != 0 || p.nx < 32 || p.ny < 1) return false;
     if (p.nx >= (1ll << 31) || p.ny >= (1ll << 31)) return false;
-    return encode_fn() != nullptr;
+    return tma::encode_fn() != nullptr;
 }
 
 size_t life_tb_bits_bytes(long long nx, long long ny) { return (size_t)(pitch_words(nx) * ny * 4); }

@@ -206,7 +206,7 @@ struct RestoreTma {
             const int x0 = (tile % tiles_x) * kTW, y0 = (tile / tiles_x) * kTH;
             const float *U = (const float *)(stages() + sb * kStage);   // [34][72]: row y0-1+r, column x0-4+c
             const unsigned char *M = stages() + sb * kStage + kUBytes;  // [34][96]: row y0-1+r, column x0-16+c
-            const bool got = tma::bounded_wait(&bars()[sb], (qn / kNS) & 1u, 2000000000ll, err);
+            const bool got = tma::bounded_wait(&bars()[sb], (qn / kNS) & 1u, tma::kLoadWaitNs, err);
             if (!__all_sync(0xffffffffu, got)) break;
             // the warp's four rows: clean pixels copied, noisy ones listed
             int n = 0;

@@ -40,7 +40,9 @@ slr_status static_fail(slr_status s, const std::string &msg)
 
 // Device address of the scratch array on the current device.  In host code the
 // array's name is only a host-side stand-in, so the address comes from the
-// runtime, once per device, with that device current.
+// runtime, once per device, with that device current.  The address is kept
+// for the life of the process: a cudaDeviceReset of that device unloads the
+// module and leaves it stale, so this entry point must not be used after one.
 slr_status scratch_address(void **out)
 {
     int dev = -1;
@@ -71,6 +73,8 @@ slr_status slr_run_static(const slr_desc *d, void *u, const void *f, int64_t max
     if (!why.empty()) return static_fail(unsup ? SLR_ERR_UNSUPPORTED : SLR_ERR_INVALID_ARG, why);
     if ((d->stencil != SLR_J2D5 && d->stencil != SLR_J3D7) || d->defect_correction)
         return static_fail(SLR_ERR_UNSUPPORTED, "slr_run_static runs the Jacobi stencils (SLR_J2D5, SLR_J3D7) only");
+    if (d->loop == SLR_LOOP_HOST)
+        return static_fail(SLR_ERR_UNSUPPORTED, "slr_run_static runs the persistent device loop only (loop AUTO or PERSISTENT)");
     if (!u || ((uintptr_t)u & 15u)) return static_fail(SLR_ERR_INVALID_ARG, "u must be a 16-byte aligned device pointer");
     if (!f) return static_fail(SLR_ERR_INVALID_ARG, "f is required");
     if (max_iters < 0) return static_fail(SLR_ERR_INVALID_ARG, "max_iters must be >= 0");
@@ -101,7 +105,7 @@ slr_status slr_run_static(const slr_desc *d, void *u, const void *f, int64_t max
     la.limit_ns = d->wait_limit_ns > 0 ? d->wait_limit_ns : 2000000000ll;
     la.tol = p.tol;
     la.reduce = p.reduce;
-    la.nblocks = 0;
+    la.nblocks = d->grid_ctas;
     la.debug_flags = 0;
     e = slr::jacobi_tb_resolve_k(p, la.a, la.b, la.aux) > 1 ? slr::jacobi_tb_persistent(p, la, st)
                                                              : slr::jacobi_persistent(p, la, st);

@@ -44,6 +44,13 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
     return done != 0;
 }
 
+// Limit of every wait for a TMA load's mbarrier: a load completes in
+// microseconds, so only a lost transfer can reach it.  It is fixed rather
+// than the caller's grid-barrier limit, which may be short enough to expire
+// during an ordinary load under contention and leave a CTA while its copy
+// is still writing shared memory.
+constexpr long long kLoadWaitNs = 2000000000ll;
+
 // Wait for phase `parity` of `bar`, giving up after limit_ns of %globaltimer
 // (sets DEV_ERR_TIMEOUT in *err and returns false).
 __device__ __forceinline__ bool bounded_wait(uint64_t *bar, uint32_t parity, long long limit_ns, int *err)

@@ -77,7 +77,7 @@ def test_static_solve_refuses_what_its_array_cannot_hold(slr):
     assert st == slr.SLR_ERR_INVALID_ARG
     # other stencils, defect correction, a misaligned u, no f, a negative cap
     for stencil, change in [(slr.SLR_LIFE, {}), (slr.SLR_RESTORE8, {}),
-                            (slr.SLR_J2D5, dict(defect_correction=1))]:
+                            (slr.SLR_J2D5, dict(defect_correction=1)), (slr.SLR_J2D5, dict(loop=slr.SLR_LOOP_HOST))]:
         d = slr.slr_desc_init(stencil, 64, 64, 1, **change)
         st, *_ = slr.slr_run_static(d, FAKE_U, FAKE_AUX, 10, 0, check=False)
         assert st == slr.SLR_ERR_UNSUPPORTED, (stencil, change)
