@@ -163,21 +163,32 @@ def max_over_ranks(x: float, world: int) -> float:
     return float(t.item())
 
 
-def oracle_life_sample(nx: int, ny: int, budget_s: float):
+def host_cores() -> int:
+    """Host cores this process may run on (nproc)."""
+    try:
+        return len(os.sched_getaffinity(0))
+    except (AttributeError, OSError):
+        return os.cpu_count() or 1
+
+
+def oracle_life_sample(nx: int, ny: int, budget_s: float, cores: int = 1):
     """Time the oracle on the same torus for as many generations as fit in
-    about budget_s seconds (at least one).  Returns (gcells_per_s, gens, secs)."""
+    about budget_s seconds (at least one), on `cores` host threads (the
+    oracle's OpenMP build; 1 = the plain single-threaded build).  Returns
+    (gcells_per_s, gens, secs, threads used)."""
     import oracle
     from paper_1609_04567_gb300 import inputs
     cells = inputs.life_cells(ny, nx)
-    t0 = time.perf_counter()
-    state, _ = oracle.life(cells, wrap=True, max_gens=1)
-    one = time.perf_counter() - t0
-    gens = max(1, min(16, int(budget_s / max(one, 1e-9)) - 1))
-    t0 = time.perf_counter()
-    oracle.life(state, wrap=True, max_gens=gens)
-    secs = time.perf_counter() - t0
+    with oracle.threads(cores) as used:
+        t0 = time.perf_counter()
+        state, _ = oracle.life(cells, wrap=True, max_gens=1)
+        one = time.perf_counter() - t0
+        gens = max(1, min(16, int(budget_s / max(one, 1e-9)) - 1))
+        t0 = time.perf_counter()
+        oracle.life(state, wrap=True, max_gens=gens)
+        secs = time.perf_counter() - t0
     total_gens, total_secs = gens + 1, secs + one
-    return nx * ny * total_gens / total_secs / 1e9, total_gens, total_secs
+    return nx * ny * total_gens / total_secs / 1e9, total_gens, total_secs, used
 
 
 def run_reference(args, wl, world, rank):
@@ -186,26 +197,30 @@ def run_reference(args, wl, world, rank):
     import oracle
     from paper_1609_04567_gb300 import inputs
     oracle.build()
-    # each step: one generation of an 8192-wide, 2048-row torus through the
-    # oracle (a bounded sample of the 2000-generation 8192 x 8192 workload with
-    # the same per-cell work; the metric is per cell-update)
-    rows = 2048
-    state = inputs.life_cells(rows, wl["nx"])
-    for _ in range(args.warmup):
-        state, _ = oracle.life(state, wrap=True, max_gens=1)
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        state, _ = oracle.life(state, wrap=True, max_gens=1)
-    secs = time.perf_counter() - t0
-    value = wl["nx"] * rows * args.steps / secs / 1e9
-    sample = f"1 generation of an {wl['nx']}x{rows} torus per step (same per-cell work), single-threaded plain C"
+    # each step: one generation of the workload's own 8192 x 8192 torus through
+    # the oracle on every host core (its OpenMP build: the rows of the sweep
+    # shared among threads, the same values as the plain build); a bounded
+    # sample of the 2000-generation run, the metric is per cell-update
+    cores = host_cores()
+    state = inputs.life_cells(wl["ny"], wl["nx"])
+    with oracle.threads(cores) as used:
+        for _ in range(args.warmup):
+            state, _ = oracle.life(state, wrap=True, max_gens=1)
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            state, _ = oracle.life(state, wrap=True, max_gens=1)
+        secs = time.perf_counter() - t0
+    value = wl["nx"] * wl["ny"] * args.steps / secs / 1e9
+    sample = (f"1 generation of the {wl['nx']}x{wl['ny']} torus per step, generations {args.warmup + 1}.."
+              f"{args.warmup + args.steps} of the seeded input, plain C oracle on {used} threads")
     line = {
         "impl": "reference", "metric": "Gcell-updates/s", "value": value, "unit": "Gcell-updates/s",
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": secs / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "u8", "data": "synthetic",
         "config": {"workload": wl["name"].format(gens=wl["gens"]), "sample": sample},
-        "cpu_baseline": {"value": value, "unit": "Gcell-updates/s", "cores": 1, "kind": "oracle", "sample": sample},
+        "cpu_baseline": {"value": value, "unit": "Gcell-updates/s", "cores": used, "kind": "oracle", "sample": sample,
+                         "host_cores": cores},
         "e2e": {"value": value, "unit": "Gcell-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -387,9 +402,14 @@ def run_ours(args, wl, world, rank, local):
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
-        v, g, s = oracle_life_sample(nx, ny, args.cpu_budget)
-        cpu = {"value": v, "unit": "Gcell-updates/s", "cores": 1, "kind": "oracle",
-               "sample": f"{g} generations of the 8192x8192 torus, {s:.1f} s, single-threaded plain C"}
+        # the oracle on every host core (OpenMP over rows) and on one core
+        cores = host_cores()
+        v, g, s, used = oracle_life_sample(nx, ny, args.cpu_budget, cores)
+        v1, g1, s1, _ = oracle_life_sample(nx, ny, args.cpu_budget, 1)
+        cpu = {"value": v, "unit": "Gcell-updates/s", "cores": used, "kind": "oracle", "host_cores": cores,
+               "sample": f"{g} generations of the 8192x8192 torus, {s:.1f} s, plain C oracle on {used} threads",
+               "single_core": {"value": v1, "unit": "Gcell-updates/s", "cores": 1, "kind": "oracle",
+                               "sample": f"{g1} generations of the 8192x8192 torus, {s1:.1f} s, single-threaded"}}
 
     if rank == 0:
         line = {
@@ -413,8 +433,32 @@ def run_ours(args, wl, world, rank, local):
             "result": {"iters": res[2], "live": res[4], "converged": res[3],
                        "same_as_warmup": first[1:] == res[1:]},
         }
+        if world == 1 and not args.no_configs:
+            line["configs"] = measure_configs(args)
         print(json.dumps(line), flush=True)
     return 0
+
+
+def measure_configs(args):
+    """The other configurations of the metric, each with its own CUDA-event
+    times and clock record: the 256^2 FP64 Helmholtz solve (plain vs fused vs
+    tuned), the 4096^2 restoration (fused EXACT/FAST vs plain, HBM and
+    special-function fractions), the large single Jacobi grids (one sweep per
+    HBM pass and temporal-blocked), and a short run of the serving
+    configuration."""
+    import torch
+    out = {}
+    for name, fn in (("helmholtz_256_f64", measure_helmholtz), ("restore_4096_f32", measure_restore),
+                     ("jacobi_large_grids", measure_jacobi),
+                     ("serve_2000rps", lambda a: measure_serve_short(a, args.configs_serve_seconds))):
+        t0 = time.perf_counter()
+        try:
+            out[name] = fn(args)
+        except Exception as e:                     # one failed leg must not hide the others
+            out[name] = {"error": f"{type(e).__name__}: {e}"}
+        out[name]["wall_s"] = time.perf_counter() - t0
+        torch.cuda.empty_cache()
+    return out
 
 
 def _stream_time(stream, fn, steps, flush=None):
@@ -445,6 +489,11 @@ def _stream_time(stream, fn, steps, flush=None):
 
 
 def run_helmholtz(args):
+    print(json.dumps(measure_helmholtz(args)), flush=True)
+    return 0
+
+
+def measure_helmholtz(args):
     """2D Helmholtz Jacobi 256 x 256 FP64, tol 1e-6, cap 5000: time to solution."""
     import numpy as np
     import torch
@@ -458,6 +507,8 @@ def run_helmholtz(args):
     l2_flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
     res = {}
     tuned = None
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
     runs = [("fused_device_loop", slr.SLR_LOOP_PERSISTENT), ("plain", slr.SLR_LOOP_HOST)]
     if not args.no_tune:
         runs.append(("fused_tuned", slr.SLR_LOOP_AUTO))
@@ -516,21 +567,38 @@ __device__ double slr_delta(slr_t a, slr_t b) { return fabs(a - b); }
     res["user_functions"] = {"ms_per_solve": user_ms, "iters": uit, "gcell_per_s": n * n * uit / user_ms / 1e6,
                              "what": "slr_update / slr_delta compiled at run time, the loop in one cooperative "
                                      "launch; wall time per solve including the handle's set-up and result read"}
+    clk = clocks.stop()
     t0 = time.perf_counter()
     _, rr = oracle.j2d5(np.zeros((n, n)), f.cpu().numpy(), tol=1e-6, max_iters=5000)
     cpu_ms = (time.perf_counter() - t0) * 1e3
+    cores = host_cores()
+    with oracle.threads(cores) as used:
+        t0 = time.perf_counter()
+        oracle.j2d5(np.zeros((n, n)), f.cpu().numpy(), tol=1e-6, max_iters=5000)
+        cpu_mt_ms = (time.perf_counter() - t0) * 1e3
     best = res.get("fused_tuned", res["fused_device_loop"])
-    line = {"workload": "helmholtz_256x256_f64_tol1e-6", "metric": "time-to-solution", "unit": "ms",
+    return {"workload": "helmholtz_256x256_f64_tol1e-6", "metric": "time-to-solution", "unit": "ms",
             "value": best["ms_per_solve"], "higher_is_better": False, "sweeps": rr.iters,
+            "same_sweeps_as_oracle": all(v["iters"] == rr.iters for v in res.values()),
             "l2": "device-loop solves: L2 flushed before each, outside its events",
             "fused": res["fused_device_loop"], "plain": res["plain"], "tuned": res.get("fused_tuned"),
-            "user_functions": res["user_functions"], "tuner": tuned,
-            "cpu_baseline": {"value": cpu_ms, "unit": "ms", "cores": 1, "kind": "oracle", "sample": "full solve"}}
-    print(json.dumps(line), flush=True)
-    return 0
+            "user_functions": res["user_functions"], "tuner": tuned, "clocks": clk,
+            "cpu_baseline": {"value": cpu_mt_ms, "unit": "ms", "cores": used, "kind": "oracle",
+                             "sample": "full solve", "host_cores": cores,
+                             "single_core": {"value": cpu_ms, "unit": "ms", "cores": 1, "kind": "oracle",
+                                             "sample": "full solve"}}}
 
 
 def run_restore(args):
+    print(json.dumps(measure_restore(args)), flush=True)
+    return 0
+
+
+# MUFU (special-function) lanes per SM per clock: 4 sub-partitions x 4
+XU_LANES_PER_SM = 16
+
+
+def measure_restore(args):
     """Restoration 4096 x 4096 FP32, 50% salt-and-pepper, tol 1e-3."""
     import numpy as np
     import torch
@@ -546,19 +614,25 @@ def run_restore(args):
     l2_flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
     res = {}
     tuned = None
-    runs = [("fused_exact", slr.SLR_LOOP_PERSISTENT, slr.SLR_MATH_EXACT),
-            ("fused_fast", slr.SLR_LOOP_PERSISTENT, slr.SLR_MATH_FAST),
-            ("plain_exact", slr.SLR_LOOP_HOST, slr.SLR_MATH_EXACT)]
+    peak, peak_src = measured_peaks()
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    # fused: the library default (temporal blocking, 8 sweeps per HBM pass);
+    # fused_exact_k1: one sweep per pass (the TMA-tiled one-sweep kernel)
+    runs = [("fused_exact", slr.SLR_LOOP_PERSISTENT, slr.SLR_MATH_EXACT, 0),
+            ("fused_exact_k1", slr.SLR_LOOP_PERSISTENT, slr.SLR_MATH_EXACT, 1),
+            ("fused_fast", slr.SLR_LOOP_PERSISTENT, slr.SLR_MATH_FAST, 0),
+            ("plain_exact", slr.SLR_LOOP_HOST, slr.SLR_MATH_EXACT, 0)]
     if not args.no_tune:
-        runs.append(("tuned_exact", slr.SLR_LOOP_AUTO, slr.SLR_MATH_EXACT))
-    for name, loop, math in runs:
+        runs.append(("tuned_exact", slr.SLR_LOOP_AUTO, slr.SLR_MATH_EXACT, 0))
+    for name, loop, math, k in runs:
         if loop == slr.SLR_LOOP_AUTO:
             t0 = time.perf_counter()
             with torch.cuda.stream(stream):
                 tuned = slr.tune(slr.SLR_RESTORE8, init, mask, stream=stream, trial_iters=16)
             tuned["seconds"] = time.perf_counter() - t0
         with torch.cuda.stream(stream):
-            desc = slr.slr_desc_init(slr.SLR_RESTORE8, n, n, 1, loop=loop, math=math)
+            desc = slr.slr_desc_init(slr.SLR_RESTORE8, n, n, 1, loop=loop, math=math, temporal_k=k)
             wsb = slr.slr_workspace_size(desc)
             ws = torch.empty(wsb + 256, dtype=torch.uint8, device="cuda")
             wp = ws.data_ptr() + ((-ws.data_ptr()) % 256)
@@ -585,21 +659,58 @@ def run_restore(args):
                 slr.slr_destroy(h)
         res[name] = {"ms_per_solve": ms, "iters": r[2], "value": r[1], "gcell_per_s": n * n * r[2] / ms / 1e6,
                      "hbm_gbs": 9.0 * n * n * r[2] / ms / 1e6}
+    clk = clocks.stop()
+    # the two ceilings of this stencil: HBM (9 algorithmic bytes per pixel and
+    # sweep: the binary32 state read and written, the uint8 mask read) and the
+    # special-function unit (each weight 1/sqrt(alpha + t^2) takes a square
+    # root and a reciprocal: two MUFU operations per in-range neighbour of a
+    # noisy pixel)
+    m = inputs.noise_mask(frame).astype(bool)
+    nbrs = np.zeros((n + 2, n + 2), dtype=np.int64)
+    inside = np.zeros((n + 2, n + 2), dtype=np.int64)
+    inside[1:-1, 1:-1] = 1
+    for dy in (-1, 0, 1):
+        for dx in (-1, 0, 1):
+            if dy or dx:
+                nbrs[1:-1, 1:-1] += inside[1 + dy:n + 1 + dy, 1 + dx:n + 1 + dx]
+    weights = int(nbrs[1:-1, 1:-1][m].sum())
+    clock_mhz = clk.get("sm_mhz") or 2070.0
+    xu_peak = XU_LANES_PER_SM * SMS * clock_mhz * 1e6 / 1e12          # T MUFU ops/s
+    for name, r in res.items():
+        if name.startswith("plain"):
+            continue
+        r["hbm_frac"] = r["hbm_gbs"] / peak
+        r["xu_tops"] = 2.0 * weights * r["iters"] / (r["ms_per_solve"] / 1e3) / 1e12
+        r["xu_frac"] = r["xu_tops"] / xu_peak
     t0 = time.perf_counter()
     oracle.restore8(frame.astype(np.float32), inputs.noise_mask(frame), tol=0.0, max_iters=2)
     cpu_s = time.perf_counter() - t0
-    line = {"workload": "restore_4096x4096_f32_tol1e-3", "metric": "Gcell-updates/s", "unit": "Gcell-updates/s",
+    cores = host_cores()
+    with oracle.threads(cores) as used:
+        t0 = time.perf_counter()
+        oracle.restore8(frame.astype(np.float32), inputs.noise_mask(frame), tol=0.0, max_iters=4)
+        cpu_mt_s = time.perf_counter() - t0
+    return {"workload": "restore_4096x4096_f32_tol1e-3", "metric": "Gcell-updates/s", "unit": "Gcell-updates/s",
             "l2": "device-loop solves: L2 flushed before each, outside its events",
             "value": res.get("tuned_exact", res["fused_exact"])["gcell_per_s"], "fused_exact": res["fused_exact"],
             "fused_fast": res["fused_fast"], "plain_exact": res["plain_exact"], "tuned_exact": res.get("tuned_exact"),
-            "tuner": tuned,
-            "cpu_baseline": {"value": n * n * 2 / cpu_s / 1e9, "unit": "Gcell-updates/s", "cores": 1,
-                             "kind": "oracle", "sample": "2 sweeps of the 4096x4096 frame"}}
-    print(json.dumps(line), flush=True)
-    return 0
+            "tuner": tuned, "clocks": clk,
+            "roofline": {"hbm_peak_gbs": peak, "peak_source": peak_src, "algorithmic_bytes_per_pixel_sweep": 9,
+                         "xu_peak_tops": xu_peak, "mufu_ops_per_sweep": 2 * weights,
+                         "xu_peak_source": f"{XU_LANES_PER_SM} MUFU lanes/SM x {SMS} SMs x median SM clock"},
+            "cpu_baseline": {"value": n * n * 4 / cpu_mt_s / 1e9, "unit": "Gcell-updates/s", "cores": used,
+                             "kind": "oracle", "sample": "4 sweeps of the 4096x4096 frame", "host_cores": cores,
+                             "single_core": {"value": n * n * 2 / cpu_s / 1e9, "unit": "Gcell-updates/s",
+                                             "cores": 1, "kind": "oracle",
+                                             "sample": "2 sweeps of the 4096x4096 frame"}}}
 
 
 def run_jacobi(args):
+    print(json.dumps(measure_jacobi(args)), flush=True)
+    return 0
+
+
+def measure_jacobi(args):
     """Large single Jacobi grids, HBM-bound: 2D 5-point 8192 x 8192 in FP32 and
     BF16 storage, 3D 7-point 512^3 in BF16 storage; a fixed number of sweeps
     (convergence test never met) in one persistent launch; HBM GB/s from the
@@ -616,8 +727,13 @@ def run_jacobi(args):
              ("j2d5_8192x8192_f32_k8", slr.SLR_J2D5, (8192, 8192), torch.float32, 200, 8),
              ("j2d5_8192x8192_bf16_k8", slr.SLR_J2D5, (8192, 8192), torch.bfloat16, 200, 8)]
     out = {}
+    rhs = {}                                       # the seeded f of each shape, generated once
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
     for name, stencil, shape, dt, sweeps, k in cases:
-        f = torch.from_numpy(inputs.helmholtz_rhs(shape)).to(torch.float32).to(dt).cuda()
+        if shape not in rhs:
+            rhs[shape] = torch.from_numpy(inputs.helmholtz_rhs(shape)).to(torch.float32)
+        f = rhs[shape].to(dt).cuda()
         u = torch.zeros(shape, dtype=dt, device="cuda")
         with torch.cuda.stream(stream):
             s = slr.Solver(stencil, u, f, stream=stream, tol=0.0, temporal_k=k)
@@ -643,10 +759,12 @@ def run_jacobi(args):
             # next to the one-sweep-per-pass equivalent above
             out[name]["pass_hbm_gbs"] = gbs / k
             out[name]["pass_frac"] = gbs / k / peak
-    line = {"workload": "jacobi_large_grids", "metric": "HBM GB/s per sweep", "unit": "GB/s",
-            "peak": peak, "peak_source": peak_src, "cases": out}
-    print(json.dumps(line), flush=True)
-    return 0
+        del f, u
+    clk = clocks.stop()
+    return {"workload": "jacobi_large_grids", "metric": "HBM GB/s per sweep", "unit": "GB/s",
+            "peak": peak, "peak_source": peak_src, "cases": out, "clocks": clk,
+            "what": "fixed sweeps (tol 0) in one persistent launch; GB/s = 3 x element size x cells x sweeps / "
+                    "CUDA-event time (u and f read, u' written once per sweep); k > 1: sweeps per HBM pass"}
 
 
 def run_precision(args):
@@ -787,6 +905,33 @@ def run_batch(args):
     print(json.dumps(line), flush=True)
     b.close()
     return 0
+
+
+def measure_serve_short(args, seconds: float):
+    """The serving configuration (Poisson 2000 req/s, half denoise jobs of
+    sides 256-4096, half Helmholtz solves of sides 64-2048) for a short run:
+    1 s of warm-up arrivals and `seconds` of measured arrivals, served to the
+    last request."""
+    import torch
+    from paper_1609_04567_gb300 import serve, slr
+    slr.load()
+    reqs = serve.make_requests(seconds + 1.0, args.rate)
+    srv = serve.Server(max_slots=1024, step_sweeps=args.step_sweeps, solo_cells=args.solo_cells or None)
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    st = srv.serve(reqs, warmup_s=1.0, time_limit_s=seconds * 6 + 30)
+    clk = clocks.stop()
+    srv.close()
+    num = (lambda x: None if x != x else x)
+    offered = sum(1 for r in reqs if r.arrival >= 1.0)
+    return {"workload": f"serve_poisson{args.rate:g}rps_denoise256-4096_solve64-2048_{seconds:g}s",
+            "metric": "p50/p99 latency and throughput", "unit": "ms", "p50_ms": num(st.p50_ms),
+            "p99_ms": num(st.p99_ms), "mean_ms": num(st.mean_ms), "throughput_rps": st.throughput_rps,
+            "offered_rps": args.rate, "offered_after_warmup": offered, "completed_after_warmup": st.measured,
+            "requests": st.requests, "completed": st.completed, "wall_s": st.wall_s,
+            "gcell_per_s": st.gcell_per_s, "max_queue": st.max_queue, "max_in_flight": st.max_in_flight,
+            "clocks": clk,
+            "what": "latency = arrival to the poll that sees the request finished; every arrival is served"}
 
 
 def run_serve(args):
@@ -959,6 +1104,11 @@ def main():
     ap.add_argument("--grid-ctas", type=int, default=0, help="CTAs of the persistent launch (0 = library choice)")
     ap.add_argument("--tune-iters", type=int, default=240, help="iterations per autotuner trial")
     ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--no-configs", action="store_true",
+                    help="default workload: leave out the other configurations (Helmholtz, restoration, "
+                         "large Jacobi grids, serving) from the line")
+    ap.add_argument("--configs-serve-seconds", type=float, default=2.5,
+                    help="seconds of measured arrivals of the serving configuration in the default line")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=12.0)
     args = ap.parse_args()

@@ -115,12 +115,14 @@ typedef struct {
     int32_t temporal_k;    /* sweeps per HBM pass, 1 = one.  Life: 1 .. 32.  SLR_J2D5 with
                               binary32 arithmetic (storage F32, BF16 or F16), a Dirichlet
                               ghost exact in the storage type, rows of whole 16-byte
-                              groups: 1 .. 8 (larger values
-                              run 8; a solve that stops inside a pass recomputes that pass
-                              up to the stopping sweep, so results equal those of k = 1).
+                              groups: 1 .. 8.  SLR_RESTORE8 with nx a multiple of 16:
+                              1 .. 8.  (Larger values run 8; a solve that stops inside a
+                              pass recomputes that pass up to the stopping sweep, so
+                              results equal those of k = 1.)
                               0 = library choice: the autotuner's, else for Life the
                               largest k in [4, 32] whose tiles fit the co-resident CTAs,
-                              for SLR_J2D5 8 when tiling is SLR_TILING_AUTO (1 otherwise) */
+                              for SLR_J2D5 and SLR_RESTORE8 8 when tiling is
+                              SLR_TILING_AUTO (1 otherwise) */
     int64_t wait_limit_ns; /* device-side barrier wait limit; <= 0 selects 2 s */
     int32_t debug_flags;   /* SLR_DEBUG_* bits; 0 in normal use */
     int32_t defect_correction; /* 1: FP64 defect correction around FP32 Jacobi inner solves
@@ -337,6 +339,51 @@ slr_status slr_batch_remove(slr_batch b, int32_t slot);
 slr_status slr_batch_destroy(slr_batch b);
 const char *slr_batch_last_error(slr_batch b);
 
+/* ---- One grid over n devices: the device step of a row-block split ----------
+ * The 1:n deployment of Sec. 3.3 (Fig. 2) cuts one grid into row blocks (3D:
+ * slabs of z-planes), one per device; before each sweep (or each pass of k
+ * sweeps) the rows next to a block are copied in from the blocks that own
+ * them, and the partial reduces of the devices are combined into the value
+ * the convergence test reads.  slr_block_sweep is the device step: one sweep
+ * of one block.  The halo exchange, the combination of the partials and the
+ * test run on the host (paper_1609_04567_gb300/split.py drives them over
+ * torch.distributed or, for several blocks on one device, local copies).
+ *
+ * d describes the whole grid (stencil, storage, boundary, nx, ny, nz, sigma,
+ * h, ghost, alpha; defect correction is not accepted).  src, dst and aux are
+ * device arrays of b->rows consecutive grid rows (3D: z-planes of ny x nx
+ * items), row-major like the grid; aux (f or mask) has the same layout as the
+ * state.  Rows [b->lo, b->hi) of dst receive the update of the same rows of
+ * src, item for item the whole-grid sweep's; rows of dst outside that range
+ * are not written.  The change is reduced over rows [b->own_lo, b->own_hi)
+ * into *partial (a device pointer, cleared by the call): the maximum
+ * |u' - u| as binary64 bits (Jacobi), the 2^-24 fixed-point sum of |u' - u|
+ * and the masked count (restoration), the live count (Life) and "any item
+ * changed".  Block row r is global row b->row0 + r; a row beyond the grid's
+ * first or last row is the boundary (the Dirichlet ghost, a dead cell, or
+ * left out of the restoration's sums) and is never updated; with SLR_WRAP the
+ * caller's copied-in rows hold the wrapped rows.  Enqueued on `stream`;
+ * SLR_ERR_INVALID_ARG when the ranges are inconsistent or an updated row's
+ * neighbour row lies outside the block array (message in
+ * slr_last_error(NULL)). */
+typedef struct {
+    int64_t rows;            /* rows (3D: z-planes) in the block arrays, copied-in rows included */
+    int64_t row0;            /* global index of block row 0 */
+    int64_t lo, hi;          /* block rows updated: [lo, hi) */
+    int64_t own_lo, own_hi;  /* block rows reduced: [own_lo, own_hi), inside [lo, hi) */
+} slr_block;
+
+typedef struct {
+    uint64_t maxbits;        /* max |delta| as binary64 bits (Jacobi) */
+    uint64_t sum;            /* sum of |delta| truncated to multiples of 2^-24 (restoration) */
+    uint64_t count;          /* live cells (Life), masked pixels (restoration) */
+    uint32_t changed;        /* any item changed */
+    uint32_t reserved;
+} slr_partial;
+
+slr_status slr_block_sweep(const slr_desc *d, const slr_block *b, const void *src, void *dst, const void *aux,
+                           slr_partial *partial, void *stream);
+
 /* ---- A Jacobi solve that allocates nothing ---------------------------------
  * The paper has no counterpart to this call; it serves callers that cannot
  * allocate device memory when they need a solve (a device-memory budget owned
@@ -383,7 +430,7 @@ const char *slr_static_last_error(void);
  * slr_tune searches the fields of *d left at their library-choice value:
  *   loop        (SLR_LOOP_AUTO: persistent device loop or the host-driven loop;
  *                defect correction keeps the persistent loop),
- *   temporal_k  (0, Life and SLR_J2D5: sweeps per HBM pass, 1 = none),
+ *   temporal_k  (0, Life, SLR_J2D5 and SLR_RESTORE8: sweeps per HBM pass, 1 = none),
  *   tiling      (SLR_TILING_AUTO, RESTORE8 and Jacobi without defect correction:
  *                TMA tiles or none),
  *   grid_ctas   (0: CTAs of the persistent launch),
@@ -398,7 +445,7 @@ const char *slr_static_last_error(void);
  *   scratch     device buffer of slr_tune_scratch_size(d) bytes, 256-byte
  *               aligned, owned by the caller; free to reuse after return.
  *   out         receives the choice with every searched field explicit (loop
- *               HOST or PERSISTENT, temporal_k >= 1 for Life and SLR_J2D5, tiling NONE or TMA
+ *               HOST or PERSISTENT, temporal_k >= 1 for Life, SLR_J2D5 and SLR_RESTORE8, tiling NONE or TMA
  *               for RESTORE8, grid_ctas >= 0 where 0 kept the default), the
  *               number of candidates timed and the two scores; may be NULL.
  * The call waits for `stream`.  It stores the choice under (device, SM count,
@@ -407,7 +454,7 @@ const char *slr_static_last_error(void);
  * (floor(log2)).  slr_create then fills the library-choice fields of a
  * descriptor from the exact entry, else from the bucket entry, else from the
  * built-in defaults; grid_ctas only when the descriptor then names the
- * choice's loop, temporal_k (Life, SLR_J2D5) and tiling, the kernel that
+ * choice's loop, temporal_k (Life, SLR_J2D5, SLR_RESTORE8) and tiling, the kernel that
  * grid size was timed with.  Returns SLR_OK, SLR_ERR_INVALID_ARG / UNSUPPORTED for a
  * descriptor slr_create would refuse or a NULL/misaligned pointer,
  * SLR_ERR_WORKSPACE for a short scratch, or the error of a failed trial

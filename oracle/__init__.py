@@ -47,6 +47,16 @@ class _CResult(ctypes.Structure):
                 ("count", ctypes.c_uint64)]
 
 
+class _CBlock(ctypes.Structure):
+    _fields_ = [("rows", ctypes.c_int64), ("row0", ctypes.c_int64), ("lo", ctypes.c_int64), ("hi", ctypes.c_int64),
+                ("own_lo", ctypes.c_int64), ("own_hi", ctypes.c_int64)]
+
+
+class _CPartial(ctypes.Structure):
+    _fields_ = [("maxbits", ctypes.c_uint64), ("sum", ctypes.c_uint64), ("count", ctypes.c_uint64),
+                ("changed", ctypes.c_uint64)]
+
+
 @dataclass
 class Result:
     iters: int
@@ -140,6 +150,17 @@ def _load(omp=None):
     lib.orc_round_storage_array.restype = None
     lib.orc_set_threads.argtypes = [i32]
     lib.orc_set_threads.restype = i32
+    B, PT = ctypes.POINTER(_CBlock), ctypes.POINTER(_CPartial)
+    f32 = ctypes.c_float
+    lib.orc_j2d5_block_f64.argtypes = [P, P, P, i64, i64, B, f64, f64, i32, f64, PT]
+    lib.orc_j2d5_block_f32.argtypes = [P, P, P, i64, i64, B, f64, f64, i32, f32, i32, PT]
+    lib.orc_j3d7_block_f64.argtypes = [P, P, P, i64, i64, i64, B, f64, f64, i32, f64, PT]
+    lib.orc_j3d7_block_f32.argtypes = [P, P, P, i64, i64, i64, B, f64, f64, i32, f32, i32, PT]
+    lib.orc_life_block.argtypes = [P, P, i64, i64, B, i32, PT]
+    lib.orc_restore8_block.argtypes = [P, P, P, i64, i64, B, f32, PT]
+    for name in ("orc_j2d5_block_f64", "orc_j2d5_block_f32", "orc_j3d7_block_f64", "orc_j3d7_block_f32",
+                 "orc_life_block", "orc_restore8_block"):
+        getattr(lib, name).restype = i32
     _libs[omp] = lib
     return lib
 
@@ -308,3 +329,43 @@ def f16_bits_to_f32_array(a) -> np.ndarray:
     out = np.empty(x.shape, dtype=np.float32)
     lib.orc_f16_to_f32_array(_ptr(x), _ptr(out), x.size)
     return out
+
+
+def block_sweep(stencil: str, src, dst, aux, *, rows: int, row0: int, lo: int, hi: int, own_lo: int, own_hi: int,
+                nx: int, ny: int, nz: int = 1, sigma=1.0, h=0.0, wrap=False, ghost=0.0, storage=None,
+                alpha=100.0):
+    """One sweep of a row block (3D: a slab of z-planes) of a larger grid:
+    rows [lo, hi) of the block array dst receive the update of src, the
+    change is reduced over rows [own_lo, own_hi); block row r is grid row
+    row0 + r.  src, dst, aux are C-ordered numpy arrays of the block
+    (rows x nx, or rows x ny x nx); nx, ny (nz) are the grid's extents.
+    ``stencil`` is "j2d5", "j3d7", "life" or "restore8".  Returns a dict with
+    maxbits, sum, count and changed."""
+    lib = _load()
+    b = _CBlock(rows, row0, lo, hi, own_lo, own_hi)
+    out = _CPartial()
+
+    def P(a):
+        return None if a is None else _ptr(a)
+    if stencil == "j2d5":
+        if storage is None:
+            rc = lib.orc_j2d5_block_f64(P(src), P(dst), P(aux), nx, ny, ctypes.byref(b), sigma, h, int(wrap), ghost,
+                                        ctypes.byref(out))
+        else:
+            rc = lib.orc_j2d5_block_f32(P(src), P(dst), P(aux), nx, ny, ctypes.byref(b), sigma, h, int(wrap), ghost,
+                                        STORAGE[storage], ctypes.byref(out))
+    elif stencil == "j3d7":
+        if storage is None:
+            rc = lib.orc_j3d7_block_f64(P(src), P(dst), P(aux), nx, ny, nz, ctypes.byref(b), sigma, h, int(wrap),
+                                        ghost, ctypes.byref(out))
+        else:
+            rc = lib.orc_j3d7_block_f32(P(src), P(dst), P(aux), nx, ny, nz, ctypes.byref(b), sigma, h, int(wrap),
+                                        ghost, STORAGE[storage], ctypes.byref(out))
+    elif stencil == "life":
+        rc = lib.orc_life_block(P(src), P(dst), nx, ny, ctypes.byref(b), int(wrap), ctypes.byref(out))
+    elif stencil == "restore8":
+        rc = lib.orc_restore8_block(P(src), P(dst), P(aux), nx, ny, ctypes.byref(b), alpha, ctypes.byref(out))
+    else:
+        raise ValueError(stencil)
+    _check(rc, "block_sweep")
+    return {"maxbits": int(out.maxbits), "sum": int(out.sum), "count": int(out.count), "changed": int(out.changed)}

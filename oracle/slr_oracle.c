@@ -696,3 +696,234 @@ int orc_sobel(const uint8_t *img, uint8_t *out, int64_t nx, int64_t ny)
         }
     return 0;
 }
+
+/* ------------------------------------------------------------------------- */
+/* One sweep of a block of rows: the 1:n deployment of Sec. 3.3 (Fig. 2), in  */
+/* which one grid is cut into row blocks (3D: slabs of z-planes) over n       */
+/* devices and, before each sweep, the rows next to a block are copied in     */
+/* from the blocks that own them.  A block array holds `rows` consecutive     */
+/* rows (planes) of the grid, the first of them global row row0 (negative or */
+/* beyond the grid where the block sits at an edge); rows [lo, hi) are       */
+/* updated from src into dst by exactly the expressions of the whole-grid     */
+/* sweeps above, and the per-item change is reduced over rows [own_lo,        */
+/* own_hi) only: the maximum as binary64 bits, the 2^-24 fixed-point sum, the */
+/* count (live cells, masked pixels) and "any changed".  A row beyond the     */
+/* grid's first or last row is the boundary (the Dirichlet ghost, a dead      */
+/* cell, or left out for the restoration); with wrap the block's copied-in    */
+/* rows already hold the wrapped rows.  Returns -1 when a row it must read    */
+/* lies outside the block array.                                             */
+/* ------------------------------------------------------------------------- */
+
+typedef struct {
+    int64_t rows, row0, lo, hi, own_lo, own_hi;
+} orc_block;
+
+typedef struct {
+    uint64_t maxbits, sum, count, changed;
+} orc_partial;
+
+/* Local index of the row d rows away from local row r, or -1 for the
+ * boundary beyond the grid, or -2 when it lies outside the block array. */
+static int64_t blk_row(const orc_block *b, int64_t r, int64_t d, int64_t ny, int wrap)
+{
+    int64_t g = b->row0 + r + d;
+    if (!wrap && (g < 0 || g >= ny)) return -1;
+    if (r + d < 0 || r + d >= b->rows) return -2;
+    return r + d;
+}
+
+/* whether local row r is a row of the grid that this sweep updates */
+static int blk_updates(const orc_block *b, int64_t r, int64_t ny, int wrap)
+{
+    int64_t g = b->row0 + r;
+    return wrap || (g >= 0 && g < ny);
+}
+
+static uint64_t f64_bits(double x) { uint64_t v; memcpy(&v, &x, 8); return v; }
+
+int orc_j2d5_block_f64(const double *u, double *v, const double *f, int64_t nx, int64_t ny,
+                       const orc_block *b, double sigma, double h, int wrap, double ghost,
+                       orc_partial *out)
+{
+    double hh = mesh_h(h, nx), h2 = hh * hh, d = 4.0 + sigma * h2;
+    double dmax = 0.0;
+    for (int64_t r = b->lo; r < b->hi; ++r) {
+        if (!blk_updates(b, r, ny, wrap)) continue;
+        int64_t rn = blk_row(b, r, -1, ny, wrap), rs = blk_row(b, r, 1, ny, wrap);
+        if (rn == -2 || rs == -2) return -1;
+        for (int64_t j = 0; j < nx; ++j) {
+            double uN = rn < 0 ? ghost : u[rn * nx + j];
+            double uS = rs < 0 ? ghost : u[rs * nx + j];
+            double uW = at2_f64(u + r * nx, nx, 1, 0, j - 1, wrap, ghost);
+            double uE = at2_f64(u + r * nx, nx, 1, 0, j + 1, wrap, ghost);
+            double s = ((uN + uS) + uW) + uE;
+            double t = h2 * f[r * nx + j];
+            double nv = (t + s) / d;
+            double dl = fabs(nv - u[r * nx + j]);
+            if (r >= b->own_lo && r < b->own_hi && dl > dmax) dmax = dl;
+            v[r * nx + j] = nv;
+        }
+    }
+    out->maxbits = f64_bits(dmax); out->sum = 0; out->count = 0; out->changed = dmax > 0.0;
+    return 0;
+}
+
+int orc_j2d5_block_f32(const float *u, float *v, const float *f, int64_t nx, int64_t ny,
+                       const orc_block *b, double sigma, double h, int wrap, float ghost,
+                       int storage, orc_partial *out)
+{
+    double hh = mesh_h(h, nx), h2d = hh * hh;
+    float h2 = (float)h2d, d = (float)(4.0 + sigma * h2d);
+    float val = 0.0f;
+    for (int64_t r = b->lo; r < b->hi; ++r) {
+        if (!blk_updates(b, r, ny, wrap)) continue;
+        int64_t rn = blk_row(b, r, -1, ny, wrap), rs = blk_row(b, r, 1, ny, wrap);
+        if (rn == -2 || rs == -2) return -1;
+        for (int64_t j = 0; j < nx; ++j) {
+            float s = (((rn < 0 ? ghost : u[rn * nx + j]) + (rs < 0 ? ghost : u[rs * nx + j])) +
+                       at2_f32(u + r * nx, nx, 1, 0, j - 1, wrap, ghost)) +
+                      at2_f32(u + r * nx, nx, 1, 0, j + 1, wrap, ghost);
+            float t = h2 * f[r * nx + j];
+            float nv = to_storage((t + s) / d, storage);
+            float dl = fabsf(nv - u[r * nx + j]);
+            if (r >= b->own_lo && r < b->own_hi && dl > val) val = dl;
+            v[r * nx + j] = nv;
+        }
+    }
+    out->maxbits = f64_bits((double)val); out->sum = 0; out->count = 0; out->changed = val > 0.0f;
+    return 0;
+}
+
+/* 3D: the block's rows are z-planes of ny x nx items; nz is the grid's plane count. */
+int orc_j3d7_block_f64(const double *u, double *v, const double *f, int64_t nx, int64_t ny, int64_t nz,
+                       const orc_block *b, double sigma, double h, int wrap, double ghost,
+                       orc_partial *out)
+{
+    double hh = mesh_h(h, nx), h2 = hh * hh, d = 6.0 + sigma * h2;
+    double dmax = 0.0;
+    int64_t pl = nx * ny;
+    for (int64_t k = b->lo; k < b->hi; ++k) {
+        if (!blk_updates(b, k, nz, wrap)) continue;
+        int64_t kd = blk_row(b, k, -1, nz, wrap), ku = blk_row(b, k, 1, nz, wrap);
+        if (kd == -2 || ku == -2) return -1;
+        for (int64_t i = 0; i < ny; ++i)
+            for (int64_t j = 0; j < nx; ++j) {
+                const double *P = u + k * pl;
+                double s = ((((at2_f64(P, nx, ny, i, j - 1, wrap, ghost) +
+                               at2_f64(P, nx, ny, i, j + 1, wrap, ghost)) +
+                              at2_f64(P, nx, ny, i - 1, j, wrap, ghost)) +
+                             at2_f64(P, nx, ny, i + 1, j, wrap, ghost)) +
+                            (kd < 0 ? ghost : u[kd * pl + i * nx + j])) +
+                           (ku < 0 ? ghost : u[ku * pl + i * nx + j]);
+                size_t c = (size_t)(k * pl + i * nx + j);
+                double nv = (h2 * f[c] + s) / d;
+                double dl = fabs(nv - u[c]);
+                if (k >= b->own_lo && k < b->own_hi && dl > dmax) dmax = dl;
+                v[c] = nv;
+            }
+    }
+    out->maxbits = f64_bits(dmax); out->sum = 0; out->count = 0; out->changed = dmax > 0.0;
+    return 0;
+}
+
+int orc_j3d7_block_f32(const float *u, float *v, const float *f, int64_t nx, int64_t ny, int64_t nz,
+                       const orc_block *b, double sigma, double h, int wrap, float ghost, int storage,
+                       orc_partial *out)
+{
+    double hh = mesh_h(h, nx), h2d = hh * hh;
+    float h2 = (float)h2d, d = (float)(6.0 + sigma * h2d);
+    float val = 0.0f;
+    int64_t pl = nx * ny;
+    for (int64_t k = b->lo; k < b->hi; ++k) {
+        if (!blk_updates(b, k, nz, wrap)) continue;
+        int64_t kd = blk_row(b, k, -1, nz, wrap), ku = blk_row(b, k, 1, nz, wrap);
+        if (kd == -2 || ku == -2) return -1;
+        for (int64_t i = 0; i < ny; ++i)
+            for (int64_t j = 0; j < nx; ++j) {
+                const float *P = u + k * pl;
+                float s = ((((at2_f32(P, nx, ny, i, j - 1, wrap, ghost) +
+                              at2_f32(P, nx, ny, i, j + 1, wrap, ghost)) +
+                             at2_f32(P, nx, ny, i - 1, j, wrap, ghost)) +
+                            at2_f32(P, nx, ny, i + 1, j, wrap, ghost)) +
+                           (kd < 0 ? ghost : u[kd * pl + i * nx + j])) +
+                          (ku < 0 ? ghost : u[ku * pl + i * nx + j]);
+                size_t c = (size_t)(k * pl + i * nx + j);
+                float t = h2 * f[c];
+                float nv = to_storage((t + s) / d, storage);
+                float dl = fabsf(nv - u[c]);
+                if (k >= b->own_lo && k < b->own_hi && dl > val) val = dl;
+                v[c] = nv;
+            }
+    }
+    out->maxbits = f64_bits((double)val); out->sum = 0; out->count = 0; out->changed = val > 0.0f;
+    return 0;
+}
+
+int orc_life_block(const uint8_t *a, uint8_t *c, int64_t nx, int64_t ny, const orc_block *b, int wrap,
+                   orc_partial *out)
+{
+    uint64_t live = 0;
+    int changed = 0;
+    for (int64_t r = b->lo; r < b->hi; ++r) {
+        if (!blk_updates(b, r, ny, wrap)) continue;
+        int64_t rows[3] = {blk_row(b, r, -1, ny, wrap), r, blk_row(b, r, 1, ny, wrap)};
+        if (rows[0] == -2 || rows[2] == -2) return -1;
+        for (int64_t j = 0; j < nx; ++j) {
+            int alive_nbrs = 0;
+            for (int di = 0; di < 3; ++di)
+                for (int64_t dj = -1; dj <= 1; ++dj) {
+                    if (di == 1 && dj == 0) continue;
+                    int64_t y = rows[di], x = j + dj;
+                    if (y < 0) continue;                          /* dead border */
+                    if (wrap) x = wrap_index(x, nx);
+                    else if (x < 0 || x >= nx) continue;
+                    alive_nbrs += a[y * nx + x] != 0;
+                }
+            int self = a[r * nx + j] != 0;
+            int next = (alive_nbrs == 3) || (self && alive_nbrs == 2);
+            c[r * nx + j] = (uint8_t)next;
+            if (r >= b->own_lo && r < b->own_hi) {
+                live += (uint64_t)next;
+                changed |= next != self;
+            }
+        }
+    }
+    out->maxbits = 0; out->sum = 0; out->count = live; out->changed = (uint64_t)changed;
+    return 0;
+}
+
+int orc_restore8_block(const float *u, float *v, const uint8_t *mask, int64_t nx, int64_t ny,
+                       const orc_block *b, float alpha, orc_partial *out)
+{
+    uint64_t sum = 0, nmask = 0;
+    for (int64_t r = b->lo; r < b->hi; ++r) {
+        if (!blk_updates(b, r, ny, 0)) continue;
+        int64_t rows[3] = {blk_row(b, r, -1, ny, 0), r, blk_row(b, r, 1, ny, 0)};
+        if (rows[0] == -2 || rows[2] == -2) return -1;
+        for (int64_t j = 0; j < nx; ++j) {
+            size_t c = (size_t)(r * nx + j);
+            float uc = u[c];
+            if (!mask[c]) { v[c] = uc; continue; }
+            float num = 0.0f, den = 0.0f;
+            for (int di = 0; di < 3; ++di)
+                for (int64_t dj = -1; dj <= 1; ++dj) {
+                    if (di == 1 && dj == 0) continue;
+                    int64_t y = rows[di], x = j + dj;
+                    if (y < 0 || x < 0 || x >= nx) continue;      /* out of range: left out */
+                    float uj = u[y * nx + x];
+                    float t = uc - uj;
+                    float w = 1.0f / sqrtf(alpha + t * t);
+                    num = num + w * uj;
+                    den = den + w;
+                }
+            float nv = den > 0.0f ? num / den : uc;
+            v[c] = nv;
+            if (r >= b->own_lo && r < b->own_hi) {
+                sum += fixed_2m24(fabsf(nv - uc));
+                nmask += 1;
+            }
+        }
+    }
+    out->maxbits = 0; out->sum = sum; out->count = nmask; out->changed = sum != 0;
+    return 0;
+}

@@ -27,6 +27,7 @@
 #include <string.h>
 
 #include "crmath.cuh"
+#include "restore_math.cuh"
 #include "slr_internal.cuh"
 #include "tma.cuh"
 
@@ -150,21 +151,6 @@ struct RestoreTma {
         __syncthreads();
     }
 
-    // one neighbour's term of the weighted mean
-    __device__ __forceinline__ void accumulate(float uc, float uj, float &num, float &den) const
-    {
-        if (FAST) {
-            const float w = rsqrtf(fmaf(uc - uj, uc - uj, alpha));
-            num = fmaf(w, uj, num);
-            den += w;
-        } else {
-            const float tt = __fsub_rn(uc, uj);
-            const float w = inv_sqrt_rn2(__fadd_rn(alpha, __fmul_rn(tt, tt)));
-            num = __fadd_rn(num, __fmul_rn(w, uj));
-            den = __fadd_rn(den, w);
-        }
-    }
-
     __device__ __forceinline__ void issue(int tile, int mi, int sb) const
     {
         const int tx = tile % tiles_x, ty = tile / tiles_x;
@@ -228,37 +214,10 @@ struct RestoreTma {
                 const int y = y0 + rr, x = x0 + cc;
                 const float *C = U + (rr + 1) * kUBoxW + cc + 4;
                 const float uc = *C;
-                float num = 0.0f, den = 0.0f;
-                if (y > 0 && y + 1 < nyi && x > 0 && x + 1 < nxi) {
-                    // all 8 neighbours exist (every pixel off the grid's border)
-                    if (FAST) {
-#pragma unroll
-                        for (int k = 0; k < 9; ++k)
-                            if (k != 4) accumulate(uc, C[(k / 3 - 1) * kUBoxW + k % 3 - 1], num, den);
-                    } else {
-                        // neighbours in pairs (row-major order kept for the sums)
-                        float2 nd = make_float2(0.0f, 0.0f);
-#pragma unroll
-                        for (int k = 0; k < 8; k += 2) {
-                            const int k0 = k < 4 ? k : k + 1, k1 = k + 1 < 4 ? k + 1 : k + 2;
-                            const float u0 = C[(k0 / 3 - 1) * kUBoxW + k0 % 3 - 1];
-                            const float u1 = C[(k1 / 3 - 1) * kUBoxW + k1 % 3 - 1];
-                            const float2 w = weights_rn2(uc, u0, u1, alpha);
-                            nd = __fadd2_rn(nd, make_float2(__fmul_rn(w.x, u0), w.x));
-                            nd = __fadd2_rn(nd, make_float2(__fmul_rn(w.y, u1), w.y));
-                        }
-                        num = nd.x;
-                        den = nd.y;
-                    }
-                } else {
-#pragma unroll
-                    for (int k = 0; k < 9; ++k) {
-                        const int di = k / 3 - 1, dj = k % 3 - 1;
-                        if (k == 4 || y + di < 0 || y + di >= nyi || x + dj < 0 || x + dj >= nxi) continue;
-                        accumulate(uc, C[di * kUBoxW + dj], num, den);
-                    }
-                }
-                const float nv = den > 0.0f ? (FAST ? __fdividef(num, den) : __fdiv_rn(num, den)) : uc;
+                // every pixel off the grid's border has all 8 neighbours
+                const float nv = y > 0 && y + 1 < nyi && x > 0 && x + 1 < nxi
+                                     ? restore_interior<FAST>(C, kUBoxW, alpha)
+                                     : restore_border<FAST>(C, kUBoxW, alpha, y > 0, y + 1 < nyi, x > 0, x + 1 < nxi);
                 dst[(size_t)y * (size_t)nxi + x] = nv;
                 if (REDUCE) sum += fixed_2m24(__fsub_rn(nv, uc));
             }
@@ -343,6 +302,7 @@ bool restore_tma_ok(const Problem &p) { return tma_ok(p); }
 
 cudaError_t restore_persistent(const Problem &p, LoopArgs la, cudaStream_t st)
 {
+    if (restore_tb_resolve_k(p, la.a, la.b, la.aux) > 1) return restore_tb_persistent(p, la, st);
     if (p.tiling != SLR_TILING_NONE && tma_ok(p))
         return p.math == SLR_MATH_FAST ? launch_tma<true>(p, la, st) : launch_tma<false>(p, la, st);
     if (p.math == SLR_MATH_FAST) {

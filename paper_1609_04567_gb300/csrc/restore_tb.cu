@@ -1,0 +1,342 @@
+// restore_tb.cu -- temporal-blocked restoration (Sec. 4.3): up to 8 sweeps per
+// pass over HBM.
+//
+// The loop-of-stencil-reduce-d of Sec. 3.1 with the restoration update of the
+// two-phase denoiser: every noisy pixel becomes the weighted mean of its
+// in-range 8-neighbours, w_j = 1 / sqrt(alpha + (u - u_j)^2) (restore_math.cuh),
+// clean pixels never change; reduce = mean |u' - u| over the noisy pixels
+// (each |delta| truncated to a multiple of 2^-24 and added as an integer), stop
+// at the first sweep whose mean is below tol or at the iteration cap.
+//
+// Tiles.  A pass cuts the grid into tiles of 64 x 64 owned pixels.  A CTA
+// loads a tile's state with a halo of 8 pixels on every side (80 x 80 floats)
+// into two shared-memory buffers and its mask (96 x 80 bytes, from 16 columns
+// to the left so that the copy starts on a 16-byte boundary), three TMA boxes
+// on one mbarrier; the hardware fills what lies outside the grid with zeros,
+// which no update reads.  The noisy pixels of the loaded region are listed
+// once per tile, ordered by their depth: the distance to the nearest edge of
+// the loaded region behind which the grid continues (edges on the grid's own
+// border do not count, nothing is missing there), capped at 8.  A pixel of
+// depth d is up to date after any sweep s <= d, so a pass of kp sweeps runs
+// sweep s over the pixels of depth >= s + 8 - kp: a prefix of the list, which
+// shrinks by one ring per sweep and ends on the owned pixels (depth 8).  Each
+// sweep reads one buffer and writes the other (clean pixels are in both), so
+// the update sees only old values, as the Jacobi form of the method requires.
+// After kp sweeps the 64 x 64 owned pixels go to the other state buffer in
+// global memory with 16-byte stores.
+//
+// Reduce and decision.  Each sweep's sum of truncated |delta| over the owned
+// noisy pixels goes to a per-sweep slot (warp, then CTA in shared memory,
+// then one 64-bit atomic per CTA and sweep), with the count of owned noisy
+// pixels.  After a pass a grid barrier publishes the slots; every CTA takes
+// the same decision: the first sweep of the pass whose mean is below tol
+// stops the loop, and when it is not the pass's last sweep the pass runs
+// again from its untouched input up to that sweep, so the state, the value,
+// the count and the iteration count equal those of one sweep per pass.
+#include <string.h>
+
+#include "restore_math.cuh"
+#include "slr_internal.cuh"
+#include "tma.cuh"
+
+namespace slr {
+namespace {
+
+constexpr int kK = 8;                        // most sweeps per pass: the tile halo
+constexpr int kOwn = 64;                     // owned pixels per tile side
+constexpr int kW = kOwn + 2 * kK;            // 80: loaded columns (x0 - 8 .. x0 + 71)
+constexpr int kH = kOwn + 2 * kK;            // 80: loaded rows
+constexpr int kMX = 16;                      // mask halo columns (16-byte aligned start)
+constexpr int kMW = kOwn + 2 * kMX;          // 96 mask bytes per row
+constexpr int kThreads = 256;
+constexpr int kPlane = kW * kH * 4;                                   // 25600
+constexpr int kMaskBytes = kMW * kH;                                  // 7680
+constexpr int kMaxList = (kW - 2) * (kH - 2);                         // pixels that can be updated
+constexpr int kListBytes = (kMaxList * 2 + 127) / 128 * 128;
+constexpr size_t kSmem = 128 + 2 * (size_t)kPlane + kMaskBytes + kListBytes + 16;
+constexpr uint32_t kTxBytes = 2u * kPlane + kMaskBytes;               // what the three boxes deliver
+static_assert(kPlane % 128 == 0 && kMaskBytes % 128 == 0, "TMA destinations stay 128-byte aligned");
+static_assert(kW * kH < (1 << 14), "a list entry keeps the position in 14 bits");
+static_assert(kK <= kMaxK, "per-sweep slots");
+
+struct RTb {
+    CUtensorMap umap[2];       // state buffers A (caller's u) and B, box 80 x 80
+    CUtensorMap mmap;          // mask, box 96 x 80
+    float *buf[2];
+    int nx, ny;
+    int tiles_x, tiles_y;
+    int K;                     // sweeps per pass
+    float alpha;
+};
+
+// Per-CTA bookkeeping in static shared memory.
+struct RTbShared {
+    int cnt[kK + 1];                    // noisy pixels per depth
+    int next[kK + 1];                   // placement cursor per depth
+    int nge[kK + 2];                    // listed pixels of depth >= d
+    unsigned owned;                     // owned noisy pixels of the tile
+    unsigned long long sum[kK];         // per-sweep sum over the CTA's tiles
+    unsigned long long own_total;       // owned noisy pixels over the CTA's tiles
+};
+
+__device__ __forceinline__ int tile_depth(int ly, int lx, bool top, bool bottom, bool left, bool right)
+{
+    int d = kK;
+    if (top) d = min(d, ly);
+    if (bottom) d = min(d, kH - 1 - ly);
+    if (left) d = min(d, lx);
+    if (right) d = min(d, kW - 1 - lx);
+    return d;
+}
+
+__device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// One pass: every tile of this CTA, kp sweeps each, from buf[cur] to
+// buf[cur ^ 1].  With REDUCE the per-sweep sums go to sh.sum and the owned
+// noisy pixels to sh.own_total.  False if a TMA wait ran out.
+template <bool FAST, bool REDUCE>
+__device__ bool rtb_pass(const RTb &tp, unsigned char *smem, uint64_t *bar, RTbShared &sh, unsigned &phase, int cur,
+                         int kp, const LoopArgs &la)
+{
+    float *S0 = (float *)smem;
+    float *S1 = (float *)(smem + kPlane);
+    const unsigned char *M = smem + 2 * kPlane;
+    unsigned short *L = (unsigned short *)(smem + 2 * kPlane + kMaskBytes);
+    float *dst = tp.buf[cur ^ 1];
+    const int tid = threadIdx.x, lane = tid & 31;
+    const int ntiles = tp.tiles_x * tp.tiles_y;
+    const int thr = kK + 1 - kp;                 // depth the first sweep needs
+    for (int t = (int)blockIdx.x; t < ntiles; t += (int)gridDim.x) {
+        const int x0 = (t % tp.tiles_x) * kOwn, y0 = (t / tp.tiles_x) * kOwn;
+        const int X0 = x0 - kK, Y0 = y0 - kK;    // origin of the loaded region in the grid
+        if (tid == 0) {
+            tma::mbar_expect_tx(bar, kTxBytes);
+            tma::load_2d(S0, &tp.umap[cur], X0, Y0, bar);
+            tma::load_2d(S1, &tp.umap[cur], X0, Y0, bar);
+            tma::load_2d((void *)M, &tp.mmap, x0 - kMX, Y0, bar);
+        }
+        if (tid <= kK) sh.cnt[tid] = 0;
+        if (tid == 0) sh.owned = 0u;
+        const bool ok = tma::bounded_wait(bar, phase & 1u, tma::kLoadWaitNs, &la.ctl->err);
+        ++phase;
+        if (!__syncthreads_and(ok)) return false;
+        // edges of the loaded region behind which the grid continues
+        const bool top = Y0 > 0, bottom = Y0 + kH < tp.ny, left = X0 > 0, right = X0 + kW < tp.nx;
+        // list the noisy pixels by depth: count, place
+        for (int i = tid; i < kW * kH; i += kThreads) {
+            const int ly = i / kW, lx = i - ly * kW;
+            const int gy = Y0 + ly, gx = X0 + lx;
+            if (gy < 0 || gy >= tp.ny || gx < 0 || gx >= tp.nx || !M[ly * kMW + lx + (kMX - kK)]) continue;
+            const int d = tile_depth(ly, lx, top, bottom, left, right);
+            if (d >= thr) atomicAdd(&sh.cnt[d], 1);
+        }
+        __syncthreads();
+        if (tid == 0) {
+            int pos = 0;
+            sh.nge[kK + 1] = 0;
+            for (int d = kK; d >= 1; --d) {
+                sh.next[d] = pos;
+                pos += d >= thr ? sh.cnt[d] : 0;
+                sh.nge[d] = pos;
+            }
+        }
+        __syncthreads();
+        for (int i = tid; i < kW * kH; i += kThreads) {
+            const int ly = i / kW, lx = i - ly * kW;
+            const int gy = Y0 + ly, gx = X0 + lx;
+            if (gy < 0 || gy >= tp.ny || gx < 0 || gx >= tp.nx || !M[ly * kMW + lx + (kMX - kK)]) continue;
+            const int d = tile_depth(ly, lx, top, bottom, left, right);
+            if (d < thr) continue;
+            const bool own = ly >= kK && ly < kK + kOwn && lx >= kK && lx < kK + kOwn;
+            const bool border = gy == 0 || gy == tp.ny - 1 || gx == 0 || gx == tp.nx - 1;
+            L[atomicAdd(&sh.next[d], 1)] = (unsigned short)(i | (own ? 1 << 14 : 0) | (border ? 1 << 15 : 0));
+            if (REDUCE && own) atomicAdd(&sh.owned, 1u);
+        }
+        __syncthreads();
+        for (int s = 1; s <= kp; ++s) {
+            const float *In = (s & 1) ? S0 : S1;
+            float *Out = (s & 1) ? S1 : S0;
+            const int n = sh.nge[s + kK - kp];
+            unsigned long long sum = 0ull;
+            for (int e = tid; e < n; e += kThreads) {
+                const unsigned ent = L[e];
+                const int pos = (int)(ent & 0x3FFFu);
+                const float *C = In + pos;
+                float nv;
+                if (ent & 0x8000u) {
+                    const int gy = Y0 + pos / kW, gx = X0 + pos % kW;
+                    nv = restore_border<FAST>(C, kW, tp.alpha, gy > 0, gy + 1 < tp.ny, gx > 0, gx + 1 < tp.nx);
+                } else {
+                    nv = restore_interior<FAST>(C, kW, tp.alpha);
+                }
+                Out[pos] = nv;
+                if (REDUCE && (ent & 0x4000u)) sum += fixed_2m24(__fsub_rn(nv, *C));
+            }
+            if (REDUCE) {
+                sum = warp_sum_u64(sum);
+                if (lane == 0 && sum) atomicAdd(&sh.sum[s - 1], sum);
+            }
+            __syncthreads();
+        }
+        if (REDUCE && tid == 0) sh.own_total += sh.owned;
+        // the owned pixels inside the grid to the output buffer
+        const float *Fin = (kp & 1) ? S1 : S0;
+        for (int i = tid; i < kOwn * (kOwn / 4); i += kThreads) {
+            const int r = i / (kOwn / 4), c4 = i % (kOwn / 4);
+            const int gy = y0 + r, gx = x0 + 4 * c4;
+            if (gy < tp.ny && gx < tp.nx)
+                *(float4 *)(dst + (size_t)gy * (size_t)tp.nx + gx) = *(const float4 *)(Fin + (r + kK) * kW + kK + 4 * c4);
+        }
+        // this tile's shared-memory accesses before the next tile's copies
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();
+    }
+    // this pass's stores before the copies of later passes (after a grid barrier)
+    tma::fence_proxy_async_global();
+    return true;
+}
+
+template <bool FAST>
+__global__ void __launch_bounds__(kThreads, 3) restore_tb_kernel(const __grid_constant__ RTb tp, LoopArgs la)
+{
+    extern __shared__ unsigned char smem_dyn[];
+    unsigned char *smem = (unsigned char *)(((uintptr_t)smem_dyn + 127) & ~(uintptr_t)127);
+    uint64_t *bar = (uint64_t *)(smem + 2 * kPlane + kMaskBytes + kListBytes);
+    __shared__ RTbShared sh;
+    __shared__ int s_stop, s_rewind;
+    __shared__ long long s_it;
+    const int tid = threadIdx.x;
+    Ctl *ctl = la.ctl;
+    const long long it0 = ctl->iters;
+    if (ctl->converged || it0 >= la.max_iters || ctl->err) return;
+    if ((la.debug_flags & SLR_DEBUG_SKIP_ARRIVAL) && blockIdx.x == gridDim.x - 1) return;
+    if (tid == 0) {
+        tma::mbar_init(bar, 1);
+        tma::mbar_init_fence();
+        tma::fence_proxy_async_global();   // earlier stores to the state before this launch's copies
+        sh.own_total = 0ull;
+    }
+    if (tid < kK) sh.sum[tid] = 0ull;
+    __syncthreads();
+
+    unsigned phase = 0;
+    unsigned long long bar_target = 0;
+    long long it = it0;
+    int cur = 0;
+    for (long long p = 0;; ++p) {
+        const long long left = la.max_iters - it;
+        const int kp = (int)((long long)tp.K < left ? (long long)tp.K : left);
+        if (!rtb_pass<FAST, true>(tp, smem, bar, sh, phase, cur, kp, la)) return;
+        __syncthreads();
+        if (tid < kp) {
+            Slot *sl = &ctl->sub[p % kSlots][tid];
+            if (sh.sum[tid]) atomicAdd(&sl->sum, sh.sum[tid]);
+            if (sh.own_total) atomicAdd(&sl->cnt, sh.own_total);
+            sh.sum[tid] = 0ull;
+        }
+        __syncthreads();
+        if (tid == 0) sh.own_total = 0ull;
+        bar_target += (unsigned long long)la.nblocks;
+        if (!grid_barrier(ctl, bar_target, la.limit_ns)) return;
+        if (tid < 32) {
+            if (blockIdx.x == 0) zero_slot(&ctl->sub[(p + 2) % kSlots][tid]);
+            // lane j decides sweep j of the pass; the first one below tol stops
+            Slot sl;
+            sl.maxbits = 0ull;
+            sl.sum = tid < kp ? ld_relaxed_u64(&ctl->sub[p % kSlots][tid].sum) : 0ull;
+            sl.cnt = tid < kp ? ld_relaxed_u64(&ctl->sub[p % kSlots][tid].cnt) : 0ull;
+            sl.changed = sl.sum != 0ull;
+            const Decision dj = decide(la.reduce, sl, la.tol);
+            const unsigned conv = __ballot_sync(0xffffffffu, tid < kp && dj.converged);
+            const int jstop = conv ? __ffs(conv) - 1 : -1;
+            const int jlast = jstop >= 0 ? jstop : kp - 1;
+            const double value = __shfl_sync(0xffffffffu, dj.value, jlast);
+            const unsigned long long count = __shfl_sync(0xffffffffu, dj.count, jlast);
+            const int changed = __shfl_sync(0xffffffffu, dj.changed, jlast);
+            const long long itn = it + jlast + 1;
+            if (tid == 0) {
+                const int stop = jstop >= 0 || itn >= la.max_iters;
+                s_stop = stop;
+                s_rewind = jstop >= 0 && jstop + 1 < kp ? jstop + 1 : 0;
+                s_it = itn;
+                if (stop && blockIdx.x == 0) {
+                    ctl->iters = itn;
+                    ctl->value = value;
+                    ctl->count = count;
+                    ctl->changed = changed;
+                    ctl->converged = jstop >= 0;
+                }
+            }
+        }
+        __syncthreads();
+        it = s_it;
+        if (s_stop) {
+            if (s_rewind) {
+                // the pass again from its input, up to the stopping sweep
+                if (tid == 0) tma::fence_proxy_async_global();
+                if (!rtb_pass<FAST, false>(tp, smem, bar, sh, phase, cur, s_rewind, la)) return;
+                bar_target += (unsigned long long)la.nblocks;
+                if (!grid_barrier(ctl, bar_target, la.limit_ns)) return;
+            }
+            if ((cur ^ 1) == 1) grid_copy(tp.buf[1], tp.buf[0], (size_t)tp.nx * tp.ny * sizeof(float));
+            return;
+        }
+        cur ^= 1;
+        if (tid == 0) tma::fence_proxy_async_global();
+    }
+}
+
+template <bool FAST>
+cudaError_t run_rtb(const Problem &p, LoopArgs la, int K, cudaStream_t st)
+{
+    RTb tp;
+    memset(&tp, 0, sizeof(tp));
+    if (!tma::make_map_2d(&tp.umap[0], la.a, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, p.nx, p.ny, kW, kH) ||
+        !tma::make_map_2d(&tp.umap[1], la.b, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, p.nx, p.ny, kW, kH) ||
+        !tma::make_map_2d(&tp.mmap, la.aux, CU_TENSOR_MAP_DATA_TYPE_UINT8, 1, p.nx, p.ny, kMW, kH))
+        return cudaErrorNotSupported;
+    tp.buf[0] = (float *)la.a;
+    tp.buf[1] = (float *)la.b;
+    tp.nx = (int)p.nx;
+    tp.ny = (int)p.ny;
+    tp.tiles_x = (int)((p.nx + kOwn - 1) / kOwn);
+    tp.tiles_y = (int)((p.ny + kOwn - 1) / kOwn);
+    tp.K = K;
+    tp.alpha = p.alpha;
+    auto kern = restore_tb_kernel<FAST>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem);
+    if (e != cudaSuccess) return e;
+    return launch_cooperative(kern, kThreads, kSmem, 3, la, &tp, st);
+}
+
+}  // namespace
+
+bool restore_tb_supported(const Problem &p, const void *a, const void *b, const void *mask)
+{
+    if (p.stencil != SLR_RESTORE8 || p.nx % 16 != 0 || p.nx >= (1ll << 31) - 4096 || p.ny >= (1ll << 31) - 4096)
+        return false;
+    if ((((uintptr_t)a | (uintptr_t)b) % 16) != 0 || ((uintptr_t)mask % 16) != 0) return false;
+    if ((double)p.nx * (double)p.ny >= 4.0e18) return false;
+    return tma::encode_fn() != nullptr;
+}
+
+int restore_tb_resolve_k(const Problem &p, const void *a, const void *b, const void *mask)
+{
+    if (p.k == 1 || !restore_tb_supported(p, a, b, mask)) return 1;
+    if (p.k == 0) return p.tiling == SLR_TILING_AUTO ? kRestoreTbDefaultK : 1;
+    return p.k > kK ? kK : p.k;
+}
+
+cudaError_t restore_tb_persistent(const Problem &p, LoopArgs la, cudaStream_t st)
+{
+    const int K = restore_tb_resolve_k(p, la.a, la.b, la.aux);
+    if (K < 2) return cudaErrorNotSupported;
+    return p.math == SLR_MATH_FAST ? run_rtb<true>(p, la, K, st) : run_rtb<false>(p, la, K, st);
+}
+
+}  // namespace slr

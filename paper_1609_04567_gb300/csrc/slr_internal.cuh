@@ -355,6 +355,16 @@ cudaError_t jacobi_persistent(const Problem &p, LoopArgs la, cudaStream_t st);
 bool jacobi_tma_ok(const Problem &p, const void *a, const void *b, const void *f, bool forced);
 cudaError_t jacobi_sweep(const Problem &p, const void *src, void *dst, const void *f, cudaStream_t st);
 cudaError_t restore_persistent(const Problem &p, LoopArgs la, cudaStream_t st);
+// Temporal-blocked restoration (restore_tb.cu): k sweeps per pass over 64 x 64
+// tiles with an 8-pixel halo.  Supported for rows of whole 16-byte mask groups
+// (nx % 16 == 0) and 16-byte aligned arrays; resolve_k gives 1 (the one-sweep
+// kernels) for temporal_k 1, for a problem it does not accept, or for
+// temporal_k 0 with an explicit tiling; kRestoreTbDefaultK for temporal_k 0
+// with SLR_TILING_AUTO; else temporal_k capped at 8.
+constexpr int kRestoreTbDefaultK = 8;
+bool restore_tb_supported(const Problem &p, const void *a, const void *b, const void *mask);
+int restore_tb_resolve_k(const Problem &p, const void *a, const void *b, const void *mask);
+cudaError_t restore_tb_persistent(const Problem &p, LoopArgs la, cudaStream_t st);
 // Whether the TMA-tiled restoration sweep accepts p (nx % 16 == 0).
 bool restore_tma_ok(const Problem &p);
 cudaError_t restore_sweep(const Problem &p, const void *src, void *dst, const void *mask, cudaStream_t st);

@@ -1,7 +1,8 @@
 // tune.cu -- the autotuner.  The paper picks its work-group layout with fixed
 // heuristics (Sec. 3.3); here the launch choices that leave results unchanged
-// (loop driver, sweeps per HBM pass of Life and of the 2D Jacobi, the
-// one-sweep kernels' tiling and the persistent grid size) are timed on the caller's own data and the
+// (loop driver, sweeps per HBM pass of Life, the 2D Jacobi and the
+// restoration, the one-sweep kernels' tiling and the persistent grid size) are
+// timed on the caller's own data and the
 // fastest is kept in a process-wide cache that slr_create consults.
 //
 // Search: stage 1 times loop x temporal_k x tiling with all co-resident CTAs
@@ -153,7 +154,8 @@ void tune_fill(slr_desc *d)
     slr_tune_result r;
     if (!lookup_locked(d, &r)) return;
     if (d->loop == SLR_LOOP_AUTO) d->loop = r.loop;
-    const bool blocked = d->stencil == SLR_LIFE || (d->stencil == SLR_J2D5 && !d->defect_correction);
+    const bool blocked = d->stencil == SLR_LIFE || d->stencil == SLR_RESTORE8 ||
+                         (d->stencil == SLR_J2D5 && !d->defect_correction);
     if (d->temporal_k == 0 && blocked) d->temporal_k = r.temporal_k;
     if (d->tiling == SLR_TILING_AUTO && d->stencil != SLR_LIFE) d->tiling = r.tiling;
     // the grid size was timed with the kernel of the cached choice only
@@ -220,12 +222,14 @@ slr_status slr_tune(const slr_desc *d, const void *u, const void *aux, void *scr
                      (jacobi && slr::jacobi_tma_ok(p, ta, tb, aux, true));
 
     const bool jacobi_tb = jacobi && d->stencil == SLR_J2D5 && slr::jacobi_tb_supported(p, ta, tb, aux);
+    const bool restore_tb = d->stencil == SLR_RESTORE8 && slr::restore_tb_supported(p, ta, tb, aux);
 
     // What the default resolves to, so that equal configurations are timed once.
     auto resolved_k = [&](const slr_desc &c) {
         if (c.loop == SLR_LOOP_HOST) return 1;
         if (life_tb) return slr::life_tb_resolve_k(slr::problem_of(&c), c.grid_ctas);
         if (jacobi_tb) return slr::jacobi_tb_resolve_k(slr::problem_of(&c), ta, tb, aux);
+        if (restore_tb) return slr::restore_tb_resolve_k(slr::problem_of(&c), ta, tb, aux);
         return 1;
     };
     auto resolved_tiling = [&](const slr_desc &c) {
@@ -252,6 +256,17 @@ slr_status slr_tune(const slr_desc *d, const void *u, const void *aux, void *scr
         // sweeps per pass of the 2D Jacobi: one (the one-sweep kernels), 4, 8
         const int def_k = resolved_k(base);
         static const int ks[] = {1, 4, 8};
+        for (int k : ks) {
+            if (k == def_k) continue;
+            slr_desc c = base;
+            c.temporal_k = k;
+            stage1.push_back(c);
+        }
+    }
+    if (persistent && restore_tb && d->temporal_k == 0) {
+        // sweeps per pass of the restoration: one (the one-sweep kernels), 2, 4, 8
+        const int def_k = resolved_k(base);
+        static const int ks[] = {1, 2, 4, 8};
         for (int k : ks) {
             if (k == def_k) continue;
             slr_desc c = base;
@@ -286,7 +301,8 @@ slr_status slr_tune(const slr_desc *d, const void *u, const void *aux, void *scr
     if (best.loop == SLR_LOOP_PERSISTENT && d->grid_ctas == 0) {
         // fix the stage-1 choice of k before shrinking the grid (the default
         // k depends on the grid size)
-        if ((d->stencil == SLR_LIFE || jacobi_tb) && best.temporal_k == 0) best.temporal_k = resolved_k(best);
+        if ((d->stencil == SLR_LIFE || jacobi_tb || restore_tb) && best.temporal_k == 0)
+            best.temporal_k = resolved_k(best);
         const int grids[] = {2 * sms, sms, sms / 2, sms / 4, sms / 8, sms / 16};
         int last = -1;
         for (int g : grids) {
@@ -307,7 +323,9 @@ slr_status slr_tune(const slr_desc *d, const void *u, const void *aux, void *scr
     slr_tune_result r;
     memset(&r, 0, sizeof(r));
     r.loop = best.loop;
-    r.temporal_k = d->stencil == SLR_LIFE || (jacobi && d->stencil == SLR_J2D5) ? resolved_k(best) : 0;
+    r.temporal_k = d->stencil == SLR_LIFE || d->stencil == SLR_RESTORE8 || (jacobi && d->stencil == SLR_J2D5)
+                       ? resolved_k(best)
+                       : 0;
     r.tiling = d->stencil == SLR_RESTORE8 || jacobi ? resolved_tiling(best) : SLR_TILING_AUTO;
     r.grid_ctas = best.loop == SLR_LOOP_PERSISTENT ? best.grid_ctas : 0;
     r.trials = b.trials;

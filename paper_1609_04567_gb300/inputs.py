@@ -161,3 +161,13 @@ def exp_gaps(count: int, rate: float, seed: int = DEFAULT_SEED,
     """Poisson-process inter-arrival gaps (seconds) with the given mean rate."""
     u = uniform01(seed, stream, count)
     return -np.log1p(-u) / rate
+
+
+def batch_grid_rhs(i: int, side: int, seed: int = DEFAULT_SEED) -> np.ndarray:
+    """Right-hand side of 2D grid i of the batched workload (its own stream)."""
+    return helmholtz_rhs((side, side), seed=seed, stream=STREAM_BATCH_F0 + i)
+
+
+def batch_cube_rhs(n: int, seed: int = DEFAULT_SEED) -> np.ndarray:
+    """Right-hand side of the batched workload's n^3 grid, (nz, ny, nx)."""
+    return helmholtz_rhs((n * n * n,), seed=seed, stream=STREAM_BATCH_F0 + 999).reshape(n, n, n)

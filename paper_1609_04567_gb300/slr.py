@@ -66,6 +66,16 @@ class slr_user_desc(ctypes.Structure):
 
 SLR_USER_MAX, SLR_USER_SUM = 0, 1
 
+
+class slr_block(ctypes.Structure):
+    _fields_ = [("rows", ctypes.c_int64), ("row0", ctypes.c_int64), ("lo", ctypes.c_int64), ("hi", ctypes.c_int64),
+                ("own_lo", ctypes.c_int64), ("own_hi", ctypes.c_int64)]
+
+
+class slr_partial(ctypes.Structure):
+    _fields_ = [("maxbits", ctypes.c_uint64), ("sum", ctypes.c_uint64), ("count", ctypes.c_uint64),
+                ("changed", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
+
 EXPORTS = ["slr_desc_init", "slr_workspace_size", "slr_create", "slr_run_until", "slr_reduce_value",
            "slr_destroy", "slr_last_error", "slr_version", "slr_run_static", "slr_static_last_error",
            "slr_batch_workspace_size", "slr_batch_scratch_size", "slr_batch_create", "slr_batch_add",
@@ -74,7 +84,7 @@ EXPORTS = ["slr_desc_init", "slr_workspace_size", "slr_create", "slr_run_until",
            "slr_tune_last_error", "slr_check_exact_math", "slr_check_exact_division", "slr_detect_noise",
            "slr_state_to_frame", "slr_sobel", "slr_check_exact_isqrt", "slr_user_workspace_size",
            "slr_user_create", "slr_user_run_until", "slr_user_reduce_value", "slr_user_destroy",
-           "slr_user_last_error"]
+           "slr_user_last_error", "slr_block_sweep"]
 SLR_STATIC_STATE_BYTES = 4 << 20
 
 _lib = None
@@ -179,6 +189,8 @@ def load(path: str = LIB_PATH):
     lib.slr_user_destroy.restype = i32
     lib.slr_user_last_error.argtypes = [P]
     lib.slr_user_last_error.restype = ctypes.c_char_p
+    lib.slr_block_sweep.argtypes = [D, ctypes.POINTER(slr_block), P, P, P, P, P]
+    lib.slr_block_sweep.restype = i32
     _lib = lib
     return lib
 
@@ -232,6 +244,17 @@ def slr_last_error(h) -> str:
 
 def slr_version() -> str:
     return load().slr_version().decode()
+
+
+def slr_block_sweep(d: slr_desc, b: slr_block, src_ptr: int, dst_ptr: int, aux_ptr: int, partial_ptr: int,
+                    stream: int, check: bool = True) -> int:
+    """One sweep of a row block (device step of the 1:n split); the partial
+    reduce goes to the device slr_partial at partial_ptr."""
+    st = load().slr_block_sweep(ctypes.byref(d), ctypes.byref(b), src_ptr or None, dst_ptr or None, aux_ptr or None,
+                                partial_ptr or None, stream or None)
+    if check and st < 0:
+        raise SlrError(st, slr_last_error(None))
+    return st
 
 
 def slr_run_static(d: slr_desc, u_ptr: int, f_ptr: int, max_iters: int, stream: int, check: bool = True):

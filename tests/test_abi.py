@@ -106,7 +106,7 @@ def _c_layout(struct, fields, tmp_path):
     return [int(x) for x in out]
 
 
-@pytest.mark.parametrize("struct", ["slr_desc", "slr_tune_result", "slr_user_desc"])
+@pytest.mark.parametrize("struct", ["slr_desc", "slr_tune_result", "slr_user_desc", "slr_block", "slr_partial"])
 def test_binding_struct_layout_matches_the_header(struct, tmp_path):
     from paper_1609_04567_gb300 import slr
     cls = getattr(slr, struct)

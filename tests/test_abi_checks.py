@@ -202,3 +202,26 @@ def test_defaults_of_every_stencil_pass_the_rules(slr):
         assert slr.slr_workspace_size(slr.slr_desc_init(s, *ext)) > 0
     # and the defect correction's own defaults
     assert slr.slr_workspace_size(slr.slr_desc_init(slr.SLR_J2D5, 8, 8, 1, defect_correction=1)) > 0
+
+
+def test_block_sweep_refuses_bad_ranges_before_any_device_work(slr):
+    d = slr.slr_desc_init(slr.SLR_J2D5, 16, 32, 1)
+    P = FAKE_WS + 4096
+    cases = [
+        (slr.slr_block(10, 5, 0, 10, 0, 10), "outside the block"),      # global row 4 is above row 0
+        (slr.slr_block(10, 0, 0, 10, 0, 10), "outside the block"),      # global row 10 is below row 9
+        (slr.slr_block(10, 0, 3, 2, 3, 2), "lo <= own_lo"),
+        (slr.slr_block(10, 0, 0, 11, 0, 10), "lo <= own_lo"),
+        (slr.slr_block(10, 0, 1, 9, 0, 9), "lo <= own_lo"),
+        (slr.slr_block(0, 0, 0, 0, 0, 0), "rows >= 1"),
+    ]
+    for blk, words in cases:
+        assert slr.slr_block_sweep(d, blk, FAKE_U, FAKE_U + 8192, FAKE_AUX, P, 0, check=False) == \
+            slr.SLR_ERR_INVALID_ARG, words
+        assert words in slr.slr_last_error(None), (words, slr.slr_last_error(None))
+    good = slr.slr_block(10, 3, 1, 9, 1, 9)
+    assert slr.slr_block_sweep(d, good, FAKE_U, FAKE_U, FAKE_AUX, P, 0, check=False) == slr.SLR_ERR_INVALID_ARG
+    assert slr.slr_block_sweep(d, good, FAKE_U, FAKE_U + 8192, 0, P, 0, check=False) == slr.SLR_ERR_INVALID_ARG
+    dc = slr.slr_desc_init(slr.SLR_J2D5, 16, 32, 1, defect_correction=1)
+    assert slr.slr_block_sweep(dc, good, FAKE_U, FAKE_U + 8192, FAKE_AUX, P, 0, check=False) == \
+        slr.SLR_ERR_UNSUPPORTED

@@ -50,6 +50,13 @@ def test_restore_tiling_and_grid_size_are_bit_exact(gpu, orc, tiling, grid):
     assert np.array_equal(out.view(np.uint32), ref.view(np.uint32)) and r.value == rr.value
 
 
+@pytest.mark.parametrize("k,grid", [(2, 1), (4, 7), (8, 152), (8, 0), (3, 600)])
+def test_restore_temporal_k_and_grid_size_are_bit_exact(gpu, orc, k, grid):
+    out, r, ref, rr = restore_case(gpu, orc, 200, 256, temporal_k=k, grid_ctas=grid)
+    assert (r.iters, r.converged, r.count, r.value) == (rr.iters, rr.converged, rr.count, rr.value)
+    assert np.array_equal(out.view(np.uint32), ref.view(np.uint32))
+
+
 @pytest.mark.parametrize("grid", [2, 11])
 def test_defect_correction_any_grid_size_is_bit_exact(gpu, orc, grid):
     from paper_1609_04567_gb300 import inputs
@@ -75,6 +82,7 @@ def check_choice(gpu, r, stencil):
         assert 1 <= r["temporal_k"] <= 32
     if stencil == gpu.SLR_RESTORE8:
         assert r["tiling"] in (gpu.SLR_TILING_NONE, gpu.SLR_TILING_TMA)
+        assert 1 <= r["temporal_k"] <= 8
 
 
 def test_tune_life_reads_only_and_later_solves_stay_exact(gpu, orc):
