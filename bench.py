@@ -329,10 +329,18 @@ def run_ours(args, wl, world, rank, local):
            "algorithmic_bytes_per_launch": algo_bytes, "passes_per_launch": passes,
            "generations_per_pass": k_eff}
     alu_ops = ALU_OPS_PER_CELL_GEN * nx * ny * gens
-    alu_peak = ALU_LANES_PER_SM * SMS * (clk.get("sm_mhz") or 2070.0) * 1e6 / 1e12
+    alu_nominal = ALU_LANES_PER_SM * SMS * (clk.get("sm_mhz") or 2070.0) * 1e6 / 1e12
+    # the logic pipe's rate measured on this GPU (independent three-input
+    # logic operations on every SM, CUDA events), the roofline's denominator
+    with torch.cuda.stream(stream):
+        logic_rate, logic_ms = slr.slr_measure_logic_rate(stream.cuda_stream)
+    alu_peak = logic_rate / 1e12
     alu = {"bound": "alu", "achieved": alu_ops / (kern_ms / 1e3) / 1e12, "peak": alu_peak, "unit": "Tops/s",
            "frac": alu_ops / (kern_ms / 1e3) / 1e12 / alu_peak, "traffic": traffic,
-           "peak_source": f"{ALU_LANES_PER_SM} lanes/SM x {SMS} SMs x median SM clock under load",
+           "peak_source": "measured: slr_measure_logic_rate (independent lop3 on every SM, 64 warps/SM, "
+                          f"CUDA events, {logic_ms:.2f} ms kernel)",
+           "peak_nominal": alu_nominal,
+           "peak_nominal_source": f"{ALU_LANES_PER_SM} lanes/SM x {SMS} SMs x median SM clock under load",
            "kernel_ms": kern_ms, "algorithmic_ops_per_launch": alu_ops}
     if k_eff == 1:
         roof = dict(hbm, kernel="life persistent loop, one generation per pass (all generations in one launch)")
@@ -450,6 +458,7 @@ def measure_configs(args):
     out = {}
     for name, fn in (("helmholtz_256_f64", measure_helmholtz), ("restore_4096_f32", measure_restore),
                      ("jacobi_large_grids", measure_jacobi),
+                     ("batch_dc_2d_to_1e-10", lambda a: measure_batch_dc(a, max_side=80, plain_grids=2)),
                      ("serve_2000rps", lambda a: measure_serve_short(a, args.configs_serve_seconds))):
         t0 = time.perf_counter()
         try:
@@ -621,6 +630,8 @@ def measure_restore(args):
     # fused_exact_k1: one sweep per pass (the TMA-tiled one-sweep kernel)
     runs = [("fused_exact", slr.SLR_LOOP_PERSISTENT, slr.SLR_MATH_EXACT, 0),
             ("fused_exact_k1", slr.SLR_LOOP_PERSISTENT, slr.SLR_MATH_EXACT, 1),
+            ("fused_exact_k2", slr.SLR_LOOP_PERSISTENT, slr.SLR_MATH_EXACT, 2),
+            ("fused_exact_k4", slr.SLR_LOOP_PERSISTENT, slr.SLR_MATH_EXACT, 4),
             ("fused_fast", slr.SLR_LOOP_PERSISTENT, slr.SLR_MATH_FAST, 0),
             ("plain_exact", slr.SLR_LOOP_HOST, slr.SLR_MATH_EXACT, 0)]
     if not args.no_tune:
@@ -693,6 +704,8 @@ def measure_restore(args):
     return {"workload": "restore_4096x4096_f32_tol1e-3", "metric": "Gcell-updates/s", "unit": "Gcell-updates/s",
             "l2": "device-loop solves: L2 flushed before each, outside its events",
             "value": res.get("tuned_exact", res["fused_exact"])["gcell_per_s"], "fused_exact": res["fused_exact"],
+            "fused_exact_k1": res["fused_exact_k1"], "fused_exact_k2": res["fused_exact_k2"],
+            "fused_exact_k4": res["fused_exact_k4"],
             "fused_fast": res["fused_fast"], "plain_exact": res["plain_exact"], "tuned_exact": res.get("tuned_exact"),
             "tuner": tuned, "clocks": clk,
             "roofline": {"hbm_peak_gbs": peak, "peak_source": peak_src, "algorithmic_bytes_per_pixel_sweep": 9,
@@ -934,6 +947,87 @@ def measure_serve_short(args, seconds: float):
             "what": "latency = arrival to the poll that sees the request finished; every arrival is served"}
 
 
+def measure_batch_dc(args, max_side=None, plain_grids=None):
+    """The precision half of the batched configuration: the 2D grids of the
+    batch workload (sides log-uniform in [64, 1024]) whose side is at most
+    `max_side`, solved until the change the next FP64 sweep would make
+    (max |h^2 r / (4 + sigma h^2)|) is below 1e-10, three ways: FP64 defect
+    correction around binary32 inner sweeps, all grids in one batched launch;
+    the fused FP64 device loop, one grid after another; and the plain
+    one-launch-per-sweep FP64 loop with a host test per sweep (timed on the
+    first `plain_grids` grids, per grid).  Every result's error is stated
+    against the discrete solution (the fused FP64 loop run to 1e-14).  Larger
+    grids need of the order of 10^5 to 10^6 sweeps to 1e-10 and are left out."""
+    import numpy as np
+    import torch
+    from paper_1609_04567_gb300 import inputs, slr
+    slr.load()
+    max_side = max_side or args.dc_max_side
+    plain_grids = plain_grids if plain_grids is not None else args.dc_plain_grids
+    sides = [int(x) for x in inputs.batch_sides(512)]
+    pick = [i for i, sd in enumerate(sides) if sd <= max_side]
+    fs = [torch.from_numpy(inputs.batch_grid_rhs(i, sides[i])).cuda() for i in pick]
+    stream = torch.cuda.Stream()
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+
+    def fused(f, tol, loop=slr.SLR_LOOP_PERSISTENT, **kw):
+        u = torch.zeros_like(f)
+        with torch.cuda.stream(stream):
+            sv = slr.Solver(slr.SLR_J2D5, u, f, stream=stream, tol=tol, loop=loop, **kw)
+            sv.run(10 ** 7)
+            r = sv.result(check=False)
+            sv.close()
+        return u, r
+    exact = [fused(f, 1e-14)[0] for f in fs]                 # the discrete solutions
+    scale = [float(e.abs().max()) for e in exact]
+    # FP64 defect correction, every grid in one batched launch
+    b = slr.Batch(len(fs) + 1, stream=stream)
+    us = [torch.zeros_like(f) for f in fs]
+    with torch.cuda.stream(stream):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        slots = [b.add(slr.SLR_J2D5, u, f, 100000, tol=1e-10, defect_correction=1) for u, f in zip(us, fs)]
+        b.run(10 ** 8)
+        _, running = b.poll()
+        dc_s = time.perf_counter() - t0
+    res = [b.result(sl) for sl in slots]
+    b.close()
+    dc_err = [float((u - e).abs().max()) / sc for u, e, sc in zip(us, exact, scale)]
+    # the fused FP64 loop, one grid after another
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    fr = [fused(f, 1e-10) for f in fs]
+    fused_s = time.perf_counter() - t0
+    fused_err = [float((u - e).abs().max()) / sc for (u, _), e, sc in zip(fr, exact, scale)]
+    # the plain loop on the first grids
+    t0 = time.perf_counter()
+    pr = [fused(f, 1e-10, loop=slr.SLR_LOOP_HOST) for f in fs[:plain_grids]]
+    plain_s = time.perf_counter() - t0
+    plain_err = [float((u - e).abs().max()) / sc for (u, _), e, sc in zip(pr, exact, scale)]
+    clk = clocks.stop()
+    n_plain = max(1, len(pr))
+    return {"workload": f"batch_dc_2d_sides64-{max_side}_to_1e-10", "grids": len(fs), "sides": [sides[i] for i in pick],
+            "metric": "time to the FP64 stopping rule 1e-10", "unit": "s", "value": dc_s,
+            "all_converged": running == 0 and all(r.converged for r in res),
+            "dc_batch": {"seconds": dc_s, "corrections_max": max(r.iters for r in res),
+                         "max_rel_err_vs_discrete": max(dc_err)},
+            "fused_fp64_sequential": {"seconds": fused_s, "sweeps_max": max(r.iters for _, r in fr),
+                                      "max_rel_err_vs_discrete": max(fused_err)},
+            "plain_fp64_host_loop": {"grids": len(pr), "seconds": plain_s, "seconds_per_grid": plain_s / n_plain,
+                                     "projected_seconds_all_grids": plain_s / n_plain * len(fs),
+                                     "max_rel_err_vs_discrete": max(plain_err) if plain_err else None},
+            "speedup_vs_plain_projected": plain_s / n_plain * len(fs) / dc_s,
+            "speedup_vs_fused_sequential": fused_s / dc_s, "clocks": clk,
+            "what": "defect correction: 50 binary32 sweeps per FP64 correction; the error is max |u - u*| / max |u*| "
+                    "against the fused FP64 loop run to 1e-14"}
+
+
+def run_batch_dc(args):
+    print(json.dumps(measure_batch_dc(args)), flush=True)
+    return 0
+
+
 def run_serve(args):
     """Continuous-batching serving: Poisson arrivals at 2000 requests/s, half
     denoise (sides 256-4096) and half Helmholtz solves (sides 64-2048)."""
@@ -1078,6 +1172,77 @@ def run_sobel(args):
     return 0
 
 
+def run_split(args):
+    """One grid over row blocks (the 1:n deployment of Sec. 3.3): the 8192 x
+    8192 Life torus cut into --split-blocks row blocks with `--split-halo`
+    copied-in rows, exchanged every pass.  Under torchrun each rank holds one
+    block on its own GPU and the halos and partial reduces travel over NCCL;
+    on one process all blocks share the GPU and the halos are device copies.
+    The result is checked against the same grid solved whole (the library's
+    own single-grid loop).  Metric: cell-updates of the whole grid per second."""
+    import hashlib
+    import torch
+    from paper_1609_04567_gb300 import inputs, slr
+    from paper_1609_04567_gb300 import split as S
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    slr.load()
+    n, gens, H = 8192, args.split_gens, args.split_halo
+    cells = inputs.life_cells(n, n)
+    parts = world if world > 1 else args.split_blocks
+    bounds = S.row_blocks(n, parts)
+    if world > 1:
+        import torch.distributed as dist
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        dist.init_process_group("nccl", rank=rank, world_size=world)
+        mine = [bounds[rank]]
+        ex = S.ProcessGroupExchanger(device="cuda")
+    else:
+        mine = bounds
+        ex = S.LocalExchanger()
+    desc = slr.slr_desc_init(slr.SLR_LIFE, n, n, 1)
+
+    def solve():
+        blocks = [(torch.from_numpy(cells[lo:hi]).cuda(), None, lo, hi) for lo, hi in mine]
+        loop = S.SplitLoop(slr.SLR_LIFE, blocks, n, halo=H, exchanger=ex, sweeper=S.DeviceSweeper(desc), tol=0.0,
+                           wrap=True)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        r = loop.run(gens)
+        torch.cuda.synchronize()
+        return loop, r, time.perf_counter() - t0
+    solve()                                            # warm-up
+    times = []
+    for _ in range(max(1, args.steps)):
+        loop, r, secs = solve()
+        times.append(secs)
+    secs = max_over_ranks(statistics.median(times), world)
+    ok = None
+    if rank == 0 and world == 1:
+        whole = torch.from_numpy(cells).cuda()
+        sv = slr.Solver(slr.SLR_LIFE, whole)
+        sv.run(gens)
+        rw = sv.result()
+        sv.close()
+        got = torch.cat([loop.own_rows(i) for i in range(len(mine))])
+        ok = bool(torch.equal(got, whole)) and (r.iters, r.count) == (rw.iters, rw.count)
+    if rank == 0:
+        print(json.dumps({
+            "workload": f"split_life_{n}x{n}_torus_{gens}gens", "metric": "Gcell-updates/s",
+            "unit": "Gcell-updates/s", "value": n * n * gens / secs / 1e9, "n_gpus": world, "blocks": parts,
+            "halo_rows": H, "passes": r.passes, "seconds": secs, "iters": r.iters, "live": r.count,
+            "scaling": "strong", "same_as_whole_grid": ok,
+            "what": "host-driven loop per pass: halo exchange, halo sweeps of the device block kernel (one cell "
+                    "per thread, the whole-grid sweep's operations), partial reduces combined on the host"}),
+              flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -1085,8 +1250,14 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="life",
-                    choices=["life", "helmholtz", "restore", "jacobi", "precision", "batch", "serve", "video", "sobel"])
+                    choices=["life", "helmholtz", "restore", "jacobi", "precision", "batch", "serve", "video", "sobel",
+                             "split", "batch_dc"])
     ap.add_argument("--video-frames", type=int, default=100, help="frames per stream of the video workload")
+    ap.add_argument("--dc-max-side", type=int, default=96, help="batch_dc workload: largest grid side")
+    ap.add_argument("--dc-plain-grids", type=int, default=4, help="batch_dc workload: grids timed on the plain loop")
+    ap.add_argument("--split-blocks", type=int, default=2, help="split workload on one process: row blocks")
+    ap.add_argument("--split-halo", type=int, default=8, help="split workload: copied-in rows per side")
+    ap.add_argument("--split-gens", type=int, default=200, help="split workload: generations")
     ap.add_argument("--batch3d", type=int, default=512, help="side of the 3D grid of the batch workload (0: none)")
     ap.add_argument("--rate", type=float, default=2000.0)
     ap.add_argument("--serve-seconds", type=float, default=10.0)
@@ -1116,7 +1287,8 @@ def main():
         ap.error("--warmup must be >= 3")
     if args.workload != "life":
         fn = {"helmholtz": run_helmholtz, "restore": run_restore, "jacobi": run_jacobi, "precision": run_precision,
-              "batch": run_batch, "serve": run_serve, "video": run_video, "sobel": run_sobel}
+              "batch": run_batch, "serve": run_serve, "video": run_video, "sobel": run_sobel, "split": run_split,
+              "batch_dc": run_batch_dc}
         return fn[args.workload](args)
     wl = WORKLOADS[args.workload]
     world, rank, local = dist_setup()

@@ -303,18 +303,23 @@ const char *slr_version(void);
 
 /* ---- Batches: many instances in one persistent launch -----------------------
  * A batch holds up to max_instances independent loops (SLR_J2D5, SLR_J3D7 in
- * any storage, SLR_RESTORE8 in EXACT math), each with its own grid, tolerance
- * and iteration cap.  slr_batch_run enqueues ONE cooperative launch that runs
- * up to `sweeps` more sweeps of every running instance with one grid barrier
- * per sweep for the whole batch; an instance stops when its test passes or
- * its cap is reached (the per-instance -d/-s tests of Sec. 3.1), and its
- * result is then in its u.  Instances may be added and removed between runs,
+ * any storage, with or without FP64 defect correction, SLR_RESTORE8 in EXACT
+ * math), each with its own grid, tolerance and iteration cap.  slr_batch_run
+ * enqueues ONE cooperative launch that runs up to `sweeps` more steps of
+ * every running instance with one grid barrier per step for the whole
+ * batch: a step is one sweep, or for a defect-correction instance one phase
+ * of its loop (the initial defect, one of its inner binary32 sweeps, or the
+ * correction with its new defect; its test follows each correction and its
+ * iteration count is the number of corrections).  An instance stops when its
+ * test passes or its cap is reached (the per-instance -d/-s tests of Sec.
+ * 3.1), and its result is then in its u.  Instances may be added and removed between runs,
  * which is how a serving loop admits new work while earlier work is still
  * running (continuous batching).  Results are identical to slr_create runs of
  * the same descriptors.
  *
  * Ownership: the caller owns u, aux and a scratch buffer per instance
- * (slr_batch_scratch_size bytes, the second state buffer), and the batch
+ * (slr_batch_scratch_size bytes: the second state buffer, plus the binary32
+ * defect and corrections of a defect-correction instance), and the batch
  * workspace (slr_batch_workspace_size bytes, 256-byte aligned).  None of them
  * may be freed or reused while the instance is in the batch and a run may be
  * in flight.  The batch handle owns host metadata only. */
@@ -326,7 +331,7 @@ slr_status slr_batch_create(int32_t max_instances, void *workspace, size_t works
 /* Add an instance with its own absolute iteration cap; returns its slot. */
 slr_status slr_batch_add(slr_batch b, const slr_desc *d, void *u, const void *aux, void *scratch,
                          int64_t max_iters, int32_t *slot);
-/* Enqueue up to `sweeps` sweeps of all running instances (asynchronous). */
+/* Enqueue up to `sweeps` steps of all running instances (asynchronous). */
 slr_status slr_batch_run(slr_batch b, int64_t sweeps);
 /* Wait for the batch's stream; list (up to max_finished) slots that finished
  * since the last poll, and count the instances still running. */
@@ -511,6 +516,16 @@ slr_status slr_check_exact_division(double d, uint64_t *mismatches, uint64_t *ch
  * counts differences (0 on a correct build), *checked the values tried.
  * Waits for `stream`; static device counters. */
 slr_status slr_check_exact_isqrt(uint64_t *mismatches, uint64_t *checked, void *stream);
+
+/* Measured throughput of the integer logic pipe on the current device, the
+ * denominator of the Game of Life roofline (the bit-sliced update of Fig. 1's
+ * rule is three-input logic operations and funnel shifts, which issue to that
+ * pipe): a kernel of independent three-input logic operations on every SM
+ * (64 warps per SM), timed with CUDA events on `stream` after one warm-up
+ * launch.  *ops_per_s receives the logic operations per second (thread
+ * operations), *ms the timed kernel's duration; either may be NULL.  Waits
+ * for `stream`.  Returns SLR_OK or SLR_ERR_CUDA. */
+slr_status slr_measure_logic_rate(double *ops_per_s, double *ms, void *stream);
 
 #ifdef __cplusplus
 }

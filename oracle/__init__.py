@@ -134,6 +134,10 @@ def _load(omp=None):
     lib.orc_sobel.restype = i32
     lib.orc_j2d5_scaled_defect.argtypes = [P, P, i64, i64, f64, f64]
     lib.orc_j2d5_scaled_defect.restype = f64
+    lib.orc_j3d7_dc.argtypes = [P, P, i64, i64, i64, f64, f64, f64, i64, i64, R]
+    lib.orc_j3d7_dc.restype = i32
+    lib.orc_j3d7_scaled_defect.argtypes = [P, P, i64, i64, i64, f64, f64]
+    lib.orc_j3d7_scaled_defect.restype = f64
     for name in ("orc_j2d5_f64", "orc_j2d5_f32", "orc_j3d7_f64", "orc_j3d7_f32",
                  "orc_life", "orc_restore8", "orc_j2d5_dc"):
         getattr(lib, name).restype = i32
@@ -279,6 +283,27 @@ def j2d5_dc(u0, f, *, sigma=1.0, h=0.0, tol=1e-10, k_in=50, max_outer=100000):
     _check(lib.orc_j2d5_dc(_ptr(u), _ptr(ff), nx, ny, sigma, h, tol, k_in, max_outer,
                            ctypes.byref(r)), "j2d5_dc")
     return u, _res(r)
+
+
+def j3d7_dc(u0, f, *, sigma=1.0, h=0.0, tol=1e-10, k_in=50, max_outer=100000):
+    """FP64 defect correction with FP32 Jacobi inner solves, 3D 7-point
+    operator (ghost 0); arrays are (nz, ny, nx)."""
+    lib = _load()
+    r = _CResult()
+    u = np.array(u0, dtype=np.float64, order="C", copy=True)
+    ff = np.ascontiguousarray(f, dtype=np.float64)
+    nz, ny, nx = u.shape
+    _check(lib.orc_j3d7_dc(_ptr(u), _ptr(ff), nx, ny, nz, sigma, h, tol, k_in, max_outer, ctypes.byref(r)),
+           "j3d7_dc")
+    return u, _res(r)
+
+
+def j3d7_scaled_defect(u, f, *, sigma=1.0, h=0.0) -> float:
+    lib = _load()
+    uu = np.ascontiguousarray(u, dtype=np.float64)
+    ff = np.ascontiguousarray(f, dtype=np.float64)
+    nz, ny, nx = uu.shape
+    return float(lib.orc_j3d7_scaled_defect(_ptr(uu), _ptr(ff), nx, ny, nz, sigma, h))
 
 
 def j2d5_scaled_defect(u, f, *, sigma=1.0, h=0.0) -> float:

@@ -587,6 +587,92 @@ double orc_j2d5_scaled_defect(const double *u, const double *f, int64_t nx, int6
     return rho;
 }
 
+/* The same defect correction for the 3D 7-point operator:
+ *   A u = ((6 + sigma h^2) u - sum of the 6 neighbours) / h^2,  ghost 0,
+ * neighbours summed x-, x+, y-, y+, z-, z+; inner binary32 Jacobi sweeps
+ *   e' = (h2 * r32 + (((((e_x- + e_x+) + e_y-) + e_y+) + e_z-) + e_z+)) / d;
+ * rho = max |h^2 r / (6 + sigma h^2)|, the change of the next FP64 sweep. */
+static double defect3_f64(const double *u, const double *f, double *r, int64_t nx, int64_t ny, int64_t nz,
+                          double h2, double d)
+{
+    double rho = 0.0;
+#pragma omp parallel for collapse(2) reduction(max : rho) schedule(static)
+    for (int64_t k = 0; k < nz; ++k)
+        for (int64_t i = 0; i < ny; ++i)
+            for (int64_t j = 0; j < nx; ++j) {
+                double s = ((((at3_f64(u, nx, ny, nz, k, i, j - 1, 0, 0.0) +
+                               at3_f64(u, nx, ny, nz, k, i, j + 1, 0, 0.0)) +
+                              at3_f64(u, nx, ny, nz, k, i - 1, j, 0, 0.0)) +
+                             at3_f64(u, nx, ny, nz, k, i + 1, j, 0, 0.0)) +
+                            at3_f64(u, nx, ny, nz, k - 1, i, j, 0, 0.0)) +
+                           at3_f64(u, nx, ny, nz, k + 1, i, j, 0, 0.0);
+                size_t c = (size_t)((k * ny + i) * nx + j);
+                double au = (d * u[c] - s) / h2;
+                double rv = f[c] - au;
+                r[c] = rv;
+                double sc = fabs(h2 * rv / d);
+                if (sc > rho) rho = sc;
+            }
+    return rho;
+}
+
+int orc_j3d7_dc(double *u, const double *f, int64_t nx, int64_t ny, int64_t nz, double sigma,
+                double h, double tol, int64_t k_in, int64_t max_outer, orc_result *res)
+{
+    if (nx < 1 || ny < 1 || nz < 1 || max_outer < 1 || k_in < 1) return -1;
+    double hh = mesh_h(h, nx), h2 = hh * hh, d = 6.0 + sigma * h2;
+    float h2f = (float)h2, df = (float)d;
+    size_t n = (size_t)(nx * ny * nz);
+    double *r = (double *)malloc(n * sizeof(double));
+    float *r32 = (float *)malloc(n * sizeof(float));
+    float *e = (float *)malloc(n * sizeof(float));
+    float *e2 = (float *)malloc(n * sizeof(float));
+    if (!r || !r32 || !e || !e2) { free(r); free(r32); free(e); free(e2); return -2; }
+    defect3_f64(u, f, r, nx, ny, nz, h2, d);
+    int64_t it = 0;
+    double rho = 0.0;
+    int conv = 0;
+    do {
+        for (size_t c = 0; c < n; ++c) { r32[c] = (float)r[c]; e[c] = 0.0f; }
+        for (int64_t s = 0; s < k_in; ++s) {
+#pragma omp parallel for collapse(2) schedule(static)
+            for (int64_t k = 0; k < nz; ++k)
+                for (int64_t i = 0; i < ny; ++i)
+                    for (int64_t j = 0; j < nx; ++j) {
+                        float sn = ((((at3_f32(e, nx, ny, nz, k, i, j - 1, 0, 0.0f) +
+                                       at3_f32(e, nx, ny, nz, k, i, j + 1, 0, 0.0f)) +
+                                      at3_f32(e, nx, ny, nz, k, i - 1, j, 0, 0.0f)) +
+                                     at3_f32(e, nx, ny, nz, k, i + 1, j, 0, 0.0f)) +
+                                    at3_f32(e, nx, ny, nz, k - 1, i, j, 0, 0.0f)) +
+                                   at3_f32(e, nx, ny, nz, k + 1, i, j, 0, 0.0f);
+                        size_t c = (size_t)((k * ny + i) * nx + j);
+                        float t = h2f * r32[c];
+                        e2[c] = (t + sn) / df;
+                    }
+            memcpy(e, e2, n * sizeof(float));
+        }
+        for (size_t c = 0; c < n; ++c) u[c] = u[c] + (double)e[c];
+        rho = defect3_f64(u, f, r, nx, ny, nz, h2, d);
+        it += 1;
+        conv = rho < tol;
+    } while (!conv && it < max_outer);
+    free(r); free(r32); free(e); free(e2);
+    res->iters = it; res->value = rho; res->converged = conv; res->changed = 1;
+    res->count = 0;
+    return 0;
+}
+
+double orc_j3d7_scaled_defect(const double *u, const double *f, int64_t nx, int64_t ny, int64_t nz,
+                              double sigma, double h)
+{
+    double hh = mesh_h(h, nx), h2 = hh * hh, d = 6.0 + sigma * h2;
+    double *r = (double *)malloc((size_t)(nx * ny * nz) * sizeof(double));
+    if (!r) return -1.0;
+    double rho = defect3_f64(u, f, r, nx, ny, nz, h2, d);
+    free(r);
+    return rho;
+}
+
 /* Array forms of the storage conversions, for the tests. */
 void orc_f32_to_bf16_array(const float *x, uint16_t *out, int64_t n)
 {

@@ -12,9 +12,15 @@
 // reached); stopped instances drop out of the index space.  At the end of a
 // run the state of every stopped instance is in its caller buffer u.
 //
-// The elemental functions and the evaluation order are those of jacobi.cu and
-// restore.cu (EXACT math), so every instance gets the same result alone, in a
-// batch, or through slr_create.
+// The elemental functions and the evaluation order are those of jacobi.cu,
+// restore.cu and dc.cu (EXACT math), so every instance gets the same result
+// alone, in a batch, or through slr_create.
+//
+// A defect-correction instance (FP64 outer loop around FP32 Jacobi inner
+// sweeps, dc.cu) advances one phase per batch step: the initial defect, then
+// per correction its inner sweeps and the correction with the new defect; its
+// test runs after each correction only, and its iteration count is the number
+// of corrections.
 #include <stdio.h>
 #include <string.h>
 
@@ -56,6 +62,11 @@ struct BInst {
     int local;        // small Jacobi instance run whole by one CTA (see cta_local_run)
     double value;
     unsigned long long count;
+    // defect correction
+    int dc;           // 1: FP64 defect correction around binary32 inner sweeps
+    int inner;        // inner sweeps per correction
+    float *r32, *e0, *e1;   // binary32 defect and correction buffers (in the instance's scratch)
+    long long phase;  // phases run so far: 0 the initial defect, then inner + 1 per correction
 };
 
 struct BatchArgs {
@@ -288,6 +299,94 @@ __device__ void restore_unit(const BInst &I, long long unit, const void *uv, voi
     __syncwarp();
 }
 
+// ---- defect correction (the operations and order of dc.cu) ----------------------
+__device__ __forceinline__ bool dc_outside(const BInst &I, long long k, long long i, long long j)
+{
+    return k < 0 || k >= I.nz || i < 0 || i >= I.ny || j < 0 || j >= I.nx;
+}
+
+template <int DIM, class T, class V>
+__device__ __forceinline__ T dc_sum(long long k, long long i, long long j, V val)
+{
+    if (DIM == 2)
+        return add_rn(add_rn(add_rn(val(k, i - 1, j), val(k, i + 1, j)), val(k, i, j - 1)), val(k, i, j + 1));
+    return add_rn(add_rn(add_rn(add_rn(add_rn(val(k, i, j - 1), val(k, i, j + 1)), val(k, i - 1, j)), val(k, i + 1, j)),
+                         val(k - 1, i, j)),
+                  val(k + 1, i, j));
+}
+
+// r = f - A v at (k, i, j), v read through `val` (ghost 0)
+template <int DIM, class V>
+__device__ __forceinline__ double dc_defect(const BInst &I, long long k, long long i, long long j, V val)
+{
+    const double sm = dc_sum<DIM, double>(k, i, j, val);
+    const double au = __ddiv_rn(__dsub_rn(__dmul_rn(I.d, val(k, i, j)), sm), I.h2);
+    return __dsub_rn(__ldg((const double *)I.aux + (k * I.ny + i) * I.nx + j), au);
+}
+
+// One warp unit of phase q of a defect-correction instance: q = 0 the
+// initial defect r32 = f - A u; then, per correction n, phases 0 .. inner-1
+// the binary32 sweeps of A e = r32 from e = 0 and phase inner the correction
+// u' = u + e with its new defect; returns the correction's max |h2 r / d| as
+// bits (0 in the other phases).
+template <int DIM>
+__device__ unsigned long long dc_unit(const BInst &I, long long unit, long long q)
+{
+    const int lane = threadIdx.x & 31;
+    const long long per_plane = I.tiles_x * I.tiles_y;
+    const long long k = unit / per_plane, rem = unit - k * per_plane;
+    const long long ty = rem / I.tiles_x, tx = rem - ty * I.tiles_x;
+    const long long P = I.inner + 1;
+    const long long n = q >= 1 ? (q - 1) / P : 0;
+    const int ph = q >= 1 ? (int)((q - 1) % P) : -1;
+    const double *uo = (const double *)((n & 1) ? I.b : I.a);
+    double *un = (double *)((n & 1) ? I.a : I.b);
+    const float *es = (ph & 1) ? I.e1 : I.e0;
+    float *ed = (ph & 1) ? I.e0 : I.e1;
+    const float *ec = (I.inner & 1) ? I.e1 : I.e0;          // e after the inner sweeps
+    unsigned long long mx = 0ull;
+    for (int r = 0; r < kTileH; ++r) {
+        const long long i = ty * kTileH + r;
+        if (i >= I.ny) break;
+        for (int c = lane; c < kTileW; c += 32) {
+            const long long j = tx * kTileW + c;
+            if (j >= I.nx) continue;
+            const long long idx = (k * I.ny + i) * I.nx + j;
+            if (ph < 0) {
+                const double rv = dc_defect<DIM>(I, k, i, j, [&](long long z, long long y, long long x) {
+                    return dc_outside(I, z, y, x) ? 0.0 : __ldcg(uo + (z * I.ny + y) * I.nx + x);
+                });
+                I.r32[idx] = (float)rv;
+            } else if (ph < I.inner) {
+                float sn = 0.0f;
+                if (ph > 0)
+                    sn = dc_sum<DIM, float>(k, i, j, [&](long long z, long long y, long long x) {
+                        return dc_outside(I, z, y, x) ? 0.0f : __ldcg(es + (z * I.ny + y) * I.nx + x);
+                    });
+                const float t = __fmul_rn(I.h2f, __ldcg(I.r32 + idx));
+                ed[idx] = __fdiv_rn(__fadd_rn(t, sn), I.df);
+            } else {
+                un[idx] = __dadd_rn(__ldcg(uo + idx), (double)__ldcg(ec + idx));
+                const double rv = dc_defect<DIM>(I, k, i, j, [&](long long z, long long y, long long x) {
+                    if (dc_outside(I, z, y, x)) return 0.0;
+                    const long long qx = (z * I.ny + y) * I.nx + x;
+                    return __dadd_rn(__ldcg(uo + qx), (double)__ldcg(ec + qx));
+                });
+                I.r32[idx] = (float)rv;
+                const unsigned long long b = (unsigned long long)__double_as_longlong(fabs(__ddiv_rn(__dmul_rn(I.h2, rv), I.d)));
+                mx = b > mx ? b : mx;
+            }
+        }
+    }
+    return mx;
+}
+
+// corrections completed after `phases` phases of a defect-correction instance
+__device__ __forceinline__ long long dc_corrections(const BInst &I, long long phases)
+{
+    return phases >= 1 ? (phases - 1) / (I.inner + 1) : 0;
+}
+
 __device__ void unit_copy(const BInst &I, long long unit, const void *src, void *dst)
 {
     const int lane = threadIdx.x & 31;
@@ -513,7 +612,8 @@ __global__ void __launch_bounds__(kBThreads, 2) batch_kernel(BatchArgs ba)
     unsigned char *tail = smem_raw + (size_t)(kBThreads / 32) * kStageBytesPerWarp;
     const int n = ba.nact;
     long long *s_iters0 = (long long *)tail;                      // [n]
-    int *s_stop = (int *)(s_iters0 + n);                          // [n]: sweep index of the stop, -1 running
+    long long *s_phase0 = s_iters0 + n;                           // [n]: defect correction's phases so far
+    int *s_stop = (int *)(s_phase0 + n);                          // [n]: sweep index of the stop, -1 running
     int *s_units = s_stop + n;                                    // [n]
     int *s_aidx = s_units + n;                                    // [n]: running instances (positions in act)
     int *s_upref = s_aidx + n;                                    // [n + 1]: unit prefix of s_aidx
@@ -524,6 +624,7 @@ __global__ void __launch_bounds__(kBThreads, 2) batch_kernel(BatchArgs ba)
     for (int i = tid; i < n; i += kBThreads) {
         const BInst &I = ba.inst[ba.act[i]];
         s_iters0[i] = I.iters;
+        s_phase0[i] = I.phase;
         s_par0[i] = (unsigned char)I.parity;
         s_stop[i] = I.done ? -2 : (I.local ? -3 : -1);   // -3: run by one CTA below
         s_units[i] = (int)I.units;
@@ -560,7 +661,16 @@ __global__ void __launch_bounds__(kBThreads, 2) batch_kernel(BatchArgs ba)
             const void *src = par ? I.b : I.a;
             void *dst = par ? I.a : I.b;
             Slot *slot = &ba.slots[(size_t)ba.act[ai] * kSlots + (size_t)(s % kSlots)];
-            if (I.stencil == SLR_RESTORE8) {
+            if (I.dc) {
+                unsigned long long mx = I.stencil == SLR_J3D7 ? dc_unit<3>(I, unit, s_phase0[ai] + s)
+                                                              : dc_unit<2>(I, unit, s_phase0[ai] + s);
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    const unsigned long long m2 = __shfl_xor_sync(0xffffffffu, mx, o);
+                    mx = m2 > mx ? m2 : mx;
+                }
+                if (lane == 0 && mx) atomicMax(&slot->maxbits, mx);
+            } else if (I.stencil == SLR_RESTORE8) {
                 unsigned long long sum = 0ull, cnt = 0ull;
                 restore_unit(I, unit, src, dst, stage, sum, cnt);
 #pragma unroll
@@ -607,8 +717,15 @@ __global__ void __launch_bounds__(kBThreads, 2) batch_kernel(BatchArgs ba)
             const Slot sl = read_slot(&ba.slots[(size_t)gi * kSlots + (size_t)(s % kSlots)]);
             BInst &I = ba.inst[gi];
             const Decision dcs = decide(I.reduce, sl, I.tol);
-            const long long it = s_iters0[i] + s + 1;
-            if (dcs.converged || it >= I.max_iters) {
+            long long it = s_iters0[i] + s + 1;
+            bool tested = true;
+            if (I.dc) {
+                // the test follows the corrections only
+                const long long q = s_phase0[i] + s;
+                tested = q >= 1 && (q - 1) % (I.inner + 1) == I.inner;
+                it = dc_corrections(I, q + 1);
+            }
+            if (tested && (dcs.converged || it >= I.max_iters)) {
                 s_stop[i] = (int)s;
                 if (blockIdx.x == 0) {
                     I.value = dcs.value;
@@ -632,8 +749,14 @@ __global__ void __launch_bounds__(kBThreads, 2) batch_kernel(BatchArgs ba)
             if (s_stop[i] == -2 || s_stop[i] == -3) continue;
             BInst &I = ba.inst[ba.act[i]];
             const long long done_sweeps = s_stop[i] >= 0 ? s_stop[i] + 1 : ran;
-            I.iters = s_iters0[i] + done_sweeps;
-            I.parity = (s_par0[i] + (int)done_sweeps) & 1;
+            if (I.dc) {
+                I.phase = s_phase0[i] + done_sweeps;
+                I.iters = dc_corrections(I, I.phase);
+                I.parity = (int)(I.iters & 1);
+            } else {
+                I.iters = s_iters0[i] + done_sweeps;
+                I.parity = (s_par0[i] + (int)done_sweeps) & 1;
+            }
             I.done = s_stop[i] >= 0;
         }
     }
@@ -641,8 +764,12 @@ __global__ void __launch_bounds__(kBThreads, 2) batch_kernel(BatchArgs ba)
     for (long long u = gw; u < U0; u += warps) {
         const int ai = find_instance(ba.prefix, n, u);
         if (s_stop[ai] < 0) continue;
-        if (((s_par0[ai] + s_stop[ai] + 1) & 1) == 0) continue;   // final state already in a
         const BInst &I = ba.inst[ba.act[ai]];
+        if (I.dc) {
+            if ((dc_corrections(I, s_phase0[ai] + s_stop[ai] + 1) & 1) == 0) continue;   // final state in a
+        } else if (((s_par0[ai] + s_stop[ai] + 1) & 1) == 0) {
+            continue;                                                // final state already in a
+        }
         unit_copy(I, u - __ldg(ba.prefix + ai), I.b, I.a);
     }
 }
@@ -710,7 +837,9 @@ size_t slr_batch_scratch_size(const slr_desc *d)
     bool unsup = false;
     if (!slr::describe_invalid(d, &unsup).empty()) return 0;
     if (d->stencil == SLR_LIFE) return 0;
-    return rup(slr::problem_of(d).state_bytes, 256);
+    const slr::Problem p = slr::problem_of(d);
+    // the second state buffer, and for defect correction the binary32 defect and two corrections
+    return rup(p.state_bytes, 256) + (d->defect_correction ? slr::dc_workspace_bytes(p.nx, p.ny, p.nz) : 0);
 }
 
 slr_status slr_batch_create(int32_t max_instances, void *workspace, size_t workspace_bytes, void *stream,
@@ -750,8 +879,8 @@ slr_status slr_batch_add(slr_batch b, const slr_desc *d, void *u, const void *au
     bool unsup = false;
     const std::string why = slr::describe_invalid(d, &unsup);
     if (!why.empty()) return bfail(b, unsup ? SLR_ERR_UNSUPPORTED : SLR_ERR_INVALID_ARG, why);
-    if (d->stencil == SLR_LIFE || d->defect_correction)
-        return bfail(b, SLR_ERR_UNSUPPORTED, "batches run the Jacobi and restoration stencils (no defect correction)");
+    if (d->stencil == SLR_LIFE)
+        return bfail(b, SLR_ERR_UNSUPPORTED, "batches run the Jacobi and restoration stencils");
     if (d->stencil == SLR_RESTORE8 && d->math != SLR_MATH_EXACT)
         return bfail(b, SLR_ERR_UNSUPPORTED, "batched restoration runs EXACT math");
     if (!u || !aux || !scratch || ((uintptr_t)u & 15u) || ((uintptr_t)scratch & 15u))
@@ -777,8 +906,18 @@ slr_status slr_batch_add(slr_batch b, const slr_desc *d, void *u, const void *au
     I.tiles_x = (p.nx + slr::kTileW - 1) / slr::kTileW;
     I.tiles_y = (p.ny + slr::kTileH - 1) / slr::kTileH;
     I.units = I.tiles_x * I.tiles_y * p.nz;
-    I.local = p.stencil != SLR_RESTORE8 &&
+    I.local = p.stencil != SLR_RESTORE8 && !d->defect_correction &&
               3 * p.nx * p.ny * p.nz * (p.storage == SLR_F64 ? 8 : 4) <= slr::kLocalBytes;
+    if (d->defect_correction) {
+        const size_t blk = rup((size_t)p.nx * (size_t)p.ny * (size_t)p.nz * 4, 256);
+        unsigned char *f32 = (unsigned char *)scratch + rup(p.state_bytes, 256);
+        I.dc = 1;
+        I.inner = d->inner_sweeps > 0 ? d->inner_sweeps : 50;
+        I.r32 = (float *)f32;
+        I.e0 = (float *)(f32 + blk);
+        I.e1 = (float *)(f32 + 2 * blk);
+        I.phase = 0;
+    }
     b->inst[(size_t)s] = I;
     b->used[(size_t)s] = 1;
     b->reported[(size_t)s] = 0;
@@ -843,7 +982,7 @@ slr_status slr_batch_run(slr_batch b, int64_t sweeps)
     ba.sweeps = sweeps;
     ba.ctl = (slr::Ctl *)b->ws;
     ba.limit_ns = 2000000000ll;
-    const size_t smem = (size_t)(slr::kBThreads / 32) * slr::kStageBytesPerWarp + (size_t)ba.nact * 8 +
+    const size_t smem = (size_t)(slr::kBThreads / 32) * slr::kStageBytesPerWarp + (size_t)ba.nact * 16 +
                         (size_t)ba.nact * 4 * 4 + 4 + (size_t)ba.nact;
     e = cudaFuncSetAttribute(slr::batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return bcuda(b, e, "batch kernel attributes");

@@ -1,10 +1,12 @@
 // dc.cu -- FP64 defect correction around FP32 Jacobi inner solves (2D
-// 5-point Helmholtz, Dirichlet ghost 0), as one persistent launch.
+// 5-point and 3D 7-point Helmholtz, Dirichlet ghost 0), as one persistent
+// launch.
 //
 // The loop of Sec. 3.1 whose elemental step is one correction: with
-// A u = ((4 + sigma h^2) u - sum of neighbours) / h^2 and r = f - A u,
-//     e = 0;  inner_sweeps binary32 Jacobi sweeps  e' = (h2 r32 + ((e_N + e_S) + e_W) + e_E) / d
+// A u = ((2n + sigma h^2) u - sum of neighbours) / h^2 and r = f - A u,
+//     e = 0;  inner_sweeps binary32 Jacobi sweeps  e' = (h2 r32 + sum of e's neighbours) / d
 //     u' = u + (double) e;   r' = f - A u'  (binary64);   rho = max |h2 r' / d|
+// neighbours summed ((N + S) + W) + E in 2D, x-, x+, y-, y+, z-, z+ in 3D.
 // until rho < tol or the cap.  FP64 arithmetic is used only for the update,
 // the defect and its reduce; the inner solves run in binary32.
 //
@@ -21,55 +23,65 @@ namespace {
 
 constexpr int kDThreads = 1024;
 
+__device__ __forceinline__ double add_rn(double x, double y) { return __dadd_rn(x, y); }
+__device__ __forceinline__ float add_rn(float x, float y) { return __fadd_rn(x, y); }
+
 struct DcArgs {
     double *u;          // caller state (A)
     double *ub;         // workspace state (B)
     const double *f;
     float *r32;
     float *e[2];
-    long long nx, ny;
+    long long nx, ny, nz;
     double h2, d;
     float h2f, df;
     int inner;
 };
 
-// Grid-stride over cells by (row, 1024-column chunk) units.
+// Grid-stride over cells by (plane, row, 1024-column chunk) units.
 template <class F>
-__device__ __forceinline__ void for_cells(long long nx, long long ny, F fn)
+__device__ __forceinline__ void for_cells(long long nx, long long ny, long long nz, F fn)
 {
     const long long chunks = (nx + blockDim.x - 1) / blockDim.x;
-    const long long units = ny * chunks;
+    const long long units = nz * ny * chunks;
     for (long long un = blockIdx.x; un < units; un += gridDim.x) {
-        const long long i = un / chunks;
-        const long long j = (un - i * chunks) * blockDim.x + threadIdx.x;
-        if (j < nx) fn(i, j);
+        const long long row = un / chunks;
+        const long long j = (un - row * chunks) * blockDim.x + threadIdx.x;
+        if (j < nx) fn(row / ny, row % ny, j);
     }
 }
 
-__device__ __forceinline__ float e_at(const float *e, long long nx, long long ny, long long i, long long j)
+__device__ __forceinline__ bool outside(const DcArgs &a, long long k, long long i, long long j)
 {
-    if (i < 0 || i >= ny || j < 0 || j >= nx) return 0.0f;
-    return __ldcg(e + i * nx + j);
+    return k < 0 || k >= a.nz || i < 0 || i >= a.ny || j < 0 || j >= a.nx;
 }
 
-// u_old + e at (i, j), or the ghost 0 outside the grid
-__device__ __forceinline__ double ue_at(const double *u, const float *e, long long nx, long long ny, long long i,
-                                        long long j)
+__device__ __forceinline__ long long cell(const DcArgs &a, long long k, long long i, long long j)
 {
-    if (i < 0 || i >= ny || j < 0 || j >= nx) return 0.0;
-    const long long c = i * nx + j;
-    return __dadd_rn(__ldcg(u + c), (double)__ldcg(e + c));
+    return (k * a.ny + i) * a.nx + j;
+}
+
+// the sum of the neighbours of (k, i, j) read through `val`, in the oracle's order
+template <int DIM, class T, class V>
+__device__ __forceinline__ T nbr_sum(long long k, long long i, long long j, V val)
+{
+    if (DIM == 2)
+        return add_rn(add_rn(add_rn(val(k, i - 1, j), val(k, i + 1, j)), val(k, i, j - 1)), val(k, i, j + 1));
+    return add_rn(add_rn(add_rn(add_rn(add_rn(val(k, i, j - 1), val(k, i, j + 1)), val(k, i - 1, j)), val(k, i + 1, j)),
+                         val(k - 1, i, j)),
+                  val(k + 1, i, j));
 }
 
 // r = f - A v with v read through `val` (ghost 0); returns r (binary64)
-template <class V>
-__device__ __forceinline__ double defect_at(const DcArgs &a, long long i, long long j, V val)
+template <int DIM, class V>
+__device__ __forceinline__ double defect_at(const DcArgs &a, long long k, long long i, long long j, V val)
 {
-    const double s = __dadd_rn(__dadd_rn(__dadd_rn(val(i - 1, j), val(i + 1, j)), val(i, j - 1)), val(i, j + 1));
-    const double au = __ddiv_rn(__dsub_rn(__dmul_rn(a.d, val(i, j)), s), a.h2);
-    return __dsub_rn(__ldg(a.f + i * a.nx + j), au);
+    const double s = nbr_sum<DIM, double>(k, i, j, val);
+    const double au = __ddiv_rn(__dsub_rn(__dmul_rn(a.d, val(k, i, j)), s), a.h2);
+    return __dsub_rn(__ldg(a.f + cell(a, k, i, j)), au);
 }
 
+template <int DIM>
 __global__ void __launch_bounds__(kDThreads, 1) dc_kernel(DcArgs a, LoopArgs la)
 {
     __shared__ int s_stop;
@@ -79,11 +91,11 @@ __global__ void __launch_bounds__(kDThreads, 1) dc_kernel(DcArgs a, LoopArgs la)
     if ((la.debug_flags & SLR_DEBUG_SKIP_ARRIVAL) && blockIdx.x == gridDim.x - 1) return;
     unsigned long long bar = 0;
     // initial defect of the caller's state
-    for_cells(a.nx, a.ny, [&](long long i, long long j) {
-        const double r = defect_at(a, i, j, [&](long long y, long long x) {
-            return (y < 0 || y >= a.ny || x < 0 || x >= a.nx) ? 0.0 : __ldcg(a.u + y * a.nx + x);
+    for_cells(a.nx, a.ny, a.nz, [&](long long k, long long i, long long j) {
+        const double r = defect_at<DIM>(a, k, i, j, [&](long long z, long long y, long long x) {
+            return outside(a, z, y, x) ? 0.0 : __ldcg(a.u + cell(a, z, y, x));
         });
-        a.r32[i * a.nx + j] = (float)r;
+        a.r32[cell(a, k, i, j)] = (float)r;
     });
     bar += la.nblocks;
     if (!grid_barrier(ctl, bar, la.limit_ns)) return;
@@ -95,14 +107,15 @@ __global__ void __launch_bounds__(kDThreads, 1) dc_kernel(DcArgs a, LoopArgs la)
             const float *es = a.e[m & 1];
             float *ed = a.e[(m + 1) & 1];
             const bool zero = m == 0;
-            for_cells(a.nx, a.ny, [&](long long i, long long j) {
+            for_cells(a.nx, a.ny, a.nz, [&](long long k, long long i, long long j) {
                 float sn = 0.0f;
                 if (!zero)
-                    sn = __fadd_rn(__fadd_rn(__fadd_rn(e_at(es, a.nx, a.ny, i - 1, j), e_at(es, a.nx, a.ny, i + 1, j)),
-                                             e_at(es, a.nx, a.ny, i, j - 1)),
-                                   e_at(es, a.nx, a.ny, i, j + 1));
-                const float t = __fmul_rn(a.h2f, __ldcg(a.r32 + i * a.nx + j));
-                ed[i * a.nx + j] = __fdiv_rn(__fadd_rn(t, sn), a.df);
+                    sn = nbr_sum<DIM, float>(k, i, j, [&](long long z, long long y, long long x) {
+                        return outside(a, z, y, x) ? 0.0f : __ldcg(es + cell(a, z, y, x));
+                    });
+                const long long c = cell(a, k, i, j);
+                const float t = __fmul_rn(a.h2f, __ldcg(a.r32 + c));
+                ed[c] = __fdiv_rn(__fadd_rn(t, sn), a.df);
             });
             bar += la.nblocks;
             if (!grid_barrier(ctl, bar, la.limit_ns)) return;
@@ -110,11 +123,16 @@ __global__ void __launch_bounds__(kDThreads, 1) dc_kernel(DcArgs a, LoopArgs la)
         // correction and new defect in one pass
         const float *e = a.e[a.inner & 1];
         unsigned long long mx = 0ull;
-        for_cells(a.nx, a.ny, [&](long long i, long long j) {
-            const long long c = i * a.nx + j;
+        for_cells(a.nx, a.ny, a.nz, [&](long long k, long long i, long long j) {
+            const long long c = cell(a, k, i, j);
             const double unew = __dadd_rn(__ldcg(uo + c), (double)__ldcg(e + c));
             un[c] = unew;
-            const double r = defect_at(a, i, j, [&](long long y, long long x) { return ue_at(uo, e, a.nx, a.ny, y, x); });
+            // u_old + e at each neighbour, the ghost 0 outside the grid
+            const double r = defect_at<DIM>(a, k, i, j, [&](long long z, long long y, long long x) {
+                if (outside(a, z, y, x)) return 0.0;
+                const long long q = cell(a, z, y, x);
+                return __dadd_rn(__ldcg(uo + q), (double)__ldcg(e + q));
+            });
             a.r32[c] = (float)r;
             const unsigned long long b =
                 (unsigned long long)__double_as_longlong(fabs(__ddiv_rn(__dmul_rn(a.h2, r), a.d)));
@@ -139,7 +157,7 @@ __global__ void __launch_bounds__(kDThreads, 1) dc_kernel(DcArgs a, LoopArgs la)
         }
         __syncthreads();
         if (s_stop) {
-            if ((n & 1) == 0) grid_copy(a.ub, a.u, (size_t)a.nx * (size_t)a.ny * sizeof(double));
+            if ((n & 1) == 0) grid_copy(a.ub, a.u, (size_t)a.nx * (size_t)a.ny * (size_t)a.nz * sizeof(double));
             return;
         }
     }
@@ -147,9 +165,9 @@ __global__ void __launch_bounds__(kDThreads, 1) dc_kernel(DcArgs a, LoopArgs la)
 
 }  // namespace
 
-size_t dc_workspace_bytes(long long nx, long long ny)
+size_t dc_workspace_bytes(long long nx, long long ny, long long nz)
 {
-    const size_t cells = (size_t)nx * (size_t)ny;
+    const size_t cells = (size_t)nx * (size_t)ny * (size_t)nz;
     return 3 * ((cells * 4 + 255) / 256 * 256);   // r32, e[0], e[1] (the FP64 buffer is the usual state buffer)
 }
 
@@ -159,13 +177,14 @@ cudaError_t dc_persistent(const Problem &p, LoopArgs la, int inner, void *fp32_a
     a.u = (double *)la.a;
     a.ub = (double *)la.b;
     a.f = (const double *)la.aux;
-    const size_t cells = (size_t)p.nx * (size_t)p.ny;
+    const size_t cells = (size_t)p.nx * (size_t)p.ny * (size_t)p.nz;
     const size_t blk = (cells * 4 + 255) / 256 * 256;
     a.r32 = (float *)fp32_area;
     a.e[0] = (float *)((unsigned char *)fp32_area + blk);
     a.e[1] = (float *)((unsigned char *)fp32_area + 2 * blk);
     a.nx = p.nx;
     a.ny = p.ny;
+    a.nz = p.nz;
     a.h2 = p.h2;
     a.d = p.d;
     a.h2f = p.h2f;
@@ -174,12 +193,13 @@ cudaError_t dc_persistent(const Problem &p, LoopArgs la, int inner, void *fp32_a
     int dev = 0, sms = 0, per_sm = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, dc_kernel, kDThreads, 0);
+    const void *kern = p.stencil == SLR_J3D7 ? (const void *)dc_kernel<3> : (const void *)dc_kernel<2>;
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kDThreads, 0);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorCooperativeLaunchTooLarge;
     la.nblocks = grid_ctas(sms, 1, la.nblocks);
     void *args[] = {&a, &la};
-    return cudaLaunchCooperativeKernel((const void *)dc_kernel, dim3(la.nblocks), dim3(kDThreads), args, 0, st);
+    return cudaLaunchCooperativeKernel(kern, dim3(la.nblocks), dim3(kDThreads), args, 0, st);
 }
 
 }  // namespace slr

@@ -398,9 +398,12 @@ __global__ void __launch_bounds__(kTThreads, 1) jacobi_tb_kernel(const __grid_co
     unsigned long long bar_target = 0;
     long long it = it0;
     int cur = 0;
+    __shared__ int s_kpn;                     // length of the next pass
+    if (tid == 0) s_kpn = tp.K;
+    __syncthreads();
     for (long long p = 0;; ++p) {
         const long long left = la.max_iters - it;
-        const int kp = (int)((long long)tp.K < left ? (long long)tp.K : left);
+        const int kp = (int)((long long)s_kpn < left ? (long long)s_kpn : left);
         if (!tb_pass<T, true>(tp, smem, bar, s_red, phase, cur, kp, la)) return;
         __syncthreads();
         if (tid < kp) {
@@ -425,7 +428,9 @@ __global__ void __launch_bounds__(kTThreads, 1) jacobi_tb_kernel(const __grid_co
             const int jlast = jstop >= 0 ? jstop : kp - 1;
             const double value = __shfl_sync(0xffffffffu, dj.value, jlast);
             const long long itn = it + jlast + 1;
+            const double v0 = __shfl_sync(0xffffffffu, dj.value, 0);
             if (tid == 0) {
+                s_kpn = predict_pass(v0, value, kp, la.tol, tp.K);
                 const int stop = jstop >= 0 || itn >= la.max_iters;
                 s_stop = stop;
                 s_rewind = jstop >= 0 && jstop + 1 < kp ? jstop + 1 : 0;

@@ -58,6 +58,7 @@ constexpr uint32_t kTxBytes = 2u * kPlane + kMaskBytes;               // what th
 static_assert(kPlane % 128 == 0 && kMaskBytes % 128 == 0, "TMA destinations stay 128-byte aligned");
 static_assert(kW * kH < (1 << 14), "a list entry keeps the position in 14 bits");
 static_assert(kK <= kMaxK, "per-sweep slots");
+static_assert((kW * kH) % kThreads == 0, "the listing loops run whole warps");
 
 struct RTb {
     CUtensorMap umap[2];       // state buffers A (caller's u) and B, box 80 x 80
@@ -127,13 +128,17 @@ __device__ bool rtb_pass(const RTb &tp, unsigned char *smem, uint64_t *bar, RTbS
         if (!__syncthreads_and(ok)) return false;
         // edges of the loaded region behind which the grid continues
         const bool top = Y0 > 0, bottom = Y0 + kH < tp.ny, left = X0 > 0, right = X0 + kW < tp.nx;
-        // list the noisy pixels by depth: count, place
+        // list the noisy pixels by depth: count, place (the lanes of a warp
+        // that share a depth add once, by their first lane)
+        const unsigned lt = (1u << lane) - 1u;
         for (int i = tid; i < kW * kH; i += kThreads) {
             const int ly = i / kW, lx = i - ly * kW;
             const int gy = Y0 + ly, gx = X0 + lx;
-            if (gy < 0 || gy >= tp.ny || gx < 0 || gx >= tp.nx || !M[ly * kMW + lx + (kMX - kK)]) continue;
+            const bool noisy = gy >= 0 && gy < tp.ny && gx >= 0 && gx < tp.nx && M[ly * kMW + lx + (kMX - kK)];
             const int d = tile_depth(ly, lx, top, bottom, left, right);
-            if (d >= thr) atomicAdd(&sh.cnt[d], 1);
+            const bool listed = noisy && d >= thr;
+            const unsigned peers = __match_any_sync(0xffffffffu, listed ? d : -1);
+            if (listed && (peers & lt) == 0u) atomicAdd(&sh.cnt[d], __popc(peers));
         }
         __syncthreads();
         if (tid == 0) {
@@ -149,13 +154,22 @@ __device__ bool rtb_pass(const RTb &tp, unsigned char *smem, uint64_t *bar, RTbS
         for (int i = tid; i < kW * kH; i += kThreads) {
             const int ly = i / kW, lx = i - ly * kW;
             const int gy = Y0 + ly, gx = X0 + lx;
-            if (gy < 0 || gy >= tp.ny || gx < 0 || gx >= tp.nx || !M[ly * kMW + lx + (kMX - kK)]) continue;
+            const bool noisy = gy >= 0 && gy < tp.ny && gx >= 0 && gx < tp.nx && M[ly * kMW + lx + (kMX - kK)];
             const int d = tile_depth(ly, lx, top, bottom, left, right);
-            if (d < thr) continue;
-            const bool own = ly >= kK && ly < kK + kOwn && lx >= kK && lx < kK + kOwn;
+            const bool listed = noisy && d >= thr;
+            const unsigned peers = __match_any_sync(0xffffffffu, listed ? d : -1);
+            const int first = __ffs(peers) - 1;
+            int base = 0;
+            if (listed && lane == first) base = atomicAdd(&sh.next[d], __popc(peers));
+            base = __shfl_sync(0xffffffffu, base, first);
+            const bool own = listed && ly >= kK && ly < kK + kOwn && lx >= kK && lx < kK + kOwn;
             const bool border = gy == 0 || gy == tp.ny - 1 || gx == 0 || gx == tp.nx - 1;
-            L[atomicAdd(&sh.next[d], 1)] = (unsigned short)(i | (own ? 1 << 14 : 0) | (border ? 1 << 15 : 0));
-            if (REDUCE && own) atomicAdd(&sh.owned, 1u);
+            if (listed)
+                L[base + __popc(peers & lt)] = (unsigned short)(i | (own ? 1 << 14 : 0) | (border ? 1 << 15 : 0));
+            if (REDUCE) {
+                const unsigned owners = __ballot_sync(0xffffffffu, own);
+                if (lane == 0 && owners) atomicAdd(&sh.owned, (unsigned)__popc(owners));
+            }
         }
         __syncthreads();
         for (int s = 1; s <= kp; ++s) {
@@ -228,9 +242,12 @@ __global__ void __launch_bounds__(kThreads, 3) restore_tb_kernel(const __grid_co
     unsigned long long bar_target = 0;
     long long it = it0;
     int cur = 0;
+    __shared__ int s_kpn;                     // length of the next pass
+    if (tid == 0) s_kpn = tp.K;
+    __syncthreads();
     for (long long p = 0;; ++p) {
         const long long left = la.max_iters - it;
-        const int kp = (int)((long long)tp.K < left ? (long long)tp.K : left);
+        const int kp = (int)((long long)s_kpn < left ? (long long)s_kpn : left);
         if (!rtb_pass<FAST, true>(tp, smem, bar, sh, phase, cur, kp, la)) return;
         __syncthreads();
         if (tid < kp) {
@@ -259,7 +276,9 @@ __global__ void __launch_bounds__(kThreads, 3) restore_tb_kernel(const __grid_co
             const unsigned long long count = __shfl_sync(0xffffffffu, dj.count, jlast);
             const int changed = __shfl_sync(0xffffffffu, dj.changed, jlast);
             const long long itn = it + jlast + 1;
+            const double v0 = __shfl_sync(0xffffffffu, dj.value, 0);
             if (tid == 0) {
+                s_kpn = predict_pass(v0, value, kp, la.tol, tp.K);
                 const int stop = jstop >= 0 || itn >= la.max_iters;
                 s_stop = stop;
                 s_rewind = jstop >= 0 && jstop + 1 < kp ? jstop + 1 : 0;

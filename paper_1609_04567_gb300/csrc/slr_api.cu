@@ -93,10 +93,10 @@ std::string check_desc(const slr_desc *d, bool *unsupported)
         break;
     }
     if (d->defect_correction) {
-        if (d->stencil != SLR_J2D5 || d->storage != SLR_F64 || d->boundary != SLR_DIRICHLET || d->ghost != 0.0 ||
-            d->loop == SLR_LOOP_HOST) {
+        if ((d->stencil != SLR_J2D5 && d->stencil != SLR_J3D7) || d->storage != SLR_F64 ||
+            d->boundary != SLR_DIRICHLET || d->ghost != 0.0 || d->loop == SLR_LOOP_HOST) {
             *unsupported = true;
-            return "defect correction runs SLR_J2D5 in F64 with ghost 0 on the persistent loop";
+            return "defect correction runs SLR_J2D5 or SLR_J3D7 in F64 with ghost 0 on the persistent loop";
         }
         if (d->inner_sweeps < 0) return "inner_sweeps must be >= 0";
     }
@@ -334,7 +334,7 @@ size_t slr_workspace_size(const slr_desc *d)
     const Problem p = make_problem(d);
     size_t bytes = slr::kCtlBytes + round_up(p.state_bytes, 256);
     if (p.stencil == SLR_LIFE) bytes += 2 * round_up(slr::life_tb_bits_bytes(p.nx, p.ny), 256);
-    if (d->defect_correction) bytes += slr::dc_workspace_bytes(p.nx, p.ny);
+    if (d->defect_correction) bytes += slr::dc_workspace_bytes(p.nx, p.ny, p.nz);
     return bytes;
 }
 

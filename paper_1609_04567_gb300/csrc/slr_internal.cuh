@@ -210,6 +210,23 @@ __host__ __device__ __forceinline__ Decision decide(int reduce, const Slot &s, d
     return d;
 }
 
+// Sweeps of the next pass of a temporal-blocked loop (at most K): where the
+// last pass's reduced values (v0 after its first sweep, v1 after its last of
+// kp), decaying geometrically, predict the first value below tol, so that a
+// stop seldom falls inside a pass and costs a rerun of it; K when the values
+// do not decay or the prediction lies K or more sweeps ahead.  Only the
+// speed depends on it: a stop inside a pass still reruns that pass.  Every
+// CTA computes it from the same values and gets the same pass length.
+__device__ __forceinline__ int predict_pass(double v0, double v1, int kp, double tol, int K)
+{
+    if (kp < 2 || !(tol > 0.0) || !(v1 > 0.0) || !(v1 < v0) || !(v1 >= tol)) return K;
+    const double lr = log(v1 / v0) / (double)(kp - 1);   // log of the per-sweep ratio, < 0
+    const double need = log(tol / v1) / lr;              // sweeps past the pass's last one
+    if (!(need < (double)(K - 1))) return K;
+    const int n = (int)floor(need) + 1;
+    return n < 1 ? 1 : n;
+}
+
 // Arguments of every loop launch.
 struct LoopArgs {
     void *a;                 // state buffer A (the caller's u)
@@ -368,8 +385,8 @@ cudaError_t restore_tb_persistent(const Problem &p, LoopArgs la, cudaStream_t st
 // Whether the TMA-tiled restoration sweep accepts p (nx % 16 == 0).
 bool restore_tma_ok(const Problem &p);
 cudaError_t restore_sweep(const Problem &p, const void *src, void *dst, const void *mask, cudaStream_t st);
-// FP64 defect correction around FP32 Jacobi inner solves (dc.cu).
-size_t dc_workspace_bytes(long long nx, long long ny);
+// FP64 defect correction around FP32 Jacobi inner solves, 2D and 3D (dc.cu).
+size_t dc_workspace_bytes(long long nx, long long ny, long long nz);
 cudaError_t dc_persistent(const Problem &p, LoopArgs la, int inner, void *fp32_area, cudaStream_t st);
 // The separate reduce kernel of the host-driven loop: delta between two
 // states (and the mask), reduced into *slot.

@@ -84,7 +84,7 @@ EXPORTS = ["slr_desc_init", "slr_workspace_size", "slr_create", "slr_run_until",
            "slr_tune_last_error", "slr_check_exact_math", "slr_check_exact_division", "slr_detect_noise",
            "slr_state_to_frame", "slr_sobel", "slr_check_exact_isqrt", "slr_user_workspace_size",
            "slr_user_create", "slr_user_run_until", "slr_user_reduce_value", "slr_user_destroy",
-           "slr_user_last_error", "slr_block_sweep"]
+           "slr_user_last_error", "slr_block_sweep", "slr_measure_logic_rate"]
 SLR_STATIC_STATE_BYTES = 4 << 20
 
 _lib = None
@@ -191,6 +191,8 @@ def load(path: str = LIB_PATH):
     lib.slr_user_last_error.restype = ctypes.c_char_p
     lib.slr_block_sweep.argtypes = [D, ctypes.POINTER(slr_block), P, P, P, P, P]
     lib.slr_block_sweep.restype = i32
+    lib.slr_measure_logic_rate.argtypes = [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double), P]
+    lib.slr_measure_logic_rate.restype = i32
     _lib = lib
     return lib
 
@@ -244,6 +246,15 @@ def slr_last_error(h) -> str:
 
 def slr_version() -> str:
     return load().slr_version().decode()
+
+
+def slr_measure_logic_rate(stream: int = 0):
+    """Measured logic-pipe throughput: (thread logic operations per second, kernel ms)."""
+    r, t = ctypes.c_double(), ctypes.c_double()
+    st = load().slr_measure_logic_rate(ctypes.byref(r), ctypes.byref(t), stream or None)
+    if st != SLR_OK:
+        raise SlrError(st, "logic-rate kernel failed")
+    return r.value, t.value
 
 
 def slr_block_sweep(d: slr_desc, b: slr_block, src_ptr: int, dst_ptr: int, aux_ptr: int, partial_ptr: int,

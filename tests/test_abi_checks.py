@@ -178,7 +178,8 @@ NAN = float("nan")
     ("J2D5", (8, 8, 1), dict(defect_correction=1, ghost=1.0), True, "defect correction"),
     ("J2D5", (8, 8, 1), dict(defect_correction=1, boundary=1), True, "defect correction"),
     ("J2D5", (8, 8, 1), dict(defect_correction=1, loop=1), True, "defect correction"),
-    ("J3D7", (8, 8, 8), dict(defect_correction=1), True, "defect correction"),
+    ("J3D7", (8, 8, 8), dict(defect_correction=1, storage=3), True, "defect correction"),
+    ("LIFE", (64, 8, 1), dict(defect_correction=1), True, "defect correction"),
     ("J2D5", (8, 8, 1), dict(defect_correction=1, inner_sweeps=-1), False, "inner_sweeps"),
     ("J3D7", (8192, 8192, 1024), {}, False, "larger than device memory"),
 ])
@@ -202,6 +203,10 @@ def test_defaults_of_every_stencil_pass_the_rules(slr):
         assert slr.slr_workspace_size(slr.slr_desc_init(s, *ext)) > 0
     # and the defect correction's own defaults
     assert slr.slr_workspace_size(slr.slr_desc_init(slr.SLR_J2D5, 8, 8, 1, defect_correction=1)) > 0
+    # 3D: the binary64 state buffer plus three binary32 buffers (r32, two e) of 6 x 7 x 8 cells
+    plain3 = slr.slr_workspace_size(slr.slr_desc_init(slr.SLR_J3D7, 8, 7, 6))
+    assert slr.slr_workspace_size(slr.slr_desc_init(slr.SLR_J3D7, 8, 7, 6, defect_correction=1)) == \
+        plain3 + 3 * (-(-6 * 7 * 8 * 4 // 256) * 256)
 
 
 def test_block_sweep_refuses_bad_ranges_before_any_device_work(slr):

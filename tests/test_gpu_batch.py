@@ -34,6 +34,10 @@ def restore_instance(ny, nx, seed, **kw):
 
 def oracle_of(orc, inst, cap):
     kw = dict(inst["kw"])
+    if kw.pop("defect_correction", 0):
+        fn = orc.j3d7_dc if len(inst["shape"]) == 3 else orc.j2d5_dc
+        k_in = kw.pop("inner_sweeps", 50)
+        return fn(np.zeros(inst["shape"]), inst["f_oracle"], k_in=k_in, max_outer=cap, **kw)
     if inst["kind"] == "r":
         out, r = orc.restore8(inst["frame"].astype(np.float32), inst["mask"], tol=kw.get("tol", 1e-3), max_iters=cap)
         return out, r
@@ -144,4 +148,64 @@ def test_batch_rejects_life_and_full_batches(gpu):
     with pytest.raises(gpu.SlrError) as e:
         add(gpu, b, inst2, 10)
     assert e.value.status == gpu.SLR_ERR_WORKSPACE
+    b.close()
+
+
+def dc_instances():
+    return [
+        (jacobi_instance((40, 36), "f64", 41, tol=1e-10, defect_correction=1, inner_sweeps=12), 5000),
+        (jacobi_instance((7, 9, 11), "f64", 42, tol=1e-10, defect_correction=1, inner_sweeps=8), 5000),
+        (jacobi_instance((96, 64), "f64", 43, tol=1e-10, defect_correction=1, inner_sweeps=25), 3),   # capped
+        (jacobi_instance((1, 1), "f64", 44, tol=1e-12, defect_correction=1, inner_sweeps=3), 100),
+    ]
+
+
+def test_defect_correction_instances_in_a_mixed_batch(gpu, orc):
+    # FP64 defect correction around binary32 inner sweeps, 2D and 3D, next to
+    # plain Jacobi and restoration instances: each equals the oracle's defect
+    # correction bit for bit (state, corrections, scaled defect) and its solo run
+    b = gpu.Batch(64)
+    dcs = dc_instances()
+    mix = dcs + make_mix()[:4] + [(restore_instance(64, 80, 45), 5000)]
+    slots = [add(gpu, b, inst, cap) for inst, cap in mix]
+    b.run(100000)
+    finished, running = b.poll()
+    assert running == 0 and sorted(finished) == sorted(slots)
+    for (inst, cap), s in zip(mix, slots):
+        r = b.result(s)
+        ref, rr = oracle_of(orc, inst, cap)
+        got = state(inst)
+        assert (r.iters, r.converged, r.value) == (rr.iters, rr.converged, rr.value), (inst["kw"], r, rr)
+        assert np.array_equal(got.view(np.uint8), ref.astype(got.dtype).view(np.uint8)), inst["kw"]
+    b.close()
+    for inst, cap in dcs:
+        solo = jacobi_instance(inst["shape"], "f64", 0, **inst["kw"])
+        solo["aux"] = inst["aux"]
+        stencil = gpu.SLR_J3D7 if len(inst["shape"]) == 3 else gpu.SLR_J2D5
+        sv = gpu.Solver(stencil, solo["u"], solo["aux"], **inst["kw"])
+        sv.run(cap)
+        rs = sv.result(check=False)
+        sv.close()
+        assert torch.equal(solo["u"], inst["u"]) and rs.iters == oracle_of(orc, inst, cap)[1].iters
+
+
+def test_defect_correction_in_short_runs_while_others_join(gpu, orc):
+    # budgets that end between the phases of a correction: the phase count
+    # carries over to the next run
+    b = gpu.Batch(16)
+    items = dc_instances()[:2]
+    slots = {add(gpu, b, inst, cap): (inst, cap) for inst, cap in items}
+    b.run(5)
+    later = (jacobi_instance((30, 20), "f64", 46, tol=1e-10, defect_correction=1, inner_sweeps=7), 5000)
+    slots[add(gpu, b, *later)] = later
+    for _ in range(20000):
+        b.run(3)
+        _, running = b.poll()
+        if running == 0:
+            break
+    for s, (inst, cap) in slots.items():
+        r = b.result(s)
+        ref, rr = oracle_of(orc, inst, cap)
+        assert (r.iters, r.converged, r.value) == (rr.iters, rr.converged, rr.value)
+        assert np.array_equal(state(inst).view(np.uint64), ref.view(np.uint64))
     b.close()

@@ -49,3 +49,21 @@ def test_defect_correction_rejects_other_setups(gpu):
     with pytest.raises(gpu.SlrError) as e:
         gpu.Solver(gpu.SLR_J2D5, torch.zeros_like(f), f, defect_correction=1)
     assert e.value.status == gpu.SLR_ERR_UNSUPPORTED
+
+
+@pytest.mark.parametrize("shape,k_in,tol", [((6, 7, 8), 15, 1e-10), ((20, 24, 32), 30, 1e-10),
+                                            ((1, 1, 1), 4, 1e-12), ((9, 1, 13), 10, 1e-11)])
+def test_defect_correction_3d_matches_oracle(gpu, orc, shape, k_in, tol):
+    from paper_1609_04567_gb300 import inputs
+    f = inputs.helmholtz_rhs(shape, seed=33)
+    u = torch.zeros(shape, dtype=torch.float64, device="cuda")
+    s = gpu.Solver(gpu.SLR_J3D7, u, torch.from_numpy(f).cuda(), tol=tol, defect_correction=1, inner_sweeps=k_in)
+    s.run(100000)
+    r = s.result()
+    s.close()
+    ref, rr = orc.j3d7_dc(np.zeros(shape), f, tol=tol, k_in=k_in, max_outer=100000)
+    assert (r.iters, r.converged) == (rr.iters, rr.converged)
+    out = u.cpu().numpy()
+    assert np.array_equal(out.view(np.uint64), ref.view(np.uint64))
+    assert r.value == rr.value < tol
+    assert orc.j3d7_scaled_defect(out, f) < tol

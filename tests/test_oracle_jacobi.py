@@ -351,3 +351,64 @@ def test_defect_correction_steps(orc):
     # the scaled defect it reports is the change the next FP64 Jacobi sweep makes
     nxt, rj = orc.j2d5(u2, f, tol=0.0, max_iters=1)
     assert r2.value == pytest.approx(rj.value, rel=1e-9)
+
+
+def dense_helmholtz_3d(nz, ny, nx, h, sigma, f):
+    """Dense matrix of the 3D operator ((6 + sigma h^2) u - sum of 6 nbrs) / h^2, ghost 0."""
+    n = nx * ny * nz
+    A = np.zeros((n, n))
+    for k in range(nz):
+        for i in range(ny):
+            for j in range(nx):
+                r = (k * ny + i) * nx + j
+                A[r, r] += (6 + sigma * h * h) / (h * h)
+                for dk, di, dj in ((-1, 0, 0), (1, 0, 0), (0, -1, 0), (0, 1, 0), (0, 0, -1), (0, 0, 1)):
+                    z, y, x = k + dk, i + di, j + dj
+                    if 0 <= z < nz and 0 <= y < ny and 0 <= x < nx:
+                        A[r, (z * ny + y) * nx + x] -= 1.0 / (h * h)
+    return A, f.reshape(-1).astype(np.float64).copy()
+
+
+def test_defect_correction_3d_reaches_dense_solution(orc):
+    from paper_1609_04567_gb300 import inputs
+    nz, ny, nx = 5, 6, 7
+    f = inputs.helmholtz_rhs((nz, ny, nx), seed=15)
+    h = 1.0 / (nx + 1)
+    A, b = dense_helmholtz_3d(nz, ny, nx, h, 1.0, f)
+    exact = np.linalg.solve(A, b).reshape(nz, ny, nx)
+    u, r = orc.j3d7_dc(np.zeros((nz, ny, nx)), f, tol=1e-10, k_in=15)
+    assert r.converged and r.value < 1e-10
+    assert orc.j3d7_scaled_defect(u, f) == r.value
+    jac = np.eye(A.shape[0]) - A / np.diag(A)[:, None]
+    rho = np.max(np.abs(np.linalg.eigvals(jac)))
+    assert np.max(np.abs(u - exact)) <= 1e-10 / (1 - rho) * 1.01
+
+
+def test_scaled_defect_3d_of_zero_state(orc):
+    from paper_1609_04567_gb300 import inputs
+    f = inputs.helmholtz_rhs((4, 5, 6), seed=2)
+    h = 1.0 / 7
+    d = 6 + h * h
+    assert orc.j3d7_scaled_defect(np.zeros_like(f), f) == pytest.approx(h * h * np.max(np.abs(f)) / d, rel=1e-14)
+
+
+def test_defect_correction_3d_steps(orc):
+    # as the 2D steps: correction 1 from u = 0 is K binary32 3D sweeps of
+    # A e = f, widened, bit for bit; correction 2 adds K sweeps of A e = r1;
+    # the reported value is the change of the next FP64 3D Jacobi sweep
+    from paper_1609_04567_gb300 import inputs
+    nz, ny, nx, K = 4, 5, 6, 6
+    f = inputs.helmholtz_rhs((nz, ny, nx), seed=9)
+    z64, z32 = np.zeros((nz, ny, nx)), np.zeros((nz, ny, nx), dtype=np.float32)
+    u1, r1 = orc.j3d7_dc(z64, f, tol=0.0, k_in=K, max_outer=1)
+    s1, _ = orc.j3d7(z32, f.astype(np.float32), tol=0.0, max_iters=K, storage="f32")
+    assert np.array_equal(u1, s1.astype(np.float64))
+    assert r1.iters == 1 and r1.value == orc.j3d7_scaled_defect(u1, f)
+    h = 1.0 / (nx + 1)
+    A, b = dense_helmholtz_3d(nz, ny, nx, h, 1.0, f)
+    res1 = (b - A @ u1.reshape(-1)).reshape(nz, ny, nx)
+    e2, _ = orc.j3d7(z32, res1.astype(np.float32), tol=0.0, max_iters=K, storage="f32")
+    u2, r2 = orc.j3d7_dc(z64, f, tol=0.0, k_in=K, max_outer=2)
+    assert np.max(np.abs(u2 - (u1 + e2.astype(np.float64)))) <= 1e-6 * np.max(np.abs(e2))
+    _, rj = orc.j3d7(u2, f, tol=0.0, max_iters=1)
+    assert r2.value == pytest.approx(rj.value, rel=1e-9)

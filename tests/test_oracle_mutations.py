@@ -130,14 +130,16 @@ MUTATIONS = [
      "            double rv = f[i * nx + j] - au;",
      "            double rv = au - f[i * nx + j];"),
     ("defect correction resumes the inner solve from the last correction",
-     "        for (size_t c = 0; c < n; ++c) { r32[c] = (float)r[c]; e[c] = 0.0f; }",
-     "        for (size_t c = 0; c < n; ++c) { r32[c] = (float)r[c]; }"),
+     "        for (size_t c = 0; c < n; ++c) { r32[c] = (float)r[c]; e[c] = 0.0f; }\n"
+     "        for (int64_t s = 0; s < k_in; ++s) {\n#pragma omp parallel for schedule(static)",
+     "        for (size_t c = 0; c < n; ++c) { r32[c] = (float)r[c]; }\n"
+     "        for (int64_t s = 0; s < k_in; ++s) {\n#pragma omp parallel for schedule(static)"),
     ("defect correction inner solve on the binary64 defect's first sweep only",
      "                    float t = h2f * r32[i * nx + j];\n                    e2[i * nx + j] = (t + sn) / df;",
      "                    float t = s == 0 ? h2f * r32[i * nx + j] : 0.0f;\n                    e2[i * nx + j] = (t + sn) / df;"),
     ("defect correction subtracts the correction",
-     "        for (size_t c = 0; c < n; ++c) u[c] = u[c] + (double)e[c];",
-     "        for (size_t c = 0; c < n; ++c) u[c] = u[c] - (double)e[c];"),
+     "        for (size_t c = 0; c < n; ++c) u[c] = u[c] + (double)e[c];\n        rho = defect_f64(",
+     "        for (size_t c = 0; c < n; ++c) u[c] = u[c] - (double)e[c];\n        rho = defect_f64("),
     ("bfloat16 rounds half up instead of to even",
      "    if (rest > 0x8000u || (rest == 0x8000u && (keep & 1u)))\n        keep += 1u;",
      "    if (rest >= 0x8000u)\n        keep += 1u;"),
@@ -180,6 +182,14 @@ MUTATIONS = [
     ("Sobel copies the border",
      "                out[i * nx + j] = 0;\n                continue;",
      "                out[i * nx + j] = img[i * nx + j];\n                continue;"),
+    ("3D defect with the wrong sign of the neighbour sum",
+     "                double au = (d * u[c] - s) / h2;",
+     "                double au = (d * u[c] + s) / h2;"),
+    ("3D defect correction with the 2D diagonal",
+     "    double hh = mesh_h(h, nx), h2 = hh * hh, d = 6.0 + sigma * h2;\n    float h2f = (float)h2, df = (float)d;\n"
+     "    size_t n = (size_t)(nx * ny * nz);",
+     "    double hh = mesh_h(h, nx), h2 = hh * hh, d = 4.0 + sigma * h2;\n    float h2f = (float)h2, df = (float)d;\n"
+     "    size_t n = (size_t)(nx * ny * nz);"),
     ("binary16 subnormal shift off by one",
      "    int32_t shift = -(e + 1);                        /* >= 14 */",
      "    int32_t shift = -(e + 2);                        /* >= 14 */"),
