@@ -404,7 +404,7 @@ struct JacobiTma {
     __device__ __forceinline__ unsigned char *stages() const
     {
         extern __shared__ unsigned char smem_dyn[];
-        return (unsigned char *)(((uintptr_t)smem_dyn + 127) & ~(uintptr_t)127);
+        return align_up(smem_dyn, 128);
     }
     __device__ __forceinline__ const T *main_of(int s) const { return (const T *)(stages() + s * kStage); }
     __device__ __forceinline__ const T *side_of(int s, int i) const

@@ -376,7 +376,7 @@ __global__ void __launch_bounds__(kTThreads, 1) jacobi_tb_kernel(const __grid_co
 {
     extern __shared__ unsigned char smem_dyn[];
     using Sh = TbShape<T>;
-    unsigned char *smem = (unsigned char *)(((uintptr_t)smem_dyn + 127) & ~(uintptr_t)127);
+    unsigned char *smem = align_up(smem_dyn, 128);
     uint64_t *bar = (uint64_t *)(smem + 2 * Sh::kPlane);
     unsigned *s_red = (unsigned *)(bar + 2);
     __shared__ int s_stop, s_rewind;

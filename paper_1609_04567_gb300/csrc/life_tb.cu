@@ -336,7 +336,7 @@ template <bool WRAP>
 __global__ void __launch_bounds__(kThreads, 1) life_tb_kernel(const __grid_constant__ TbParams tp, LoopArgs la)
 {
     extern __shared__ unsigned char smem_raw[];
-    unsigned char *base = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    unsigned char *base = align_up(smem_raw, 1024);
     unsigned char *stage = base;                                   // [2][kStageBytes]
     uint32_t *xch = (uint32_t *)(base + 2 * kStageBytes);          // [2][8][2][36]
     uint64_t *mbar = (uint64_t *)(xch + kXchWords);                // [2]

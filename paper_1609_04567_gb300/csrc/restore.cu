@@ -131,7 +131,7 @@ struct RestoreTma {
     __device__ __forceinline__ unsigned char *stages() const
     {
         extern __shared__ unsigned char smem_dyn[];
-        return (unsigned char *)(((uintptr_t)smem_dyn + 127) & ~(uintptr_t)127);
+        return align_up(smem_dyn, 128);
     }
     __device__ __forceinline__ uint64_t *bars() const { return (uint64_t *)(stages() + kNS * kStage); }
     __device__ __forceinline__ unsigned *done() const { return (unsigned *)(bars() + kNS); }

@@ -67,6 +67,33 @@ __device__ __forceinline__ float restore_interior(const float *C, int P, float a
     return restore_quotient<FAST>(num, den, uc);
 }
 
+// EXACT new value of a pixel all of whose 8 neighbours lie in the grid, for
+// states known to stay in range: alpha in [2^-100, 2^124) and every |u| below
+// 2^61, so that every t = u - u_j has |t| < 2^62 and every x = alpha + t*t lies
+// in [2^-100, 2^126), the weights' fast route, with no check per weight.  The
+// same operations in the same order as restore_interior<false>.
+__device__ __forceinline__ float restore_interior_in_range(const float *C, int P, float alpha)
+{
+    const float uc = *C;
+    float2 nd = make_float2(0.0f, 0.0f);
+#pragma unroll
+    for (int k = 0; k < 8; k += 2) {
+        const int k0 = k < 4 ? k : k + 1, k1 = k + 1 < 4 ? k + 1 : k + 2;
+        const float u0 = C[(k0 / 3 - 1) * P + k0 % 3 - 1];
+        const float u1 = C[(k1 / 3 - 1) * P + k1 % 3 - 1];
+        const float2 w = weights_rn2_in_range(uc, u0, u1, alpha);
+        nd = __fadd2_rn(nd, make_float2(__fmul_rn(w.x, u0), w.x));
+        nd = __fadd2_rn(nd, make_float2(__fmul_rn(w.y, u1), w.y));
+    }
+    return restore_quotient<false>(nd.x, nd.y, uc);
+}
+
+// Whether alpha lets restore_interior_in_range run (states below 2^61 in magnitude).
+__host__ __device__ __forceinline__ bool restore_alpha_in_range(float alpha)
+{
+    return alpha >= 0x1p-100f && alpha < 0x1p124f;
+}
+
 // New value of a pixel on the grid's border: the neighbours outside the grid
 // (up: the row above exists, and so on) are left out of both sums.
 template <bool FAST>

@@ -68,6 +68,7 @@ struct RTb {
     int tiles_x, tiles_y;
     int K;                     // sweeps per pass
     float alpha;
+    int alpha_in_range;        // restore_alpha_in_range(alpha)
 };
 
 // Per-CTA bookkeeping in static shared memory.
@@ -76,6 +77,7 @@ struct RTbShared {
     int next[kK + 1];                   // placement cursor per depth
     int nge[kK + 2];                    // listed pixels of depth >= d
     unsigned owned;                     // owned noisy pixels of the tile
+    int tile;                           // the tile this CTA works on
     unsigned long long sum[kK];         // per-sweep sum over the CTA's tiles
     unsigned long long own_total;       // owned noisy pixels over the CTA's tiles
 };
@@ -97,12 +99,14 @@ __device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long v)
     return v;
 }
 
-// One pass: every tile of this CTA, kp sweeps each, from buf[cur] to
-// buf[cur ^ 1].  With REDUCE the per-sweep sums go to sh.sum and the owned
-// noisy pixels to sh.own_total.  False if a TMA wait ran out.
+// One pass: kp sweeps of every tile, from buf[cur] to buf[cur ^ 1]; the
+// CTAs take tiles from the counter *next as they finish the previous one, so
+// tiles with more noisy pixels even out.  With REDUCE the per-sweep sums go
+// to sh.sum and the owned noisy pixels to sh.own_total.  False if a TMA wait
+// ran out.
 template <bool FAST, bool REDUCE>
 __device__ bool rtb_pass(const RTb &tp, unsigned char *smem, uint64_t *bar, RTbShared &sh, unsigned &phase, int cur,
-                         int kp, const LoopArgs &la)
+                         int kp, const LoopArgs &la, unsigned int *next)
 {
     float *S0 = (float *)smem;
     float *S1 = (float *)(smem + kPlane);
@@ -112,7 +116,11 @@ __device__ bool rtb_pass(const RTb &tp, unsigned char *smem, uint64_t *bar, RTbS
     const int tid = threadIdx.x, lane = tid & 31;
     const int ntiles = tp.tiles_x * tp.tiles_y;
     const int thr = kK + 1 - kp;                 // depth the first sweep needs
-    for (int t = (int)blockIdx.x; t < ntiles; t += (int)gridDim.x) {
+    for (;;) {
+        if (tid == 0) sh.tile = (int)atomicAdd(next, 1u);
+        __syncthreads();
+        const int t = sh.tile;
+        if (t >= ntiles) break;
         const int x0 = (t % tp.tiles_x) * kOwn, y0 = (t / tp.tiles_x) * kOwn;
         const int X0 = x0 - kK, Y0 = y0 - kK;    // origin of the loaded region in the grid
         if (tid == 0) {
@@ -130,7 +138,11 @@ __device__ bool rtb_pass(const RTb &tp, unsigned char *smem, uint64_t *bar, RTbS
         const bool top = Y0 > 0, bottom = Y0 + kH < tp.ny, left = X0 > 0, right = X0 + kW < tp.nx;
         // list the noisy pixels by depth: count, place (the lanes of a warp
         // that share a depth add once, by their first lane)
+        // and check that every loaded value is below 2^60 in magnitude: the
+        // pass's weighted means then stay below 2^61 and the weights can skip
+        // their range checks (restore_interior_in_range)
         const unsigned lt = (1u << lane) - 1u;
+        bool small = true;
         for (int i = tid; i < kW * kH; i += kThreads) {
             const int ly = i / kW, lx = i - ly * kW;
             const int gy = Y0 + ly, gx = X0 + lx;
@@ -139,8 +151,9 @@ __device__ bool rtb_pass(const RTb &tp, unsigned char *smem, uint64_t *bar, RTbS
             const bool listed = noisy && d >= thr;
             const unsigned peers = __match_any_sync(0xffffffffu, listed ? d : -1);
             if (listed && (peers & lt) == 0u) atomicAdd(&sh.cnt[d], __popc(peers));
+            small = small && fabsf(S0[i]) < 0x1p60f;           // false for a NaN
         }
-        __syncthreads();
+        const bool in_range = __syncthreads_and(small) && tp.alpha_in_range;
         if (tid == 0) {
             int pos = 0;
             sh.nge[kK + 1] = 0;
@@ -185,6 +198,8 @@ __device__ bool rtb_pass(const RTb &tp, unsigned char *smem, uint64_t *bar, RTbS
                 if (ent & 0x8000u) {
                     const int gy = Y0 + pos / kW, gx = X0 + pos % kW;
                     nv = restore_border<FAST>(C, kW, tp.alpha, gy > 0, gy + 1 < tp.ny, gx > 0, gx + 1 < tp.nx);
+                } else if (!FAST && in_range) {
+                    nv = restore_interior_in_range(C, kW, tp.alpha);
                 } else {
                     nv = restore_interior<FAST>(C, kW, tp.alpha);
                 }
@@ -219,7 +234,7 @@ template <bool FAST>
 __global__ void __launch_bounds__(kThreads, 3) restore_tb_kernel(const __grid_constant__ RTb tp, LoopArgs la)
 {
     extern __shared__ unsigned char smem_dyn[];
-    unsigned char *smem = (unsigned char *)(((uintptr_t)smem_dyn + 127) & ~(uintptr_t)127);
+    unsigned char *smem = align_up(smem_dyn, 128);
     uint64_t *bar = (uint64_t *)(smem + 2 * kPlane + kMaskBytes + kListBytes);
     __shared__ RTbShared sh;
     __shared__ int s_stop, s_rewind;
@@ -248,7 +263,7 @@ __global__ void __launch_bounds__(kThreads, 3) restore_tb_kernel(const __grid_co
     for (long long p = 0;; ++p) {
         const long long left = la.max_iters - it;
         const int kp = (int)((long long)s_kpn < left ? (long long)s_kpn : left);
-        if (!rtb_pass<FAST, true>(tp, smem, bar, sh, phase, cur, kp, la)) return;
+        if (!rtb_pass<FAST, true>(tp, smem, bar, sh, phase, cur, kp, la, &ctl->next_tile[p % kSlots])) return;
         __syncthreads();
         if (tid < kp) {
             Slot *sl = &ctl->sub[p % kSlots][tid];
@@ -261,7 +276,10 @@ __global__ void __launch_bounds__(kThreads, 3) restore_tb_kernel(const __grid_co
         bar_target += (unsigned long long)la.nblocks;
         if (!grid_barrier(ctl, bar_target, la.limit_ns)) return;
         if (tid < 32) {
-            if (blockIdx.x == 0) zero_slot(&ctl->sub[(p + 2) % kSlots][tid]);
+            if (blockIdx.x == 0) {
+                zero_slot(&ctl->sub[(p + 2) % kSlots][tid]);
+                if (tid == 0) ctl->next_tile[(p + 2) % kSlots] = 0u;
+            }
             // lane j decides sweep j of the pass; the first one below tol stops
             Slot sl;
             sl.maxbits = 0ull;
@@ -298,7 +316,9 @@ __global__ void __launch_bounds__(kThreads, 3) restore_tb_kernel(const __grid_co
             if (s_rewind) {
                 // the pass again from its input, up to the stopping sweep
                 if (tid == 0) tma::fence_proxy_async_global();
-                if (!rtb_pass<FAST, false>(tp, smem, bar, sh, phase, cur, s_rewind, la)) return;
+                if (!rtb_pass<FAST, false>(tp, smem, bar, sh, phase, cur, s_rewind, la,
+                                           &ctl->next_tile[(p + 1) % kSlots]))
+                    return;
                 bar_target += (unsigned long long)la.nblocks;
                 if (!grid_barrier(ctl, bar_target, la.limit_ns)) return;
             }
@@ -327,6 +347,7 @@ cudaError_t run_rtb(const Problem &p, LoopArgs la, int K, cudaStream_t st)
     tp.tiles_y = (int)((p.ny + kOwn - 1) / kOwn);
     tp.K = K;
     tp.alpha = p.alpha;
+    tp.alpha_in_range = restore_alpha_in_range(p.alpha);
     auto kern = restore_tb_kernel<FAST>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem);
     if (e != cudaSuccess) return e;

@@ -160,6 +160,7 @@ slr_status run_persistent(slr_handle h, int64_t max_iters)
     cudaError_t e = cudaMemsetAsync(&ctl->bar, 0, sizeof(ctl->bar), h->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(&ctl->slot[0], 0, 2 * sizeof(Slot), h->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(&ctl->sub[0][0], 0, 2 * sizeof(ctl->sub[0]), h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(&ctl->next_tile[0], 0, 2 * sizeof(ctl->next_tile[0]), h->stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "reset loop state");
     slr::LoopArgs la;
     la.a = h->u;

@@ -57,10 +57,23 @@ struct Ctl {
     int pad;
     Slot slot[kSlots];
     Slot sub[kSlots][kMaxK];      // per-sub-step slots of temporal-blocked passes
+    unsigned int next_tile[kSlots];   // tiles handed out in a pass (dynamically scheduled passes)
+    unsigned int pad2;
 };
 
 constexpr size_t kCtlBytes = 4096;            // Ctl padded; state buffer B follows
 static_assert(sizeof(Ctl) <= kCtlBytes, "control block too large");
+
+// p advanced to the next multiple of `align` bytes (a power of two) by pointer
+// arithmetic on p itself, so that a pointer into shared memory stays one: a
+// round trip through an integer would leave the compiler a generic pointer
+// and turn every access through it into a generic load or store.
+template <class T>
+__device__ __forceinline__ T *align_up(T *p, uintptr_t align)
+{
+    const uintptr_t off = (align - ((uintptr_t)p & (align - 1))) & (align - 1);
+    return (T *)((unsigned char *)p + off);
+}
 
 __device__ __forceinline__ long long global_timer_ns()
 {

@@ -129,3 +129,22 @@ def test_exact_weight_arithmetic_matches_ieee_for_every_input(gpu):
     mismatches, checked = gpu.slr_check_exact_math()
     assert checked == 1 << 31
     assert mismatches == [0, 0, 0]
+
+
+@pytest.mark.parametrize("scale,alpha", [(2.0 ** 55, 100.0), (1.0, 1e-35), (2.0 ** -70, 1e-30)])
+def test_temporal_blocked_outside_the_unchecked_range(gpu, orc, scale, alpha):
+    # states above 2^60 in magnitude (some tiles take the weights' checked
+    # route), an alpha below 2^-100 (every tile does), tiny states: still bit
+    # for bit the oracle
+    from paper_1609_04567_gb300 import inputs
+    frame, _ = inputs.noisy_frame(150, 208, seed=12)
+    mask = inputs.noise_mask(frame)
+    u0 = (frame.astype(np.float64) * scale).astype(np.float32)
+    u = torch.from_numpy(u0).cuda()
+    s = gpu.Solver(gpu.SLR_RESTORE8, u, torch.from_numpy(mask).cuda(), tol=0.0, alpha=alpha, temporal_k=8)
+    s.run(12)
+    r = s.result(check=False)
+    s.close()
+    ref, rr = orc.restore8(u0, mask, alpha=alpha, tol=0.0, max_iters=12)
+    assert (r.iters, r.value, r.count) == (rr.iters, rr.value, rr.count)
+    assert np.array_equal(u.cpu().numpy().view(np.uint32), ref.view(np.uint32))
