@@ -167,8 +167,11 @@ typedef enum {
  * h = 1/(nx+1), alpha 100, AUTO loop, EXACT math. */
 void slr_desc_init(slr_desc *d, int32_t stencil, int64_t nx, int64_t ny, int64_t nz);
 
-/* Bytes of device workspace a handle for *d needs (second state buffer,
- * reduce slots, control block).  Returns 0 for an invalid descriptor. */
+/* Bytes of device workspace a handle for *d needs (control block, second
+ * state buffer; Life: two bit-packed buffers; defect correction: three binary32
+ * buffers; SLR_RESTORE8 with nx a multiple of 16: one 12,352-byte record per
+ * 64 x 64 tile, the tile's noisy-pixel list built in a run's first pass and
+ * read by its later ones).  Returns 0 for an invalid descriptor. */
 size_t slr_workspace_size(const slr_desc *d);
 
 /* Create a handle (constructor of Sec. 3.2: elemental function, combinator

@@ -300,9 +300,9 @@ bool tma_ok(const Problem &p) { return p.nx % 16 == 0 && p.nx < (1ll << 31) && p
 
 bool restore_tma_ok(const Problem &p) { return tma_ok(p); }
 
-cudaError_t restore_persistent(const Problem &p, LoopArgs la, cudaStream_t st)
+cudaError_t restore_persistent(const Problem &p, LoopArgs la, void *lists, cudaStream_t st)
 {
-    if (restore_tb_resolve_k(p, la.a, la.b, la.aux) > 1) return restore_tb_persistent(p, la, st);
+    if (restore_tb_resolve_k(p, la.a, la.b, la.aux) > 1) return restore_tb_persistent(p, la, lists, st);
     if (p.tiling != SLR_TILING_NONE && tma_ok(p))
         return p.math == SLR_MATH_FAST ? launch_tma<true>(p, la, st) : launch_tma<false>(p, la, st);
     if (p.math == SLR_MATH_FAST) {

@@ -25,6 +25,12 @@
 // After kp sweeps the 64 x 64 owned pixels go to the other state buffer in
 // global memory with 16-byte stores.
 //
+// Lists across passes.  The mask does not change, so a tile's list does not
+// either: the first pass of a launch lists every noisy pixel of depth >= 1
+// and stores the list, its per-depth counts and its owned count in the
+// workspace (one fixed-size record per tile); later passes read the record
+// while the state arrives, and load no mask.
+//
 // Reduce and decision.  Each sweep's sum of truncated |delta| over the owned
 // noisy pixels goes to a per-sweep slot (warp, then CTA in shared memory,
 // then one 64-bit atomic per CTA and sweep), with the count of owned noisy
@@ -59,6 +65,10 @@ static_assert(kPlane % 128 == 0 && kMaskBytes % 128 == 0, "TMA destinations stay
 static_assert(kW * kH < (1 << 14), "a list entry keeps the position in 14 bits");
 static_assert(kK <= kMaxK, "per-sweep slots");
 static_assert((kW * kH) % kThreads == 0, "the listing loops run whole warps");
+// a tile's stored list: counts (nge[0 .. kK + 1], owned) in 64 bytes, then the entries
+constexpr int kRecHead = 64;
+constexpr size_t kRecBytes = kRecHead + (size_t)kListBytes;
+static_assert(kListBytes % 16 == 0 && (kK + 3) * 4 <= kRecHead, "record layout");
 
 struct RTb {
     CUtensorMap umap[2];       // state buffers A (caller's u) and B, box 80 x 80
@@ -69,6 +79,7 @@ struct RTb {
     int K;                     // sweeps per pass
     float alpha;
     int alpha_in_range;        // restore_alpha_in_range(alpha)
+    unsigned char *lists;      // one kRecBytes record per tile (workspace)
 };
 
 // Per-CTA bookkeeping in static shared memory.
@@ -106,7 +117,7 @@ __device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long v)
 // ran out.
 template <bool FAST, bool REDUCE>
 __device__ bool rtb_pass(const RTb &tp, unsigned char *smem, uint64_t *bar, RTbShared &sh, unsigned &phase, int cur,
-                         int kp, const LoopArgs &la, unsigned int *next)
+                         int kp, const LoopArgs &la, unsigned int *next, bool cached)
 {
     float *S0 = (float *)smem;
     float *S1 = (float *)(smem + kPlane);
@@ -115,7 +126,6 @@ __device__ bool rtb_pass(const RTb &tp, unsigned char *smem, uint64_t *bar, RTbS
     float *dst = tp.buf[cur ^ 1];
     const int tid = threadIdx.x, lane = tid & 31;
     const int ntiles = tp.tiles_x * tp.tiles_y;
-    const int thr = kK + 1 - kp;                 // depth the first sweep needs
     for (;;) {
         if (tid == 0) sh.tile = (int)atomicAdd(next, 1u);
         __syncthreads();
@@ -123,19 +133,33 @@ __device__ bool rtb_pass(const RTb &tp, unsigned char *smem, uint64_t *bar, RTbS
         if (t >= ntiles) break;
         const int x0 = (t % tp.tiles_x) * kOwn, y0 = (t / tp.tiles_x) * kOwn;
         const int X0 = x0 - kK, Y0 = y0 - kK;    // origin of the loaded region in the grid
+        unsigned char *rec = tp.lists + (size_t)t * kRecBytes;
         if (tid == 0) {
-            tma::mbar_expect_tx(bar, kTxBytes);
+            tma::mbar_expect_tx(bar, cached ? 2u * kPlane : kTxBytes);
             tma::load_2d(S0, &tp.umap[cur], X0, Y0, bar);
             tma::load_2d(S1, &tp.umap[cur], X0, Y0, bar);
-            tma::load_2d((void *)M, &tp.mmap, x0 - kMX, Y0, bar);
+            if (!cached) tma::load_2d((void *)M, &tp.mmap, x0 - kMX, Y0, bar);
         }
-        if (tid <= kK) sh.cnt[tid] = 0;
-        if (tid == 0) sh.owned = 0u;
+        if (cached) {
+            // the stored record, read while the state arrives
+            const int *head = (const int *)rec;
+            if (tid < kK + 2) sh.nge[tid] = __ldcg(head + tid);
+            if (tid == kK + 2) sh.owned = (unsigned)__ldcg(head + kK + 2);
+            const int n = __ldcg(head + 1);
+            const uint4 *src = (const uint4 *)(rec + kRecHead);
+            for (int i = tid; i < (2 * n + 15) / 16; i += kThreads) ((uint4 *)L)[i] = __ldcg(src + i);
+        } else {
+            if (tid <= kK) sh.cnt[tid] = 0;
+            if (tid == 0) sh.owned = 0u;
+        }
         const bool ok = tma::bounded_wait(bar, phase & 1u, tma::kLoadWaitNs, &la.ctl->err);
         ++phase;
         if (!__syncthreads_and(ok)) return false;
-        // edges of the loaded region behind which the grid continues
+        // edges of the loaded region behind which the grid continues; a
+        // tile that reaches none of the grid's borders has all its pixels'
+        // neighbours in the grid
         const bool top = Y0 > 0, bottom = Y0 + kH < tp.ny, left = X0 > 0, right = X0 + kW < tp.nx;
+        const bool edge_tile = !(top && bottom && left && right);
         // list the noisy pixels by depth: count, place (the lanes of a warp
         // that share a depth add once, by their first lane)
         // and check that every loaded value is below 2^60 in magnitude: the
@@ -143,25 +167,31 @@ __device__ bool rtb_pass(const RTb &tp, unsigned char *smem, uint64_t *bar, RTbS
         // their range checks (restore_interior_in_range)
         const unsigned lt = (1u << lane) - 1u;
         bool small = true;
-        for (int i = tid; i < kW * kH; i += kThreads) {
-            const int ly = i / kW, lx = i - ly * kW;
-            const int gy = Y0 + ly, gx = X0 + lx;
-            const bool noisy = gy >= 0 && gy < tp.ny && gx >= 0 && gx < tp.nx && M[ly * kMW + lx + (kMX - kK)];
-            const int d = tile_depth(ly, lx, top, bottom, left, right);
-            const bool listed = noisy && d >= thr;
-            const unsigned peers = __match_any_sync(0xffffffffu, listed ? d : -1);
-            if (listed && (peers & lt) == 0u) atomicAdd(&sh.cnt[d], __popc(peers));
-            small = small && fabsf(S0[i]) < 0x1p60f;           // false for a NaN
+        if (cached) {
+            for (int i = tid; i < kW * kH; i += kThreads) small = small && fabsf(S0[i]) < 0x1p60f;
+        } else {
+            for (int i = tid; i < kW * kH; i += kThreads) {
+                const int ly = i / kW, lx = i - ly * kW;
+                const int gy = Y0 + ly, gx = X0 + lx;
+                const bool noisy = gy >= 0 && gy < tp.ny && gx >= 0 && gx < tp.nx && M[ly * kMW + lx + (kMX - kK)];
+                const int d = tile_depth(ly, lx, top, bottom, left, right);
+                const bool listed = noisy && d >= 1;
+                const unsigned peers = __match_any_sync(0xffffffffu, listed ? d : -1);
+                if (listed && (peers & lt) == 0u) atomicAdd(&sh.cnt[d], __popc(peers));
+                small = small && fabsf(S0[i]) < 0x1p60f;           // false for a NaN
+            }
         }
         const bool in_range = __syncthreads_and(small) && tp.alpha_in_range;
+        if (!cached) {
         if (tid == 0) {
             int pos = 0;
             sh.nge[kK + 1] = 0;
             for (int d = kK; d >= 1; --d) {
                 sh.next[d] = pos;
-                pos += d >= thr ? sh.cnt[d] : 0;
+                pos += sh.cnt[d];
                 sh.nge[d] = pos;
             }
+            sh.nge[0] = pos;
         }
         __syncthreads();
         for (int i = tid; i < kW * kH; i += kThreads) {
@@ -169,7 +199,7 @@ __device__ bool rtb_pass(const RTb &tp, unsigned char *smem, uint64_t *bar, RTbS
             const int gy = Y0 + ly, gx = X0 + lx;
             const bool noisy = gy >= 0 && gy < tp.ny && gx >= 0 && gx < tp.nx && M[ly * kMW + lx + (kMX - kK)];
             const int d = tile_depth(ly, lx, top, bottom, left, right);
-            const bool listed = noisy && d >= thr;
+            const bool listed = noisy && d >= 1;
             const unsigned peers = __match_any_sync(0xffffffffu, listed ? d : -1);
             const int first = __ffs(peers) - 1;
             int base = 0;
@@ -179,32 +209,53 @@ __device__ bool rtb_pass(const RTb &tp, unsigned char *smem, uint64_t *bar, RTbS
             const bool border = gy == 0 || gy == tp.ny - 1 || gx == 0 || gx == tp.nx - 1;
             if (listed)
                 L[base + __popc(peers & lt)] = (unsigned short)(i | (own ? 1 << 14 : 0) | (border ? 1 << 15 : 0));
-            if (REDUCE) {
-                const unsigned owners = __ballot_sync(0xffffffffu, own);
-                if (lane == 0 && owners) atomicAdd(&sh.owned, (unsigned)__popc(owners));
-            }
+            const unsigned owners = __ballot_sync(0xffffffffu, own);
+            if (lane == 0 && owners) atomicAdd(&sh.owned, (unsigned)__popc(owners));
         }
         __syncthreads();
+        // store the record for the later passes of this launch
+        int *head = (int *)rec;
+        if (tid < kK + 2) head[tid] = sh.nge[tid];
+        if (tid == kK + 2) head[kK + 2] = (int)sh.owned;
+        const int nl = sh.nge[1];
+        for (int i = tid; i < (2 * nl + 15) / 16; i += kThreads) ((uint4 *)(rec + kRecHead))[i] = ((const uint4 *)L)[i];
+        }
         for (int s = 1; s <= kp; ++s) {
             const float *In = (s & 1) ? S0 : S1;
             float *Out = (s & 1) ? S1 : S0;
             const int n = sh.nge[s + kK - kp];
             unsigned long long sum = 0ull;
-            for (int e = tid; e < n; e += kThreads) {
-                const unsigned ent = L[e];
-                const int pos = (int)(ent & 0x3FFFu);
-                const float *C = In + pos;
-                float nv;
-                if (ent & 0x8000u) {
-                    const int gy = Y0 + pos / kW, gx = X0 + pos % kW;
-                    nv = restore_border<FAST>(C, kW, tp.alpha, gy > 0, gy + 1 < tp.ny, gx > 0, gx + 1 < tp.nx);
-                } else if (!FAST && in_range) {
-                    nv = restore_interior_in_range(C, kW, tp.alpha);
-                } else {
-                    nv = restore_interior<FAST>(C, kW, tp.alpha);
+            if (!FAST && in_range && !edge_tile) {
+                // the common case, with no branch per pixel: no pixel on the
+                // grid's border, weights without range checks
+                for (int e = tid; e < n; e += kThreads) {
+                    const unsigned ent = L[e];
+                    const int pos = (int)(ent & 0x3FFFu);
+                    const float *C = In + pos;
+                    const float nv = restore_interior_in_range(C, kW, tp.alpha);
+                    Out[pos] = nv;
+                    if (REDUCE) {
+                        const unsigned long long fx = fixed_2m24_nb(__fsub_rn(nv, *C));
+                        sum += (ent & 0x4000u) ? fx : 0ull;
+                    }
                 }
-                Out[pos] = nv;
-                if (REDUCE && (ent & 0x4000u)) sum += fixed_2m24(__fsub_rn(nv, *C));
+            } else {
+                for (int e = tid; e < n; e += kThreads) {
+                    const unsigned ent = L[e];
+                    const int pos = (int)(ent & 0x3FFFu);
+                    const float *C = In + pos;
+                    float nv;
+                    if (ent & 0x8000u) {
+                        const int gy = Y0 + pos / kW, gx = X0 + pos % kW;
+                        nv = restore_border<FAST>(C, kW, tp.alpha, gy > 0, gy + 1 < tp.ny, gx > 0, gx + 1 < tp.nx);
+                    } else if (!FAST && in_range) {
+                        nv = restore_interior_in_range(C, kW, tp.alpha);
+                    } else {
+                        nv = restore_interior<FAST>(C, kW, tp.alpha);
+                    }
+                    Out[pos] = nv;
+                    if (REDUCE && (ent & 0x4000u)) sum += fixed_2m24(__fsub_rn(nv, *C));
+                }
             }
             if (REDUCE) {
                 sum = warp_sum_u64(sum);
@@ -263,7 +314,7 @@ __global__ void __launch_bounds__(kThreads, 3) restore_tb_kernel(const __grid_co
     for (long long p = 0;; ++p) {
         const long long left = la.max_iters - it;
         const int kp = (int)((long long)s_kpn < left ? (long long)s_kpn : left);
-        if (!rtb_pass<FAST, true>(tp, smem, bar, sh, phase, cur, kp, la, &ctl->next_tile[p % kSlots])) return;
+        if (!rtb_pass<FAST, true>(tp, smem, bar, sh, phase, cur, kp, la, &ctl->next_tile[p % kSlots], p > 0)) return;
         __syncthreads();
         if (tid < kp) {
             Slot *sl = &ctl->sub[p % kSlots][tid];
@@ -317,7 +368,7 @@ __global__ void __launch_bounds__(kThreads, 3) restore_tb_kernel(const __grid_co
                 // the pass again from its input, up to the stopping sweep
                 if (tid == 0) tma::fence_proxy_async_global();
                 if (!rtb_pass<FAST, false>(tp, smem, bar, sh, phase, cur, s_rewind, la,
-                                           &ctl->next_tile[(p + 1) % kSlots]))
+                                           &ctl->next_tile[(p + 1) % kSlots], true))
                     return;
                 bar_target += (unsigned long long)la.nblocks;
                 if (!grid_barrier(ctl, bar_target, la.limit_ns)) return;
@@ -331,7 +382,7 @@ __global__ void __launch_bounds__(kThreads, 3) restore_tb_kernel(const __grid_co
 }
 
 template <bool FAST>
-cudaError_t run_rtb(const Problem &p, LoopArgs la, int K, cudaStream_t st)
+cudaError_t run_rtb(const Problem &p, LoopArgs la, int K, void *lists, cudaStream_t st)
 {
     RTb tp;
     memset(&tp, 0, sizeof(tp));
@@ -348,6 +399,7 @@ cudaError_t run_rtb(const Problem &p, LoopArgs la, int K, cudaStream_t st)
     tp.K = K;
     tp.alpha = p.alpha;
     tp.alpha_in_range = restore_alpha_in_range(p.alpha);
+    tp.lists = (unsigned char *)lists;
     auto kern = restore_tb_kernel<FAST>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem);
     if (e != cudaSuccess) return e;
@@ -372,11 +424,17 @@ int restore_tb_resolve_k(const Problem &p, const void *a, const void *b, const v
     return p.k > kK ? kK : p.k;
 }
 
-cudaError_t restore_tb_persistent(const Problem &p, LoopArgs la, cudaStream_t st)
+size_t restore_tb_list_bytes(long long nx, long long ny)
+{
+    if (nx % 16 != 0) return 0;
+    return (size_t)((nx + kOwn - 1) / kOwn) * (size_t)((ny + kOwn - 1) / kOwn) * kRecBytes;
+}
+
+cudaError_t restore_tb_persistent(const Problem &p, LoopArgs la, void *lists, cudaStream_t st)
 {
     const int K = restore_tb_resolve_k(p, la.a, la.b, la.aux);
-    if (K < 2) return cudaErrorNotSupported;
-    return p.math == SLR_MATH_FAST ? run_rtb<true>(p, la, K, st) : run_rtb<false>(p, la, K, st);
+    if (K < 2 || !lists || ((uintptr_t)lists % 16) != 0) return cudaErrorNotSupported;
+    return p.math == SLR_MATH_FAST ? run_rtb<true>(p, la, K, lists, st) : run_rtb<false>(p, la, K, lists, st);
 }
 
 }  // namespace slr

@@ -188,7 +188,10 @@ slr_status run_persistent(slr_handle h, int64_t max_iters)
                       ? slr::jacobi_tb_persistent(h->prob, la, h->stream)
                       : slr::jacobi_persistent(h->prob, la, h->stream);
         break;
-    case SLR_RESTORE8: e = slr::restore_persistent(h->prob, la, h->stream); break;
+    case SLR_RESTORE8:
+        e = slr::restore_persistent(h->prob, la, h->ws + slr::kCtlBytes + round_up(h->prob.state_bytes, 256),
+                                    h->stream);
+        break;
     default: e = cudaErrorInvalidValue;
     }
     if (e != cudaSuccess) return cuda_fail(h, e, "persistent loop launch");
@@ -336,6 +339,7 @@ size_t slr_workspace_size(const slr_desc *d)
     size_t bytes = slr::kCtlBytes + round_up(p.state_bytes, 256);
     if (p.stencil == SLR_LIFE) bytes += 2 * round_up(slr::life_tb_bits_bytes(p.nx, p.ny), 256);
     if (d->defect_correction) bytes += slr::dc_workspace_bytes(p.nx, p.ny, p.nz);
+    if (p.stencil == SLR_RESTORE8) bytes += slr::restore_tb_list_bytes(p.nx, p.ny);
     return bytes;
 }
 

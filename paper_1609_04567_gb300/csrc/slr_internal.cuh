@@ -196,6 +196,15 @@ __device__ __forceinline__ unsigned long long fixed_2m24(float d)
     return fixed_2m24_large(a);
 }
 
+// fixed_2m24 without a branch, for hot loops: the product a * 2^24 is exact
+// and below 2^64 for every a < 2^40, so one conversion to a 64-bit integer
+// gives the same integer; larger values and NaN saturate as above.
+__device__ __forceinline__ unsigned long long fixed_2m24_nb(float d)
+{
+    const float a = fabsf(d);
+    return a < 1099511627776.0f ? __float2ull_rz(a * 16777216.0f) : ~0ull;
+}
+
 // What every stencil's loop needs to decide after a sweep.
 struct Decision {
     double value;
@@ -384,7 +393,8 @@ cudaError_t jacobi_persistent(const Problem &p, LoopArgs la, cudaStream_t st);
 // side f takes the TMA path (forced: as for SLR_TILING_TMA, any grid size).
 bool jacobi_tma_ok(const Problem &p, const void *a, const void *b, const void *f, bool forced);
 cudaError_t jacobi_sweep(const Problem &p, const void *src, void *dst, const void *f, cudaStream_t st);
-cudaError_t restore_persistent(const Problem &p, LoopArgs la, cudaStream_t st);
+// `lists`: the workspace area of restore_tb_list_bytes(nx, ny) bytes (16-byte aligned).
+cudaError_t restore_persistent(const Problem &p, LoopArgs la, void *lists, cudaStream_t st);
 // Temporal-blocked restoration (restore_tb.cu): k sweeps per pass over 64 x 64
 // tiles with an 8-pixel halo.  Supported for rows of whole 16-byte mask groups
 // (nx % 16 == 0) and 16-byte aligned arrays; resolve_k gives 1 (the one-sweep
@@ -394,7 +404,10 @@ cudaError_t restore_persistent(const Problem &p, LoopArgs la, cudaStream_t st);
 constexpr int kRestoreTbDefaultK = 8;
 bool restore_tb_supported(const Problem &p, const void *a, const void *b, const void *mask);
 int restore_tb_resolve_k(const Problem &p, const void *a, const void *b, const void *mask);
-cudaError_t restore_tb_persistent(const Problem &p, LoopArgs la, cudaStream_t st);
+// Workspace bytes of the per-tile noisy-pixel records (0 for rows that are not
+// whole 16-byte mask groups, where the temporal-blocked kernel does not run).
+size_t restore_tb_list_bytes(long long nx, long long ny);
+cudaError_t restore_tb_persistent(const Problem &p, LoopArgs la, void *lists, cudaStream_t st);
 // Whether the TMA-tiled restoration sweep accepts p (nx % 16 == 0).
 bool restore_tma_ok(const Problem &p);
 cudaError_t restore_sweep(const Problem &p, const void *src, void *dst, const void *mask, cudaStream_t st);

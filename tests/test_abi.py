@@ -193,3 +193,15 @@ def test_plain_c_caller_links_and_uses_the_header(tmp_path):
     create = out[3].split(maxsplit=3)
     assert int(create[1]) == -1 and create[2] == "1" and "16-byte aligned" in create[3]
     assert int(out[4].split()[1]) == 4 << 20
+
+
+def test_restoration_workspace_holds_the_tile_records(lib):
+    from paper_1609_04567_gb300 import slr
+    up = lambda x: -(-x // 256) * 256
+    # 4096 x 4096: control block, second state buffer, one 12,352-byte record per 64 x 64 tile
+    d = slr.slr_desc_init(slr.SLR_RESTORE8, 4096, 4096, 1)
+    assert slr.slr_workspace_size(d) == 4096 + up(4096 * 4096 * 4) + 64 * 64 * 12352
+    # ragged tiles count whole; rows that are not whole 16-byte mask groups get no records
+    assert slr.slr_workspace_size(slr.slr_desc_init(slr.SLR_RESTORE8, 80, 65, 1)) == \
+        4096 + up(80 * 65 * 4) + 2 * 2 * 12352
+    assert slr.slr_workspace_size(slr.slr_desc_init(slr.SLR_RESTORE8, 100, 50, 1)) == 4096 + up(100 * 50 * 4)
