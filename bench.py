@@ -1261,7 +1261,7 @@ def main():
     ap.add_argument("--batch3d", type=int, default=512, help="side of the 3D grid of the batch workload (0: none)")
     ap.add_argument("--rate", type=float, default=2000.0)
     ap.add_argument("--serve-seconds", type=float, default=10.0)
-    ap.add_argument("--step-sweeps", type=int, default=32)
+    ap.add_argument("--step-sweeps", type=int, default=64)
     ap.add_argument("--solo-cells", type=int, default=1024 * 1024,
                     help="serving: denoise jobs of at least this many pixels take the solo lane (0: none)")
     ap.add_argument("--k", type=int, default=0, help="generations per HBM pass (0 = library choice)")

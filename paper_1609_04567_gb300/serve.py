@@ -129,7 +129,7 @@ class ServeStats:
 class Server:
     """One resident batch served with continuous batching."""
 
-    def __init__(self, *, max_slots: int = 1024, budget_bytes: int | None = None, step_sweeps: int = 32,
+    def __init__(self, *, max_slots: int = 1024, budget_bytes: int | None = None, step_sweeps: int = 64,
                  denoise_tol: float = 1e-3, solve_tol: float = 1e-6, cap: int = 5000, device=None,
                  solo_cells: int | None = 1024 * 1024):
         import torch
