@@ -16,11 +16,12 @@ footprints of admitted requests stays inside the budget (by default a fraction
 of the free memory reported by the driver at start-up).
 
 Large denoise jobs (at least ``solo_cells`` pixels) take a second lane: each
-gets its own resident solver (the TMA-tiled restoration loop, which streams a
-large frame several times faster than the batch's warp units) and is resumed
-for the same number of sweeps per iteration, on the same stream, right after
-the batch launch.  Both lanes therefore advance every admitted request by the
-same number of sweeps per iteration; results do not depend on the lane.
+gets its own solver (the temporal-blocked restoration loop, which restores a
+large frame several times faster than the batch's warp units) and runs to its
+stop in one launch on the lane's own stream, in admission order, while the
+batch steps on the first stream; the host sees a solo job finish through an
+event on that stream, without waiting for it.  Results do not depend on the
+lane.
 """
 from __future__ import annotations
 
@@ -50,7 +51,7 @@ class Request:
     slot: int = -1
     tensors: tuple = field(default=(), repr=False)
     solver: object = field(default=None, repr=False)   # the solo lane's solver
-    target: int = 0                                     # the solo lane's iteration cap so far
+    event: object = field(default=None, repr=False)    # the solo lane's completion event
 
 
 def bucket_sides(lo: int, hi: int, n: int) -> list[int]:
@@ -136,6 +137,7 @@ class Server:
         self.torch = torch
         self.device = torch.device(device or "cuda")
         self.stream = torch.cuda.Stream(self.device)
+        self.solo_stream = torch.cuda.Stream(self.device)
         self.batch = slr.Batch(max_slots, device=self.device, stream=self.stream)
         self.max_slots = max_slots
         if budget_bytes is None:
@@ -148,7 +150,7 @@ class Server:
         self.cap = cap
         self.pool = InputPool()
         self.active = {}          # batch slot -> request
-        self.solo = {}            # request id -> request with its own solver
+        self.solo = {}            # request id -> request with its own solver (admission order)
         self.solo_cells = solo_cells
 
     def is_solo(self, r: Request) -> bool:
@@ -160,15 +162,20 @@ class Server:
             return False
         torch = self.torch
         host_u, host_aux = self.pool.get(r.kind, r.side)
-        with torch.cuda.stream(self.stream):
+        solo = self.is_solo(r)
+        st = self.solo_stream if solo else self.stream
+        with torch.cuda.stream(st):
             u = torch.empty(host_u.shape, dtype=host_u.dtype, device=self.device)
             aux = torch.empty(host_aux.shape, dtype=host_aux.dtype, device=self.device)
             u.copy_(host_u, non_blocking=True)
             aux.copy_(host_aux, non_blocking=True)
             stencil = slr.SLR_RESTORE8 if r.kind == KIND_DENOISE else slr.SLR_J2D5
-            if self.is_solo(r):
-                r.solver = slr.Solver(stencil, u, aux, stream=self.stream, tol=self.tol[r.kind])
-                r.target = 0
+            if solo:
+                # the whole loop in one launch, queued behind the lane's earlier jobs
+                r.solver = slr.Solver(stencil, u, aux, stream=st, tol=self.tol[r.kind])
+                r.solver.run(self.cap)
+                r.event = torch.cuda.Event()
+                r.event.record(st)
                 self.solo[r.rid] = r
             else:
                 r.slot = self.batch.add(stencil, u, aux, self.cap, tol=self.tol[r.kind])
@@ -192,32 +199,33 @@ class Server:
         return self._finish(r, now, res, keep)
 
     def step(self) -> list[int]:
-        """Enqueue step_sweeps more sweeps of every admitted request (the
-        batch launch, then each solo solver), wait, and return the finished
-        batch slots."""
+        """Enqueue step_sweeps more sweeps of every request in the batch, wait
+        for them and return the finished batch slots; with only solo jobs in
+        flight, wait for the oldest of them instead."""
         if self.active:
             self.batch.run(self.step_sweeps)
-        for r in self.solo.values():
-            r.target = min(self.cap, r.target + self.step_sweeps)
-            r.solver.run(r.target)
-        if self.active:
             finished, _ = self.batch.poll()
             return finished
-        self.stream.synchronize()
+        if self.solo:
+            next(iter(self.solo.values())).event.synchronize()
         return []
 
     def retire_solo(self, now: float, keep: bool) -> list[Request]:
+        """The solo jobs whose launch has finished, in admission order (the
+        lane runs them in that order)."""
         out = []
         for rid in list(self.solo):
             r = self.solo[rid]
+            if not r.event.query():
+                break
             res = r.solver.result(check=False)
             if res.status < 0:
                 raise slr.SlrError(res.status, "solo solve failed")
-            if res.converged or res.iters >= self.cap:
-                del self.solo[rid]
-                r.solver.close()
-                r.solver = None
-                out.append(self._finish(r, now, res, keep))
+            del self.solo[rid]
+            r.solver.close()
+            r.solver = None
+            r.event = None
+            out.append(self._finish(r, now, res, keep))
         return out
 
     def serve(self, requests: list[Request], *, warmup_s: float = 0.0, keep_results: bool = False,
