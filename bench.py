@@ -929,7 +929,8 @@ def measure_serve_short(args, seconds: float):
     from paper_1609_04567_gb300 import serve, slr
     slr.load()
     reqs = serve.make_requests(seconds + 1.0, args.rate)
-    srv = serve.Server(max_slots=1024, step_sweeps=args.step_sweeps, solo_cells=args.solo_cells or None)
+    srv = serve.Server(max_slots=1024, step_sweeps=args.step_sweeps, solo_cells=args.solo_cells or None,
+                       light_solo=args.light_solo)
     clocks = ClockSampler(torch.cuda.current_device())
     clocks.start()
     st = srv.serve(reqs, warmup_s=1.0, time_limit_s=seconds * 6 + 30)
@@ -1035,7 +1036,8 @@ def run_serve(args):
     from paper_1609_04567_gb300 import serve, slr
     slr.load()
     reqs = serve.make_requests(args.serve_seconds + 1.0, args.rate)
-    srv = serve.Server(max_slots=1024, step_sweeps=args.step_sweeps, solo_cells=args.solo_cells or None)
+    srv = serve.Server(max_slots=1024, step_sweeps=args.step_sweeps, solo_cells=args.solo_cells or None,
+                       light_solo=args.light_solo)
     st = srv.serve(reqs, warmup_s=1.0, time_limit_s=args.serve_seconds * 6 + 30)
     srv.close()
     # the same arrivals served by a queue alone, one request at a time: with the
@@ -1056,9 +1058,11 @@ def run_serve(args):
             "p99_ms": num(st.p99_ms), "mean_ms": num(st.mean_ms), "throughput_rps": st.throughput_rps, "gcell_per_s": st.gcell_per_s,
             "requests": st.requests, "completed": st.completed, "wall_s": st.wall_s, "steps": st.steps,
             "max_in_flight": st.max_in_flight, "max_queue": st.max_queue,
-            "solo_lane": {"min_cells": args.solo_cells, "requests": sum(srv.is_solo(r) for r in reqs),
-                          "what": "denoise jobs of at least min_cells pixels run on their own TMA-tiled solver, "
-                                  "resumed step_sweeps sweeps per iteration after the batch launch"},
+            "solo_lane": {"min_cells": args.solo_cells, "light_solo": args.light_solo,
+                          "requests": sum(r.lane == "solo" for r in srv.done),
+                          "what": "denoise jobs of at least min_cells pixels, and any request while fewer than "
+                                  "light_solo jobs are in the lane, run to their stop on solvers of their own, "
+                                  "one after another, beside the batch"},
             "latency_sample": st.measured,
             "queue_alone": dict(fifo, what="the same arrivals, one request at a time in arrival order, each "
                                            "solved alone; p50/p99 over the served requests that arrived after "
@@ -1264,6 +1268,8 @@ def main():
     ap.add_argument("--step-sweeps", type=int, default=64)
     ap.add_argument("--solo-cells", type=int, default=1024 * 1024,
                     help="serving: denoise jobs of at least this many pixels take the solo lane (0: none)")
+    ap.add_argument("--light-solo", type=int, default=4,
+                    help="serving: any request takes the solo lane while fewer than this many jobs are in it")
     ap.add_argument("--k", type=int, default=0, help="generations per HBM pass (0 = library choice)")
     ap.add_argument("--gens", type=int, default=2000,
                     help="generations per solve (the workload has 2000; shorter runs are for profiler captures "

@@ -169,9 +169,14 @@ void slr_desc_init(slr_desc *d, int32_t stencil, int64_t nx, int64_t ny, int64_t
 
 /* Bytes of device workspace a handle for *d needs (control block, second
  * state buffer; Life: two bit-packed buffers; defect correction: three binary32
- * buffers; SLR_RESTORE8 with nx a multiple of 16: one 12,352-byte record per
- * 64 x 64 tile, the tile's noisy-pixel list built in a run's first pass and
- * read by its later ones).  Returns 0 for an invalid descriptor. */
+ * buffers; SLR_RESTORE8: one 12,352-byte record per 64 x 64 tile, the tile's
+ * noisy-pixel list built in a run's first pass and read by its later ones,
+ * the records rounded up to 256 bytes; when nx is not a multiple of 16 also
+ * a copy of the mask with rows padded to a multiple of 16 bytes, and when nx
+ * is not a multiple of 4 two copies of the state with rows padded to a
+ * multiple of 4 floats, each rounded up to 256 bytes: the temporal-blocked
+ * loop reads rows that start on 16-byte boundaries).  Returns 0 for an
+ * invalid descriptor. */
 size_t slr_workspace_size(const slr_desc *d);
 
 /* Create a handle (constructor of Sec. 3.2: elemental function, combinator

@@ -25,6 +25,13 @@
 // After kp sweeps the 64 x 64 owned pixels go to the other state buffer in
 // global memory with 16-byte stores.
 //
+// Row pitch.  The tensor maps need rows that start on 16-byte boundaries:
+// the mask's (bytes) when nx is a multiple of 16, the state's (floats) when nx
+// is a multiple of 4.  Otherwise the run works on copies in the workspace
+// whose rows are padded to the next such multiple: the mask copied in at the
+// start of a run, the state copied in and, after the loop, back out.  The
+// padding columns lie outside the maps' extent (nx), so no copy reads them.
+//
 // Lists across passes.  The mask does not change, so a tile's list does not
 // either: the first pass of a launch lists every noisy pixel of depth >= 1
 // and stores the list, its per-depth counts and its owned count in the
@@ -74,6 +81,7 @@ struct RTb {
     CUtensorMap umap[2];       // state buffers A (caller's u) and B, box 80 x 80
     CUtensorMap mmap;          // mask, box 96 x 80
     float *buf[2];
+    long long pitch;           // floats per row of buf[0] and buf[1]
     int nx, ny;
     int tiles_x, tiles_y;
     int K;                     // sweeps per pass
@@ -270,7 +278,7 @@ __device__ bool rtb_pass(const RTb &tp, unsigned char *smem, uint64_t *bar, RTbS
             const int r = i / (kOwn / 4), c4 = i % (kOwn / 4);
             const int gy = y0 + r, gx = x0 + 4 * c4;
             if (gy < tp.ny && gx < tp.nx)
-                *(float4 *)(dst + (size_t)gy * (size_t)tp.nx + gx) = *(const float4 *)(Fin + (r + kK) * kW + kK + 4 * c4);
+                *(float4 *)(dst + (size_t)gy * (size_t)tp.pitch + gx) = *(const float4 *)(Fin + (r + kK) * kW + kK + 4 * c4);
         }
         // this tile's shared-memory accesses before the next tile's copies
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -373,7 +381,7 @@ __global__ void __launch_bounds__(kThreads, 3) restore_tb_kernel(const __grid_co
                 bar_target += (unsigned long long)la.nblocks;
                 if (!grid_barrier(ctl, bar_target, la.limit_ns)) return;
             }
-            if ((cur ^ 1) == 1) grid_copy(tp.buf[1], tp.buf[0], (size_t)tp.nx * tp.ny * sizeof(float));
+            if ((cur ^ 1) == 1) grid_copy(tp.buf[1], tp.buf[0], (size_t)tp.pitch * tp.ny * sizeof(float));
             return;
         }
         cur ^= 1;
@@ -381,17 +389,21 @@ __global__ void __launch_bounds__(kThreads, 3) restore_tb_kernel(const __grid_co
     }
 }
 
+// state buffers la.a / la.b with `pitch` floats per row, mask rows `mpitch` bytes
 template <bool FAST>
-cudaError_t run_rtb(const Problem &p, LoopArgs la, int K, void *lists, cudaStream_t st)
+cudaError_t run_rtb(const Problem &p, LoopArgs la, int K, void *lists, const void *mask, long long pitch,
+                    long long mpitch, cudaStream_t st)
 {
     RTb tp;
     memset(&tp, 0, sizeof(tp));
-    if (!tma::make_map_2d(&tp.umap[0], la.a, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, p.nx, p.ny, kW, kH) ||
-        !tma::make_map_2d(&tp.umap[1], la.b, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, p.nx, p.ny, kW, kH) ||
-        !tma::make_map_2d(&tp.mmap, la.aux, CU_TENSOR_MAP_DATA_TYPE_UINT8, 1, p.nx, p.ny, kMW, kH))
+    const auto none = CU_TENSOR_MAP_SWIZZLE_NONE;
+    if (!tma::make_map_2d(&tp.umap[0], la.a, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, p.nx, p.ny, kW, kH, none, 4 * pitch) ||
+        !tma::make_map_2d(&tp.umap[1], la.b, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, p.nx, p.ny, kW, kH, none, 4 * pitch) ||
+        !tma::make_map_2d(&tp.mmap, mask, CU_TENSOR_MAP_DATA_TYPE_UINT8, 1, p.nx, p.ny, kMW, kH, none, mpitch))
         return cudaErrorNotSupported;
     tp.buf[0] = (float *)la.a;
     tp.buf[1] = (float *)la.b;
+    tp.pitch = pitch;
     tp.nx = (int)p.nx;
     tp.ny = (int)p.ny;
     tp.tiles_x = (int)((p.nx + kOwn - 1) / kOwn);
@@ -408,11 +420,33 @@ cudaError_t run_rtb(const Problem &p, LoopArgs la, int K, void *lists, cudaStrea
 
 }  // namespace
 
+namespace {
+// padded row pitches (see the header comment)
+bool mask_padded(long long nx) { return nx % 16 != 0; }
+bool state_padded(long long nx) { return nx % 4 != 0; }
+long long mask_pitch(long long nx) { return (nx + 15) / 16 * 16; }
+long long state_pitch(long long nx) { return (nx + 3) / 4 * 4; }
+size_t up256(size_t x) { return (x + 255) / 256 * 256; }
+size_t records_bytes(long long nx, long long ny)
+{
+    return up256((size_t)((nx + kOwn - 1) / kOwn) * (size_t)((ny + kOwn - 1) / kOwn) * kRecBytes);
+}
+size_t mask_copy_bytes(long long nx, long long ny)
+{
+    return mask_padded(nx) ? up256((size_t)mask_pitch(nx) * (size_t)ny) : 0;
+}
+size_t state_copy_bytes(long long nx, long long ny)      // one of the two buffers
+{
+    return state_padded(nx) ? up256((size_t)state_pitch(nx) * (size_t)ny * sizeof(float)) : 0;
+}
+}  // namespace
+
 bool restore_tb_supported(const Problem &p, const void *a, const void *b, const void *mask)
 {
-    if (p.stencil != SLR_RESTORE8 || p.nx % 16 != 0 || p.nx >= (1ll << 31) - 4096 || p.ny >= (1ll << 31) - 4096)
-        return false;
-    if ((((uintptr_t)a | (uintptr_t)b) % 16) != 0 || ((uintptr_t)mask % 16) != 0) return false;
+    if (p.stencil != SLR_RESTORE8 || p.nx >= (1ll << 31) - 4096 || p.ny >= (1ll << 31) - 4096) return false;
+    // buffers the maps read in place must start on 16-byte boundaries
+    if (!state_padded(p.nx) && (((uintptr_t)a | (uintptr_t)b) % 16) != 0) return false;
+    if (!mask_padded(p.nx) && ((uintptr_t)mask % 16) != 0) return false;
     if ((double)p.nx * (double)p.ny >= 4.0e18) return false;
     return tma::encode_fn() != nullptr;
 }
@@ -426,15 +460,42 @@ int restore_tb_resolve_k(const Problem &p, const void *a, const void *b, const v
 
 size_t restore_tb_list_bytes(long long nx, long long ny)
 {
-    if (nx % 16 != 0) return 0;
-    return (size_t)((nx + kOwn - 1) / kOwn) * (size_t)((ny + kOwn - 1) / kOwn) * kRecBytes;
+    return records_bytes(nx, ny) + mask_copy_bytes(nx, ny) + 2 * state_copy_bytes(nx, ny);
 }
 
 cudaError_t restore_tb_persistent(const Problem &p, LoopArgs la, void *lists, cudaStream_t st)
 {
     const int K = restore_tb_resolve_k(p, la.a, la.b, la.aux);
-    if (K < 2 || !lists || ((uintptr_t)lists % 16) != 0) return cudaErrorNotSupported;
-    return p.math == SLR_MATH_FAST ? run_rtb<true>(p, la, K, lists, st) : run_rtb<false>(p, la, K, lists, st);
+    if (K < 2 || !lists || ((uintptr_t)lists % 256) != 0) return cudaErrorNotSupported;
+    unsigned char *scratch = (unsigned char *)lists + records_bytes(p.nx, p.ny);
+    const void *mask = la.aux;
+    long long mpitch = p.nx, pitch = p.nx;
+    cudaError_t e = cudaSuccess;
+    if (mask_padded(p.nx)) {
+        mpitch = mask_pitch(p.nx);
+        e = cudaMemcpy2DAsync(scratch, (size_t)mpitch, la.aux, (size_t)p.nx, (size_t)p.nx, (size_t)p.ny,
+                              cudaMemcpyDeviceToDevice, st);
+        mask = scratch;
+        scratch += mask_copy_bytes(p.nx, p.ny);
+    }
+    LoopArgs lp = la;
+    const size_t row = (size_t)p.nx * sizeof(float);
+    if (state_padded(p.nx)) {
+        pitch = state_pitch(p.nx);
+        lp.a = scratch;
+        lp.b = scratch + state_copy_bytes(p.nx, p.ny);
+        if (e == cudaSuccess)
+            e = cudaMemcpy2DAsync(lp.a, (size_t)pitch * sizeof(float), la.a, row, row, (size_t)p.ny,
+                                  cudaMemcpyDeviceToDevice, st);
+    }
+    if (e != cudaSuccess) return e;
+    e = p.math == SLR_MATH_FAST ? run_rtb<true>(p, lp, K, lists, mask, pitch, mpitch, st)
+                                : run_rtb<false>(p, lp, K, lists, mask, pitch, mpitch, st);
+    // the loop leaves its state in lp.a
+    if (e == cudaSuccess && state_padded(p.nx))
+        e = cudaMemcpy2DAsync(la.a, row, lp.a, (size_t)pitch * sizeof(float), row, (size_t)p.ny,
+                              cudaMemcpyDeviceToDevice, st);
+    return e;
 }
 
 }  // namespace slr

@@ -107,16 +107,17 @@ inline PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
     return fn;
 }
 
-// Row-major 2D map of nx x ny elements of `esize` bytes (row stride nx * esize,
-// a multiple of 16), box box_w x box_h, no swizzle, zero fill out of range.
+// Row-major 2D map of nx x ny elements of `esize` bytes (row stride
+// pitch_bytes, or nx * esize when 0; a multiple of 16), box box_w x box_h,
+// zero fill out of range.
 inline bool make_map_2d(CUtensorMap *m, const void *base, CUtensorMapDataType dt, size_t esize, long long nx,
                         long long ny, uint32_t box_w, uint32_t box_h,
-                        CUtensorMapSwizzle swz = CU_TENSOR_MAP_SWIZZLE_NONE)
+                        CUtensorMapSwizzle swz = CU_TENSOR_MAP_SWIZZLE_NONE, long long pitch_bytes = 0)
 {
     auto fn = encode_fn();
     if (!fn) return false;
     cuuint64_t dims[2] = {(cuuint64_t)nx, (cuuint64_t)ny};
-    cuuint64_t strides[1] = {(cuuint64_t)(nx * (long long)esize)};
+    cuuint64_t strides[1] = {(cuuint64_t)(pitch_bytes > 0 ? pitch_bytes : nx * (long long)esize)};
     cuuint32_t box[2] = {box_w, box_h};
     cuuint32_t estr[2] = {1, 1};
     return fn(m, dt, 2, const_cast<void *>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, swz,

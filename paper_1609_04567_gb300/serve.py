@@ -18,10 +18,15 @@ of the free memory reported by the driver at start-up).
 Large denoise jobs (at least ``solo_cells`` pixels) take a second lane: each
 gets its own solver (the temporal-blocked restoration loop, which restores a
 large frame several times faster than the batch's warp units) and runs to its
-stop in one launch on the lane's own stream, in admission order, while the
-batch steps on the first stream; the host sees a solo job finish through an
-event on that stream, without waiting for it.  Results do not depend on the
-lane.
+stop in one launch, while the batch steps on the first stream.  Each solo job
+has a stream of its own from a small pool: its input copies start at once and
+overlap the jobs before it, and its launch waits (by an event) for the previous
+solo job's, so the lane runs its jobs one after another in admission order;
+the host sees a job finish through its event and reads its result from its own
+stream, without waiting for the jobs queued behind it.  At light load any
+request takes the solo lane while fewer than ``light_solo`` jobs are in it: a
+request then has the GPU to itself, as in a queue over the fused loop, and
+the batch takes the overflow.  Results do not depend on the lane.
 """
 from __future__ import annotations
 
@@ -50,6 +55,7 @@ class Request:
     value: float = 0.0
     slot: int = -1
     tensors: tuple = field(default=(), repr=False)
+    lane: str = ""                 # "batch" or "solo", set at admission
     solver: object = field(default=None, repr=False)   # the solo lane's solver
     event: object = field(default=None, repr=False)    # the solo lane's completion event
 
@@ -132,12 +138,16 @@ class Server:
 
     def __init__(self, *, max_slots: int = 1024, budget_bytes: int | None = None, step_sweeps: int = 64,
                  denoise_tol: float = 1e-3, solve_tol: float = 1e-6, cap: int = 5000, device=None,
-                 solo_cells: int | None = 1024 * 1024):
+                 solo_cells: int | None = 1024 * 1024, solo_streams: int = 64, light_solo: int = 4):
         import torch
         self.torch = torch
         self.device = torch.device(device or "cuda")
         self.stream = torch.cuda.Stream(self.device)
-        self.solo_stream = torch.cuda.Stream(self.device)
+        # one solo job per stream at a time: a job's result is read on its own
+        # stream, which then holds no later job
+        self.solo_streams = [torch.cuda.Stream(self.device) for _ in range(max(1, solo_streams))]
+        self.solo_issued = 0
+        self.solo_tail = None     # completion event of the last solo job launched
         self.batch = slr.Batch(max_slots, device=self.device, stream=self.stream)
         self.max_slots = max_slots
         if budget_bytes is None:
@@ -152,6 +162,7 @@ class Server:
         self.active = {}          # batch slot -> request
         self.solo = {}            # request id -> request with its own solver (admission order)
         self.solo_cells = solo_cells
+        self.light_solo = light_solo
 
     def is_solo(self, r: Request) -> bool:
         return self.solo_cells is not None and r.kind == KIND_DENOISE and r.side * r.side >= self.solo_cells
@@ -160,10 +171,12 @@ class Server:
         need = footprint(r.kind, r.side)
         if len(self.active) + len(self.solo) >= self.max_slots or self.in_use + need > self.budget:
             return False
+        solo = self.is_solo(r) or len(self.solo) < self.light_solo
+        if solo and len(self.solo) >= len(self.solo_streams):
+            return False
         torch = self.torch
         host_u, host_aux = self.pool.get(r.kind, r.side)
-        solo = self.is_solo(r)
-        st = self.solo_stream if solo else self.stream
+        st = self.solo_streams[self.solo_issued % len(self.solo_streams)] if solo else self.stream
         with torch.cuda.stream(st):
             u = torch.empty(host_u.shape, dtype=host_u.dtype, device=self.device)
             aux = torch.empty(host_aux.shape, dtype=host_aux.dtype, device=self.device)
@@ -171,16 +184,21 @@ class Server:
             aux.copy_(host_aux, non_blocking=True)
             stencil = slr.SLR_RESTORE8 if r.kind == KIND_DENOISE else slr.SLR_J2D5
             if solo:
-                # the whole loop in one launch, queued behind the lane's earlier jobs
+                # the whole loop in one launch, after the lane's previous job
                 r.solver = slr.Solver(stencil, u, aux, stream=st, tol=self.tol[r.kind])
+                if self.solo_tail is not None:
+                    st.wait_event(self.solo_tail)
                 r.solver.run(self.cap)
                 r.event = torch.cuda.Event()
                 r.event.record(st)
+                self.solo_tail = r.event
+                self.solo_issued += 1
                 self.solo[r.rid] = r
             else:
                 r.slot = self.batch.add(stencil, u, aux, self.cap, tol=self.tol[r.kind])
                 self.active[r.slot] = r
         r.tensors = (u, aux)
+        r.lane = "solo" if solo else "batch"
         r.admitted = now
         self.in_use += need
         return True
@@ -212,7 +230,8 @@ class Server:
 
     def retire_solo(self, now: float, keep: bool) -> list[Request]:
         """The solo jobs whose launch has finished, in admission order (the
-        lane runs them in that order)."""
+        lane runs them in that order); each result is read on the job's own
+        stream, which holds nothing after it."""
         out = []
         for rid in list(self.solo):
             r = self.solo[rid]

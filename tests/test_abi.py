@@ -201,7 +201,12 @@ def test_restoration_workspace_holds_the_tile_records(lib):
     # 4096 x 4096: control block, second state buffer, one 12,352-byte record per 64 x 64 tile
     d = slr.slr_desc_init(slr.SLR_RESTORE8, 4096, 4096, 1)
     assert slr.slr_workspace_size(d) == 4096 + up(4096 * 4096 * 4) + 64 * 64 * 12352
-    # ragged tiles count whole; rows that are not whole 16-byte mask groups get no records
+    # ragged tiles count whole
     assert slr.slr_workspace_size(slr.slr_desc_init(slr.SLR_RESTORE8, 80, 65, 1)) == \
-        4096 + up(80 * 65 * 4) + 2 * 2 * 12352
-    assert slr.slr_workspace_size(slr.slr_desc_init(slr.SLR_RESTORE8, 100, 50, 1)) == 4096 + up(100 * 50 * 4)
+        4096 + up(80 * 65 * 4) + up(2 * 2 * 12352)
+    # rows that are not whole 16-byte mask groups: a copy of the mask with rows padded to 112 bytes
+    assert slr.slr_workspace_size(slr.slr_desc_init(slr.SLR_RESTORE8, 100, 50, 1)) == \
+        4096 + up(100 * 50 * 4) + up(2 * 12352) + up(112 * 50)
+    # rows that are not whole 16-byte state groups: two copies of the state with rows of 92 floats too
+    assert slr.slr_workspace_size(slr.slr_desc_init(slr.SLR_RESTORE8, 90, 30, 1)) == \
+        4096 + up(90 * 30 * 4) + up(2 * 12352) + up(96 * 30) + 2 * up(92 * 30 * 4)

@@ -48,11 +48,14 @@ def test_fast_math_within_tolerance(gpu, orc, ny, nx):
 
 
 # ---- temporal-blocked path (k sweeps per pass over 64 x 64 tiles with an
-# 8-pixel halo; rows of whole 16-byte mask groups) ----
+# 8-pixel halo); widths that are not a multiple of 16 run on padded copies of
+# the mask, widths that are not a multiple of 4 on padded copies of the state
+# too ----
 
 @pytest.mark.parametrize("k", [1, 2, 3, 4, 8])
 @pytest.mark.parametrize("ny,nx", [(256, 256), (300, 528), (65, 208), (1, 16), (2, 64), (130, 144),
-                                   (200, 1040), (64, 64), (9, 32)])
+                                   (200, 1040), (64, 64), (9, 32),
+                                   (40, 2760), (100, 136), (70, 130), (67, 131), (300, 517), (5, 3), (1, 1)])
 def test_temporal_blocked_matches_oracle(gpu, orc, ny, nx, k):
     out, r, ref, rr = restore_case(gpu, orc, ny, nx, temporal_k=k)
     assert (r.iters, r.converged, r.count, r.value) == (rr.iters, rr.converged, rr.count, rr.value)
@@ -61,11 +64,13 @@ def test_temporal_blocked_matches_oracle(gpu, orc, ny, nx, k):
 
 @pytest.mark.parametrize("k", [2, 4, 8])
 @pytest.mark.parametrize("cap", [1, 3, 5, 9])
-def test_temporal_blocked_cap_inside_a_pass_then_resume(gpu, orc, k, cap):
+@pytest.mark.parametrize("nx", [272, 270])
+def test_temporal_blocked_cap_inside_a_pass_then_resume(gpu, orc, k, cap, nx):
     # a cap that ends inside a pass runs only the sweeps left; a later run
     # with a higher cap resumes from the state in u and equals a straight run
+    # (270: the state goes through padded copies, in and out, on each run)
     from paper_1609_04567_gb300 import inputs
-    frame, _ = inputs.noisy_frame(150, 272, seed=4)
+    frame, _ = inputs.noisy_frame(150, nx, seed=4)
     mask = inputs.noise_mask(frame)
     u = torch.from_numpy(frame.astype(np.float32)).cuda()
     s = gpu.Solver(gpu.SLR_RESTORE8, u, torch.from_numpy(mask).cuda(), tol=1e-3, temporal_k=k)

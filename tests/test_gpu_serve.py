@@ -20,20 +20,28 @@ def solve_alone(slr, r, server):
     return u, res
 
 
-@pytest.mark.parametrize("solo_cells", [None, 128 * 128])
-def test_results_alone_equal_results_in_the_mix(gpu, solo_cells):
-    # solo_cells = 128^2: the denoise jobs of 128^2 pixels and more take the solo lane
+@pytest.mark.parametrize("solo_cells,light_solo,rate", [(None, 0, 300.0), (128 * 128, 0, 300.0), (None, 1, 3000.0)])
+def test_results_alone_equal_results_in_the_mix(gpu, solo_cells, light_solo, rate):
+    # solo_cells = 128^2: the denoise jobs of 128^2 pixels and more take the
+    # solo lane; light_solo = 1: any request does while the lane is empty (at
+    # 3000 requests/s the lane is busy often enough for the batch to get work)
     from paper_1609_04567_gb300 import serve
-    reqs = serve.make_requests(0.4, 300.0, seed=3, denoise_sides=(32, 256), solve_sides=(16, 128), buckets=5)
+    reqs = serve.make_requests(0.4, rate, seed=3, denoise_sides=(32, 256), solve_sides=(16, 128), buckets=5)
     assert len(reqs) > 60
-    srv = serve.Server(max_slots=64, step_sweeps=8, solo_cells=solo_cells)
+    srv = serve.Server(max_slots=64, step_sweeps=8, solo_cells=solo_cells, light_solo=light_solo)
     n_solo = sum(srv.is_solo(r) for r in reqs)
     assert (n_solo > 5) == (solo_cells is not None)
     stats = srv.serve(reqs, keep_results=True)
     assert stats.completed == len(reqs)
-    assert stats.max_in_flight > 1                     # work really overlapped in the batch
+    assert stats.max_in_flight > 1                     # work really overlapped
+    lanes = [r.lane for r in srv.done]
+    if solo_cells is None and light_solo == 0:
+        assert set(lanes) == {"batch"}
+    else:
+        assert lanes.count("solo") > 5 and lanes.count("batch") > 5
     done = {r.rid: r for r in srv.done}
-    picks = list(done.values())[::7] + [r for r in done.values() if srv.is_solo(r)][:6]
+    picks = list(done.values())[::37] + [r for r in done.values() if r.lane == "solo"][:6] + \
+        [r for r in done.values() if r.lane == "batch"][:6]
     for r in picks:
         u_alone, res = solve_alone(gpu, r, srv)
         assert (r.iters, r.converged) == (res.iters, res.converged)

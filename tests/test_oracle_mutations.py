@@ -17,8 +17,8 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 # (name, exact text in slr_oracle.c, replacement)
 MUTATIONS = [
     ("J2D5 drops the east neighbour",
-     "            double s = ((uN + uS) + uW) + uE;",
-     "            double s = ((uN + uS) + uW);"),
+     "            double uE = at2_f64(u, nx, ny, i, j + 1, wrap, ghost);\n            double s = ((uN + uS) + uW) + uE;",
+     "            double uE = at2_f64(u, nx, ny, i, j + 1, wrap, ghost);\n            double s = ((uN + uS) + uW);"),
     ("J2D5 sigma term with the wrong sign",
      "    double hh = mesh_h(h, nx), h2 = hh * hh, d = 4.0 + sigma * h2;\n    size_t n = (size_t)(nx * ny);\n"
      "    double *v = (double *)malloc(n * sizeof(double));",
