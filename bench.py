@@ -733,12 +733,14 @@ def measure_jacobi(args):
     slr.load()
     peak, peak_src = measured_peaks()
     stream = torch.cuda.Stream()
-    # one sweep per HBM pass, and k = 8 sweeps per pass (temporal blocking) for 2D
+    # one sweep per HBM pass, and temporal blocking: k = 8 sweeps per pass in
+    # 2D, k = 4 in 3D
     cases = [("j2d5_8192x8192_f32", slr.SLR_J2D5, (8192, 8192), torch.float32, 200, 1),
              ("j2d5_8192x8192_bf16", slr.SLR_J2D5, (8192, 8192), torch.bfloat16, 200, 1),
              ("j3d7_512x512x512_bf16", slr.SLR_J3D7, (512, 512, 512), torch.bfloat16, 50, 1),
              ("j2d5_8192x8192_f32_k8", slr.SLR_J2D5, (8192, 8192), torch.float32, 200, 8),
-             ("j2d5_8192x8192_bf16_k8", slr.SLR_J2D5, (8192, 8192), torch.bfloat16, 200, 8)]
+             ("j2d5_8192x8192_bf16_k8", slr.SLR_J2D5, (8192, 8192), torch.bfloat16, 200, 8),
+             ("j3d7_512x512x512_bf16_k4", slr.SLR_J3D7, (512, 512, 512), torch.bfloat16, 48, 4)]
     out = {}
     rhs = {}                                       # the seeded f of each shape, generated once
     clocks = ClockSampler(torch.cuda.current_device())

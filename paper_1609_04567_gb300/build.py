@@ -17,7 +17,7 @@ CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libslr.so")
 INCLUDE = os.path.join(ROOT, "include")
-SOURCES = ["slr_api.cu", "life.cu", "life_tb.cu", "jacobi.cu", "jacobi_tb.cu", "restore.cu", "restore_tb.cu", "reduce.cu", "static_scratch.cu", "batch.cu", "dc.cu", "tune.cu", "selfcheck.cu", "detect.cu", "user.cu", "split.cu", "peak.cu"]
+SOURCES = ["slr_api.cu", "life.cu", "life_tb.cu", "jacobi.cu", "jacobi_tb.cu", "jacobi_tb3.cu", "restore.cu", "restore_tb.cu", "reduce.cu", "static_scratch.cu", "batch.cu", "dc.cu", "tune.cu", "selfcheck.cu", "detect.cu", "user.cu", "split.cu", "peak.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -507,9 +507,11 @@ size_t elem_bytes(int storage)
     }
 }
 
+}  // namespace
+
 // The ghost value as the tile holds it (storage form) must be the value the
 // update reads: exactly representable in the storage type.
-bool ghost_exact(const Problem &p)
+bool jacobi_tb_ghost_exact(const Problem &p)
 {
     const float g = p.ghostf;
     if (g != g) return false;
@@ -526,12 +528,11 @@ bool ghost_exact(const Problem &p)
     }
 }
 
-}  // namespace
-
 bool jacobi_tb_supported(const Problem &p, const void *a, const void *b, const void *f)
 {
+    if (p.stencil == SLR_J3D7) return jacobi_tb3_supported(p, a, b, f);
     const size_t es = elem_bytes(p.storage);
-    if (p.stencil != SLR_J2D5 || es == 0 || p.wrap || !ghost_exact(p)) return false;
+    if (p.stencil != SLR_J2D5 || es == 0 || p.wrap || !jacobi_tb_ghost_exact(p)) return false;
     if ((p.nx * (long long)es) % 16 != 0 || p.nx >= (1ll << 31) - 4096 || p.ny >= (1ll << 31) - 4096) return false;
     if (((uintptr_t)a | (uintptr_t)b | (uintptr_t)f) % 16 != 0) return false;
     return tma::encode_fn() != nullptr;
@@ -540,16 +541,18 @@ bool jacobi_tb_supported(const Problem &p, const void *a, const void *b, const v
 int jacobi_tb_resolve_k(const Problem &p, const void *a, const void *b, const void *f)
 {
     if (p.k == 1 || !jacobi_tb_supported(p, a, b, f)) return 1;
-    // the library's choice: 8 sweeps per pass unless a staging of the
-    // one-sweep kernel was asked for
-    if (p.k == 0) return p.tiling == SLR_TILING_AUTO ? kJacobiTbMaxK : 1;
-    return p.k > kJacobiTbMaxK ? kJacobiTbMaxK : p.k;
+    const bool d3 = p.stencil == SLR_J3D7;
+    const int most = d3 ? kJacobiTb3MaxK : kJacobiTbMaxK;
+    // the library's choice unless a staging of the one-sweep kernel was asked for
+    if (p.k == 0) return p.tiling == SLR_TILING_AUTO ? (d3 ? kJacobiTb3DefaultK : kJacobiTbMaxK) : 1;
+    return p.k > most ? most : p.k;
 }
 
 cudaError_t jacobi_tb_persistent(const Problem &p, LoopArgs la, cudaStream_t st)
 {
     const int K = jacobi_tb_resolve_k(p, la.a, la.b, la.aux);
     if (K < 2) return cudaErrorNotSupported;
+    if (p.stencil == SLR_J3D7) return jacobi_tb3_persistent(p, la, K, st);
     switch (p.storage) {
     case SLR_F32: return run_tb<float>(p, la, K, st);
     case SLR_BF16: return run_tb<__nv_bfloat16>(p, la, K, st);

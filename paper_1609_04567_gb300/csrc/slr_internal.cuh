@@ -393,11 +393,12 @@ cudaError_t jacobi_persistent(const Problem &p, LoopArgs la, cudaStream_t st);
 // side f takes the TMA path (forced: as for SLR_TILING_TMA, any grid size).
 bool jacobi_tma_ok(const Problem &p, const void *a, const void *b, const void *f, bool forced);
 cudaError_t jacobi_sweep(const Problem &p, const void *src, void *dst, const void *f, cudaStream_t st);
-// `lists`: the workspace area of restore_tb_list_bytes(nx, ny) bytes (16-byte aligned).
+// `lists`: the workspace area of restore_tb_list_bytes(nx, ny) bytes (256-byte aligned).
 cudaError_t restore_persistent(const Problem &p, LoopArgs la, void *lists, cudaStream_t st);
 // Temporal-blocked restoration (restore_tb.cu): k sweeps per pass over 64 x 64
-// tiles with an 8-pixel halo.  Supported for rows of whole 16-byte mask groups
-// (nx % 16 == 0) and 16-byte aligned arrays; resolve_k gives 1 (the one-sweep
+// tiles with an 8-pixel halo.  Supported for any width (rows that do not start
+// on 16-byte boundaries go through padded copies in `lists`' area) and, where
+// a buffer is read in place, 16-byte aligned arrays; resolve_k gives 1 (the one-sweep
 // kernels) for temporal_k 1, for a problem it does not accept, or for
 // temporal_k 0 with an explicit tiling; kRestoreTbDefaultK for temporal_k 0
 // with SLR_TILING_AUTO; else temporal_k capped at 8.

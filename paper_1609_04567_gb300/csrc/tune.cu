@@ -221,7 +221,7 @@ slr_status slr_tune(const slr_desc *d, const void *u, const void *aux, void *scr
     const bool tma = (d->stencil == SLR_RESTORE8 && slr::restore_tma_ok(p)) ||
                      (jacobi && slr::jacobi_tma_ok(p, ta, tb, aux, true));
 
-    const bool jacobi_tb = jacobi && d->stencil == SLR_J2D5 && slr::jacobi_tb_supported(p, ta, tb, aux);
+    const bool jacobi_tb = jacobi && slr::jacobi_tb_supported(p, ta, tb, aux);
     const bool restore_tb = d->stencil == SLR_RESTORE8 && slr::restore_tb_supported(p, ta, tb, aux);
 
     // What the default resolves to, so that equal configurations are timed once.
@@ -253,10 +253,11 @@ slr_status slr_tune(const slr_desc *d, const void *u, const void *aux, void *scr
         }
     }
     if (persistent && jacobi_tb && d->temporal_k == 0) {
-        // sweeps per pass of the 2D Jacobi: one (the one-sweep kernels), 4, 8
+        // sweeps per pass of the Jacobi: one (the one-sweep kernels), 4, 8 in
+        // 2D; one, 2, 4 in 3D
         const int def_k = resolved_k(base);
-        static const int ks[] = {1, 4, 8};
-        for (int k : ks) {
+        static const int ks2[] = {1, 4, 8}, ks3[] = {1, 2, 4};
+        for (int k : (d->stencil == SLR_J3D7 ? ks3 : ks2)) {
             if (k == def_k) continue;
             slr_desc c = base;
             c.temporal_k = k;
