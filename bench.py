@@ -58,11 +58,36 @@ KERNEL_SOURCES = ["paper_1609_04567_gb300/csrc/life.cu", "paper_1609_04567_gb300
                   "paper_1609_04567_gb300/csrc/slr_internal.cuh"]
 
 
+def strip_comments(src: str) -> str:
+    """C/C++ source without its comments and blank lines (string literals kept)."""
+    out, i, n = [], 0, len(src)
+    while i < n:
+        c = src[i]
+        if c == '"' or c == "'":
+            j = i + 1
+            while j < n and src[j] != c:
+                j += 2 if src[j] == "\\" else 1
+            out.append(src[i:j + 1])
+            i = j + 1
+        elif src.startswith("//", i):
+            j = src.find("\n", i)
+            i = n if j < 0 else j
+        elif src.startswith("/*", i):
+            j = src.find("*/", i + 2)
+            i = n if j < 0 else j + 2
+        else:
+            out.append(c)
+            i += 1
+    return "\n".join(l.rstrip() for l in "".join(out).splitlines() if l.strip())
+
+
 def kernel_hash() -> str:
+    """Hash of the dominant kernel's code (comments left out: editing one does
+    not invalidate the recorded ncu traffic)."""
     h = hashlib.sha256()
     for f in KERNEL_SOURCES:
-        with open(os.path.join(ROOT, f), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(ROOT, f), encoding="utf-8") as fh:
+            h.update(strip_comments(fh.read()).encode())
     return h.hexdigest()[:16]
 
 
