@@ -743,6 +743,27 @@ def measure_restore(args):
                                              "sample": "2 sweeps of the 4096x4096 frame"}}}
 
 
+def jacobi_case_of(name: str, slr, torch):
+    """A Jacobi grid named {j2d5|j3d7}_{side x side[ x side]}_{f32|bf16|f16}[_k{K}][_s{S}]:
+    stencil, shape (listed x first), storage, sweeps per pass (default 1) and
+    sweeps (default 200 in 2D, 50 in 3D)."""
+    parts = name.split("_")
+    stencil = {"j2d5": slr.SLR_J2D5, "j3d7": slr.SLR_J3D7}[parts[0]]
+    shape = tuple(int(v) for v in reversed(parts[1].split("x")))
+    dt = {"f32": torch.float32, "bf16": torch.bfloat16, "f16": torch.float16}[parts[2]]
+    k, sweeps = 1, 200 if len(shape) == 2 else 50
+    for extra in parts[3:]:
+        if extra[0] == "k":
+            k = int(extra[1:])
+        elif extra[0] == "s":
+            sweeps = int(extra[1:])
+        else:
+            raise ValueError(f"unknown field {extra!r} in {name!r}")
+    if (stencil == slr.SLR_J3D7) != (len(shape) == 3):
+        raise ValueError(f"{name!r}: the stencil does not match the shape")
+    return name, stencil, shape, dt, sweeps, k
+
+
 def run_jacobi(args):
     print(json.dumps(measure_jacobi(args)), flush=True)
     return 0
@@ -760,12 +781,10 @@ def measure_jacobi(args):
     stream = torch.cuda.Stream()
     # one sweep per HBM pass, and temporal blocking: k = 8 sweeps per pass in
     # 2D, k = 4 in 3D
-    cases = [("j2d5_8192x8192_f32", slr.SLR_J2D5, (8192, 8192), torch.float32, 200, 1),
-             ("j2d5_8192x8192_bf16", slr.SLR_J2D5, (8192, 8192), torch.bfloat16, 200, 1),
-             ("j3d7_512x512x512_bf16", slr.SLR_J3D7, (512, 512, 512), torch.bfloat16, 50, 1),
-             ("j2d5_8192x8192_f32_k8", slr.SLR_J2D5, (8192, 8192), torch.float32, 200, 8),
-             ("j2d5_8192x8192_bf16_k8", slr.SLR_J2D5, (8192, 8192), torch.bfloat16, 200, 8),
-             ("j3d7_512x512x512_bf16_k4", slr.SLR_J3D7, (512, 512, 512), torch.bfloat16, 48, 4)]
+    names = (args.jacobi_cases.split(",") if getattr(args, "jacobi_cases", "") else
+             ["j2d5_8192x8192_f32", "j2d5_8192x8192_bf16", "j3d7_512x512x512_bf16", "j2d5_8192x8192_f32_k8",
+              "j2d5_8192x8192_bf16_k8", "j3d7_512x512x512_bf16_k4_s48"])
+    cases = [jacobi_case_of(n, slr, torch) for n in names]
     out = {}
     rhs = {}                                       # the seeded f of each shape, generated once
     clocks = ClockSampler(torch.cuda.current_device())
@@ -1297,6 +1316,9 @@ def main():
                     help="serving: denoise jobs of at least this many pixels take the solo lane (0: none)")
     ap.add_argument("--light-solo", type=int, default=4,
                     help="serving: any request takes the solo lane while fewer than this many jobs are in it")
+    ap.add_argument("--jacobi-cases", default="",
+                    help="jacobi workload: comma-separated grids named {j2d5|j3d7}_{NxN[xN]}_{f32|bf16|f16}"
+                         "[_k{sweeps per pass}][_s{sweeps}] (default: the large grids)")
     ap.add_argument("--k", type=int, default=0, help="generations per HBM pass (0 = library choice)")
     ap.add_argument("--gens", type=int, default=2000,
                     help="generations per solve (the workload has 2000; shorter runs are for profiler captures "
