@@ -423,8 +423,7 @@ slr_status slr_block_sweep(const slr_desc *d, const slr_block *b, const void *sr
  * never the autotuner's cache, and debug_flags is ignored.
  *
  * The first call on each device looks up the array's device address (once per
- * device, with that device current); make that first call before any stream
- * capture begins.  The address is kept for the life of the process, so the
+ * device, with that device current).  The address is kept for the life of the process, so the
  * call must not be used on a device after a cudaDeviceReset of it.  Every
  * call shares the one array: each call clears the control block before it
  * starts, and calls whose GPU work overlaps (several streams or host threads
