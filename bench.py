@@ -603,6 +603,33 @@ def measure_helmholtz(args):
             r = s.result()
             s.close()
         res[name] = {"ms_per_solve": ms, "iters": r.iters, "gcell_per_s": n * n * r.iters / ms / 1e6}
+    # fixed sweeps (test off): the per-sweep cost at steady state, which the
+    # 26-sweep solve above hides behind its start-up
+    fixed = {}
+    fixed_sweeps = 1000
+    for name, loop in (("fused_device_loop", slr.SLR_LOOP_PERSISTENT), ("plain", slr.SLR_LOOP_HOST)):
+        with torch.cuda.stream(stream):
+            s = slr.Solver(slr.SLR_J2D5, u, f, stream=stream, tol=0.0, loop=loop)
+
+            def fstep():
+                u.zero_()
+                slr.slr_destroy(s.handle)
+                s.handle = slr.slr_create(s.desc, u.data_ptr(), f.data_ptr(),
+                                          s.ws.data_ptr() + ((-s.ws.data_ptr()) % 256),
+                                          slr.slr_workspace_size(s.desc), stream.cuda_stream)
+                s.run(fixed_sweeps)
+            fstep()
+            if loop == slr.SLR_LOOP_HOST:
+                t0 = time.perf_counter()
+                fstep()
+                torch.cuda.synchronize()
+                ms = (time.perf_counter() - t0) * 1e3
+            else:
+                ms = _stream_time(stream, fstep, 3, flush=l2_flush)
+            r = s.result(check=False)
+            s.close()
+        fixed[name] = {"ms": ms, "sweeps": r.iters, "us_per_sweep": ms * 1e3 / r.iters,
+                       "gcell_per_s": n * n * r.iters / ms / 1e6}
     # the same solve written as user elemental functions (compiled at run time,
     # host-driven loop): the cost of the general form next to the fixed one
     user_src = """
@@ -645,6 +672,8 @@ __device__ double slr_delta(slr_t a, slr_t b) { return fabs(a - b); }
             "l2": "device-loop solves: L2 flushed before each, outside its events",
             "fused": res["fused_device_loop"], "plain": res["plain"], "tuned": res.get("fused_tuned"),
             "user_functions": res["user_functions"], "tuner": tuned, "clocks": clk,
+            "fixed_1000_sweeps": dict(fixed, what="the convergence test off, 1000 sweeps: steady-state cost per "
+                                                  "sweep of the fused device loop and of the plain host-driven one"),
             "cpu_baseline": {"value": cpu_mt_ms, "unit": "ms", "cores": used, "kind": "oracle",
                              "sample": "full solve", "host_cores": cores,
                              "single_core": {"value": cpu_ms, "unit": "ms", "cores": 1, "kind": "oracle",
@@ -983,15 +1012,69 @@ def run_batch(args):
             s.close()
     torch.cuda.synchronize()
     seq_s = time.perf_counter() - t0
+    # the oracle on the host cores: the 2D grids of side <= 256 in order, each
+    # to the same stop, until about cpu_budget seconds are spent; the whole
+    # batch's CPU time projected from its rate at the batch's sweep counts
+    import oracle
+    cores = host_cores()
+    cpu_cells = cpu_s = 0.0
+    cpu_grids = 0
+    cpu_same = True
+    with oracle.threads(cores) as used:
+        for (f, u), it in zip(grids, its):
+            if u.dim() != 2 or u.shape[0] > 256:
+                continue
+            fo = f.float().cpu().numpy()
+            t0 = time.perf_counter()
+            _, rr = oracle.j2d5(np.zeros(fo.shape, dtype=np.float32), fo, tol=1e-6, max_iters=5000, storage="bf16")
+            cpu_s += time.perf_counter() - t0
+            cpu_cells += float(fo.size) * rr.iters
+            cpu_grids += 1
+            cpu_same = cpu_same and rr.iters == it
+            if cpu_s > args.cpu_budget:
+                break
+    cpu_rate = cpu_cells / cpu_s if cpu_s > 0 else float("nan")
+    cpu = {"value": cpu_rate / 1e9, "unit": "Gcell-updates/s", "cores": used, "kind": "oracle", "host_cores": cores,
+           "sample": f"{cpu_grids} 2D grids of side <= 256 in batch order, each to its stop ({cpu_s:.1f} s)",
+           "same_sweeps_as_gpu": cpu_same, "projected_s_whole_batch": upd / cpu_rate if cpu_s > 0 else None}
     line = {"workload": f"batch_512x2d_bf16_side64-1024_plus_{n3}^3_tol1e-6", "metric": "Gcell-updates/s",
             "unit": "Gcell-updates/s", "value": upd / batch_s / 1e9, "batch_s": batch_s,
             "sequential_s": seq_s, "sequential_gcell_per_s": upd / seq_s / 1e9, "same_iters": its == seq_its,
             "cell_updates": upd, "grids": len(grids), "max_sweeps": max(its), "min_sweeps": min(its),
             "converged": int(sum(conv)), "capped_at_5000": int(len(conv) - sum(conv)),
+            "cpu_baseline": cpu,
             "note": "bfloat16 storage can trap Jacobi in a +-1 ulp cycle that never meets tol; such grids stop at the cap"}
     print(json.dumps(line), flush=True)
     b.close()
     return 0
+
+
+def serve_oracle_sample(reqs, pool, budget_s: float):
+    """The oracle on the host cores serving the same mix: requests in arrival
+    order, each solved alone to its stop, until budget_s seconds are spent;
+    the mean service time and the request rate it implies."""
+    import numpy as np
+    import oracle
+    from paper_1609_04567_gb300 import serve
+    cores = host_cores()
+    spent, done, cells = 0.0, 0, 0.0
+    with oracle.threads(cores) as used:
+        for r in reqs:
+            host_u, host_aux = pool.get(r.kind, r.side)
+            t0 = time.perf_counter()
+            if r.kind == serve.KIND_DENOISE:
+                _, rr = oracle.restore8(host_u.numpy(), host_aux.numpy(), tol=1e-3, max_iters=5000)
+            else:
+                _, rr = oracle.j2d5(np.zeros((r.side, r.side)), host_aux.numpy(), tol=1e-6, max_iters=5000)
+            spent += time.perf_counter() - t0
+            done += 1
+            cells += float(r.side) * r.side * rr.iters
+            if spent > budget_s:
+                break
+    mean_ms = spent / max(done, 1) * 1e3
+    return {"value": 1e3 / mean_ms, "unit": "requests/s", "cores": used, "kind": "oracle", "host_cores": cores,
+            "sample": f"the first {done} requests of the mix in arrival order, each solved alone ({spent:.1f} s)",
+            "mean_service_ms": mean_ms, "gcell_per_s": cells / spent / 1e9 if spent > 0 else None}
 
 
 def measure_serve_short(args, seconds: float):
@@ -1010,6 +1093,7 @@ def measure_serve_short(args, seconds: float):
     st = srv.serve(reqs, warmup_s=1.0, time_limit_s=seconds * 6 + 30)
     clk = clocks.stop()
     srv.close()
+    cpu = serve_oracle_sample(reqs, srv.pool, budget_s=5.0)
     num = (lambda x: None if x != x else x)
     offered = sum(1 for r in reqs if r.arrival >= 1.0)
     return {"workload": f"serve_poisson{args.rate:g}rps_denoise256-4096_solve64-2048_{seconds:g}s",
@@ -1018,7 +1102,7 @@ def measure_serve_short(args, seconds: float):
             "offered_rps": args.rate, "offered_after_warmup": offered, "completed_after_warmup": st.measured,
             "requests": st.requests, "completed": st.completed, "wall_s": st.wall_s,
             "gcell_per_s": st.gcell_per_s, "max_queue": st.max_queue, "max_in_flight": st.max_in_flight,
-            "clocks": clk,
+            "clocks": clk, "cpu_baseline": cpu,
             "what": "latency = arrival to the poll that sees the request finished; every arrival is served"}
 
 
@@ -1138,6 +1222,7 @@ def run_serve(args):
                                   "light_solo jobs are in the lane, run to their stop on solvers of their own, "
                                   "one after another, beside the batch"},
             "latency_sample": st.measured,
+            "cpu_baseline": serve_oracle_sample(reqs, srv.pool, budget_s=5.0),
             "queue_alone": dict(fifo, what="the same arrivals, one request at a time in arrival order, each "
                                            "solved alone; p50/p99 over the served requests that arrived after "
                                            "the 1 s warm-up (latency_sample of them; null when none)")}
