@@ -100,8 +100,9 @@ __device__ __forceinline__ int ld_volatile_int(const int *p)
 }
 
 // Grid-wide barrier for a co-resident (cooperative) grid.  Thread 0 of each
-// CTA publishes the CTA's writes (bar.sync then a gpu-scope release), arrives,
-// and spins with acquire loads until `target` arrivals are counted.  The spin
+// CTA publishes the CTA's writes (bar.sync, then its arrival as a gpu-scope
+// release, which covers the writes the CTA barrier ordered before it), and
+// spins with acquire loads until `target` arrivals are counted.  The spin
 // is bounded by `limit_ns` of %globaltimer: on expiry it sets DEV_ERR_TIMEOUT
 // and every CTA returns false (and then leaves the kernel), so a missing CTA
 // can never hang the GPU.
@@ -111,7 +112,6 @@ __device__ __forceinline__ bool grid_barrier(Ctl *ctl, unsigned long long target
     __syncthreads();
     if (threadIdx.x == 0) {
         int ok = 1;
-        __threadfence();
         red_release_add(&ctl->bar, 1ull);
         const long long t0 = global_timer_ns();
         unsigned spins = 0;
