@@ -167,11 +167,16 @@ class Server:
     def is_solo(self, r: Request) -> bool:
         return self.solo_cells is not None and r.kind == KIND_DENOISE and r.side * r.side >= self.solo_cells
 
+    def takes_solo(self, r: Request) -> bool:
+        """The lane a request is admitted to: solo for large denoise jobs, and
+        for any request while fewer than light_solo jobs are in the solo lane."""
+        return self.is_solo(r) or len(self.solo) < self.light_solo
+
     def admit(self, r: Request, now: float) -> bool:
         need = footprint(r.kind, r.side)
         if len(self.active) + len(self.solo) >= self.max_slots or self.in_use + need > self.budget:
             return False
-        solo = self.is_solo(r) or len(self.solo) < self.light_solo
+        solo = self.takes_solo(r)
         if solo and len(self.solo) >= len(self.solo_streams):
             return False
         torch = self.torch

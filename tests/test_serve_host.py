@@ -53,6 +53,21 @@ def test_solo_lane_rule(solo_cells):
     assert not srv.is_solo(solve)                       # solves stay in the batch
 
 
+@pytest.mark.parametrize("light_solo,in_lane,expect", [(0, 0, False), (4, 0, True), (4, 3, True), (4, 4, False),
+                                                       (1, 1, False)])
+def test_light_load_routing(light_solo, in_lane, expect):
+    # any request takes the solo lane while it holds fewer than light_solo
+    # jobs; large denoise jobs take it whatever the lane holds
+    from paper_1609_04567_gb300 import serve
+    srv = object.__new__(serve.Server)                  # the rule needs no GPU state
+    srv.solo_cells, srv.light_solo = 1024 * 1024, light_solo
+    srv.solo = {i: None for i in range(in_lane)}
+    small = serve.Request(1, serve.KIND_SOLVE, 64, 0.0)
+    big = serve.Request(2, serve.KIND_DENOISE, 2048, 0.0)
+    assert srv.takes_solo(small) == expect
+    assert srv.takes_solo(big)
+
+
 def test_video_streams_are_seeded_permutations():
     # every round of a stream deals each distinct frame once; the same seed
     # gives the same stream
