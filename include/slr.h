@@ -313,9 +313,13 @@ const char *slr_version(void);
  * A batch holds up to max_instances independent loops (SLR_J2D5, SLR_J3D7 in
  * any storage, with or without FP64 defect correction, SLR_RESTORE8 in EXACT
  * math), each with its own grid, tolerance and iteration cap.  slr_batch_run
- * enqueues ONE cooperative launch that runs up to `sweeps` more steps of
- * every running instance with one grid barrier per step for the whole
- * batch: a step is one sweep, or for a defect-correction instance one phase
+ * enqueues the launches that run up to `sweeps` more steps of every running
+ * instance: the Jacobi instances of at most 32K cells (not defect
+ * correction) each on a thread-block cluster of 1-16 CTAs holding the grid in
+ * shared memory, one cluster barrier per sweep (one launch per cluster size,
+ * on side streams the batch's stream then waits for), and the others in ONE
+ * cooperative launch with one grid barrier per step for all of them: a step
+ * is one sweep, or for a defect-correction instance one phase
  * of its loop (the initial defect, one of its inner binary32 sweeps, or the
  * correction with its new defect; its test follows each correction and its
  * iteration count is the number of corrections).  An instance stops when its

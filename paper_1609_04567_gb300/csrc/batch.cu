@@ -28,6 +28,8 @@
 #include <string>
 #include <vector>
 
+#include <cooperative_groups.h>
+
 #include "crmath.cuh"
 #include "slr_internal.cuh"
 
@@ -40,7 +42,6 @@ constexpr int kMaxBatch = 1024;
 // Jacobi instances whose grid (two states and f in the compute type) fits the
 // CTA's staging area are run by one CTA, in shared memory, for all the sweeps
 // of a launch, with CTA barriers instead of the grid barrier.
-constexpr long long kLocalBytes = 8 * (long long)(64 + 2) * (16 + 2) * 8;   // the 8 warps' staging areas
 
 // One instance as the kernel sees it.  Host-written fields first; the kernel
 // writes the results at the end of a run (and value/count/converged when the
@@ -59,7 +60,8 @@ struct BInst {
     int parity;       // 0: current state in a, 1: in b
     int done;         // stopped (converged or capped)
     int converged;
-    int local;        // small Jacobi instance run whole by one CTA (see cta_local_run)
+    int cs;           // > 0: run by a thread-block cluster of cs CTAs (cluster_run), not in batch_kernel
+    int pad;
     double value;
     unsigned long long count;
     // defect correction
@@ -81,6 +83,39 @@ struct BatchArgs {
     int nblocks;
 };
 
+// Instances run by a thread-block cluster of their own (cluster_run).
+struct ClusterArgs {
+    BInst *inst;
+    const int *list;           // table indices of this launch's instances, one per cluster
+    int cs;                    // CTAs per cluster
+    long long sweeps;
+};
+
+// Jacobi instances of at most kMaxCluster * kClusterCells cells (not defect
+// correction) run on a cluster of cs CTAs, cs the power of two that gives
+// each CTA at most kClusterCells cells (see cluster_run)
+constexpr int kClusterCells = 2048;
+constexpr int kMaxCluster = 16;                 // beyond the portable 8: the kernel allows it
+constexpr int kClusterGroups = 5;               // cluster sizes 1, 2, 4, 8, 16
+constexpr size_t kClusterSmem = 200 * 1024;     // most shared memory a cluster CTA may take
+
+// The cluster size of an instance (0: not run by a cluster) and its CTAs' shared memory.
+size_t cluster_smem(const BInst &I, int cs)
+{
+    const long long planes = I.stencil == SLR_J3D7 ? I.nz : I.ny;
+    const long long pc = I.stencil == SLR_J3D7 ? I.nx * I.ny : I.nx;
+    return 16 + 3 * (size_t)((planes + cs - 1) / cs) * (size_t)pc * (I.storage == SLR_F64 ? 8 : 4);
+}
+int cluster_size(const BInst &I)
+{
+    if (I.stencil == SLR_RESTORE8 || I.dc) return 0;
+    const long long cells = I.nx * I.ny * I.nz;
+    int cs = 1;
+    while (cs < kMaxCluster && cells > (long long)cs * kClusterCells) cs <<= 1;
+    if (cells > (long long)cs * kClusterCells || cluster_smem(I, cs) > kClusterSmem) return 0;
+    return cs;
+}
+
 // ---- per-cell elemental functions (same order as jacobi.cu / restore.cu) -----
 template <class T> struct St;
 template <> struct St<double> {
@@ -88,12 +123,14 @@ template <> struct St<double> {
     __device__ static C ld(const void *p, long long i) { return __ldcg((const double *)p + i); }
     __device__ static C ldf(const void *p, long long i) { return __ldg((const double *)p + i); }
     __device__ static C put(void *p, long long i, C v) { ((double *)p)[i] = v; return v; }
+    __device__ static C rnd(C v) { return v; }
 };
 template <> struct St<float> {
     using C = float;
     __device__ static C ld(const void *p, long long i) { return __ldcg((const float *)p + i); }
     __device__ static C ldf(const void *p, long long i) { return __ldg((const float *)p + i); }
     __device__ static C put(void *p, long long i, C v) { ((float *)p)[i] = v; return v; }
+    __device__ static C rnd(C v) { return v; }
 };
 template <> struct St<__nv_bfloat16> {
     using C = float;
@@ -111,6 +148,7 @@ template <> struct St<__nv_bfloat16> {
         ((__nv_bfloat16 *)p)[i] = s;
         return __bfloat162float(s);
     }
+    __device__ static C rnd(C v) { return __bfloat162float(__float2bfloat16_rn(v)); }   // to storage and back
 };
 template <> struct St<__half> {
     using C = float;
@@ -128,6 +166,7 @@ template <> struct St<__half> {
         ((__half *)p)[i] = s;
         return __half2float(s);
     }
+    __device__ static C rnd(C v) { return __half2float(__float2half_rn(v)); }            // to storage and back
 };
 
 __device__ __forceinline__ double add_rn(double a, double b) { return __dadd_rn(a, b); }
@@ -479,72 +518,89 @@ __device__ __forceinline__ int find_running(const int *s_upref, int nrun, int u)
     return lo;
 }
 
-// A small Jacobi instance run whole by one CTA: the grid (both states and f,
-// in the compute type) is held in shared memory for all the sweeps of a
-// launch; each sweep updates every cell (the same operations in the same
-// order as jacobi_unit), takes a block max of |delta| and the instance's test,
-// so the instance stops at exactly the sweep it would stop at in the
-// batch-wide loop, with CTA barriers instead of grid barriers.  The final
-// state goes back to a (parity 0).  `smem` holds 3 * cells compute values.
+namespace cg = cooperative_groups;
+
+// A Jacobi instance run by one thread-block cluster of cs CTAs with the grid
+// in their shared memory: CTA r holds the rows (2D) or planes (3D)
+// [r * per, (r + 1) * per) of both states and of f, in the compute type.  A
+// sweep updates the CTA's own cells, reading neighbours held by the other
+// CTAs through distributed shared memory, with the same operations in the
+// same order as jacobi_unit; the CTA's max |delta| goes to a per-parity
+// shared word; one cluster barrier then makes the new states and the maxima
+// visible, and every CTA reads the cs maxima and takes the same decision, so
+// the CTAs stop together at the sweep the instance would stop at in the
+// batch-wide loop.  The final state goes back to a (parity 0).  No CTA
+// leaves before the others are done reading its shared memory.
 template <class T, int DIM>
-__device__ void cta_local_run(BInst &Ig, long long iters0, int par0, long long sweeps, unsigned char *smem)
+__device__ void cluster_run(BInst &Ig, int cs, long long sweeps, unsigned char *smem)
 {
     using C = typename St<T>::C;
+    cg::cluster_group cl = cg::this_cluster();
     __shared__ unsigned long long s_wmax[kBThreads / 32];
+    __shared__ unsigned long long s_cmax[2];
     __shared__ unsigned long long s_max;
-    const BInst I = Ig;                 // a private copy: the stores below cannot alias it
+    const BInst I = Ig;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int rank = (int)cl.block_rank();
     const C ghost = sizeof(C) == 8 ? (C)I.ghost : (C)I.ghostf;
     const C h2 = sizeof(C) == 8 ? (C)I.h2 : (C)I.h2f;
     const C d = sizeof(C) == 8 ? (C)I.d : (C)I.df;
-    const int nx = (int)I.nx, ny = (int)I.ny, nz = (int)I.nz, cells = nx * ny * nz;
-    C *buf0 = (C *)smem, *buf1 = buf0 + cells, *fs = buf1 + cells;
-    const void *cur0 = par0 ? I.b : I.a;
-    for (int c = tid; c < cells; c += kBThreads) {
-        buf0[c] = St<T>::ld(cur0, c);
-        fs[c] = St<T>::ldf(I.aux, c);
+    const int nx = (int)I.nx, ny = (int)I.ny, nz = (int)I.nz;
+    const int planes = DIM == 3 ? nz : ny, pc = DIM == 3 ? nx * ny : nx;   // partition unit and its cells
+    const int per = (planes + cs - 1) / cs;
+    const int p0 = min(rank * per, planes), p1 = min(p0 + per, planes);
+    const int own = (p1 - p0) * pc;
+    C *buf0 = (C *)smem, *buf1 = buf0 + (size_t)per * pc, *fs = buf1 + (size_t)per * pc;
+    const int par0 = I.parity;
+    const void *g0 = par0 ? I.b : I.a;
+    for (int c = tid; c < own; c += kBThreads) {
+        buf0[c] = St<T>::ld(g0, (long long)p0 * pc + c);
+        fs[c] = St<T>::ldf(I.aux, (long long)p0 * pc + c);
     }
-    __syncthreads();
-    auto get = [&](const C *u, int k, int i, int j) -> C {
+    cl.sync();                                        // every CTA's part is loaded
+    // cell (k, i, j) of buffer `b` wherever it is held (the ghost outside the grid)
+    auto get = [&](int b, int k, int i, int j) -> C {
         if (i < 0 || i >= ny || j < 0 || j >= nx || k < 0 || k >= nz) {
             if (!I.wrap) return ghost;
             i = i < 0 ? i + ny : (i >= ny ? i - ny : i);
             j = j < 0 ? j + nx : (j >= nx ? j - nx : j);
             k = k < 0 ? k + nz : (k >= nz ? k - nz : k);
         }
-        return u[(k * ny + i) * nx + j];
+        const int pl = DIM == 3 ? k : i, r = pl / per;
+        const int off = DIM == 3 ? ((k - r * per) * ny + i) * nx + j : (i - r * per) * nx + j;
+        C *base = b ? buf1 : buf0;
+        if (r == rank) return base[off];
+        return cl.map_shared_rank(base, r)[off];
     };
-    long long it = iters0;
+    long long it = I.iters;
     int cur = 0;
     bool stop = false;
     Decision dcs;
     dcs.value = 0.0; dcs.count = 0ull; dcs.changed = 0; dcs.converged = 0;
-    const int rows = ny * nz;
     for (long long s = 0; s < sweeps && !stop; ++s) {
-        const C *u = cur ? buf1 : buf0;
         C *v = cur ? buf0 : buf1;
+        const C *u = cur ? buf1 : buf0;
         typename MaxBits<C>::type mx = 0;
-        for (int row = warp; row < rows; row += kBThreads / 32) {
-            const int k = row / ny, i = row - k * ny;
-            for (int j = lane; j < nx; j += 32) {
-                const int idx = (k * ny + i) * nx + j;
-                const C uc = u[idx];
-                C sum;
-                if (DIM == 2) {
-                    sum = add_rn(add_rn(add_rn(get(u, k, i - 1, j), get(u, k, i + 1, j)), get(u, k, i, j - 1)),
-                                 get(u, k, i, j + 1));
-                } else {
-                    sum = add_rn(add_rn(add_rn(add_rn(add_rn(get(u, k, i, j - 1), get(u, k, i, j + 1)),
-                                                      get(u, k, i - 1, j)), get(u, k, i + 1, j)),
-                                        get(u, k - 1, i, j)), get(u, k + 1, i, j));
-                }
-                const C tt = mul_rn(h2, fs[idx]);
-                // the value rounded to the storage type, widened back (exact)
-                T stv;
-                const C stored = St<T>::put(&stv, 0, div_rn(add_rn(tt, sum), d));
-                v[idx] = stored;
-                max_bits(mx, sub_rn(stored, uc));
+        for (int c = tid; c < own; c += kBThreads) {
+            const int lp = c / pc, w = c - lp * pc;
+            const int k = DIM == 3 ? p0 + lp : 0;
+            const int i = DIM == 3 ? w / nx : p0 + lp;
+            const int j = DIM == 3 ? w - i * nx : w;
+            const C uc = u[c];
+            C sum;
+            if (DIM == 2) {
+                sum = add_rn(add_rn(add_rn(get(cur, k, i - 1, j), get(cur, k, i + 1, j)), get(cur, k, i, j - 1)),
+                             get(cur, k, i, j + 1));
+            } else {
+                sum = add_rn(add_rn(add_rn(add_rn(add_rn(get(cur, k, i, j - 1), get(cur, k, i, j + 1)),
+                                                  get(cur, k, i - 1, j)), get(cur, k, i + 1, j)),
+                                    get(cur, k - 1, i, j)), get(cur, k + 1, i, j));
             }
+            const C tt = mul_rn(h2, fs[c]);
+            // the value rounded to the storage type, widened back (exact)
+            const C stored = St<T>::rnd(div_rn(add_rn(tt, sum), d));
+            v[c] = stored;
+            max_bits(mx, sub_rn(stored, uc));
         }
         unsigned long long m = widen_bits(mx);
 #pragma unroll
@@ -553,10 +609,19 @@ __device__ void cta_local_run(BInst &Ig, long long iters0, int par0, long long s
             m = t > m ? t : m;
         }
         if (lane == 0) s_wmax[warp] = m;
-        __syncthreads();                             // the sweep's values are visible to the CTA
+        __syncthreads();
         if (tid == 0) {
             unsigned long long b = 0ull;
-            for (int w = 0; w < kBThreads / 32; ++w) b = s_wmax[w] > b ? s_wmax[w] : b;
+            for (int x = 0; x < kBThreads / 32; ++x) b = s_wmax[x] > b ? s_wmax[x] : b;
+            s_cmax[s & 1] = b;
+        }
+        cl.sync();                                    // the new states and the CTAs' maxima
+        if (tid == 0) {
+            unsigned long long b = 0ull;
+            for (int r = 0; r < cs; ++r) {
+                const unsigned long long x = *cl.map_shared_rank(&s_cmax[s & 1], r);
+                b = x > b ? x : b;
+            }
             s_max = b;
         }
         __syncthreads();
@@ -568,11 +633,11 @@ __device__ void cta_local_run(BInst &Ig, long long iters0, int par0, long long s
         it += 1;
         cur ^= 1;
         stop = dcs.converged || it >= I.max_iters;
-        __syncthreads();                             // s_max is read before the next sweep writes it
+        __syncthreads();                              // s_max is read before the next sweep writes it
     }
     const C *fin = cur ? buf1 : buf0;
-    for (int c = tid; c < cells; c += kBThreads) St<T>::put(I.a, c, fin[c]);
-    if (tid == 0) {
+    for (int c = tid; c < own; c += kBThreads) St<T>::put(I.a, (long long)p0 * pc + c, fin[c]);
+    if (rank == 0 && tid == 0) {
         Ig.iters = it;
         Ig.parity = 0;
         Ig.done = stop;
@@ -582,26 +647,22 @@ __device__ void cta_local_run(BInst &Ig, long long iters0, int par0, long long s
             Ig.converged = dcs.converged;
         }
     }
-    __syncthreads();                                 // the shared grid is free for the next instance
+    cl.sync();                                        // the others' last reads of this CTA's memory are done
 }
 
-__device__ void cta_local_dispatch(BInst &I, long long iters0, int par0, long long sweeps, unsigned char *smem)
+__global__ void __launch_bounds__(kBThreads) batch_cluster_kernel(ClusterArgs ca)
 {
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char *smem = align_up(smem_raw, 16);
+    BInst &I = ca.inst[ca.list[blockIdx.x / ca.cs]];
     const bool d3 = I.stencil == SLR_J3D7;
     switch (I.storage) {
-    case SLR_F64:
-        d3 ? cta_local_run<double, 3>(I, iters0, par0, sweeps, smem) : cta_local_run<double, 2>(I, iters0, par0, sweeps, smem);
-        break;
-    case SLR_F32:
-        d3 ? cta_local_run<float, 3>(I, iters0, par0, sweeps, smem) : cta_local_run<float, 2>(I, iters0, par0, sweeps, smem);
-        break;
+    case SLR_F64: d3 ? cluster_run<double, 3>(I, ca.cs, ca.sweeps, smem) : cluster_run<double, 2>(I, ca.cs, ca.sweeps, smem); break;
+    case SLR_F32: d3 ? cluster_run<float, 3>(I, ca.cs, ca.sweeps, smem) : cluster_run<float, 2>(I, ca.cs, ca.sweeps, smem); break;
     case SLR_BF16:
-        d3 ? cta_local_run<__nv_bfloat16, 3>(I, iters0, par0, sweeps, smem)
-           : cta_local_run<__nv_bfloat16, 2>(I, iters0, par0, sweeps, smem);
+        d3 ? cluster_run<__nv_bfloat16, 3>(I, ca.cs, ca.sweeps, smem) : cluster_run<__nv_bfloat16, 2>(I, ca.cs, ca.sweeps, smem);
         break;
-    default:
-        d3 ? cta_local_run<__half, 3>(I, iters0, par0, sweeps, smem) : cta_local_run<__half, 2>(I, iters0, par0, sweeps, smem);
-        break;
+    default: d3 ? cluster_run<__half, 3>(I, ca.cs, ca.sweeps, smem) : cluster_run<__half, 2>(I, ca.cs, ca.sweeps, smem); break;
     }
 }
 
@@ -626,26 +687,12 @@ __global__ void __launch_bounds__(kBThreads, 2) batch_kernel(BatchArgs ba)
         s_iters0[i] = I.iters;
         s_phase0[i] = I.phase;
         s_par0[i] = (unsigned char)I.parity;
-        s_stop[i] = I.done ? -2 : (I.local ? -3 : -1);   // -3: run by one CTA below
+        s_stop[i] = I.done ? -2 : -1;
         s_units[i] = (int)I.units;
     }
     __syncthreads();
     int nrun = compact_running(n, s_stop, s_units, s_aidx, s_upref);
-    // the small instances get CTAs of their own (the highest indices), which
-    // run them concurrently with the batch-wide loop of the other CTAs; every
-    // CTA counts them alike
-    int nlocal = 0;
-    for (int i = 0; i < n; ++i) nlocal += s_stop[i] == -3;
-    const int nloc = nlocal == 0 ? 0 : (nrun == 0 ? (int)gridDim.x : min(nlocal, (int)gridDim.x / 2));
-    const int G = (int)gridDim.x - nloc;               // CTAs of the batch-wide loop
-    if ((int)blockIdx.x >= G) {
-        for (int i = 0, q = 0; i < n; ++i) {
-            if (s_stop[i] != -3) continue;
-            if (q++ % nloc != (int)blockIdx.x - G) continue;
-            cta_local_dispatch(ba.inst[ba.act[i]], s_iters0[i], s_par0[i], ba.sweeps, smem_raw);
-        }
-        return;
-    }
+    const int G = (int)gridDim.x;                      // CTAs of the batch-wide loop
     // warps interleave across CTAs so that consecutive units land on different SMs
     const int warps = G * (kBThreads / 32);
     const int gw = (tid >> 5) * G + (int)blockIdx.x;
@@ -746,7 +793,7 @@ __global__ void __launch_bounds__(kBThreads, 2) batch_kernel(BatchArgs ba)
     // results (CTA 0) and the write-back of stopped instances whose state is in b
     if (blockIdx.x == 0) {
         for (int i = tid; i < n; i += kBThreads) {
-            if (s_stop[i] == -2 || s_stop[i] == -3) continue;
+            if (s_stop[i] == -2) continue;
             BInst &I = ba.inst[ba.act[i]];
             const long long done_sweeps = s_stop[i] >= 0 ? s_stop[i] + 1 : ran;
             if (I.dc) {
@@ -788,6 +835,17 @@ struct slr_batch_ctx {
     std::vector<int> reported;   // finished and already returned by poll
     std::string err;
     bool dirty;                  // host mirror newer than the device table
+    // side streams of the cluster launches (one per cluster size, created on
+    // first use) and their completion events, which `stream` waits for
+    cudaStream_t side[slr::kClusterGroups] = {};
+    cudaEvent_t done[slr::kClusterGroups] = {};
+    ~slr_batch_ctx()
+    {
+        for (int i = 0; i < slr::kClusterGroups; ++i) {
+            if (done[i]) cudaEventDestroy(done[i]);
+            if (side[i]) cudaStreamDestroy(side[i]);
+        }
+    }
 };
 
 namespace {
@@ -906,8 +964,8 @@ slr_status slr_batch_add(slr_batch b, const slr_desc *d, void *u, const void *au
     I.tiles_x = (p.nx + slr::kTileW - 1) / slr::kTileW;
     I.tiles_y = (p.ny + slr::kTileH - 1) / slr::kTileH;
     I.units = I.tiles_x * I.tiles_y * p.nz;
-    I.local = p.stencil != SLR_RESTORE8 && !d->defect_correction &&
-              3 * p.nx * p.ny * p.nz * (p.storage == SLR_F64 ? 8 : 4) <= slr::kLocalBytes;
+    I.dc = d->defect_correction ? 1 : 0;
+    I.cs = slr::cluster_size(I);
     if (d->defect_correction) {
         const size_t blk = rup((size_t)p.nx * (size_t)p.ny * (size_t)p.nz * 4, 256);
         unsigned char *f32 = (unsigned char *)scratch + rup(p.state_bytes, 256);
@@ -948,14 +1006,22 @@ slr_status slr_batch_run(slr_batch b, int64_t sweeps)
         slr_status st = sync_mirror(b);
         if (st != SLR_OK) return st;
     }
-    std::vector<int> act;
+    // the running instances: the batch-wide launch's, then those run by
+    // clusters, grouped by cluster size (1, 2, 4, 8, 16), all in one list
+    std::vector<int> act, grp[slr::kClusterGroups];
     std::vector<long long> prefix(1, 0);
     for (int i = 0; i < b->max_inst; ++i) {
         const BInst &I = b->inst[(size_t)i];
         if (!b->used[(size_t)i] || I.done || I.iters >= I.max_iters) continue;
-        act.push_back(i);
-        prefix.push_back(prefix.back() + I.units);
+        if (I.cs) {
+            grp[__builtin_ctz((unsigned)I.cs)].push_back(i);
+        } else {
+            act.push_back(i);
+            prefix.push_back(prefix.back() + I.units);
+        }
     }
+    const size_t nact = act.size();
+    for (auto &g : grp) act.insert(act.end(), g.begin(), g.end());
     cudaError_t e = cudaMemcpyAsync(b->ws + off_inst(), b->inst.data(), (size_t)b->max_inst * sizeof(BInst),
                                     cudaMemcpyHostToDevice, b->stream);
     b->dirty = false;
@@ -978,10 +1044,54 @@ slr_status slr_batch_run(slr_batch b, int64_t sweeps)
     ba.slots = (slr::Slot *)(b->ws + off_slots(b->max_inst));
     ba.act = (const int *)(b->ws + off_act(b->max_inst));
     ba.prefix = (const long long *)(b->ws + off_prefix(b->max_inst));
-    ba.nact = (int)act.size();
+    ba.nact = (int)nact;
     ba.sweeps = sweeps;
     ba.ctl = (slr::Ctl *)b->ws;
     ba.limit_ns = 2000000000ll;
+    // the clusters' instances: one launch per cluster size, each on a side
+    // stream of its own so that they run together (the staging above is
+    // complete: the stream was synchronised); the batch-wide launch follows on
+    // `stream` once they are all done
+    size_t off = nact;
+    for (int gi = 0; gi < slr::kClusterGroups; ++gi) {
+        const size_t ng = grp[gi].size();
+        if (ng == 0) continue;
+        if (!b->side[gi]) {
+            e = cudaStreamCreateWithFlags(&b->side[gi], cudaStreamNonBlocking);
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->done[gi], cudaEventDisableTiming);
+            if (e != cudaSuccess) return bcuda(b, e, "cluster stream");
+        }
+        slr::ClusterArgs ca;
+        ca.inst = ba.inst;
+        ca.list = ba.act + off;
+        ca.cs = 1 << gi;
+        ca.sweeps = sweeps;
+        size_t csm = 0;
+        for (int i : grp[gi]) csm = std::max(csm, slr::cluster_smem(b->inst[(size_t)i], ca.cs));
+        off += ng;
+        e = cudaFuncSetAttribute(slr::batch_cluster_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)csm);
+        if (e == cudaSuccess && ca.cs > 8)
+            e = cudaFuncSetAttribute(slr::batch_cluster_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        if (e != cudaSuccess) return bcuda(b, e, "cluster kernel attributes");
+        cudaLaunchConfig_t cfg;
+        memset(&cfg, 0, sizeof(cfg));
+        cfg.gridDim = dim3((unsigned)(ng * (size_t)ca.cs));
+        cfg.blockDim = dim3(slr::kBThreads);
+        cfg.dynamicSmemBytes = csm;
+        cfg.stream = b->side[gi];
+        cudaLaunchAttribute attr;
+        attr.id = cudaLaunchAttributeClusterDimension;
+        attr.val.clusterDim.x = (unsigned)ca.cs;
+        attr.val.clusterDim.y = 1;
+        attr.val.clusterDim.z = 1;
+        cfg.attrs = &attr;
+        cfg.numAttrs = 1;
+        e = cudaLaunchKernelEx(&cfg, slr::batch_cluster_kernel, ca);
+        if (e == cudaSuccess) e = cudaEventRecord(b->done[gi], b->side[gi]);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(b->stream, b->done[gi], 0);
+        if (e != cudaSuccess) return bcuda(b, e, "cluster kernel launch");
+    }
+    if (nact == 0) return SLR_OK;
     const size_t smem = (size_t)(slr::kBThreads / 32) * slr::kStageBytesPerWarp + (size_t)ba.nact * 16 +
                         (size_t)ba.nact * 4 * 4 + 4 + (size_t)ba.nact;
     e = cudaFuncSetAttribute(slr::batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
