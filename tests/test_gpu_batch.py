@@ -209,3 +209,33 @@ def test_defect_correction_in_short_runs_while_others_join(gpu, orc):
         assert (r.iters, r.converged, r.value) == (rr.iters, rr.converged, rr.value)
         assert np.array_equal(state(inst).view(np.uint64), ref.view(np.uint64))
     b.close()
+
+
+def test_cluster_sizes_and_partitions_match_the_oracle(gpu, orc):
+    # Jacobi grids of at most 32K cells run on thread-block clusters of 1-16
+    # CTAs (2048 cells a CTA at most), split into row blocks (2D) or z-slabs
+    # (3D): clusters of 16, 8, 4 and 2; fewer rows or planes than CTAs (some
+    # CTAs hold nothing); a periodic 3D grid; and a single row too long for one
+    # CTA's shared memory, which stays in the batch-wide loop
+    mix = [
+        (jacobi_instance((150, 150), "bf16", 31, tol=1e-6), 700),          # 16 CTAs
+        (jacobi_instance((181, 181), "f32", 32, tol=1e-7), 400),           # 16 CTAs
+        (jacobi_instance((127, 129), "f16", 33, tol=1e-6), 900),           # 8 CTAs
+        (jacobi_instance((3, 40, 48), "f32", 34, tol=1e-7), 2000),         # 4 CTAs, 3 planes
+        (jacobi_instance((6, 20, 30), "f64", 35, tol=1e-9, boundary=1), 3000),
+        (jacobi_instance((2, 4000), "f32", 36, tol=1e-7), 2000),           # 4 CTAs, 2 rows
+        (jacobi_instance((1, 32768), "f32", 37, tol=1e-7), 50),            # no cluster
+    ]
+    b = gpu.Batch(len(mix))
+    slots = [add(gpu, b, inst, cap) for inst, cap in mix]
+    b.run(100000)
+    b.poll()
+    for (inst, cap), s in zip(mix, slots):
+        r = b.result(s)
+        ref, rr = oracle_of(orc, inst, cap)
+        assert (r.iters, r.converged) == (rr.iters, rr.converged), (inst["shape"], r, rr)
+        out = inst["u"].float().cpu().numpy() if inst["storage"] in ("bf16", "f16") else inst["u"].cpu().numpy()
+        assert np.array_equal(out.view(np.uint64 if out.dtype == np.float64 else np.uint32),
+                              ref.view(np.uint64 if ref.dtype == np.float64 else np.uint32)), inst["shape"]
+        assert r.value == rr.value
+    b.close()
