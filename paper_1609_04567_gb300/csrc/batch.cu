@@ -91,9 +91,10 @@ struct ClusterArgs {
     long long sweeps;
 };
 
-// Jacobi instances of at most kMaxCluster * kClusterCells cells (not defect
-// correction) run on a cluster of cs CTAs, cs the power of two that gives
-// each CTA at most kClusterCells cells (see cluster_run)
+// Jacobi instances (with or without defect correction) of at most
+// kMaxCluster * kClusterCells cells run on a cluster of cs CTAs, cs the power
+// of two that gives each CTA at most kClusterCells cells (see cluster_run and
+// cluster_dc_run)
 constexpr int kClusterCells = 2048;
 constexpr int kMaxCluster = 16;                 // beyond the portable 8: the kernel allows it
 constexpr int kClusterGroups = 5;               // cluster sizes 1, 2, 4, 8, 16
@@ -104,11 +105,12 @@ size_t cluster_smem(const BInst &I, int cs)
 {
     const long long planes = I.stencil == SLR_J3D7 ? I.nz : I.ny;
     const long long pc = I.stencil == SLR_J3D7 ? I.nx * I.ny : I.nx;
-    return 16 + 3 * (size_t)((planes + cs - 1) / cs) * (size_t)pc * (I.storage == SLR_F64 ? 8 : 4);
+    // Jacobi: both states and f in the compute type; defect correction: r32, e0, e1
+    return 16 + 3 * (size_t)((planes + cs - 1) / cs) * (size_t)pc * (I.storage == SLR_F64 && !I.dc ? 8 : 4);
 }
 int cluster_size(const BInst &I)
 {
-    if (I.stencil == SLR_RESTORE8 || I.dc) return 0;
+    if (I.stencil == SLR_RESTORE8) return 0;
     const long long cells = I.nx * I.ny * I.nz;
     int cs = 1;
     while (cs < kMaxCluster && cells > (long long)cs * kClusterCells) cs <<= 1;
@@ -650,12 +652,157 @@ __device__ void cluster_run(BInst &Ig, int cs, long long sweeps, unsigned char *
     cl.sync();                                        // the others' last reads of this CTA's memory are done
 }
 
+// A defect-correction instance run by one thread-block cluster, phase by
+// phase as dc_unit runs it in the batch-wide loop (the same operations in the
+// same order): the binary32 defect r32 and the corrections e0, e1 of the
+// CTA's rows or planes live in its shared memory for the launch (loaded at
+// its start and stored at its end, so that a later launch resumes at the same
+// phase), the binary64 state and f in global memory.  One cluster barrier per
+// phase orders both; the scaled defect's maximum is taken over the cluster at
+// the correction phases, where the test runs.
+template <int DIM>
+__device__ void cluster_dc_run(BInst &Ig, int cs, long long sweeps, unsigned char *smem)
+{
+    cg::cluster_group cl = cg::this_cluster();
+    __shared__ unsigned long long s_wmax[kBThreads / 32];
+    __shared__ unsigned long long s_cmax[2];
+    __shared__ unsigned long long s_max;
+    const BInst I = Ig;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int rank = (int)cl.block_rank();
+    const int nx = (int)I.nx, ny = (int)I.ny, nz = (int)I.nz;
+    const int planes = DIM == 3 ? nz : ny, pc = DIM == 3 ? nx * ny : nx;
+    const int per = (planes + cs - 1) / cs;
+    const int p0 = min(rank * per, planes), p1 = min(p0 + per, planes);
+    const int own = (p1 - p0) * pc;
+    const long long base = (long long)p0 * pc;
+    float *sr = (float *)smem, *se0 = sr + (size_t)per * pc, *se1 = se0 + (size_t)per * pc;
+    for (int c = tid; c < own; c += kBThreads) {
+        sr[c] = __ldcg(I.r32 + base + c);
+        se0[c] = __ldcg(I.e0 + base + c);
+        se1[c] = __ldcg(I.e1 + base + c);
+    }
+    cl.sync();
+    // cell (k, i, j) of one of the shared arrays, wherever it is held
+    auto at = [&](float *arr, long long k, long long i, long long j) -> float {
+        const int pl = (int)(DIM == 3 ? k : i), r = pl / per;
+        const int off = DIM == 3 ? (int)(((k - r * per) * ny + i) * nx + j) : (int)((i - r * per) * nx + j);
+        if (r == rank) return arr[off];
+        return cl.map_shared_rank(arr, r)[off];
+    };
+    const long long P = I.inner + 1, q0 = I.phase;
+    const float *ec = (I.inner & 1) ? se1 : se0;            // e after the inner sweeps
+    bool stop = false;
+    long long s = 0;
+    Decision dcs;
+    dcs.value = 0.0; dcs.count = 0ull; dcs.changed = 0; dcs.converged = 0;
+    for (; s < sweeps && !stop; ++s) {
+        const long long q = q0 + s;
+        const long long n = q >= 1 ? (q - 1) / P : 0;
+        const int ph = q >= 1 ? (int)((q - 1) % P) : -1;
+        const double *uo = (const double *)((n & 1) ? I.b : I.a);
+        double *un = (double *)((n & 1) ? I.a : I.b);
+        float *es = (ph & 1) ? se1 : se0;
+        float *ed = (ph & 1) ? se0 : se1;
+        unsigned long long mx = 0ull;
+        for (int c = tid; c < own; c += kBThreads) {
+            const int lp = c / pc, w = c - lp * pc;
+            const long long k = DIM == 3 ? p0 + lp : 0;
+            const long long i = DIM == 3 ? w / nx : p0 + lp;
+            const long long j = DIM == 3 ? w - (w / nx) * nx : w;
+            const long long idx = base + c;
+            if (ph < 0) {
+                const double rv = dc_defect<DIM>(I, k, i, j, [&](long long z, long long y, long long x) {
+                    return dc_outside(I, z, y, x) ? 0.0 : __ldcg(uo + (z * I.ny + y) * I.nx + x);
+                });
+                sr[c] = (float)rv;
+            } else if (ph < I.inner) {
+                float sn = 0.0f;
+                if (ph > 0)
+                    sn = dc_sum<DIM, float>(k, i, j, [&](long long z, long long y, long long x) {
+                        return dc_outside(I, z, y, x) ? 0.0f : at(es, z, y, x);
+                    });
+                const float t = __fmul_rn(I.h2f, sr[c]);
+                ed[c] = __fdiv_rn(__fadd_rn(t, sn), I.df);
+            } else {
+                un[idx] = __dadd_rn(__ldcg(uo + idx), (double)ec[c]);
+                const double rv = dc_defect<DIM>(I, k, i, j, [&](long long z, long long y, long long x) {
+                    if (dc_outside(I, z, y, x)) return 0.0;
+                    return __dadd_rn(__ldcg(uo + (z * I.ny + y) * I.nx + x), (double)at((float *)ec, z, y, x));
+                });
+                sr[c] = (float)rv;
+                const unsigned long long b =
+                    (unsigned long long)__double_as_longlong(fabs(__ddiv_rn(__dmul_rn(I.h2, rv), I.d)));
+                mx = b > mx ? b : mx;
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const unsigned long long t = __shfl_xor_sync(0xffffffffu, mx, o);
+            mx = t > mx ? t : mx;
+        }
+        if (lane == 0) s_wmax[warp] = mx;
+        __syncthreads();
+        if (tid == 0) {
+            unsigned long long b = 0ull;
+            for (int x = 0; x < kBThreads / 32; ++x) b = s_wmax[x] > b ? s_wmax[x] : b;
+            s_cmax[s & 1] = b;
+        }
+        cl.sync();                                    // this phase's values (shared and global) everywhere
+        const bool tested = q >= 1 && ph == I.inner;
+        if (tested) {
+            if (tid == 0) {
+                unsigned long long b = 0ull;
+                for (int r = 0; r < cs; ++r) {
+                    const unsigned long long x = *cl.map_shared_rank(&s_cmax[s & 1], r);
+                    b = x > b ? x : b;
+                }
+                s_max = b;
+            }
+            __syncthreads();
+            Slot sl;
+            memset(&sl, 0, sizeof(sl));
+            sl.maxbits = s_max;
+            dcs = decide(I.reduce, sl, I.tol);
+            stop = dcs.converged || dc_corrections(I, q + 1) >= I.max_iters;
+            __syncthreads();                          // s_max is read before it is written again
+        }
+    }
+    const long long phase = q0 + s;
+    const long long iters = dc_corrections(I, phase);
+    for (int c = tid; c < own; c += kBThreads) {
+        I.r32[base + c] = sr[c];
+        I.e0[base + c] = se0[c];
+        I.e1[base + c] = se1[c];
+    }
+    if (stop && (iters & 1)) {
+        // the final state is in b: into a
+        for (int c = tid; c < own; c += kBThreads) ((double *)I.a)[base + c] = __ldcg((const double *)I.b + base + c);
+    }
+    if (rank == 0 && tid == 0) {
+        Ig.phase = phase;
+        Ig.iters = iters;
+        Ig.parity = stop ? 0 : (int)(iters & 1);
+        Ig.done = stop;
+        if (stop) {
+            Ig.value = dcs.value;
+            Ig.count = dcs.count;
+            Ig.converged = dcs.converged;
+        }
+    }
+    cl.sync();                                        // the others' last reads of this CTA's memory are done
+}
+
 __global__ void __launch_bounds__(kBThreads) batch_cluster_kernel(ClusterArgs ca)
 {
     extern __shared__ unsigned char smem_raw[];
     unsigned char *smem = align_up(smem_raw, 16);
     BInst &I = ca.inst[ca.list[blockIdx.x / ca.cs]];
     const bool d3 = I.stencil == SLR_J3D7;
+    if (I.dc) {
+        d3 ? cluster_dc_run<3>(I, ca.cs, ca.sweeps, smem) : cluster_dc_run<2>(I, ca.cs, ca.sweeps, smem);
+        return;
+    }
     switch (I.storage) {
     case SLR_F64: d3 ? cluster_run<double, 3>(I, ca.cs, ca.sweeps, smem) : cluster_run<double, 2>(I, ca.cs, ca.sweeps, smem); break;
     case SLR_F32: d3 ? cluster_run<float, 3>(I, ca.cs, ca.sweeps, smem) : cluster_run<float, 2>(I, ca.cs, ca.sweeps, smem); break;
