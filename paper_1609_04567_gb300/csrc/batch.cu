@@ -568,10 +568,12 @@ __device__ void cluster_run(BInst &Ig, int cs, long long sweeps, unsigned char *
             j = j < 0 ? j + nx : (j >= nx ? j - nx : j);
             k = k < 0 ? k + nz : (k >= nz ? k - nz : k);
         }
-        const int pl = DIM == 3 ? k : i, r = pl / per;
-        const int off = DIM == 3 ? ((k - r * per) * ny + i) * nx + j : (i - r * per) * nx + j;
+        const int pl = DIM == 3 ? k : i;
         C *base = b ? buf1 : buf0;
-        if (r == rank) return base[off];
+        if (pl >= p0 && pl < p1)                     // held by this CTA: no division
+            return base[DIM == 3 ? ((k - p0) * ny + i) * nx + j : (i - p0) * nx + j];
+        const int r = pl / per;
+        const int off = DIM == 3 ? ((k - r * per) * ny + i) * nx + j : (i - r * per) * nx + j;
         return cl.map_shared_rank(base, r)[off];
     };
     long long it = I.iters;
@@ -583,11 +585,13 @@ __device__ void cluster_run(BInst &Ig, int cs, long long sweeps, unsigned char *
         C *v = cur ? buf0 : buf1;
         const C *u = cur ? buf1 : buf0;
         typename MaxBits<C>::type mx = 0;
-        for (int c = tid; c < own; c += kBThreads) {
-            const int lp = c / pc, w = c - lp * pc;
-            const int k = DIM == 3 ? p0 + lp : 0;
-            const int i = DIM == 3 ? w / nx : p0 + lp;
-            const int j = DIM == 3 ? w - i * nx : w;
+        // warp per row of the CTA's part (rows of its planes in 3D), lanes across x
+        const int nrows = (p1 - p0) * (DIM == 3 ? ny : 1);
+        for (int row = warp; row < nrows; row += kBThreads / 32)
+        for (int j = lane; j < nx; j += 32) {
+            const int k = DIM == 3 ? p0 + row / ny : 0;
+            const int i = DIM == 3 ? row - (row / ny) * ny : p0 + row;
+            const int c = row * nx + j;
             const C uc = u[c];
             C sum;
             if (DIM == 2) {
@@ -685,9 +689,11 @@ __device__ void cluster_dc_run(BInst &Ig, int cs, long long sweeps, unsigned cha
     cl.sync();
     // cell (k, i, j) of one of the shared arrays, wherever it is held
     auto at = [&](float *arr, long long k, long long i, long long j) -> float {
-        const int pl = (int)(DIM == 3 ? k : i), r = pl / per;
+        const int pl = (int)(DIM == 3 ? k : i);
+        if (pl >= p0 && pl < p1)                     // held by this CTA: no division
+            return arr[DIM == 3 ? (int)(((k - p0) * ny + i) * nx + j) : (int)((i - p0) * nx + j)];
+        const int r = pl / per;
         const int off = DIM == 3 ? (int)(((k - r * per) * ny + i) * nx + j) : (int)((i - r * per) * nx + j);
-        if (r == rank) return arr[off];
         return cl.map_shared_rank(arr, r)[off];
     };
     const long long P = I.inner + 1, q0 = I.phase;
@@ -705,11 +711,14 @@ __device__ void cluster_dc_run(BInst &Ig, int cs, long long sweeps, unsigned cha
         float *es = (ph & 1) ? se1 : se0;
         float *ed = (ph & 1) ? se0 : se1;
         unsigned long long mx = 0ull;
-        for (int c = tid; c < own; c += kBThreads) {
-            const int lp = c / pc, w = c - lp * pc;
-            const long long k = DIM == 3 ? p0 + lp : 0;
-            const long long i = DIM == 3 ? w / nx : p0 + lp;
-            const long long j = DIM == 3 ? w - (w / nx) * nx : w;
+        // warp per row of the CTA's part (rows of its planes in 3D), lanes across x
+        const int nrows = (p1 - p0) * (DIM == 3 ? ny : 1);
+        for (int row = warp; row < nrows; row += kBThreads / 32)
+        for (int jj = lane; jj < nx; jj += 32) {
+            const long long k = DIM == 3 ? p0 + row / ny : 0;
+            const long long i = DIM == 3 ? row - (row / ny) * ny : p0 + row;
+            const long long j = jj;
+            const int c = row * nx + jj;
             const long long idx = base + c;
             if (ph < 0) {
                 const double rv = dc_defect<DIM>(I, k, i, j, [&](long long z, long long y, long long x) {
