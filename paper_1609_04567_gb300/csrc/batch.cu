@@ -94,8 +94,10 @@ struct ClusterArgs {
 // Jacobi instances (with or without defect correction) of at most
 // kMaxCluster * kClusterCells cells run on a cluster of cs CTAs, cs the power
 // of two that gives each CTA at most kClusterCells cells (see cluster_run and
-// cluster_dc_run)
-constexpr int kClusterCells = 2048;
+// cluster_dc_run).  A defect-correction cell costs several binary64
+// operations a phase, so those grids are spread over twice the CTAs.
+constexpr int kClusterCells = 4096;
+constexpr int kClusterCellsDc = 2048;
 constexpr int kMaxCluster = 16;                 // beyond the portable 8: the kernel allows it
 constexpr int kClusterGroups = 5;               // cluster sizes 1, 2, 4, 8, 16
 constexpr size_t kClusterSmem = 200 * 1024;     // most shared memory a cluster CTA may take
@@ -112,9 +114,10 @@ int cluster_size(const BInst &I)
 {
     if (I.stencil == SLR_RESTORE8) return 0;
     const long long cells = I.nx * I.ny * I.nz;
+    const long long lim = I.dc ? kClusterCellsDc : kClusterCells;
     int cs = 1;
-    while (cs < kMaxCluster && cells > (long long)cs * kClusterCells) cs <<= 1;
-    if (cells > (long long)cs * kClusterCells || cluster_smem(I, cs) > kClusterSmem) return 0;
+    while (cs < kMaxCluster && cells > cs * lim) cs <<= 1;
+    if (cells > cs * lim || cluster_smem(I, cs) > kClusterSmem) return 0;
     return cs;
 }
 
@@ -538,9 +541,7 @@ __device__ void cluster_run(BInst &Ig, int cs, long long sweeps, unsigned char *
 {
     using C = typename St<T>::C;
     cg::cluster_group cl = cg::this_cluster();
-    __shared__ unsigned long long s_wmax[kBThreads / 32];
-    __shared__ unsigned long long s_cmax[2];
-    __shared__ unsigned long long s_max;
+    __shared__ unsigned long long s_wmax[2][kBThreads / 32];   // per sweep parity, one word per warp
     const BInst I = Ig;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int rank = (int)cl.block_rank();
@@ -548,6 +549,7 @@ __device__ void cluster_run(BInst &Ig, int cs, long long sweeps, unsigned char *
     const C h2 = sizeof(C) == 8 ? (C)I.h2 : (C)I.h2f;
     const C d = sizeof(C) == 8 ? (C)I.d : (C)I.df;
     const int nx = (int)I.nx, ny = (int)I.ny, nz = (int)I.nz;
+    const bool wrap = I.wrap != 0;
     const int planes = DIM == 3 ? nz : ny, pc = DIM == 3 ? nx * ny : nx;   // partition unit and its cells
     const int per = (planes + cs - 1) / cs;
     const int p0 = min(rank * per, planes), p1 = min(p0 + per, planes);
@@ -560,21 +562,19 @@ __device__ void cluster_run(BInst &Ig, int cs, long long sweeps, unsigned char *
         fs[c] = St<T>::ldf(I.aux, (long long)p0 * pc + c);
     }
     cl.sync();                                        // every CTA's part is loaded
-    // cell (k, i, j) of buffer `b` wherever it is held (the ghost outside the grid)
-    auto get = [&](int b, int k, int i, int j) -> C {
-        if (i < 0 || i >= ny || j < 0 || j >= nx || k < 0 || k >= nz) {
-            if (!I.wrap) return ghost;
+    // row (k, i) of the buffer whose local copy is `base`, in whichever CTA
+    // holds plane k (row i in 2D); null outside the grid unless it wraps
+    auto row_at = [&](const C *base, int k, int i) -> const C * {
+        if (i < 0 || i >= ny || k < 0 || k >= nz) {
+            if (!wrap) return nullptr;
             i = i < 0 ? i + ny : (i >= ny ? i - ny : i);
-            j = j < 0 ? j + nx : (j >= nx ? j - nx : j);
             k = k < 0 ? k + nz : (k >= nz ? k - nz : k);
         }
         const int pl = DIM == 3 ? k : i;
-        C *base = b ? buf1 : buf0;
-        if (pl >= p0 && pl < p1)                     // held by this CTA: no division
-            return base[DIM == 3 ? ((k - p0) * ny + i) * nx + j : (i - p0) * nx + j];
+        if (pl >= p0 && pl < p1)
+            return base + (DIM == 3 ? ((k - p0) * ny + i) * nx : (i - p0) * nx);
         const int r = pl / per;
-        const int off = DIM == 3 ? ((k - r * per) * ny + i) * nx + j : (i - r * per) * nx + j;
-        return cl.map_shared_rank(base, r)[off];
+        return cl.map_shared_rank((C *)base, r) + (DIM == 3 ? ((k - r * per) * ny + i) * nx : (i - r * per) * nx);
     };
     long long it = I.iters;
     int cur = 0;
@@ -585,28 +585,35 @@ __device__ void cluster_run(BInst &Ig, int cs, long long sweeps, unsigned char *
         C *v = cur ? buf0 : buf1;
         const C *u = cur ? buf1 : buf0;
         typename MaxBits<C>::type mx = 0;
-        // warp per row of the CTA's part (rows of its planes in 3D), lanes across x
+        // warp per row of the CTA's part (rows of its planes in 3D), lanes
+        // across x; the neighbouring rows are found once per row
         const int nrows = (p1 - p0) * (DIM == 3 ? ny : 1);
-        for (int row = warp; row < nrows; row += kBThreads / 32)
-        for (int j = lane; j < nx; j += 32) {
+        for (int row = warp; row < nrows; row += kBThreads / 32) {
             const int k = DIM == 3 ? p0 + row / ny : 0;
             const int i = DIM == 3 ? row - (row / ny) * ny : p0 + row;
-            const int c = row * nx + j;
-            const C uc = u[c];
-            C sum;
-            if (DIM == 2) {
-                sum = add_rn(add_rn(add_rn(get(cur, k, i - 1, j), get(cur, k, i + 1, j)), get(cur, k, i, j - 1)),
-                             get(cur, k, i, j + 1));
-            } else {
-                sum = add_rn(add_rn(add_rn(add_rn(add_rn(get(cur, k, i, j - 1), get(cur, k, i, j + 1)),
-                                                  get(cur, k, i - 1, j)), get(cur, k, i + 1, j)),
-                                    get(cur, k - 1, i, j)), get(cur, k + 1, i, j));
+            const C *rc = u + row * nx;
+            const C *rn = row_at(u, k, i - 1), *rs = row_at(u, k, i + 1);
+            const C *rb = DIM == 3 ? row_at(u, k - 1, i) : nullptr, *ra = DIM == 3 ? row_at(u, k + 1, i) : nullptr;
+            const C *fr = fs + row * nx;
+            C *vr = v + row * nx;
+            for (int j = lane; j < nx; j += 32) {
+                const C uc = rc[j];
+                const C w = j > 0 ? rc[j - 1] : (wrap ? rc[nx - 1] : ghost);
+                const C e = j + 1 < nx ? rc[j + 1] : (wrap ? rc[0] : ghost);
+                const C n = rn ? rn[j] : ghost, so = rs ? rs[j] : ghost;
+                C sum;
+                if (DIM == 2) {
+                    sum = add_rn(add_rn(add_rn(n, so), w), e);
+                } else {
+                    const C b = rb ? rb[j] : ghost, a = ra ? ra[j] : ghost;
+                    sum = add_rn(add_rn(add_rn(add_rn(add_rn(w, e), n), so), b), a);
+                }
+                const C tt = mul_rn(h2, fr[j]);
+                // the value rounded to the storage type, widened back (exact)
+                const C stored = St<T>::rnd(div_rn(add_rn(tt, sum), d));
+                vr[j] = stored;
+                max_bits(mx, sub_rn(stored, uc));
             }
-            const C tt = mul_rn(h2, fs[c]);
-            // the value rounded to the storage type, widened back (exact)
-            const C stored = St<T>::rnd(div_rn(add_rn(tt, sum), d));
-            v[c] = stored;
-            max_bits(mx, sub_rn(stored, uc));
         }
         unsigned long long m = widen_bits(mx);
 #pragma unroll
@@ -614,32 +621,29 @@ __device__ void cluster_run(BInst &Ig, int cs, long long sweeps, unsigned char *
             const unsigned long long t = __shfl_xor_sync(0xffffffffu, m, o);
             m = t > m ? t : m;
         }
-        if (lane == 0) s_wmax[warp] = m;
-        __syncthreads();
-        if (tid == 0) {
-            unsigned long long b = 0ull;
-            for (int x = 0; x < kBThreads / 32; ++x) b = s_wmax[x] > b ? s_wmax[x] : b;
-            s_cmax[s & 1] = b;
+        if (lane == 0) s_wmax[s & 1][warp] = m;
+        // the new states and every warp's maximum, cluster-wide; the words of
+        // this parity are written again two sweeps on, after the next barrier,
+        // which no CTA passes before all have read them
+        cl.sync();
+        unsigned long long b = 0ull;
+        for (int x = lane; x < cs * (kBThreads / 32); x += 32) {
+            const unsigned long long y = *cl.map_shared_rank(&s_wmax[s & 1][x % (kBThreads / 32)], x / (kBThreads / 32));
+            b = y > b ? y : b;
         }
-        cl.sync();                                    // the new states and the CTAs' maxima
-        if (tid == 0) {
-            unsigned long long b = 0ull;
-            for (int r = 0; r < cs; ++r) {
-                const unsigned long long x = *cl.map_shared_rank(&s_cmax[s & 1], r);
-                b = x > b ? x : b;
-            }
-            s_max = b;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const unsigned long long t = __shfl_xor_sync(0xffffffffu, b, o);
+            b = t > b ? t : b;
         }
-        __syncthreads();
         Slot sl;
         memset(&sl, 0, sizeof(sl));
-        sl.maxbits = s_max;
-        sl.changed = s_max != 0ull;
+        sl.maxbits = b;
+        sl.changed = b != 0ull;
         dcs = decide(I.reduce, sl, I.tol);
         it += 1;
         cur ^= 1;
         stop = dcs.converged || it >= I.max_iters;
-        __syncthreads();                              // s_max is read before the next sweep writes it
     }
     const C *fin = cur ? buf1 : buf0;
     for (int c = tid; c < own; c += kBThreads) St<T>::put(I.a, (long long)p0 * pc + c, fin[c]);
@@ -668,9 +672,7 @@ template <int DIM>
 __device__ void cluster_dc_run(BInst &Ig, int cs, long long sweeps, unsigned char *smem)
 {
     cg::cluster_group cl = cg::this_cluster();
-    __shared__ unsigned long long s_wmax[kBThreads / 32];
-    __shared__ unsigned long long s_cmax[2];
-    __shared__ unsigned long long s_max;
+    __shared__ unsigned long long s_wmax[2][kBThreads / 32];   // per phase parity, one word per warp
     const BInst I = Ig;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int rank = (int)cl.block_rank();
@@ -750,31 +752,29 @@ __device__ void cluster_dc_run(BInst &Ig, int cs, long long sweeps, unsigned cha
             const unsigned long long t = __shfl_xor_sync(0xffffffffu, mx, o);
             mx = t > mx ? t : mx;
         }
-        if (lane == 0) s_wmax[warp] = mx;
-        __syncthreads();
-        if (tid == 0) {
-            unsigned long long b = 0ull;
-            for (int x = 0; x < kBThreads / 32; ++x) b = s_wmax[x] > b ? s_wmax[x] : b;
-            s_cmax[s & 1] = b;
-        }
-        cl.sync();                                    // this phase's values (shared and global) everywhere
+        if (lane == 0) s_wmax[s & 1][warp] = mx;
+        // this phase's values (shared and global) and every warp's maximum,
+        // cluster-wide; the words of this parity are written again two phases
+        // on, after the next barrier, which no CTA passes before all have read them
+        cl.sync();
         const bool tested = q >= 1 && ph == I.inner;
         if (tested) {
-            if (tid == 0) {
-                unsigned long long b = 0ull;
-                for (int r = 0; r < cs; ++r) {
-                    const unsigned long long x = *cl.map_shared_rank(&s_cmax[s & 1], r);
-                    b = x > b ? x : b;
-                }
-                s_max = b;
+            unsigned long long b = 0ull;
+            for (int x = lane; x < cs * (kBThreads / 32); x += 32) {
+                const unsigned long long y =
+                    *cl.map_shared_rank(&s_wmax[s & 1][x % (kBThreads / 32)], x / (kBThreads / 32));
+                b = y > b ? y : b;
             }
-            __syncthreads();
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const unsigned long long t = __shfl_xor_sync(0xffffffffu, b, o);
+                b = t > b ? t : b;
+            }
             Slot sl;
             memset(&sl, 0, sizeof(sl));
-            sl.maxbits = s_max;
+            sl.maxbits = b;
             dcs = decide(I.reduce, sl, I.tol);
             stop = dcs.converged || dc_corrections(I, q + 1) >= I.max_iters;
-            __syncthreads();                          // s_max is read before it is written again
         }
     }
     const long long phase = q0 + s;
@@ -802,7 +802,7 @@ __device__ void cluster_dc_run(BInst &Ig, int cs, long long sweeps, unsigned cha
     cl.sync();                                        // the others' last reads of this CTA's memory are done
 }
 
-__global__ void __launch_bounds__(kBThreads) batch_cluster_kernel(ClusterArgs ca)
+__global__ void __launch_bounds__(kBThreads, 4) batch_cluster_kernel(ClusterArgs ca)
 {
     extern __shared__ unsigned char smem_raw[];
     unsigned char *smem = align_up(smem_raw, 16);

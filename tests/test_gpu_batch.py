@@ -212,18 +212,21 @@ def test_defect_correction_in_short_runs_while_others_join(gpu, orc):
 
 
 def test_cluster_sizes_and_partitions_match_the_oracle(gpu, orc):
-    # Jacobi grids of at most 32K cells run on thread-block clusters of 1-16
-    # CTAs (2048 cells a CTA at most), split into row blocks (2D) or z-slabs
-    # (3D): clusters of 16, 8, 4 and 2; fewer rows or planes than CTAs (some
-    # CTAs hold nothing); a periodic 3D grid; and a single row too long for one
-    # CTA's shared memory, which stays in the batch-wide loop
+    # Jacobi grids of at most 64K cells run on thread-block clusters of 1-16
+    # CTAs (4096 cells a CTA at most), split into row blocks (2D) or z-slabs
+    # (3D): clusters of 16, 8, 4, 2 and 1; fewer rows or planes than CTAs (some
+    # CTAs hold nothing); a periodic 3D grid split across CTAs; and a single
+    # row too long for one CTA's shared memory, which stays in the batch-wide loop
     mix = [
-        (jacobi_instance((150, 150), "bf16", 31, tol=1e-6), 700),          # 16 CTAs
-        (jacobi_instance((181, 181), "f32", 32, tol=1e-7), 400),           # 16 CTAs
-        (jacobi_instance((127, 129), "f16", 33, tol=1e-6), 900),           # 8 CTAs
-        (jacobi_instance((3, 40, 48), "f32", 34, tol=1e-7), 2000),         # 4 CTAs, 3 planes
-        (jacobi_instance((6, 20, 30), "f64", 35, tol=1e-9, boundary=1), 3000),
-        (jacobi_instance((2, 4000), "f32", 36, tol=1e-7), 2000),           # 4 CTAs, 2 rows
+        (jacobi_instance((256, 256), "bf16", 31, tol=1e-6), 700),          # 16 CTAs, 16 rows each
+        (jacobi_instance((200, 181), "f32", 32, tol=1e-7), 400),           # 16 CTAs, ragged last block
+        (jacobi_instance((150, 150), "bf16", 38, tol=1e-6), 600),          # 8 CTAs
+        (jacobi_instance((127, 129), "f16", 33, tol=1e-6), 900),           # 4 CTAs
+        (jacobi_instance((3, 60, 64), "f32", 34, tol=1e-7), 2000),         # 4 CTAs, 3 planes
+        (jacobi_instance((6, 40, 40), "f64", 35, tol=1e-9, boundary=1), 3000),   # 4 CTAs, periodic
+        (jacobi_instance((2, 6000), "f32", 36, tol=1e-7), 2000),           # 4 CTAs, 2 rows
+        (jacobi_instance((70, 100), "f32", 40, tol=1e-7), 2000),           # 2 CTAs
+        (jacobi_instance((40, 100), "f32", 39, tol=1e-7), 2000),           # one CTA
         (jacobi_instance((1, 32768), "f32", 37, tol=1e-7), 50),            # no cluster
     ]
     b = gpu.Batch(len(mix))
