@@ -585,34 +585,50 @@ __device__ void cluster_run(BInst &Ig, int cs, long long sweeps, unsigned char *
         C *v = cur ? buf0 : buf1;
         const C *u = cur ? buf1 : buf0;
         typename MaxBits<C>::type mx = 0;
+        // one cell: the neighbours in the order of jacobi_unit
+        auto cell = [&](const C *rc, const C *fr, C *vr, int j, C n, C so, C bl, C ab) {
+            const C uc = rc[j];
+            // the x-neighbours by index (wrapped, or the cell itself where the ghost goes)
+            C w = rc[j > 0 ? j - 1 : (wrap ? nx - 1 : j)];
+            C e = rc[j + 1 < nx ? j + 1 : (wrap ? 0 : j)];
+            if (!wrap) {
+                w = j > 0 ? w : ghost;
+                e = j + 1 < nx ? e : ghost;
+            }
+            C sum;
+            if (DIM == 2)
+                sum = add_rn(add_rn(add_rn(n, so), w), e);
+            else
+                sum = add_rn(add_rn(add_rn(add_rn(add_rn(w, e), n), so), bl), ab);
+            const C tt = mul_rn(h2, fr[j]);
+            // the value rounded to the storage type, widened back (exact)
+            const C stored = St<T>::rnd(div_rn(add_rn(tt, sum), d));
+            vr[j] = stored;
+            max_bits(mx, sub_rn(stored, uc));
+        };
         // warp per row of the CTA's part (rows of its planes in 3D), lanes
-        // across x; the neighbouring rows are found once per row
+        // across x; rows whose neighbouring rows are all this CTA's and inside
+        // the grid read them at fixed offsets, the others find them once per row
         const int nrows = (p1 - p0) * (DIM == 3 ? ny : 1);
         for (int row = warp; row < nrows; row += kBThreads / 32) {
             const int k = DIM == 3 ? p0 + row / ny : 0;
             const int i = DIM == 3 ? row - (row / ny) * ny : p0 + row;
             const C *rc = u + row * nx;
-            const C *rn = row_at(u, k, i - 1), *rs = row_at(u, k, i + 1);
-            const C *rb = DIM == 3 ? row_at(u, k - 1, i) : nullptr, *ra = DIM == 3 ? row_at(u, k + 1, i) : nullptr;
             const C *fr = fs + row * nx;
             C *vr = v + row * nx;
-            for (int j = lane; j < nx; j += 32) {
-                const C uc = rc[j];
-                const C w = j > 0 ? rc[j - 1] : (wrap ? rc[nx - 1] : ghost);
-                const C e = j + 1 < nx ? rc[j + 1] : (wrap ? rc[0] : ghost);
-                const C n = rn ? rn[j] : ghost, so = rs ? rs[j] : ghost;
-                C sum;
-                if (DIM == 2) {
-                    sum = add_rn(add_rn(add_rn(n, so), w), e);
-                } else {
-                    const C b = rb ? rb[j] : ghost, a = ra ? ra[j] : ghost;
-                    sum = add_rn(add_rn(add_rn(add_rn(add_rn(w, e), n), so), b), a);
-                }
-                const C tt = mul_rn(h2, fr[j]);
-                // the value rounded to the storage type, widened back (exact)
-                const C stored = St<T>::rnd(div_rn(add_rn(tt, sum), d));
-                vr[j] = stored;
-                max_bits(mx, sub_rn(stored, uc));
+            const bool inner = DIM == 2 ? (i - 1 >= p0 && i + 1 < p1)
+                                        : (k - 1 >= p0 && k + 1 < p1 && i >= 1 && i + 1 < ny);
+            if (inner) {
+                const int pz = ny * nx;
+                for (int j = lane; j < nx; j += 32)
+                    cell(rc, fr, vr, j, rc[j - nx], rc[j + nx], DIM == 3 ? rc[j - pz] : ghost,
+                         DIM == 3 ? rc[j + pz] : ghost);
+            } else {
+                const C *rn = row_at(u, k, i - 1), *rs = row_at(u, k, i + 1);
+                const C *rb = DIM == 3 ? row_at(u, k - 1, i) : nullptr, *ra = DIM == 3 ? row_at(u, k + 1, i) : nullptr;
+                for (int j = lane; j < nx; j += 32)
+                    cell(rc, fr, vr, j, rn ? rn[j] : ghost, rs ? rs[j] : ghost, rb ? rb[j] : ghost,
+                         ra ? ra[j] : ghost);
             }
         }
         unsigned long long m = widen_bits(mx);
