@@ -314,9 +314,10 @@ const char *slr_version(void);
  * any storage, with or without FP64 defect correction, SLR_RESTORE8 in EXACT
  * math), each with its own grid, tolerance and iteration cap.  slr_batch_run
  * enqueues the launches that run up to `sweeps` more steps of every running
- * instance: the Jacobi instances of at most 32K cells each on a
- * thread-block cluster of 1-16 CTAs holding the grid in shared memory (with
- * defect correction: its binary32 defect and corrections), one cluster
+ * instance: the Jacobi instances of at most 64K cells (32K with defect
+ * correction) each on a thread-block cluster of 1-16 CTAs holding the grid in
+ * shared memory (with defect correction: its binary32 defect and
+ * corrections), one cluster
  * barrier per sweep or phase (one launch per cluster size,
  * on side streams the batch's stream then waits for), and the others in ONE
  * cooperative launch with one grid barrier per step for all of them: a step
