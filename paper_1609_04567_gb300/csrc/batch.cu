@@ -714,6 +714,15 @@ __device__ void cluster_dc_run(BInst &Ig, int cs, long long sweeps, unsigned cha
         const int off = DIM == 3 ? (int)(((k - r * per) * ny + i) * nx + j) : (int)((i - r * per) * nx + j);
         return cl.map_shared_rank(arr, r)[off];
     };
+    // row (k, i) of one of the shared arrays in whichever CTA holds it; null
+    // outside the grid (the corrections' ghost is 0)
+    auto row_of = [&](float *arr, int k, int i) -> const float * {
+        if (i < 0 || i >= ny || k < 0 || k >= nz) return nullptr;
+        const int pl = DIM == 3 ? k : i;
+        if (pl >= p0 && pl < p1) return arr + (DIM == 3 ? ((k - p0) * ny + i) * nx : (i - p0) * nx);
+        const int r = pl / per;
+        return cl.map_shared_rank(arr, r) + (DIM == 3 ? ((k - r * per) * ny + i) * nx : (i - r * per) * nx);
+    };
     const long long P = I.inner + 1, q0 = I.phase;
     const float *ec = (I.inner & 1) ? se1 : se0;            // e after the inner sweeps
     bool stop = false;
@@ -731,36 +740,59 @@ __device__ void cluster_dc_run(BInst &Ig, int cs, long long sweeps, unsigned cha
         unsigned long long mx = 0ull;
         // warp per row of the CTA's part (rows of its planes in 3D), lanes across x
         const int nrows = (p1 - p0) * (DIM == 3 ? ny : 1);
-        for (int row = warp; row < nrows; row += kBThreads / 32)
-        for (int jj = lane; jj < nx; jj += 32) {
-            const long long k = DIM == 3 ? p0 + row / ny : 0;
-            const long long i = DIM == 3 ? row - (row / ny) * ny : p0 + row;
-            const long long j = jj;
-            const int c = row * nx + jj;
-            const long long idx = base + c;
-            if (ph < 0) {
-                const double rv = dc_defect<DIM>(I, k, i, j, [&](long long z, long long y, long long x) {
-                    return dc_outside(I, z, y, x) ? 0.0 : __ldcg(uo + (z * I.ny + y) * I.nx + x);
-                });
-                sr[c] = (float)rv;
-            } else if (ph < I.inner) {
-                float sn = 0.0f;
-                if (ph > 0)
-                    sn = dc_sum<DIM, float>(k, i, j, [&](long long z, long long y, long long x) {
-                        return dc_outside(I, z, y, x) ? 0.0f : at(es, z, y, x);
+        for (int row = warp; row < nrows; row += kBThreads / 32) {
+            if (ph >= 0 && ph < I.inner) {
+                // an inner binary32 sweep: the neighbouring rows of e found once per row
+                const int kk = DIM == 3 ? p0 + row / ny : 0;
+                const int ii = DIM == 3 ? row - (row / ny) * ny : p0 + row;
+                const float *rc = es + row * nx, *rr = sr + row * nx;
+                float *rd = ed + row * nx;
+                const bool sum = ph > 0;
+                const float *rn = sum ? row_of(es, kk, ii - 1) : nullptr, *rs = sum ? row_of(es, kk, ii + 1) : nullptr;
+                const float *rb = sum && DIM == 3 ? row_of(es, kk - 1, ii) : nullptr;
+                const float *ra = sum && DIM == 3 ? row_of(es, kk + 1, ii) : nullptr;
+                for (int j = lane; j < nx; j += 32) {
+                    float sn = 0.0f;
+                    if (sum) {
+                        // the neighbours in the order of dc_sum; 0 outside the grid
+                        float w = rc[j > 0 ? j - 1 : j], e = rc[j + 1 < nx ? j + 1 : j];
+                        w = j > 0 ? w : 0.0f;
+                        e = j + 1 < nx ? e : 0.0f;
+                        const float n = rn ? rn[j] : 0.0f, so = rs ? rs[j] : 0.0f;
+                        if (DIM == 2) {
+                            sn = __fadd_rn(__fadd_rn(__fadd_rn(n, so), w), e);
+                        } else {
+                            const float bl = rb ? rb[j] : 0.0f, ab = ra ? ra[j] : 0.0f;
+                            sn = __fadd_rn(__fadd_rn(__fadd_rn(__fadd_rn(__fadd_rn(w, e), n), so), bl), ab);
+                        }
+                    }
+                    const float t = __fmul_rn(I.h2f, rr[j]);
+                    rd[j] = __fdiv_rn(__fadd_rn(t, sn), I.df);
+                }
+                continue;
+            }
+            for (int jj = lane; jj < nx; jj += 32) {
+                const long long k = DIM == 3 ? p0 + row / ny : 0;
+                const long long i = DIM == 3 ? row - (row / ny) * ny : p0 + row;
+                const long long j = jj;
+                const int c = row * nx + jj;
+                const long long idx = base + c;
+                if (ph < 0) {
+                    const double rv = dc_defect<DIM>(I, k, i, j, [&](long long z, long long y, long long x) {
+                        return dc_outside(I, z, y, x) ? 0.0 : __ldcg(uo + (z * I.ny + y) * I.nx + x);
                     });
-                const float t = __fmul_rn(I.h2f, sr[c]);
-                ed[c] = __fdiv_rn(__fadd_rn(t, sn), I.df);
-            } else {
-                un[idx] = __dadd_rn(__ldcg(uo + idx), (double)ec[c]);
-                const double rv = dc_defect<DIM>(I, k, i, j, [&](long long z, long long y, long long x) {
-                    if (dc_outside(I, z, y, x)) return 0.0;
-                    return __dadd_rn(__ldcg(uo + (z * I.ny + y) * I.nx + x), (double)at((float *)ec, z, y, x));
-                });
-                sr[c] = (float)rv;
-                const unsigned long long b =
-                    (unsigned long long)__double_as_longlong(fabs(__ddiv_rn(__dmul_rn(I.h2, rv), I.d)));
-                mx = b > mx ? b : mx;
+                    sr[c] = (float)rv;
+                } else {
+                    un[idx] = __dadd_rn(__ldcg(uo + idx), (double)ec[c]);
+                    const double rv = dc_defect<DIM>(I, k, i, j, [&](long long z, long long y, long long x) {
+                        if (dc_outside(I, z, y, x)) return 0.0;
+                        return __dadd_rn(__ldcg(uo + (z * I.ny + y) * I.nx + x), (double)at((float *)ec, z, y, x));
+                    });
+                    sr[c] = (float)rv;
+                    const unsigned long long b =
+                        (unsigned long long)__double_as_longlong(fabs(__ddiv_rn(__dmul_rn(I.h2, rv), I.d)));
+                    mx = b > mx ? b : mx;
+                }
             }
         }
 #pragma unroll

@@ -157,6 +157,12 @@ def dc_instances():
         (jacobi_instance((7, 9, 11), "f64", 42, tol=1e-10, defect_correction=1, inner_sweeps=8), 5000),
         (jacobi_instance((96, 64), "f64", 43, tol=1e-10, defect_correction=1, inner_sweeps=25), 3),   # capped
         (jacobi_instance((1, 1), "f64", 44, tol=1e-12, defect_correction=1, inner_sweeps=3), 100),
+        # on clusters of several CTAs (2048 cells a CTA at most): 3D z-slabs of
+        # 3 planes, 3D with one plane a CTA (every plane below and above is
+        # another CTA's), 2D row blocks
+        (jacobi_instance((12, 20, 24), "f64", 47, tol=1e-10, defect_correction=1, inner_sweeps=10), 5000),
+        (jacobi_instance((2, 30, 40), "f64", 48, tol=1e-10, defect_correction=1, inner_sweeps=6), 5000),
+        (jacobi_instance((60, 50), "f64", 49, tol=1e-10, defect_correction=1, inner_sweeps=20), 5000),
     ]
 
 
