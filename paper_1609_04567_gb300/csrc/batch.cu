@@ -1277,8 +1277,7 @@ slr_status slr_batch_run(slr_batch b, int64_t sweeps)
         if (e == cudaSuccess && ca.cs > 8)
             e = cudaFuncSetAttribute(slr::batch_cluster_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
         if (e != cudaSuccess) return bcuda(b, e, "cluster kernel attributes");
-        cudaLaunchConfig_t cfg;
-        memset(&cfg, 0, sizeof(cfg));
+        cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3((unsigned)(ng * (size_t)ca.cs));
         cfg.blockDim = dim3(slr::kBThreads);
         cfg.dynamicSmemBytes = csm;
